@@ -465,3 +465,42 @@ def test_collinear_backtracking_cubic_pivots():
     c = bezier_eval(CUBIC, pts, 1, np.linspace(0, 1, 100001))
     assert xs.max() == pytest.approx(c[:, 0].max(), abs=1e-9)
     assert xs.min() == pytest.approx(c[:, 0].min(), abs=1e-9)
+
+
+def test_miter_ratio_uses_interior_angle():
+    """60 degree turn: interior angle 120, miter ratio 1/sin(60) = 1.1547 <= 1.5, so the
+    miter is kept, tip at r * ratio along the outer bisector."""
+    o = oracle.tessellate(_two_lines(60.0, W.JOIN_MITER, miter=1.5))
+    ribs = _link_ribs(o, 2)
+    a = math.radians(30.0)
+    bis = np.array([math.sin(a), -math.cos(a)])  # outer (right-hand) bisector normal
+    tip = np.array([10.0, 0.0]) + bis / math.cos(a)
+    assert np.allclose(ribs[1, :2], tip, atol=1e-12) and np.allclose(ribs[2, :2], tip, atol=1e-12)
+    o = oracle.tessellate(_two_lines(60.0, W.JOIN_MITER, miter=1.1))
+    ribs = _link_ribs(o, 2)
+    assert np.allclose(ribs[1, :2], ribs[0, :2]) and np.allclose(ribs[2, :2], ribs[3, :2])
+
+
+@pytest.mark.parametrize("kind,pts,w", [
+    (CUBIC, [[0, 0], [0, 0], [10, 10], [20, 0]], 1.0),       # B = A: start along C - A
+    (CUBIC, [[0, 0], [0, 0], [0, 0], [20, 5]], 1.0),         # B = C = A: along D - A
+    (CUBIC, [[0, 0], [10, 10], [20, 0], [20, 0]], 1.0),      # C = D: end along D - B
+    (CUBIC, [[0, 0], [20, 5], [20, 5], [20, 5]], 1.0),       # B = C = D: end along D - A
+    (QUAD, [[0, 0], [0, 0], [0, 0], [20, 5]], 1.0),          # B = A
+    (QUAD, [[0, 0], [20, 5], [20, 5], [20, 5]], 1.0),        # B = D
+    (CONIC, [[0, 0], [10, 10], [10, 10], [20, 0]], -0.5),    # negative weight flips
+    (CONIC, [[0, 0], [10, 10], [10, 10], [20, 0]], 3.0),
+])
+def test_end_gradients_are_one_sided_limits(kind, pts, w):
+    """Table 1's normalized end gradients equal the one-sided limits of g'/|g'|."""
+    pts = np.array(pts, np.float32)
+    I = oracle.segment_intervals(kind, pts, w, q32(1.0))
+    # where g' vanishes at an end the chord is second order in h, so the chord
+    # direction converges like O(h); h = 1e-5 keeps rounding far below that
+    h = 1e-5
+    g = lambda t: bezier_eval(kind, pts, w, np.array([t]))[0]
+    d0 = g(h) - g(0.0)
+    d1 = g(1.0) - g(1.0 - h)
+    a0, a1 = math.atan2(d0[1], d0[0]), math.atan2(d1[1], d1[0])
+    assert abs(np.angle(np.exp(1j * (I["Psi"][0] - a0)))) < 1e-3
+    assert abs(np.angle(np.exp(1j * (I["Psi"][-1] - a1)))) < 1e-3
