@@ -50,6 +50,24 @@ enum { ORC_CAP_BUTT = 0, ORC_CAP_SQUARE = 1, ORC_CAP_ROUND = 2, ORC_CAP_TRIANGLE
 #define TWO_PI (2.0 * PI)
 #define MAXI 12 /* intervals per link: <= 3 curve intervals, each split once,
                    plus collinear pivots (<= 2) and their flat pieces */
+/* Reading R13: q is a nominal step.  A turning whose ratio to q exceeds an
+ * integer n by less than STEP_SNAP steps takes n steps, not n + 1, so that
+ * exactly-divisible turnings (a 180-degree cap at q = 2 degrees, say) do not
+ * depend on the last bit of q's rounding.  Every step then turns at most
+ * q (1 + STEP_SNAP). */
+#define STEP_SNAP 1e-4
+
+/* steps for a turning of magnitude ad > 0 (Eq. 12 with R13) */
+static int step_count(double ad, double q) {
+  int D = (int)ceil(ad / q - STEP_SNAP);
+  return D < 1 ? 1 : D;
+}
+/* distance of a count's argument to its rounding boundary, in steps */
+static double step_margin(double ad, double q) {
+  double x = ad / q - STEP_SNAP;
+  double f = x - floor(x);
+  return f < 1.0 - f ? f : 1.0 - f;
+}
 
 typedef struct { double x, y; } V2;
 static V2 mk(double x, double y) { V2 r; r.x = x; r.y = y; return r; }
@@ -369,10 +387,9 @@ static void mark_count_fragility(Intervals* I, double q) {
   for (int k = 0; k < I->M; ++k) {
     if (I->pivot[k]) continue;
     double x = fabs(I->delta[k]) / q;
-    double f = x - floor(x);
-    double dist = f < 1.0 - f ? f : 1.0 - f;
+    double dist = step_margin(fabs(I->delta[k]), q);
     if (x > 0 && dist < 1e-9 * (1.0 + x)) I->fragile64 = 1;
-    if (x > 0 && dist < 2e-4) I->fragile32 = 1;
+    if (x > 0 && dist < 2e-5 * (1.0 + x)) I->fragile32 = 1;
     if (I->delta[k] != 0.0 && fabs(I->delta[k]) < 1e-4) I->fragile32 = 1;
     if (fabs(fabs(I->delta[k]) - PI) < 1e-5) I->fragile32 = 1; /* split decision */
     if (fabs(fabs(I->delta[k]) - PI) < 1e-12) I->fragile64 = 1;
@@ -387,8 +404,7 @@ static void finish_counts(Intervals* I, double q) {
     if (ad == 0.0)
       D = (I->p[k + 1] > I->p[k]) ? 1 : 0; /* flat interval: one quad (R5) */
     else
-      D = (int)ceil(ad / q);
-    if (D < 1 && ad > 0) D = 1;
+      D = step_count(ad, q);
     I->Delta[k] = D;
     I->N += D;
   }
@@ -531,8 +547,7 @@ static Seg load_seg(int64_t i, const uint8_t* type, const float* pts, const floa
 static int round_count(double delta, double q) {
   double ad = fabs(delta);
   if (ad == 0.0) return 0;
-  int J = (int)ceil(ad / q);
-  return J < 1 ? 1 : J;
+  return step_count(ad, q);
 }
 
 static int join_count(int style, double delta, double q) {
@@ -721,9 +736,9 @@ int orc_tessellate(int64_t n_seg, const uint8_t* seg_type, const float* seg_pts,
         J = join_count(L.style, L.delta, q);
         if (J > 0) nrib = J + 1;
         if (L.style == ORC_JOIN_ROUND && L.delta != 0.0) {
-          double x = fabs(L.delta) / q, f = x - floor(x), dd = f < 1 - f ? f : 1 - f;
+          double x = fabs(L.delta) / q, dd = step_margin(fabs(L.delta), q);
           if (dd < 1e-9 * (1 + x)) info |= INFO_FRAGILE64;
-          if (dd < 2e-4) info |= INFO_FRAGILE32;
+          if (dd < 2e-5 * (1 + x)) info |= INFO_FRAGILE32;
         }
         if (fabs(L.delta) < 1e-4) info |= INFO_FRAGILE32;
         if (L.style == ORC_JOIN_MITER || L.style == ORC_JOIN_MITER_TRUNCATE) {
@@ -734,6 +749,11 @@ int orc_tessellate(int64_t n_seg, const uint8_t* seg_type, const float* seg_pts,
       } else if (L.kind == 3) {
         J = cap_count(L.style, q);
         if (J > 0) nrib = J + 1;
+        if (L.style == ORC_CAP_ROUND) {
+          double x = PI / q, dd = step_margin(PI, q);
+          if (dd < 1e-9 * (1 + x)) info |= INFO_FRAGILE64;
+          if (dd < 2e-5 * (1 + x)) info |= INFO_FRAGILE32;
+        }
       }
       if (nrib == 0) L.kind = L.kind ? L.kind : 0;
       info |= (uint8_t)((nrib > 0 ? L.kind : 0) << INFO_KIND_SHIFT);

@@ -1,0 +1,103 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI and
+compare it with the FP64 oracle."""
+import numpy as np
+
+import oracle
+
+F32_EPS = 2.0 ** -24
+
+
+def gpu_tessellate(batch, precision, want_t=True):
+    import torch
+    import paper_2007_00308_gb300 as ps
+    ctx = ps.Context()
+    db = ps.DeviceBatch(batch)
+    out = ps.tessellate(ctx, db, precision, arclength=True, want_t=want_t)
+    torch.cuda.synchronize()
+    R = int(out.n_rib.item())
+    res = dict(
+        R=R,
+        rib=out.rib[:R].cpu().numpy().astype(np.float64),
+        tag=out.tag[:R].cpu().numpy().view(np.uint32),
+        s=out.s[:R].cpu().numpy().astype(np.float64),
+        t=out.t[:R].cpu().numpy().astype(np.float64) if want_t else None,
+        link_rib_off=out.link_rib_off.cpu().numpy().astype(np.int64),
+        path_rib_off=out.path_rib_off.cpu().numpy().astype(np.int64),
+        path_len=out.path_len.cpu().numpy().astype(np.float64),
+        status=ctx.status(), ctx=ctx, out=out)
+    return res
+
+
+def ulp32(x):
+    x = np.abs(np.asarray(x, np.float64))
+    e = np.floor(np.log2(np.maximum(x, 1e-30)))
+    return np.where(x > 0, 2.0 ** (e - 23), 2.0 ** -149)
+
+
+def vertex_tolerance(o_rib, rho, r, eps_ang):
+    """Per-coordinate bound: 1e-4 px, plus FP32 representation (2 ulp of the
+    coordinate), plus the along-curve shift of a rib whose angle is off by eps_ang
+    (radius of curvature rho) and the normal's rotation (r eps_ang)."""
+    mag = np.abs(o_rib)
+    return 1e-4 + 2.0 * ulp32(mag) + ((np.minimum(rho, 1e12) + r) * eps_ang)[:, None]
+
+
+def compare_tess(o, g, batch, fragile_bit, eps_ang, s_rel=1e-5, s_abs=1e-5):
+    """Compare GPU output g with oracle output o.  Returns a stats dict and a list of
+    failure strings (empty = parity)."""
+    fails = []
+    stats = {}
+    g_n = np.diff(g["link_rib_off"])
+    o_n = o["link_nrib"]
+    frag = (o["link_info"] & fragile_bit) != 0
+    mism = g_n != o_n
+    stats["links"] = len(o_n)
+    stats["count_mismatch_nonfragile"] = int((mism & ~frag).sum())
+    stats["count_mismatch_fragile"] = int((mism & frag).sum())
+    stats["fragile_links"] = int(frag.sum())
+    if stats["count_mismatch_nonfragile"]:
+        bad = np.where(mism & ~frag)[0][:5]
+        fails.append(f"count mismatch on non-fragile links {bad.tolist()}: gpu {g_n[bad].tolist()} "
+                     f"oracle {o_n[bad].tolist()}")
+    o_off = o["link_rib_off"]
+    g_off = g["link_rib_off"]
+    ok = ~mism & (o_n > 0)
+    idx_o = np.concatenate([np.arange(o_off[l], o_off[l + 1]) for l in np.where(ok)[0]]) if ok.any() else np.zeros(0, np.int64)
+    idx_g = np.concatenate([np.arange(g_off[l], g_off[l + 1]) for l in np.where(ok)[0]]) if ok.any() else np.zeros(0, np.int64)
+    P = batch.n_path
+    r_path = 0.5 * batch.path_width.astype(np.float64)
+    r_rib = r_path[(o["tag"][idx_o] >> 2).astype(np.int64)]
+    if len(idx_o):
+        if not np.array_equal(g["tag"][idx_g], o["tag"][idx_o]):
+            fails.append("tag mismatch")
+        err = np.abs(g["rib"][idx_g] - o["rib"][idx_o])
+        tol = vertex_tolerance(o["rib"][idx_o], o["rho"][idx_o], r_rib, eps_ang)
+        ratio = err / tol
+        stats["vertex_err_max"] = float(err.max())
+        stats["vertex_err_p99"] = float(np.quantile(err, 0.99))
+        stats["vertex_err_p50"] = float(np.median(err))
+        stats["vertex_ratio_max"] = float(ratio.max())
+        if ratio.max() > 1.0:
+            w = np.unravel_index(np.argmax(ratio), ratio.shape)
+            fails.append(f"vertex error {err[w]:.3e} > tol {tol[w]:.3e} at oracle rib {idx_o[w[0]]} "
+                         f"(rho {o['rho'][idx_o[w[0]]]:.3g})")
+    # arc length on paths whose every link matched
+    bad_path = np.zeros(P, bool)
+    lbase = 2 * batch.path_seg_off[:-1].astype(np.int64) + np.arange(P)
+    link_path = np.repeat(np.arange(P), np.diff(np.r_[lbase, len(o_n)]))
+    bad_path[link_path[mism]] = True
+    good = ~bad_path
+    if good.any() and len(idx_o):
+        sel = good[(o["tag"][idx_o] >> 2).astype(np.int64)]
+        so, sg = o["s"][idx_o][sel], g["s"][idx_g][sel]
+        serr = np.abs(sg - so)
+        stol = s_rel * np.maximum(so, 1.0) + s_abs
+        stats["s_err_max"] = float(serr.max()) if len(serr) else 0.0
+        stats["s_rel_max"] = float((serr / np.maximum(so, 1.0)).max()) if len(serr) else 0.0
+        if len(serr) and (serr > stol).any():
+            w = np.argmax(serr / stol)
+            fails.append(f"s error {serr[w]:.3e} > {stol[w]:.3e} (s={so[w]:.4g})")
+        lerr = np.abs(g["path_len"][good] - o["path_len"][good])
+        if (lerr > s_rel * np.maximum(o["path_len"][good], 1.0) + s_abs).any():
+            fails.append(f"path length error {lerr.max():.3e}")
+    return stats, fails
