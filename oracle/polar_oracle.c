@@ -411,6 +411,61 @@ static void finish_counts(Intervals* I, double q) {
   mark_count_fragility(I, q);
 }
 
+/* Reversals of a segment whose control points are collinear (reading R5): along
+ * the common direction v, H(t) . v is a Bernstein quadratic
+ *   lam1 u^2 + 2 lam2 u t + lam3 t^2
+ * (a linear one, lam1 u + lam3 t, for the quadratic Bezier).  The direction
+ * reverses at its simple roots strictly inside (0,1): two when
+ * lam2^2 - lam1 lam3 > 0, none when it is <= 0 (a double root is a kink, where
+ * g' touches zero and resumes its direction).  Roots at t = 0 or 1 (lam1 = 0 or
+ * lam3 = 0) are factored out exactly.  lam_i are dot products of FP32
+ * differences, exact in FP64; the discriminant uses error-free products. */
+static int collinear_reversals(const Seg* g, double* rts) {
+  V2 v = end_grad0(g);
+  double l1, l2, l3;
+  switch (g->type) {
+    case ORC_CUBIC:
+      l1 = dot(sub(g->B, g->A), v); l2 = dot(sub(g->C, g->B), v); l3 = dot(sub(g->D, g->C), v);
+      break;
+    case ORC_QUAD: {
+      double a1 = dot(sub(g->B, g->A), v), a3 = dot(sub(g->D, g->B), v);
+      if ((a1 > 0 && a3 < 0) || (a1 < 0 && a3 > 0)) { rts[0] = a1 / (a1 - a3); return 1; }
+      return 0;
+    }
+    case ORC_CONIC:
+      if (g->w == 0.0) return 0;
+      /* w(B-A) u^2 + (D-A) u t + w(D-B) t^2 : middle Bernstein coefficient (D-A)/2 */
+      l1 = g->w * dot(sub(g->B, g->A), v); l2 = 0.5 * dot(sub(g->D, g->A), v);
+      l3 = g->w * dot(sub(g->D, g->B), v);
+      break;
+    default:
+      return 0;
+  }
+  int n = 0;
+  if (l1 == 0.0 && l3 == 0.0) return 0;
+  if (l1 == 0.0) { /* t (2 l2 u + l3 t): other root where 2 l2 u + l3 t = 0 */
+    double den = 2.0 * l2 - l3;
+    if (den != 0.0) { double r = 2.0 * l2 / den; if (r > 0.0 && r < 1.0) rts[n++] = r; }
+    return n;
+  }
+  if (l3 == 0.0) { /* u (l1 u + 2 l2 t) */
+    double den = l1 - 2.0 * l2;
+    if (den != 0.0) { double r = l1 / den; if (r > 0.0 && r < 1.0) rts[n++] = r; }
+    return n;
+  }
+  double h1 = l2 * l2, e1 = two_prod_err(l2, l2, h1);
+  double h2 = l1 * l3, e2 = two_prod_err(l1, l3, h2);
+  double disc = (h1 - h2) + (e1 - e2);
+  if (!(disc > 0.0)) return 0;
+  /* power form: a + b t + c t^2 with a = l1, b = 2(l2 - l1), c = l1 - 2 l2 + l3 */
+  double a = l1, b = 2.0 * (l2 - l1), c = l1 - 2.0 * l2 + l3, r[2];
+  int m = quad_roots(a, b, c, 4.0 * disc, 1.0, 0.0, r);
+  for (int i = 0; i < m; ++i)
+    if (r[i] > 0.0 && r[i] < 1.0) rts[n++] = r[i];
+  if (n == 2 && rts[0] > rts[1]) { double t = rts[0]; rts[0] = rts[1]; rts[1] = t; }
+  return n;
+}
+
 /* Segment link intervals. */
 static void seg_intervals(const Seg* g, double q, Intervals* I) {
   memset(I, 0, sizeof *I);
@@ -422,28 +477,8 @@ static void seg_intervals(const Seg* g, double q, Intervals* I) {
      * the direction can still reverse where H passes through 0 (collinear
      * control points with back-tracking); each such reversal is a pivot of
      * +pi at a fixed t, and the flat pieces between pivots are one quad each. */
-    V2 e = end_grad0(g);
-    double el = len(e);
-    e = mul(e, 1.0 / el);
     double rts[2];
-    int nr = 0;
-    if (g->type != ORC_LINE) {
-      /* h(t) = H(t) . e as a power-form quadratic */
-      double h0 = dot(hodo(g, 0.0), e), hm = dot(hodo(g, 0.5), e), h1 = dot(hodo(g, 1.0), e);
-      double a = h0, c = 2.0 * h1 - 4.0 * hm + 2.0 * h0, b = h1 - h0 - c;
-      if (g->type == ORC_QUAD) c = 0.0, b = h1 - h0;
-      double disc = b * b - 4.0 * a * c, scale = b * b + fabs(4.0 * a * c);
-      double r[2];
-      int n = quad_roots(a, b, c, disc, scale, 0.0, r);
-      for (int i = 0; i < n; ++i) {
-        if (!(r[i] > 0.0 && r[i] < 1.0)) continue;
-        if (n == 2 && r[0] == r[1]) continue; /* double root: a kink, no reversal */
-        /* keep sign changes only */
-        double lo = r[i] - 1e-9, hi = r[i] + 1e-9;
-        double flo = a + lo * (b + lo * c), fhi = a + hi * (b + hi * c);
-        if ((flo > 0 && fhi < 0) || (flo < 0 && fhi > 0)) rts[nr++] = r[i];
-      }
-    }
+    int nr = collinear_reversals(g, rts);
     double psi = Psi0, pp = 0.0;
     int M = 0;
     for (int i = 0; i <= nr; ++i) {
@@ -598,7 +633,8 @@ static void emit_pivot(const Link* L, int J, double r, V2* Nv, V2* Pv, double* p
     V2 O0 = add(L->at, mul(normal_of(L->Psi0), sd * r));
     V2 O3 = add(L->at, mul(normal_of(L->Psi0 + L->delta), sd * r));
     /* miter ratio = miter length / stroke width = 1 / sin(phi/2), phi = pi - |delta| */
-    double ratio = 1.0 / cos(0.5 * ad);
+    double cm = cos(0.5 * ad);
+    double ratio = cm > 0.0 ? 1.0 / cm : INFINITY;
     V2 v1, v2;
     if (ratio <= L->miter_limit) {
       V2 tip = add(L->at, mul(normal_of(L->Psi0 + 0.5 * L->delta), sd * r * ratio));

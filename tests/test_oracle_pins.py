@@ -507,3 +507,22 @@ def test_end_gradients_are_one_sided_limits(kind, pts, w):
     a0, a1 = math.atan2(d0[1], d0[0]), math.atan2(d1[1], d1[0])
     assert abs(np.angle(np.exp(1j * (I["Psi"][0] - a0)))) < 1e-3
     assert abs(np.angle(np.exp(1j * (I["Psi"][-1] - a1)))) < 1e-3
+
+
+@pytest.mark.parametrize("pts,n_pivot", [
+    ([[0, 0], [30, 0], [-10, 0], [10, 0]], 2),   # forward, back past A, forward past D
+    ([[0, 0], [10, 0], [0, 0], [10, 0]], 0),     # A B A B: g' touches zero at t=1/2 (kink)
+    ([[0, 0], [20, 0], [10, 0], [10, 0]], 1),    # C = D: one reversal inside, root at t=1 excluded
+    ([[0, 0], [0, 0], [20, 0], [10, 0]], 1),     # B = A: root at t=0 excluded
+])
+def test_collinear_reversal_count(pts, n_pivot):
+    """The number of direction reversals of a collinear cubic, measured from the sign
+    changes of g'(t) . (D - A) on a dense grid."""
+    pts = np.array(pts, np.float32)
+    I = oracle.segment_intervals(CUBIC, pts, 1.0, q32(2.0))
+    assert int(I["pivot"].sum()) == n_pivot
+    t = np.linspace(1e-6, 1 - 1e-6, 200001)
+    h = 1e-7
+    d = (bezier_eval(CUBIC, pts, 1, t + h) - bezier_eval(CUBIC, pts, 1, t - h))[:, 0]
+    sgn = np.sign(d[np.abs(d) > 1e-12])
+    assert int((np.diff(sgn) != 0).sum()) == n_pivot
