@@ -1,0 +1,411 @@
+#!/usr/bin/env python3
+"""Polar stroking hot path on GB300: stroked segments/s and covered samples/s.
+
+Workload (the configuration the metric is quoted on): 10,000 open paths of mixed
+line / quadratic / cubic / conic segments (mean 30 segments, max 200), 20% of the
+cubics exact cusps or loops, widths 0.5-64 px, miter/round/bevel joins and
+butt/square/round caps, dtheta = 1 degree, rasterized at 2048x2048 with 16
+samples per pixel; synthetic, seeded.
+
+One step = the whole hot path over the batch: link setup and rib offsets,
+rib emission (t(psi) solve, vertices, joins, caps), cumulative arc length,
+tile binning and 16-sample per-path coverage.  The batched variant captures the
+step's launches in one CUDA graph; the plain variant runs one path per launch.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank processes its own copy
+of the batch (weak scaling, no collective on the data path); the timed region is
+bracketed by barriers and the maximum over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "stroked segments/s and covered samples/s at 1 GB300: batched+mixed vs plain"
+WORKLOAD = ("c2 batching: 10,000 paths, segments/path geometric (mean 30, max 200), "
+            "20% line / 20% quadratic / 45% cubic / 15% conic (w_B log-uniform 0.1-10), "
+            "20% of cubics exact cusps or loops, widths log-uniform 0.5-64 px, "
+            "miter(4)/round/bevel joins, butt/square/round caps, dtheta 1 deg, "
+            "2048x2048 at 16 samples/pixel")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-paths", type=int, default=10000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(batch, paths):
+    """FP64 oracle on a subset of paths: tessellation + arc length + coverage."""
+    import numpy as np
+    import oracle
+    sub = batch.subset(paths)
+    t0 = time.perf_counter()
+    o = oracle.tessellate(sub)
+    oracle.raster(o["rib"], o["tag"], batch.canvas[0], batch.canvas[1], sub.n_path)
+    return time.perf_counter() - t0, int(sub.n_seg)
+
+
+def cpu_baseline(batch, budget_s=15.0):
+    import numpy as np
+    rng = np.random.default_rng(0)
+    order = rng.permutation(batch.n_path)
+    spent, segs, k = 0.0, 0, 0
+    while spent < budget_s and k < len(order):
+        chunk = order[k:k + 25]
+        dt, n = oracle_sample(batch, chunk)
+        spent += dt
+        segs += n
+        k += len(chunk)
+    return {"value": segs / spent, "unit": "segments/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} random paths of the workload ({segs} segments), FP64 tessellation + "
+                      f"arc length + 16-sample raster, single thread, {spent:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2007_00308_gb300 import workloads as W
+    import numpy as np
+    batch = W.c2_batching(n_paths=args.n_paths)
+    rng = np.random.default_rng(1)
+    per_step = 6  # paths per reference step: keeps steps * warmup within minutes
+    for _ in range(args.warmup):
+        oracle_sample(batch, rng.choice(batch.n_path, per_step, replace=False))
+    total, segs = 0.0, 0
+    for _ in range(args.steps):
+        dt, n = oracle_sample(batch, rng.choice(batch.n_path, per_step, replace=False))
+        total += dt
+        segs += n
+    value = segs / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "segments/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "variant": "FP64 CPU oracle (reference arm)",
+                   "sample": f"{per_step} random paths per step"},
+        "cpu_baseline": {"value": value, "unit": "segments/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} random paths per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": "segments/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic bytes per unit of each kernel (what the method must move).
+def algorithmic(kernel, c):
+    R, L, S, P, pairs, px = c["R"], c["L"], c["S"], c["P"], c["pairs"], c["px"]
+    table = {
+        "k_link_setup": ("hbm", 40 * S + 24 * P + (160 + 4) * L),
+        "k_emit": ("hbm", 24 * R + (160 + 4 + 4) * L),
+        "k_arclen_scan": ("hbm", 12 * R + 4 * P),
+        "k_bin_count": ("hbm", 20 * R),
+        "k_bin_scatter": ("hbm", 20 * R + 4 * pairs),
+        "k_coverage": ("hbm", 40 * pairs + 2 * px + 8 * P),
+    }
+    return table.get(kernel)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2007_00308_gb300 as ps
+    from paper_2007_00308_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    batch = W.c2_batching(n_paths=args.n_paths)
+    Wd, Ht = batch.canvas
+    ctx = ps.Context()
+    db = ps.DeviceBatch(batch, device=dev)
+    prec = ps.PS_PREC_MIXED
+    # exact rib count once at set-up; the step itself never synchronizes
+    probe = ps.TessOutput(db.n_link, db.n_path, 0, arclength=False, device=dev)
+    R = ps.ps_count_ribs_sync(ctx, db, probe, prec)
+    out = ps.TessOutput(db.n_link, db.n_path, R, arclength=True, device=dev)
+    canvas = torch.zeros((Ht, Wd), dtype=torch.int16, device=dev)
+    covered = torch.zeros(db.n_path, dtype=torch.int64, device=dev)
+    ctx.reserve(n_link=db.n_link, n_rib=R, n_tile=((Wd + 15) // 16) * ((Ht + 15) // 16),
+                n_pair=6 * R)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(stream=None):
+        ps.ps_tessellate_strokes(ctx, db, out, prec, ps.PS_TESS_ARCLENGTH, stream=stream)
+        ps.ps_rasterize_coverage(ctx, out.rib, out.tag, out.n_rib, out.capacity, db.n_path, Wd, Ht,
+                                 canvas, covered, stream=stream)
+
+    # eager warm-up (allocates workspace), then capture one step in a graph
+    step()
+    torch.cuda.synchronize()
+    st = ctx.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st}: {ps.error_string(st)}")
+    ctx.profile(True)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step(stream=s)  # warm the side stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        step()
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        g.replay()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kern = {}
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()  # L2 (129 MB) flushed before every step
+        ev[i][0].record()
+        g.replay()
+        ev[i][1].record()
+        for k, v in ctx.profile_read().items():  # waits for this step's events
+            kern.setdefault(k, []).append(v)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    st = ctx.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st}: {ps.error_string(st)}")
+    ms_per_step = total_ms / args.steps
+    segs = batch.n_seg
+    value = world * segs / (ms_per_step * 1e-3)
+    cov_samples = int(covered.sum().item())
+    R_now = int(out.n_rib.item())
+
+    # kernel table and the dominant kernel's roofline
+    import math
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    kmean = {k: statistics.mean(v) for k, v in kern.items()}
+    dom = max(kmean, key=kmean.get)
+    n_tile = ((Wd + 15) // 16) * ((Ht + 15) // 16)
+    counts = {"R": R_now, "L": db.n_link, "S": segs, "P": db.n_path, "px": Wd * Ht,
+              "pairs": int(ps_bin_pairs(ctx, ps, n_tile))}
+    alg = algorithmic(dom, counts)
+    roof = None
+    if alg:
+        bound, nbytes = alg
+        achieved = nbytes / (kmean[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
+                "algorithmic_bytes": nbytes}
+
+    # end to end through the C ABI with host buffers
+    e2e = run_e2e(args, ps, batch, ctx, db, out, canvas, covered, prec, dev)
+
+    plain = None if args.no_plain else run_plain(ps, batch, dev)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "segments/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "variant": "batched+mixed: one CUDA graph per step, "
+                   "FP32 with compensated g(t) and FP64 islands", "n_segments": segs,
+                   "n_paths": db.n_path, "n_ribs": R_now, "canvas": [Wd, Ht], "spp": 16,
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "wall_s_timed_region": t_wall},
+        "covered_samples_per_s": world * cov_samples / (ms_per_step * 1e-3),
+        "covered_samples": cov_samples,
+        "kernel_ms": kmean,
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": 8 * args.steps,
+        "clocks": clk,
+        "plain": plain,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(batch)
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def ps_bin_pairs(ctx, ps, n_tile):
+    """Total raster bin entries of the last step (read from the context's workspace)."""
+    return ps.ps_raster_pair_count(ctx)
+
+
+def run_e2e(args, ps, batch, ctx, db, out, canvas, covered, prec, dev):
+    import numpy as np
+    import torch
+    Wd, Ht = batch.canvas
+    host = {k: getattr(db, k).cpu().pin_memory() for k in
+            ("seg_type", "seg_pts", "seg_w", "path_seg_off", "path_width", "path_join", "path_cap",
+             "path_miter", "path_closed")}
+    h_canvas = torch.empty(canvas.shape, dtype=canvas.dtype).pin_memory()
+    h_cov = torch.empty(covered.shape, dtype=covered.dtype).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = h_canvas.numel() * 2 + h_cov.numel() * 8
+    n = max(5, min(args.steps, 30))
+    times = []
+    for i in range(n + 2):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for k, t in host.items():
+            getattr(db, k).copy_(t, non_blocking=True)
+        ps.ps_tessellate_strokes(ctx, db, out, prec, ps.PS_TESS_ARCLENGTH)
+        ps.ps_rasterize_coverage(ctx, out.rib, out.tag, out.n_rib, out.capacity, db.n_path, Wd, Ht,
+                                 canvas, covered)
+        h_canvas.copy_(canvas, non_blocking=True)
+        h_cov.copy_(covered, non_blocking=True)
+        b.record()
+        b.synchronize()
+        if i >= 2:
+            times.append(a.elapsed_time(b))
+    ms = statistics.mean(times)
+    return {"value": batch.n_seg / (ms * 1e-3), "unit": "segments/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+def run_plain(ps, batch, dev, max_paths=2000):
+    """One path per launch, all FP32, host-driven (count synchronously, then emit)."""
+    import torch
+    n = min(max_paths, batch.n_path)
+    sub = batch.subset(range(n))
+    ctx = ps.Context()
+    dbs = []
+    for p in range(n):
+        dbs.append(ps.DeviceBatch(sub.subset([p]), device=dev))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    segs = 0
+    for d in dbs:
+        probe = ps.TessOutput(d.n_link, d.n_path, 0, arclength=False, device=dev)
+        R = ps.ps_count_ribs_sync(ctx, d, probe, ps.PS_PREC_FP32)
+        o = ps.TessOutput(d.n_link, d.n_path, max(R, 1), arclength=True, device=dev)
+        ps.ps_tessellate_strokes(ctx, d, o, ps.PS_PREC_FP32, ps.PS_TESS_ARCLENGTH)
+        segs += d.n_seg
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"segments_per_s": segs / dt, "sample": f"first {n} paths, tessellation only, "
+            "one path per launch, FP32, host-synchronous count", "s": dt}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

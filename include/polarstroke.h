@@ -1,0 +1,233 @@
+/*
+ * polarstroke.h — C ABI of the GB300 polar stroking library (libpolarstroke.so).
+ *
+ * The library implements the data-parallel hot path of polar stroking
+ * (M. J. Kilgard, "Polar Stroking: New Theory and Methods for Stroking
+ * Paths", ACM TOG 39(4), 2020) as sm_103a CUDA kernels:
+ *
+ *   ps_tessellate_strokes   per-link intervals and step counts (Sec. 3.3-3.4,
+ *                           Eq. 4-6, 12-13), rib offsets, the t(psi) solve
+ *                           (Eq. 11), rib vertices (Eq. 14-17), joins and caps
+ *                           (Sec. 4.3) and cumulative arc length (Eq. 18, Sec. 5.1)
+ *   ps_arclength_scan       cumulative arc length of a rib stream (Eq. 18)
+ *   ps_dash                 dashing by cumulative arc length (Sec. 5.2)
+ *   ps_rasterize_coverage   16-sample coverage of the stroked quads, binned into
+ *                           16x16-pixel tiles (Sec. 4.1: quads drawn as two
+ *                           triangles; Sec. 3.3.6: per-path union)
+ *
+ * Conventions shared by every call
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
+ *     pointers.  The library never frees caller memory.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = legacy default stream) and never synchronizes the host, except
+ *     ps_get_status and ps_count_ribs_sync, which say so.
+ *   - Sizes that depend on the data (rib count, bin entries) live in device
+ *     memory; kernels read them there, so a sequence of calls can be captured
+ *     in a CUDA graph once the context's workspace has been reserved (the first
+ *     call with given sizes may cudaMalloc; capture the second).
+ *   - Return codes: PS_OK or a negative PS_ERR_* for argument errors detected on
+ *     the host.  Errors found by kernels (capacity exceeded, a bounded wait that
+ *     gave up, out-of-range coordinates) are recorded in the context's device
+ *     status word, read by ps_get_status.
+ *
+ * Input layout (structure of arrays)
+ *   segment i:  d_seg_type[i]   uint8   PS_LINE / PS_QUAD / PS_CUBIC / PS_CONIC
+ *               d_seg_pts[8i..8i+7]  float32  A.x A.y B.x B.y C.x C.y D.x D.y
+ *                           (Table 1's control points; quadratic and conic use
+ *                            A, B, D; a line uses A, D)
+ *               d_seg_w[i]      float32 conic weight w_B (must be > -1)
+ *   path p:     segments [d_path_seg_off[p], d_path_seg_off[p+1]) (non-decreasing,
+ *               d_path_seg_off[0] = 0), d_path_width[p] (> 0), d_path_join[p],
+ *               d_path_cap[p], d_path_miter[p] (miter limit, ratio of miter length
+ *               to stroke width), d_path_closed[p] (0/1)
+ *
+ * Link order: path p owns links [2*seg_off[p] + p, 2*seg_off[p+1] + p + 1) in the
+ * order start cap, segment 0, join 0/1, segment 1, ..., segment n-1, end cap (an
+ * open path) or closing join (a closed path) (Sec. 4.4: a path is divided into
+ * links, one per segment, join and cap).  Links with no ribs are empty.
+ *
+ * Output layout
+ *   rib r:  d_rib[4r..4r+3] = N.x N.y P.x P.y (Eq. 16-17; N = g - r_N n,
+ *           P = g + r_P n with n = <-sin psi, cos psi>)
+ *           d_tag[r] = (path << 2) | (is segment link << 1) | (first rib of link)
+ *           d_s[r] cumulative arc length of the path at the rib (Eq. 18)
+ *   quad:   ribs r-1, r with d_tag[r] & 1 == 0 form one quad (Sec. 4.1)
+ */
+#ifndef POLARSTROKE_H
+#define POLARSTROKE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return / status codes ----------------------------------------------- */
+#define PS_OK 0
+#define PS_ERR_INVALID (-1)   /* bad argument (null pointer, bad size, bad enum) */
+#define PS_ERR_CAPACITY (-2)  /* an output or workspace capacity was too small */
+#define PS_ERR_TIMEOUT (-3)   /* a bounded inter-CTA wait gave up */
+#define PS_ERR_CUDA (-4)      /* a CUDA runtime call failed */
+#define PS_ERR_RANGE (-5)     /* a vertex outside +-2^21 px reached the rasterizer */
+
+/* ---- enums ---------------------------------------------------------------- */
+#define PS_LINE 0
+#define PS_QUAD 1
+#define PS_CUBIC 2
+#define PS_CONIC 3
+
+#define PS_JOIN_NONE 0
+#define PS_JOIN_BEVEL 1
+#define PS_JOIN_MITER 2          /* miter; reverts to bevel above the limit */
+#define PS_JOIN_MITER_TRUNCATE 3 /* miter clipped at limit * w/2 */
+#define PS_JOIN_ROUND 4
+#define PS_JOIN_TRIANGLE 5
+
+#define PS_CAP_BUTT 0
+#define PS_CAP_SQUARE 1
+#define PS_CAP_ROUND 2
+#define PS_CAP_TRIANGLE 3
+
+#define PS_PREC_FP32 0  /* all-FP32 arithmetic */
+#define PS_PREC_MIXED 1 /* FP32 bulk, compensated evaluation of g(t), FP64 in the
+                           inflection discriminant, near-integer step counts and
+                           near-degenerate t(psi) solves */
+
+/* ps_tessellate_strokes flags */
+#define PS_TESS_ARCLENGTH 1u  /* also write d_s and d_path_len */
+#define PS_TESS_COUNT_ONLY 2u /* only per-link offsets, path offsets and *d_n_rib */
+
+#define PS_TAG_LINK_START 1u
+#define PS_TAG_SEGMENT 2u
+
+typedef struct ps_context ps_context;
+
+typedef struct {
+  const uint8_t* d_type; /* [n_seg] */
+  const float* d_pts;    /* [n_seg * 8] */
+  const float* d_w;      /* [n_seg] */
+  int64_t n_seg;
+} ps_segments;
+
+typedef struct {
+  const int32_t* d_seg_off; /* [n_path + 1] */
+  const float* d_width;     /* [n_path] */
+  const uint8_t* d_join;    /* [n_path] */
+  const uint8_t* d_cap;     /* [n_path] */
+  const float* d_miter;     /* [n_path] */
+  const uint8_t* d_closed;  /* [n_path] */
+  int32_t n_path;
+} ps_paths;
+
+typedef struct {
+  float* d_rib;             /* [capacity * 4] */
+  uint32_t* d_tag;          /* [capacity] */
+  float* d_s;               /* [capacity]; NULL unless PS_TESS_ARCLENGTH */
+  float* d_t;               /* [capacity]; optional t(j) per rib, may be NULL */
+  int32_t* d_link_rib_off;  /* [n_link + 1], n_link = 2 n_seg + n_path */
+  int32_t* d_path_rib_off;  /* [n_path + 1] */
+  float* d_path_len;        /* [n_path]; NULL unless PS_TESS_ARCLENGTH */
+  int64_t* d_n_rib;         /* [1]: total ribs R (written even when R > capacity) */
+  int64_t capacity;         /* rib capacity of d_rib / d_tag / d_s / d_t */
+} ps_tess_out;
+
+/* ---- context ---------------------------------------------------------------
+ * A context owns device workspace (tile states for the single-pass scans, the
+ * per-link interval records, raster bins) and a device status word.  It is
+ * bound to the device that is current at ps_create.  Not thread-safe: use one
+ * context per host thread / stream. */
+int ps_create(ps_context** ctx);
+void ps_destroy(ps_context* ctx);
+
+/* Reserve workspace for up to n_link links, n_rib ribs, n_tile raster tiles
+ * and n_pair raster bin entries (any may be 0 = keep).  Allocates with
+ * cudaMalloc (synchronous); call before capturing a graph. */
+int ps_reserve(ps_context* ctx, int64_t n_link, int64_t n_rib, int64_t n_tile, int64_t n_pair);
+
+/* Host-only static bound on the rib count of n_seg segments in n_path paths
+ * at step dtheta (radians): a segment turns < 2 pi in at most 6 intervals
+ * (Sec. 3.3.5), a join or cap pivots at most pi (Sec. 4.3). */
+int ps_max_ribs(int64_t n_seg, int32_t n_path, float dtheta, int64_t* h_bound);
+
+/* Read and clear the device status word.  SYNCHRONIZES the context's last
+ * stream.  *h_status receives PS_OK or the first PS_ERR_* a kernel recorded. */
+int ps_get_status(ps_context* ctx, int* h_status);
+
+const char* ps_error_string(int code);
+
+/* ---- the hot path ------------------------------------------------------------ */
+
+/* Tessellate every path (Sec. 4.4's complete algorithm, all links in parallel).
+ *   dtheta     q, the tangent-angle step in radians (Sec. 4.2), > 0
+ *   precision  PS_PREC_FP32 or PS_PREC_MIXED
+ *   flags      PS_TESS_ARCLENGTH, PS_TESS_COUNT_ONLY
+ * Writes out->d_link_rib_off, d_path_rib_off, *d_n_rib, and (unless COUNT_ONLY)
+ * the first min(R, capacity) ribs.  R > capacity records PS_ERR_CAPACITY.
+ * Ribs of path p are [path_rib_off[p], path_rib_off[p+1]); ribs of link l are
+ * [link_rib_off[l], link_rib_off[l+1]).  Offsets are int32: R < 2^31. */
+int ps_tessellate_strokes(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
+                          float dtheta, int precision, uint32_t flags, ps_tess_out* out,
+                          void* stream);
+
+/* Convenience: run the count phase and return R on the host.  SYNCHRONIZES. */
+int ps_count_ribs_sync(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
+                       float dtheta, int precision, ps_tess_out* out, void* stream,
+                       int64_t* h_n_rib);
+
+/* Cumulative arc length of an existing rib stream (Eq. 18): the centreline
+ * point of a segment rib is its midpoint (N + P)/2 (exact when r_N = r_P, as in
+ * segment links); joins and caps add 0; s restarts at 0 at every path's first
+ * rib.  d_n_rib: device rib count; capacity bounds it.  d_path_len may be NULL. */
+int ps_arclength_scan(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
+                      const int64_t* d_n_rib, int64_t capacity, float* d_s,
+                      float* d_path_len, int32_t n_path, void* stream);
+
+/* Dash a rib stream by its cumulative arc length (Sec. 5.2).  h_pattern holds
+ * n_pattern (1..32) non-negative lengths, on/off alternating (an odd count is
+ * repeated twice), restarting at s = 0 of every path, shifted by `offset`.
+ * Each quad is clipped to the "on" stretches [a, b) by interpolating both rib
+ * vertices; every piece is emitted as an independent 2-rib strip; a zero-length
+ * quad (join, cap, cusp pivot) is kept whole iff its s is "on".
+ * Outputs: d_out_rib[4 cap], d_out_s[cap], d_out_tag[cap], d_out_src[cap]
+ * (index of the source quad's end rib, may be NULL), *d_n_out (device).  More
+ * than out_capacity ribs records PS_ERR_CAPACITY. */
+int ps_dash(ps_context* ctx, const float* d_rib, const float* d_s, const uint32_t* d_tag,
+            const int64_t* d_n_rib, int64_t capacity, const float* h_pattern, int n_pattern,
+            float offset, float* d_out_rib, float* d_out_s, uint32_t* d_out_tag,
+            int32_t* d_out_src, int64_t* d_n_out, int64_t out_capacity, void* stream);
+
+/* Coverage of the quads of a rib stream on a width x height canvas with 16
+ * samples per pixel (spp must be 16).  Vertices snap to round-half-even(v*256);
+ * sample k of pixel (x, y) sits at (x + (16k+8)/256, y + (16((5k) mod 16)+8)/256);
+ * a sample is covered by a triangle iff its three edge functions are >= 0 with
+ * the triangle oriented counter-clockwise (zero-area triangles cover nothing);
+ * quad (r-1, r) is the triangles (N_{r-1}, P_{r-1}, P_r), (N_{r-1}, P_r, N_r).
+ *   d_canvas[y*width + x]   uint16 sample mask, OR over all paths (overwritten)
+ *   d_covered[p]            uint64 samples covered by path p (union of its
+ *                           quads; overwritten)
+ * Quads with a vertex beyond +-2^21 px are skipped and record PS_ERR_RANGE. */
+int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
+                          const int64_t* d_n_rib, int64_t capacity, int32_t n_path,
+                          int width, int height, int spp, uint16_t* d_canvas,
+                          uint64_t* d_covered, void* stream);
+
+/* ---- kernel timing (measurement hooks) ------------------------------------------
+ * With profiling enabled the library records a CUDA event pair around each of its
+ * kernel launches on the launching stream (as external event-record nodes when
+ * the stream is being captured into a graph, so graph replays are timed too).
+ * Slot s names one kernel (ps_profile_slot_name).  ps_profile_read waits for the
+ * events and returns, per slot, the duration in ms of the most recent launch,
+ * or -1 if the slot has not been recorded since profiling was enabled. */
+#define PS_PROF_SLOTS 10
+int ps_profile_enable(ps_context* ctx, int enable);
+int ps_profile_read(ps_context* ctx, float* h_ms /* [PS_PROF_SLOTS] */);
+const char* ps_profile_slot_name(int slot);
+
+/* Number of (quad, tile) bin entries of the context's most recent
+ * ps_rasterize_coverage call, read from its device workspace.  SYNCHRONIZES. */
+int ps_raster_pair_count(ps_context* ctx, int64_t* h_pairs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLARSTROKE_H */

@@ -1,0 +1,275 @@
+"""GB300 polar stroking: Python binding of libpolarstroke.so.
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels (see ``include/polarstroke.h``).  PyTorch supplies device memory
+and streams.  There is no CPU fallback: if the compiled library is missing the
+import of any entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpolarstroke.so")
+
+PS_OK, PS_ERR_INVALID, PS_ERR_CAPACITY, PS_ERR_TIMEOUT, PS_ERR_CUDA, PS_ERR_RANGE = 0, -1, -2, -3, -4, -5
+PS_PREC_FP32, PS_PREC_MIXED = 0, 1
+PS_TESS_ARCLENGTH, PS_TESS_COUNT_ONLY = 1, 2
+TAG_LINK_START, TAG_SEGMENT = 1, 2
+
+EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_status",
+           "ps_error_string", "ps_tessellate_strokes", "ps_count_ribs_sync", "ps_arclength_scan",
+           "ps_dash", "ps_rasterize_coverage", "ps_profile_enable", "ps_profile_read",
+           "ps_profile_slot_name", "ps_raster_pair_count"]
+PS_PROF_SLOTS = 10
+
+
+class PolarStrokeError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {error_string(code)} ({code})")
+
+
+class _Segments(ctypes.Structure):
+    _fields_ = [("d_type", ctypes.c_void_p), ("d_pts", ctypes.c_void_p), ("d_w", ctypes.c_void_p),
+                ("n_seg", ctypes.c_int64)]
+
+
+class _Paths(ctypes.Structure):
+    _fields_ = [("d_seg_off", ctypes.c_void_p), ("d_width", ctypes.c_void_p),
+                ("d_join", ctypes.c_void_p), ("d_cap", ctypes.c_void_p),
+                ("d_miter", ctypes.c_void_p), ("d_closed", ctypes.c_void_p),
+                ("n_path", ctypes.c_int32)]
+
+
+class _TessOut(ctypes.Structure):
+    _fields_ = [("d_rib", ctypes.c_void_p), ("d_tag", ctypes.c_void_p), ("d_s", ctypes.c_void_p),
+                ("d_t", ctypes.c_void_p), ("d_link_rib_off", ctypes.c_void_p),
+                ("d_path_rib_off", ctypes.c_void_p), ("d_path_len", ctypes.c_void_p),
+                ("d_n_rib", ctypes.c_void_p), ("capacity", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        L.ps_create.argtypes = [ctypes.POINTER(ctypes.c_void_p)]
+        L.ps_destroy.argtypes = [P]
+        L.ps_destroy.restype = None
+        L.ps_reserve.argtypes = [P, I64, I64, I64, I64]
+        L.ps_max_ribs.argtypes = [I64, I32, ctypes.c_float, ctypes.POINTER(I64)]
+        L.ps_get_status.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+        L.ps_error_string.argtypes = [ctypes.c_int]
+        L.ps_error_string.restype = ctypes.c_char_p
+        L.ps_tessellate_strokes.argtypes = [P, ctypes.POINTER(_Segments), ctypes.POINTER(_Paths),
+                                            ctypes.c_float, ctypes.c_int, ctypes.c_uint32,
+                                            ctypes.POINTER(_TessOut), P]
+        L.ps_count_ribs_sync.argtypes = [P, ctypes.POINTER(_Segments), ctypes.POINTER(_Paths),
+                                         ctypes.c_float, ctypes.c_int, ctypes.POINTER(_TessOut), P,
+                                         ctypes.POINTER(I64)]
+        L.ps_arclength_scan.argtypes = [P, P, P, P, I64, P, P, I32, P]
+        L.ps_dash.argtypes = [P, P, P, P, P, I64, P, ctypes.c_int, ctypes.c_float, P, P, P, P, P,
+                              I64, P]
+        L.ps_rasterize_coverage.argtypes = [P, P, P, P, I64, I32, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, P, P, P]
+        L.ps_profile_enable.argtypes = [P, ctypes.c_int]
+        L.ps_profile_read.argtypes = [P, P]
+        L.ps_profile_slot_name.argtypes = [ctypes.c_int]
+        L.ps_profile_slot_name.restype = ctypes.c_char_p
+        L.ps_raster_pair_count.argtypes = [P, ctypes.POINTER(I64)]
+        _lib = L
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return lib().ps_error_string(int(code)).decode()
+
+
+def _check(rc, what):
+    if rc != PS_OK:
+        raise PolarStrokeError(rc, what)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """Owns a ps_context (device workspace + status word) on the current device."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(lib().ps_create(ctypes.byref(h)), "ps_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().ps_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, n_link=0, n_rib=0, n_tile=0, n_pair=0):
+        _check(lib().ps_reserve(self.handle, n_link, n_rib, n_tile, n_pair), "ps_reserve")
+
+    def profile(self, enable: bool = True):
+        """Record a CUDA event pair around every library kernel launch."""
+        _check(lib().ps_profile_enable(self.handle, int(bool(enable))), "ps_profile_enable")
+
+    def profile_read(self) -> dict:
+        """Duration (ms) of the most recent launch of each kernel (waits for it)."""
+        ms = (ctypes.c_float * PS_PROF_SLOTS)()
+        _check(lib().ps_profile_read(self.handle, ctypes.cast(ms, ctypes.c_void_p)), "ps_profile_read")
+        return {lib().ps_profile_slot_name(i).decode(): ms[i] for i in range(PS_PROF_SLOTS)
+                if ms[i] >= 0}
+
+    def status(self) -> int:
+        """Read and clear the device status word (synchronizes)."""
+        v = ctypes.c_int(0)
+        _check(lib().ps_get_status(self.handle, ctypes.byref(v)), "ps_get_status")
+        return v.value
+
+
+class DeviceBatch:
+    """A stroke batch's input arrays on the GPU (torch tensors)."""
+
+    def __init__(self, batch, device="cuda"):
+        import torch
+        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(device)
+        self.seg_type = t(batch.seg_type, np.uint8)
+        self.seg_pts = t(np.asarray(batch.seg_pts, np.float32).reshape(-1), np.float32)
+        self.seg_w = t(batch.seg_w, np.float32)
+        self.path_seg_off = t(batch.path_seg_off, np.int32)
+        self.path_width = t(batch.path_width, np.float32)
+        self.path_join = t(batch.path_join, np.uint8)
+        self.path_cap = t(batch.path_cap, np.uint8)
+        self.path_miter = t(batch.path_miter, np.float32)
+        self.path_closed = t(batch.path_closed, np.uint8)
+        self.n_seg = int(batch.seg_type.shape[0])
+        self.n_path = int(batch.path_width.shape[0])
+        self.dtheta = float(np.float32(batch.dtheta))
+
+    @property
+    def n_link(self):
+        return 2 * self.n_seg + self.n_path
+
+    def _structs(self):
+        seg = _Segments(_ptr(self.seg_type).value, _ptr(self.seg_pts).value, _ptr(self.seg_w).value,
+                        self.n_seg)
+        paths = _Paths(_ptr(self.path_seg_off).value, _ptr(self.path_width).value,
+                       _ptr(self.path_join).value, _ptr(self.path_cap).value,
+                       _ptr(self.path_miter).value, _ptr(self.path_closed).value, self.n_path)
+        return seg, paths
+
+
+class TessOutput:
+    """Caller-owned output buffers of ps_tessellate_strokes."""
+
+    def __init__(self, n_link, n_path, capacity, arclength=True, want_t=False, device="cuda"):
+        import torch
+        self.capacity = int(capacity)
+        self.rib = torch.empty((self.capacity, 4), dtype=torch.float32, device=device)
+        self.tag = torch.empty(self.capacity, dtype=torch.int32, device=device)
+        self.s = torch.empty(self.capacity, dtype=torch.float32, device=device) if arclength else None
+        self.t = torch.empty(self.capacity, dtype=torch.float32, device=device) if want_t else None
+        self.link_rib_off = torch.empty(n_link + 1, dtype=torch.int32, device=device)
+        self.path_rib_off = torch.empty(n_path + 1, dtype=torch.int32, device=device)
+        self.path_len = torch.empty(n_path, dtype=torch.float32, device=device) if arclength else None
+        self.n_rib = torch.zeros(1, dtype=torch.int64, device=device)
+
+    def _struct(self):
+        p = lambda x: None if x is None else x.data_ptr()
+        return _TessOut(p(self.rib), p(self.tag), p(self.s), p(self.t), p(self.link_rib_off),
+                        p(self.path_rib_off), p(self.path_len), p(self.n_rib), self.capacity)
+
+
+def ps_raster_pair_count(ctx: Context) -> int:
+    n = ctypes.c_int64(0)
+    _check(lib().ps_raster_pair_count(ctx.handle, ctypes.byref(n)), "ps_raster_pair_count")
+    return n.value
+
+
+def ps_max_ribs(n_seg, n_path, dtheta) -> int:
+    b = ctypes.c_int64(0)
+    _check(lib().ps_max_ribs(int(n_seg), int(n_path), float(dtheta), ctypes.byref(b)), "ps_max_ribs")
+    return b.value
+
+
+def ps_tessellate_strokes(ctx: Context, db: DeviceBatch, out: TessOutput, precision=PS_PREC_FP32,
+                          flags=PS_TESS_ARCLENGTH, dtheta=None, stream=None):
+    seg, paths = db._structs()
+    o = out._struct()
+    q = db.dtheta if dtheta is None else float(dtheta)
+    rc = lib().ps_tessellate_strokes(ctx.handle, ctypes.byref(seg), ctypes.byref(paths), q,
+                                     int(precision), int(flags), ctypes.byref(o), _stream(stream))
+    _check(rc, "ps_tessellate_strokes")
+
+
+def ps_count_ribs_sync(ctx: Context, db: DeviceBatch, out: TessOutput, precision=PS_PREC_FP32,
+                       dtheta=None, stream=None) -> int:
+    seg, paths = db._structs()
+    o = out._struct()
+    n = ctypes.c_int64(0)
+    q = db.dtheta if dtheta is None else float(dtheta)
+    rc = lib().ps_count_ribs_sync(ctx.handle, ctypes.byref(seg), ctypes.byref(paths), q,
+                                  int(precision), ctypes.byref(o), _stream(stream), ctypes.byref(n))
+    _check(rc, "ps_count_ribs_sync")
+    return n.value
+
+
+def ps_arclength_scan(ctx: Context, rib, tag, n_rib, capacity, s, path_len, n_path, stream=None):
+    rc = lib().ps_arclength_scan(ctx.handle, _ptr(rib), _ptr(tag), _ptr(n_rib), int(capacity),
+                                 _ptr(s), _ptr(path_len), int(n_path), _stream(stream))
+    _check(rc, "ps_arclength_scan")
+
+
+def ps_dash(ctx: Context, rib, s, tag, n_rib, capacity, pattern, offset, out_rib, out_s, out_tag,
+            out_src, n_out, out_capacity, stream=None):
+    pat = (ctypes.c_float * len(pattern))(*[float(v) for v in pattern])
+    rc = lib().ps_dash(ctx.handle, _ptr(rib), _ptr(s), _ptr(tag), _ptr(n_rib), int(capacity),
+                       ctypes.cast(pat, ctypes.c_void_p), len(pattern), float(offset), _ptr(out_rib),
+                       _ptr(out_s), _ptr(out_tag), _ptr(out_src), _ptr(n_out), int(out_capacity),
+                       _stream(stream))
+    _check(rc, "ps_dash")
+
+
+def ps_rasterize_coverage(ctx: Context, rib, tag, n_rib, capacity, n_path, width, height, canvas,
+                          covered, spp=16, stream=None):
+    rc = lib().ps_rasterize_coverage(ctx.handle, _ptr(rib), _ptr(tag), _ptr(n_rib), int(capacity),
+                                     int(n_path), int(width), int(height), int(spp), _ptr(canvas),
+                                     _ptr(covered), _stream(stream))
+    _check(rc, "ps_rasterize_coverage")
+
+
+def tessellate(ctx: Context, db: DeviceBatch, precision=PS_PREC_FP32, arclength=True,
+               want_t=False, capacity=None, stream=None) -> TessOutput:
+    """Allocate exact-size outputs (one host sync for the count) and tessellate."""
+    if capacity is None:
+        probe = TessOutput(db.n_link, db.n_path, 0, arclength=False)
+        capacity = ps_count_ribs_sync(ctx, db, probe, precision, stream=stream)
+    out = TessOutput(db.n_link, db.n_path, max(int(capacity), 1), arclength=arclength, want_t=want_t)
+    ps_tessellate_strokes(ctx, db, out, precision,
+                          PS_TESS_ARCLENGTH if arclength else 0, stream=stream)
+    return out

@@ -1,0 +1,191 @@
+// Context, workspace and status handling of the C ABI.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "ps_internal.cuh"
+
+int ps_cuda_check(cudaError_t e) { return e == cudaSuccess ? PS_OK : PS_ERR_CUDA; }
+
+static int grow(void** p, size_t bytes) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  if (bytes == 0) return PS_OK;
+  return ps_cuda_check(cudaMalloc(p, bytes));
+}
+
+int ps_ensure_tiles(ps_context* ctx, int64_t n) {
+  if (n <= ctx->tile_cap) return PS_OK;
+  int64_t cap = n + n / 4 + 64;
+  int rc;
+  if ((rc = grow((void**)&ctx->d_tile_flag, sizeof(uint32_t) * cap)) != PS_OK) return rc;
+  if ((rc = grow((void**)&ctx->d_tile_agg, sizeof(long long) * cap)) != PS_OK) return rc;
+  if ((rc = grow((void**)&ctx->d_tile_incl, sizeof(long long) * cap)) != PS_OK) return rc;
+  if ((rc = grow((void**)&ctx->d_tile_aggd, sizeof(double) * cap)) != PS_OK) return rc;
+  if ((rc = grow((void**)&ctx->d_tile_incld, sizeof(double) * cap)) != PS_OK) return rc;
+  ctx->tile_cap = cap;
+  return PS_OK;
+}
+
+int ps_ensure_recs(ps_context* ctx, int64_t n_link) {
+  if (n_link <= ctx->rec_cap) return PS_OK;
+  int64_t cap = n_link + n_link / 4 + 64;
+  // records followed by one int32 path index per link
+  int rc = grow((void**)&ctx->d_recs, (sizeof(LinkRec) + sizeof(int32_t)) * cap);
+  if (rc != PS_OK) return rc;
+  ctx->rec_cap = cap;
+  return PS_OK;
+}
+
+int ps_ensure_raster(ps_context* ctx, int64_t n_tile, int64_t n_pair) {
+  int rc;
+  if (n_tile > ctx->raster_tile_cap) {
+    int64_t cap = n_tile + 64;
+    if ((rc = grow((void**)&ctx->d_tile_count, sizeof(int32_t) * (cap + 1))) != PS_OK) return rc;
+    if ((rc = grow((void**)&ctx->d_tile_off, sizeof(int32_t) * (cap + 1))) != PS_OK) return rc;
+    if ((rc = grow((void**)&ctx->d_tile_cursor, sizeof(int32_t) * (cap + 1))) != PS_OK) return rc;
+    ctx->raster_tile_cap = cap;
+  }
+  if (n_pair > ctx->pair_cap) {
+    int64_t cap = n_pair + n_pair / 8 + 1024;
+    if ((rc = grow((void**)&ctx->d_bin, sizeof(uint32_t) * cap)) != PS_OK) return rc;
+    ctx->pair_cap = cap;
+  }
+  return PS_OK;
+}
+
+int ps_persistent_grid(ps_context* ctx, const void* kernel, int block, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return ctx->num_sms * per_sm;
+}
+
+extern "C" int ps_create(ps_context** out) {
+  if (!out) return PS_ERR_INVALID;
+  ps_context* ctx = (ps_context*)calloc(1, sizeof(ps_context));
+  if (!ctx) return PS_ERR_INVALID;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+    free(ctx);
+    return PS_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (ctx->num_sms <= 0) ctx->num_sms = 1;
+  if (cudaMalloc((void**)&ctx->d_status, 64) != cudaSuccess ||
+      cudaMalloc((void**)&ctx->d_counters, sizeof(int32_t) * 16) != cudaSuccess ||
+      cudaMalloc((void**)&ctx->d_scratch64, sizeof(int64_t) * 16) != cudaSuccess) {
+    ps_destroy(ctx);
+    return PS_ERR_CUDA;
+  }
+  cudaMemset(ctx->d_status, 0, 64);
+  cudaMemset(ctx->d_counters, 0, sizeof(int32_t) * 16);
+  *out = ctx;
+  return PS_OK;
+}
+
+extern "C" void ps_destroy(ps_context* ctx) {
+  if (!ctx) return;
+  if (ctx->prof_on) ps_profile_enable(ctx, 0);
+  void* ptrs[] = {ctx->d_status, ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
+                  ctx->d_tile_aggd, ctx->d_tile_incld, ctx->d_counters, ctx->d_recs,
+                  ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor, ctx->d_bin,
+                  ctx->d_scratch64, ctx->d_mask_scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  free(ctx);
+}
+
+extern "C" int ps_reserve(ps_context* ctx, int64_t n_link, int64_t n_rib, int64_t n_tile,
+                          int64_t n_pair) {
+  if (!ctx || n_link < 0 || n_rib < 0 || n_tile < 0 || n_pair < 0) return PS_ERR_INVALID;
+  int rc;
+  if (n_link && (rc = ps_ensure_recs(ctx, n_link)) != PS_OK) return rc;
+  int64_t tiles = (n_link + 511) / 512 + (n_rib + 2047) / 2048 + 4 + n_rib / 512;
+  if ((rc = ps_ensure_tiles(ctx, tiles)) != PS_OK) return rc;
+  if ((n_tile || n_pair) && (rc = ps_ensure_raster(ctx, n_tile, n_pair)) != PS_OK) return rc;
+  return PS_OK;
+}
+
+extern "C" int ps_max_ribs(int64_t n_seg, int32_t n_path, float dtheta, int64_t* h_bound) {
+  if (!h_bound || n_seg < 0 || n_path < 0 || !(dtheta > 0.f)) return PS_ERR_INVALID;
+  double q = dtheta;
+  int64_t per_seg = (int64_t)ceil(2.0 * 3.14159265358979323846 / q) + 7;
+  int64_t half = (int64_t)ceil(3.14159265358979323846 / q);
+  int64_t per_pivot = (half > 4 ? half : 4) + 1;
+  *h_bound = n_seg * per_seg + (n_seg + (int64_t)n_path) * per_pivot;
+  return PS_OK;
+}
+
+extern "C" int ps_get_status(ps_context* ctx, int* h_status) {
+  if (!ctx || !h_status) return PS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)ctx->last_stream;
+  int32_t v = 0;
+  int rc = ps_cuda_check(cudaMemcpyAsync(&v, ctx->d_status, sizeof(int32_t),
+                                         cudaMemcpyDeviceToHost, st));
+  if (rc == PS_OK) rc = ps_cuda_check(cudaStreamSynchronize(st));
+  if (rc != PS_OK) return rc;
+  *h_status = v;
+  cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), st);
+  return ps_cuda_check(cudaStreamSynchronize(st));
+}
+
+void ps_prof_mark(ps_context* ctx, int slot, int end, cudaStream_t st) {
+  if (!ctx->prof_on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(ctx->prof_ev[slot][end], st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(ctx->prof_ev[slot][end], st);
+  if (end) ctx->prof_recorded[slot] = 1;
+}
+
+extern "C" int ps_profile_enable(ps_context* ctx, int enable) {
+  if (!ctx) return PS_ERR_INVALID;
+  if (enable && !ctx->prof_on) {
+    for (int s = 0; s < PK_COUNT; ++s)
+      for (int e = 0; e < 2; ++e)
+        if (cudaEventCreate(&ctx->prof_ev[s][e]) != cudaSuccess) return PS_ERR_CUDA;
+  }
+  if (!enable && ctx->prof_on) {
+    cudaDeviceSynchronize();
+    for (int s = 0; s < PK_COUNT; ++s)
+      for (int e = 0; e < 2; ++e) cudaEventDestroy(ctx->prof_ev[s][e]);
+  }
+  for (int s = 0; s < PK_COUNT; ++s) ctx->prof_recorded[s] = 0;
+  ctx->prof_on = enable ? 1 : 0;
+  return PS_OK;
+}
+
+extern "C" int ps_profile_read(ps_context* ctx, float* h_ms) {
+  if (!ctx || !h_ms) return PS_ERR_INVALID;
+  for (int s = 0; s < PK_COUNT; ++s) {
+    h_ms[s] = -1.f;
+    if (!ctx->prof_on || !ctx->prof_recorded[s]) continue;
+    if (cudaEventSynchronize(ctx->prof_ev[s][1]) != cudaSuccess) return PS_ERR_CUDA;
+    float ms = -1.f;
+    if (cudaEventElapsedTime(&ms, ctx->prof_ev[s][0], ctx->prof_ev[s][1]) == cudaSuccess) h_ms[s] = ms;
+  }
+  return PS_OK;
+}
+
+extern "C" const char* ps_profile_slot_name(int slot) {
+  static const char* names[PK_COUNT] = {"k_link_path", "k_link_setup", "k_emit", "k_arclen_scan",
+                                        "k_midpoint_chords", "k_bin_count", "k_tile_scan",
+                                        "k_bin_scatter", "k_coverage", "k_dash"};
+  return (slot >= 0 && slot < PK_COUNT) ? names[slot] : "";
+}
+
+extern "C" const char* ps_error_string(int code) {
+  switch (code) {
+    case PS_OK: return "ok";
+    case PS_ERR_INVALID: return "invalid argument";
+    case PS_ERR_CAPACITY: return "capacity exceeded";
+    case PS_ERR_TIMEOUT: return "bounded inter-CTA wait timed out";
+    case PS_ERR_CUDA: return "CUDA runtime error";
+    case PS_ERR_RANGE: return "vertex coordinate out of the rasterizer's range";
+    default: return "unknown error";
+  }
+}

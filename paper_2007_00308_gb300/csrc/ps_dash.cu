@@ -1,0 +1,196 @@
+// Dashing by cumulative arc length (Sec. 5.2).
+//
+// On-stretch i of period k covers s in [k*period + cum[2i] - offset,
+// k*period + cum[2i+1] - offset).  Each quad [s_{r-1}, s_r] of a rib strip is
+// clipped to those stretches by interpolating both rib vertices; every piece is
+// an independent 2-rib strip.  A quad of zero length (join, cap, cusp pivot) is
+// kept whole iff its s is "on".  Stretch boundaries are evaluated in FP64 with
+// explicitly rounded operations (no contraction).
+#include <cuda_runtime.h>
+
+#include "ps_internal.cuh"
+
+namespace {
+
+struct DashPattern {
+  double cum[65];
+  double period;
+  double offset;
+  int m2;
+};
+
+constexpr int DASH_NT = 256;
+
+template <bool EMIT>
+__device__ __forceinline__ int dash_quad(const DashPattern& P, double sa, double sb, int64_t r,
+                                         const float4* rib, float sa_f, float sb_f,
+                                         uint32_t tg, int64_t out0, float4* out_rib,
+                                         float* out_s, uint32_t* out_tag, int32_t* out_src,
+                                         int64_t out_cap, int32_t* status) {
+  int n = 0;
+  double k0 = floor(__ddiv_rn(__dadd_rn(sa, P.offset), P.period)) - 1.0;
+  float4 v0, v1;
+  if (EMIT) {
+    v0 = rib[r - 1];
+    v1 = rib[r];
+  }
+  for (int guard = 0; guard < (1 << 20); ++guard) {
+    double k = k0 + (double)guard;
+    double base = __dmul_rn(k, P.period);
+    if (__dsub_rn(base, P.offset) > sb) break;
+    for (int i = 0; i < P.m2; i += 2) {
+      double a = __dsub_rn(__dadd_rn(base, P.cum[i]), P.offset);
+      double b = __dsub_rn(__dadd_rn(base, P.cum[i + 1]), P.offset);
+      if (!(b > a)) continue;
+      double lo, hi;
+      bool keep;
+      if (sb > sa) {
+        lo = a > sa ? a : sa;
+        hi = b < sb ? b : sb;
+        keep = hi > lo;
+      } else {
+        lo = sa;
+        hi = sb;
+        keep = (sa >= a && sa < b);
+      }
+      if (!keep) continue;
+      if (EMIT) {
+        int64_t o = out0 + 2 * n;
+        if (o + 2 <= out_cap) {
+          double f0 = 0.0, f1 = 1.0;
+          if (sb > sa) {
+            double d = __dsub_rn(sb, sa);
+            f0 = __ddiv_rn(__dsub_rn(lo, sa), d);
+            f1 = __ddiv_rn(__dsub_rn(hi, sa), d);
+          }
+          float a0[4] = {v0.x, v0.y, v0.z, v0.w}, a1[4] = {v1.x, v1.y, v1.z, v1.w};
+          float p0[4], p1[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            double dv = __dsub_rn((double)a1[c], (double)a0[c]);
+            p0[c] = (float)__dadd_rn((double)a0[c], __dmul_rn(f0, dv));
+            p1[c] = (float)__dadd_rn((double)a0[c], __dmul_rn(f1, dv));
+          }
+          out_rib[o] = make_float4(p0[0], p0[1], p0[2], p0[3]);
+          out_rib[o + 1] = make_float4(p1[0], p1[1], p1[2], p1[3]);
+          out_s[o] = (float)lo;
+          out_s[o + 1] = (float)hi;
+          out_tag[o] = tg | PS_TAG_LINK_START;
+          out_tag[o + 1] = tg;
+          if (out_src) {
+            out_src[o] = (int32_t)r;
+            out_src[o + 1] = (int32_t)r;
+          }
+        } else {
+          ps_record_error(status, PS_ERR_CAPACITY);
+        }
+      }
+      ++n;
+    }
+  }
+  return n;
+}
+
+// One pass: per-rib piece counts, block scan, decoupled look-back for the
+// tile's output offset, emission.
+__global__ void __launch_bounds__(DASH_NT) k_dash(
+    const float4* __restrict__ rib, const float* __restrict__ s, const uint32_t* __restrict__ tag,
+    const int64_t* __restrict__ n_rib, int64_t capacity, DashPattern P,
+    float4* __restrict__ out_rib, float* __restrict__ out_s, uint32_t* __restrict__ out_tag,
+    int32_t* __restrict__ out_src, int64_t* __restrict__ n_out, int64_t out_cap, uint32_t* tflag,
+    long long* tagg, long long* tincl, int32_t* counters, int32_t* status) {
+  __shared__ long long sm[DASH_NT / 32];
+  __shared__ long long s_prefix;
+  __shared__ int s_tile;
+  int64_t R = *n_rib;
+  if (R > capacity) R = capacity;
+  int64_t n_tiles = (R + DASH_NT - 1) / DASH_NT;
+  if (n_tiles == 0) n_tiles = 1;
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&counters[3], 1);
+    __syncthreads();
+    int64_t tile = s_tile;
+    __syncthreads();
+    if (tile >= n_tiles) return;
+    int64_t r = tile * DASH_NT + threadIdx.x;
+    int cnt = 0;
+    double sa = 0, sb = 0;
+    uint32_t tg = 0;
+    bool active = r >= 1 && r < R;
+    if (active) {
+      tg = tag[r];
+      if (tg & PS_TAG_LINK_START) active = false;
+    }
+    if (active) {
+      sa = (double)s[r - 1];
+      sb = (double)s[r];
+      cnt = dash_quad<false>(P, sa, sb, r, rib, 0.f, 0.f, 0u, 0, nullptr, nullptr, nullptr, nullptr,
+                             0, status);
+    }
+    long long x = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[wid] = x;
+    __syncthreads();
+    long long total = 0, wpre = 0;
+    for (int w = 0; w < DASH_NT / 32; ++w) {
+      if (w < wid) wpre += sm[w];
+      total += sm[w];
+    }
+    long long excl = x - cnt + wpre;
+    if (threadIdx.x == 0) s_prefix = lookback_sum(tflag, tagg, tincl, total, tile, status);
+    __syncthreads();
+    int64_t out0 = 2 * (s_prefix + excl);
+    if (active && cnt)
+      dash_quad<true>(P, sa, sb, r, rib, 0.f, 0.f, tg & ~PS_TAG_LINK_START, out0, out_rib, out_s,
+                      out_tag, out_src, out_cap, status);
+    if (tile == n_tiles - 1 && threadIdx.x == DASH_NT - 1) {
+      long long tot = 2 * (s_prefix + total);
+      *n_out = tot;
+      if (tot > out_cap) ps_record_error(status, PS_ERR_CAPACITY);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+extern "C" int ps_dash(ps_context* ctx, const float* d_rib, const float* d_s,
+                       const uint32_t* d_tag, const int64_t* d_n_rib, int64_t capacity,
+                       const float* h_pattern, int n_pattern, float offset, float* d_out_rib,
+                       float* d_out_s, uint32_t* d_out_tag, int32_t* d_out_src, int64_t* d_n_out,
+                       int64_t out_capacity, void* stream) {
+  if (!ctx || !d_rib || !d_s || !d_tag || !d_n_rib || !h_pattern || !d_out_rib || !d_out_s ||
+      !d_out_tag || !d_n_out || capacity < 0 || out_capacity < 0)
+    return PS_ERR_INVALID;
+  if (n_pattern < 1 || n_pattern > 32 || !(offset == offset)) return PS_ERR_INVALID;
+  DashPattern P;
+  P.m2 = (n_pattern % 2) ? 2 * n_pattern : n_pattern;
+  P.cum[0] = 0.0;
+  for (int i = 0; i < P.m2; ++i) {
+    double d = (double)h_pattern[i % n_pattern];
+    if (!(d >= 0.0)) return PS_ERR_INVALID;
+    P.cum[i + 1] = P.cum[i] + d;
+  }
+  P.period = P.cum[P.m2];
+  P.offset = (double)offset;
+  if (!(P.period > 0.0)) return PS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = stream;
+  int64_t n_tiles = (capacity + DASH_NT - 1) / DASH_NT + 1;
+  int rc = ps_ensure_tiles(ctx, n_tiles + 1);
+  if (rc != PS_OK) return rc;
+  cudaMemsetAsync(ctx->d_tile_flag, 0, sizeof(uint32_t) * (n_tiles + 1), st);
+  cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
+  int grid = ps_persistent_grid(ctx, (const void*)k_dash, DASH_NT, 0);
+  ProfScope ps_(ctx, PK_DASH, st);
+  k_dash<<<grid, DASH_NT, 0, st>>>(reinterpret_cast<const float4*>(d_rib), d_s, d_tag, d_n_rib,
+                                    capacity, P, reinterpret_cast<float4*>(d_out_rib), d_out_s,
+                                    d_out_tag, d_out_src, d_n_out, out_capacity, ctx->d_tile_flag,
+                                    ctx->d_tile_agg, ctx->d_tile_incl, ctx->d_counters,
+                                    ctx->d_status);
+  return ps_cuda_check(cudaGetLastError());
+}

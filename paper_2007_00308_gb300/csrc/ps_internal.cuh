@@ -1,0 +1,225 @@
+// Internal declarations of the GB300 polar stroking library.
+//
+// Device-side geometry is FP32; FP64 appears only in the predicated islands of
+// the PS_PREC_MIXED variant (GB300 issues FP64 FMAs ~57x slower than FP32).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/polarstroke.h"
+
+#define PS_PI_F 3.14159265358979323846f
+#define PS_TWO_PI_F 6.28318530717958647692f
+#define PS_PI_D 3.14159265358979323846
+#define PS_TWO_PI_D 6.28318530717958647692
+
+// Bounded spin for inter-CTA waits: after this many polls a wait gives up,
+// records PS_ERR_TIMEOUT and proceeds (results of that launch are invalid).
+#define PS_SPIN_LIMIT (1 << 22)
+
+// Link kinds stored in LinkRec::meta bits 0-1.
+enum { LK_EMPTY = 0, LK_SEG = 1, LK_JOIN = 2, LK_CAP = 3 };
+
+// Per-link interval record written by the setup pass and read by the rib pass.
+// 160 bytes; at most 6 intervals (3 curvature-monotone intervals of a cubic,
+// each split once at pi -- Sec. 3.3.5), boundaries k = 0..M.
+struct __align__(16) LinkRec {
+  float2 P[4];        // control points (segment) / P[0] = pivot point (join, cap)
+  float w;            // conic weight
+  float rN, rP;       // radii of the N and P sides (Eq. 16-17)
+  uint32_t meta;      // kind | type<<2 | M<<4 | pivot mask<<8 | style<<16 | flags<<20
+  float psi[7];       // Psi_k at interval boundaries (Eq. 5)
+  float p[7];         // p_k (Eq. 4)
+  float step[6];      // delta_k / Delta_k (Eq. 12, psi(j) of Sec. 4.2.1)
+  uint16_t dsum[7];   // Delta_Sigma(k) (Eq. 13)
+  uint16_t pad;
+  float2 v1, v2;      // miter override vertices for ribs 1 and 2
+};
+static_assert(sizeof(LinkRec) == 160, "LinkRec layout");
+
+#define META_KIND(m) ((m) & 3u)
+#define META_TYPE(m) (((m) >> 2) & 3u)
+#define META_M(m) (((m) >> 4) & 15u)
+#define META_PIVOT(m, k) (((m) >> (8 + (k))) & 1u)
+#define META_STYLE(m) (((m) >> 16) & 15u)
+#define META_FLAG_OVERRIDE (1u << 20)  // ribs 1,2 outer vertex = v1, v2 (miter)
+#define META_FLAG_SQUARE (1u << 21)    // square cap: ribs 1,3 outer radius * sqrt(2)
+
+// Profiling slots (one per kernel).
+enum {
+  PK_LINK_PATH = 0, PK_LINK_SETUP, PK_EMIT, PK_ARCLEN, PK_MIDCHORD, PK_BIN_COUNT, PK_TILE_SCAN,
+  PK_BIN_SCATTER, PK_COVERAGE, PK_DASH, PK_COUNT
+};
+static_assert(PK_COUNT == PS_PROF_SLOTS, "profile slots");
+
+// Host-side context.
+struct ps_context {
+  int prof_on;
+  cudaEvent_t prof_ev[PK_COUNT][2];
+  int prof_recorded[PK_COUNT];
+  int device;
+  void* last_stream;
+  int32_t* d_status;        // first error recorded by a kernel
+  // scan tile states (shared by the passes of one call; calls on one context
+  // are serialized on the stream they are issued to)
+  uint32_t* d_tile_flag;
+  long long* d_tile_agg;
+  long long* d_tile_incl;
+  double* d_tile_aggd;
+  double* d_tile_incld;
+  int64_t tile_cap;
+  int32_t* d_counters;      // ticket counters, 16 ints
+  LinkRec* d_recs;
+  int64_t rec_cap;
+  // raster workspace
+  int32_t* d_tile_count;    // [n_tile + 1]
+  int32_t* d_tile_off;      // [n_tile + 1]
+  int32_t* d_tile_cursor;   // [n_tile]
+  int64_t raster_tile_cap;
+  uint32_t* d_bin;          // [pair_cap]
+  int64_t pair_cap;
+  int64_t* d_scratch64;     // 16 int64 of per-call scalars
+  int64_t last_n_tile;      // tiles of the most recent raster call
+  uint32_t* d_mask_scratch; // per-CTA per-path tile masks beyond shared memory
+  size_t d_scratch_words;
+  int num_sms;
+};
+
+// ---- status -----------------------------------------------------------------
+__device__ __forceinline__ void ps_record_error(int32_t* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ---- release / acquire ------------------------------------------------------
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_s64(long long* p, long long v) {
+  asm volatile("st.relaxed.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ long long ld_relaxed_s64(const long long* p) {
+  long long v;
+  asm volatile("ld.relaxed.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ double ld_relaxed_f64(const double* p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Tile flags of the single-pass scans (decoupled look-back, Merrill & Garland
+// 2016): 0 = not ready, 1 = aggregate published, 2 = inclusive prefix published.
+// Bit 2 marks a segment head (segmented scans).
+#define TF_AGG 1u
+#define TF_INCL 2u
+#define TF_HEAD 4u
+
+// Exclusive prefix of tile `t` for an int64 sum.  Called by one thread.
+__device__ __forceinline__ long long lookback_sum(uint32_t* flag, long long* agg, long long* incl,
+                                                  long long tile_agg, int64_t t, int32_t* status) {
+  if (t == 0) {
+    st_relaxed_s64(&incl[0], tile_agg);
+    st_release_u32(&flag[0], TF_INCL);
+    return 0;
+  }
+  st_relaxed_s64(&agg[t], tile_agg);
+  st_release_u32(&flag[t], TF_AGG);
+  long long prefix = 0;
+  int64_t i = t - 1;
+  int spins = 0;
+  while (i >= 0) {
+    uint32_t f = ld_acquire_u32(&flag[i]);
+    if (f & TF_INCL) {
+      prefix += ld_relaxed_s64(&incl[i]);
+      break;
+    }
+    if (f & TF_AGG) {
+      prefix += ld_relaxed_s64(&agg[i]);
+      --i;
+      continue;
+    }
+    if (++spins > PS_SPIN_LIMIT) {
+      ps_record_error(status, PS_ERR_TIMEOUT);
+      break;
+    }
+    __nanosleep(64);
+  }
+  st_relaxed_s64(&incl[t], prefix + tile_agg);
+  st_release_u32(&flag[t], TF_INCL);
+  return prefix;
+}
+
+// Segmented (by head flags) double sum: returns the carry into tile t, i.e. the
+// sum of the elements since the last head before the tile (needed by the tile's
+// elements that precede its own first head).  A tile with a head publishes its
+// inclusive value at once, since that value does not depend on the carry.
+__device__ __forceinline__ double lookback_segsum(uint32_t* flag, double* agg, double* incl,
+                                                  double tile_agg, bool tile_head, int64_t t,
+                                                  int32_t* status) {
+  uint32_t hb = tile_head ? TF_HEAD : 0u;
+  if (t == 0) {
+    st_relaxed_f64(&incl[0], tile_agg);
+    st_release_u32(&flag[0], TF_INCL | hb);
+    return 0.0;
+  }
+  if (tile_head) {
+    st_relaxed_f64(&incl[t], tile_agg);
+    st_release_u32(&flag[t], TF_INCL | hb);
+  } else {
+    st_relaxed_f64(&agg[t], tile_agg);
+    st_release_u32(&flag[t], TF_AGG);
+  }
+  double carry = 0.0;
+  int64_t i = t - 1;
+  int spins = 0;
+  while (i >= 0) {
+    uint32_t f = ld_acquire_u32(&flag[i]);
+    if (f & TF_INCL) {
+      carry += ld_relaxed_f64(&incl[i]);
+      break;
+    }
+    if (f & TF_AGG) {
+      carry += ld_relaxed_f64(&agg[i]);
+      if (f & TF_HEAD) break;
+      --i;
+      continue;
+    }
+    if (++spins > PS_SPIN_LIMIT) {
+      ps_record_error(status, PS_ERR_TIMEOUT);
+      break;
+    }
+    __nanosleep(64);
+  }
+  if (!tile_head) {
+    st_relaxed_f64(&incl[t], carry + tile_agg);
+    st_release_u32(&flag[t], TF_INCL);
+  }
+  return carry;
+}
+
+// ---- host helpers -------------------------------------------------------------
+int ps_ensure_tiles(ps_context* ctx, int64_t n_tile);
+int ps_ensure_recs(ps_context* ctx, int64_t n_link);
+int ps_ensure_raster(ps_context* ctx, int64_t n_tile, int64_t n_pair);
+int ps_cuda_check(cudaError_t e);
+int ps_persistent_grid(ps_context* ctx, const void* kernel, int block, size_t smem);
+void ps_prof_mark(ps_context* ctx, int slot, int end, cudaStream_t st);
+struct ProfScope {
+  ps_context* c;
+  int slot;
+  cudaStream_t st;
+  ProfScope(ps_context* c_, int s_, cudaStream_t st_) : c(c_), slot(s_), st(st_) {
+    ps_prof_mark(c, slot, 0, st);
+  }
+  ~ProfScope() { ps_prof_mark(c, slot, 1, st); }
+};

@@ -1,0 +1,1214 @@
+// Tessellation hot path: per-link intervals and step counts, single-pass rib
+// offsets, the rib emitter (t(psi) solve, Eq. 11; ribs, Eq. 14-17) and the
+// segmented arc-length scan (Eq. 18).
+#include <cuda_runtime.h>
+
+#include "ps_geom.cuh"
+#include "ps_internal.cuh"
+
+namespace ps {
+
+// ---------------------------------------------------------------------------
+// quadratic roots of a + b t + c t^2 (constant term first), cancellation-free
+template <typename R>
+__device__ __forceinline__ int quad_roots(R a, R b, R c, R disc, R scale, R tol, R* r) {
+  if (c == R(0)) {
+    if (b == R(0)) return 0;
+    r[0] = -a / b;
+    return 1;
+  }
+  if (disc < R(0)) {
+    if (-disc > tol * scale) return 0;
+    disc = R(0);
+  }
+  R sq = sqrt(disc);
+  R q = R(-0.5) * (b + (b >= R(0) ? sq : -sq));
+  if (q != R(0)) {
+    r[0] = q / c;
+    r[1] = a / q;
+  } else {
+    r[0] = R(0);
+    r[1] = R(0);
+  }
+  if (r[0] > r[1]) {
+    R s = r[0];
+    r[0] = r[1];
+    r[1] = s;
+  }
+  return 2;
+}
+
+// f(t) = H(t) . N as a power-form quadratic a + b t + c t^2 (Eq. 11; the conic's
+// positive denominator is dropped, Sec. 3.4).
+template <typename R, typename V>
+__device__ __forceinline__ void solve_coeffs(const Seg& g, V N, R& a, R& b, R& c) {
+  R Ax = g.A.x, Ay = g.A.y, Bx = g.B.x, By = g.B.y, Cx = g.C.x, Cy = g.C.y, Dx = g.D.x, Dy = g.D.y;
+  switch (g.type) {
+    case PS_CUBIC: {
+      R al = (Bx - Ax) * N.x + (By - Ay) * N.y;
+      R be = (Cx - Bx) * N.x + (Cy - By) * N.y;
+      R ga = (Dx - Cx) * N.x + (Dy - Cy) * N.y;
+      a = al;
+      b = R(2) * (be - al);
+      c = al - R(2) * be + ga;
+      break;
+    }
+    case PS_QUAD: {
+      R al = (Bx - Ax) * N.x + (By - Ay) * N.y;
+      R be = (Dx - Bx) * N.x + (Dy - By) * N.y;
+      a = al;
+      b = be - al;
+      c = R(0);
+      break;
+    }
+    default: {  // conic
+      R w = g.w;
+      R al = w * ((Bx - Ax) * N.x + (By - Ay) * N.y);
+      R be = (Dx - Ax) * N.x + (Dy - Ay) * N.y;
+      R ga = w * ((Dx - Bx) * N.x + (Dy - By) * N.y);
+      a = al;
+      b = be - R(2) * al;
+      c = al - be + ga;
+    }
+  }
+}
+
+// t(psi) in [pa, pb] (Sec. 3.4): roots of H(t).N(psi) = 0 inside the range (with a
+// small slack), the one whose tangent points along psi (largest H.T(psi)), else
+// the endpoint with the smaller |H.N|.  MIXED redoes near-double roots in FP64.
+template <bool MIXED>
+__device__ float solve_t(const Seg& g, float psi, float pa, float pb) {
+  if (g.type == PS_LINE) return pa;
+  float sn, cs;
+  sincosf(psi, &sn, &cs);
+  float2 N = mk(-sn, cs), T = mk(cs, sn);
+  float a, b, c;
+  solve_coeffs<float>(g, N, a, b, c);
+  float disc = b * b - 4.f * a * c, scale = b * b + fabsf(4.f * a * c);
+  if (MIXED && c != 0.f && fabsf(disc) < 1e-3f * scale) {
+    double sd, cd;
+    sincos((double)psi, &sd, &cd);
+    D2 Nd{-sd, cd};
+    double ad, bd, cd2;
+    solve_coeffs<double>(g, Nd, ad, bd, cd2);
+    double discd = bd * bd - 4.0 * ad * cd2, scaled = bd * bd + fabs(4.0 * ad * cd2);
+    double r[2];
+    int n = quad_roots<double>(ad, bd, cd2, discd, scaled, 1e-12, r);
+    double best = 0.0, bestv = -1e300;
+    bool found = false;
+    for (int i = 0; i < n; ++i) {
+      double t = r[i];
+      if (!(t >= (double)pa - 1e-9 && t <= (double)pb + 1e-9)) continue;
+      t = fmin(fmax(t, (double)pa), (double)pb);
+      D2 H = hodo_d64(g, t);
+      double v = H.x * cd + H.y * sd;
+      if (!found || v > bestv) {
+        bestv = v;
+        best = t;
+        found = true;
+      }
+    }
+    if (found) return (float)best;
+  }
+  float r[2];
+  int n = quad_roots<float>(a, b, c, disc, scale, 1e-5f, r);
+  float best = 0.f, bestv = -3.0e38f;
+  bool found = false;
+  for (int i = 0; i < n; ++i) {
+    float t = r[i];
+    if (!(t >= pa - 1e-5f && t <= pb + 1e-5f)) continue;
+    t = fminf(fmaxf(t, pa), pb);
+    float v = dot2(hodo(g, t), T);
+    if (!found || v > bestv) {
+      bestv = v;
+      best = t;
+      found = true;
+    }
+  }
+  if (found) return best;
+  float fa = fabsf(dot2(hodo(g, pa), N)), fb = fabsf(dot2(hodo(g, pb), N));
+  return fa < fb ? pa : pb;
+}
+
+// ---------------------------------------------------------------------------
+// Curvature-sign polynomial C(t) ~ g'(t) x g''(t) in power form c0 + c1 t + c2 t^2.
+template <typename R>
+struct CrossPoly {
+  R c0, c1, c2, disc, scale;
+  bool flat;
+  __device__ R eval(R t) const { return c0 + t * (c1 + t * c2); }
+};
+
+template <typename R>
+__device__ CrossPoly<R> cross_poly(const Seg& g) {
+  CrossPoly<R> P;
+  P.c0 = P.c1 = P.c2 = P.disc = P.scale = R(0);
+  P.flat = true;
+  R Ax = g.A.x, Ay = g.A.y, Bx = g.B.x, By = g.B.y, Cx = g.C.x, Cy = g.C.y, Dx = g.D.x, Dy = g.D.y;
+  switch (g.type) {
+    case PS_CUBIC: {
+      R d1x = Bx - Ax, d1y = By - Ay, d2x = Cx - Bx, d2y = Cy - By, d3x = Dx - Cx, d3y = Dy - Cy;
+      R X12 = d1x * d2y - d1y * d2x, X13 = d1x * d3y - d1y * d3x, X23 = d2x * d3y - d2y * d3x;
+      P.c0 = X12;
+      P.c1 = X13 - R(2) * X12;
+      P.c2 = X12 - X13 + X23;
+      // discriminant X13^2 - 4 X12 X23 with error-free products: an exact cusp
+      // (double root) gives exactly zero
+      R h1 = X13 * X13, l1 = fma(X13, X13, -h1);
+      R h2 = (R(4) * X12) * X23, l2 = fma(R(4) * X12, X23, -h2);
+      P.disc = (h1 - h2) + (l1 - l2);
+      P.scale = fabs(h1) + fabs(h2);
+      P.flat = (X12 == R(0) && X13 == R(0) && X23 == R(0));
+      break;
+    }
+    case PS_QUAD: {
+      R K = (Bx - Ax) * (Dy - By) - (By - Ay) * (Dx - Bx);
+      P.c0 = K;
+      P.flat = (K == R(0));
+      break;
+    }
+    case PS_CONIC: {
+      R K = (Bx - Ax) * (Dy - By) - (By - Ay) * (Dx - Bx);
+      R w = g.w, wK = w * K;
+      P.c0 = wK;
+      P.c1 = wK * (R(2) * w - R(2));
+      P.c2 = wK * (R(2) - R(2) * w);
+      P.disc = P.c1 * P.c1 - R(4) * P.c0 * P.c2;
+      P.scale = P.c1 * P.c1 + fabs(R(4) * P.c0 * P.c2);
+      P.flat = (wK == R(0));
+      break;
+    }
+    default:
+      break;
+  }
+  return P;
+}
+
+__device__ __forceinline__ float wrap2pi(float x) {
+  if (x < 0.f) x += PS_TWO_PI_F;
+  if (x >= PS_TWO_PI_F) x -= PS_TWO_PI_F;
+  return x;
+}
+
+// Steps for a turning of magnitude ad (Eq. 12).  q is a nominal step: a ratio
+// exceeding an integer n by less than STEP_SNAP steps takes n steps, so turnings
+// that q divides exactly (caps, 90-degree arcs) do not hinge on q's last bit.
+#define STEP_SNAP 1e-4f
+__device__ __forceinline__ int ceil_steps(float ad, float q) {
+  if (ad == 0.f) return 0;
+  int D = (int)ceilf(ad / q - STEP_SNAP);
+  return D < 1 ? 1 : D;
+}
+__device__ __forceinline__ int ceil_steps_d(double ad, double q) {
+  if (ad == 0.0) return 0;
+  int D = (int)ceil(ad / q - 1e-4);
+  return D < 1 ? 1 : D;
+}
+// MIXED: re-evaluate a step count in FP64 when its FP32 argument is within
+// rounding of the boundary
+__device__ __forceinline__ bool near_integer(float x) {
+  x -= STEP_SNAP;
+  float f = x - floorf(x);
+  return fminf(f, 1.f - f) < 4e-5f * fmaxf(1.f, x);
+}
+
+// Reversals of a segment with collinear control points: along the common
+// direction v, H(t).v is the Bernstein quadratic lam1 u^2 + 2 lam2 u t + lam3 t^2
+// (linear lam1 u + lam3 t for the quadratic Bezier).  The direction reverses at
+// its simple roots inside (0,1): two when lam2^2 - lam1 lam3 > 0 (sign taken with
+// error-free products), none otherwise (a double root is a kink); roots at the
+// ends (lam1 = 0, lam3 = 0) are factored out exactly.
+template <typename R>
+__device__ int collinear_reversals(const Seg& g, float* rts) {
+  float2 vf = end_grad0(g);
+  R vx = vf.x, vy = vf.y;
+  R Ax = g.A.x, Ay = g.A.y, Bx = g.B.x, By = g.B.y, Cx = g.C.x, Cy = g.C.y, Dx = g.D.x, Dy = g.D.y;
+  R l1, l2, l3;
+  switch (g.type) {
+    case PS_CUBIC:
+      l1 = (Bx - Ax) * vx + (By - Ay) * vy;
+      l2 = (Cx - Bx) * vx + (Cy - By) * vy;
+      l3 = (Dx - Cx) * vx + (Dy - Cy) * vy;
+      break;
+    case PS_QUAD: {
+      R a1 = (Bx - Ax) * vx + (By - Ay) * vy, a3 = (Dx - Bx) * vx + (Dy - By) * vy;
+      if ((a1 > R(0) && a3 < R(0)) || (a1 < R(0) && a3 > R(0))) {
+        rts[0] = (float)(a1 / (a1 - a3));
+        return 1;
+      }
+      return 0;
+    }
+    case PS_CONIC: {
+      R w = g.w;
+      if (w == R(0)) return 0;
+      l1 = w * ((Bx - Ax) * vx + (By - Ay) * vy);
+      l2 = R(0.5) * ((Dx - Ax) * vx + (Dy - Ay) * vy);
+      l3 = w * ((Dx - Bx) * vx + (Dy - By) * vy);
+      break;
+    }
+    default:
+      return 0;
+  }
+  int n = 0;
+  if (l1 == R(0) && l3 == R(0)) return 0;
+  if (l1 == R(0)) {
+    R den = R(2) * l2 - l3;
+    if (den != R(0)) {
+      R r = R(2) * l2 / den;
+      if (r > R(0) && r < R(1)) rts[n++] = (float)r;
+    }
+    return n;
+  }
+  if (l3 == R(0)) {
+    R den = l1 - R(2) * l2;
+    if (den != R(0)) {
+      R r = l1 / den;
+      if (r > R(0) && r < R(1)) rts[n++] = (float)r;
+    }
+    return n;
+  }
+  R h1 = l2 * l2, e1 = fma(l2, l2, -h1);
+  R h2 = l1 * l3, e2 = fma(l1, l3, -h2);
+  R disc = (h1 - h2) + (e1 - e2);
+  if (!(disc > R(0))) return 0;
+  R a = l1, b = R(2) * (l2 - l1), c = l1 - R(2) * l2 + l3, r[2];
+  int m = quad_roots<R>(a, b, c, R(4) * disc, R(1), R(0), r);
+  for (int i = 0; i < m; ++i)
+    if (r[i] > R(0) && r[i] < R(1)) rts[n++] = (float)r[i];
+  if (n == 2 && rts[0] > rts[1]) {
+    float t = rts[0];
+    rts[0] = rts[1];
+    rts[1] = t;
+  }
+  return n;
+}
+
+// Interval table of a segment link (Sec. 3.3.4-3.3.6, Eq. 4-6, 12-13).
+// Returns N (total steps) or -1 if the table does not fit.
+template <bool MIXED>
+__device__ int seg_intervals(const Seg& g, float q, LinkRec& L) {
+  float Psi0 = angf(end_grad0(g)), Psin = angf(end_grad1(g));
+  CrossPoly<float> Pf;
+  CrossPoly<double> Pd;
+  bool flat;
+  if (MIXED) {
+    Pd = cross_poly<double>(g);
+    flat = Pd.flat;
+  } else {
+    Pf = cross_poly<float>(g);
+    flat = Pf.flat;
+  }
+  int M = 0;
+  uint32_t pivots = 0;
+  if (flat) {
+    // zero curvature: flat pieces with +pi pivots where H reverses (collinear
+    // control points with back-tracking); one quad per flat piece
+    float rts[2];
+    int nr = MIXED ? collinear_reversals<double>(g, rts) : collinear_reversals<float>(g, rts);
+    float psi = Psi0, pp = 0.f;
+    for (int i = 0; i <= nr; ++i) {
+      float pe = (i < nr) ? rts[i] : 1.f;
+      L.p[M] = pp;
+      L.psi[M] = psi;
+      L.step[M] = 0.f;  // flat: Delta = 1, no interior ribs
+      L.dsum[M + 1] = 0;
+      M++;
+      if (i < nr) {
+        L.p[M] = pe;
+        L.psi[M] = psi;
+        pivots |= 1u << M;
+        L.step[M] = PS_PI_F;  // overwritten below with pi / Delta
+        M++;
+        psi = psi + PS_PI_F;
+      }
+      pp = pe;
+    }
+    L.p[M] = 1.f;
+    L.psi[M] = psi;
+    int N = 0;
+    L.dsum[0] = 0;
+    for (int k = 0; k < M; ++k) {
+      int D;
+      if ((pivots >> k) & 1u) {
+        D = ceil_steps(PS_PI_F, q);
+        L.step[k] = PS_PI_F / (float)D;
+      } else {
+        D = 1;
+        L.step[k] = 0.f;
+      }
+      N += D;
+      L.dsum[k + 1] = (uint16_t)N;
+    }
+    L.meta |= ((uint32_t)M << 4) | (pivots << 8);
+    return N;
+  }
+
+  // Eq. 4: curvature-sign changes strictly inside (0,1)
+  float roots[2];
+  int nroot = 0;
+  if (MIXED) {
+    if (Pd.c1 != 0.0 || Pd.c2 != 0.0) {
+      double r[2];
+      int n = quad_roots<double>(Pd.c0, Pd.c1, Pd.c2, Pd.disc, Pd.scale, 0.0, r);
+      if (n == 2 && Pd.disc <= 0.0) n = 0;
+      for (int i = 0; i < n; ++i)
+        if (r[i] > 0.0 && r[i] < 1.0 && (nroot == 0 || (float)r[i] > roots[nroot - 1]))
+          roots[nroot++] = (float)r[i];
+    }
+  } else {
+    if (Pf.c1 != 0.f || Pf.c2 != 0.f) {
+      float r[2];
+      int n = quad_roots<float>(Pf.c0, Pf.c1, Pf.c2, Pf.disc, Pf.scale, 0.f, r);
+      if (n == 2 && Pf.disc <= 0.f) n = 0;
+      for (int i = 0; i < n; ++i)
+        if (r[i] > 0.f && r[i] < 1.f && (nroot == 0 || r[i] > roots[nroot - 1]))
+          roots[nroot++] = r[i];
+    }
+  }
+  // Eq. 5
+  float p[4], Psi[4];
+  int n = 0;
+  p[n] = 0.f;
+  Psi[n] = Psi0;
+  n++;
+  for (int i = 0; i < nroot; ++i) {
+    p[n] = roots[i];
+    if (MIXED) {
+      // H near an inflection of a near-cusp cubic is a small difference of
+      // large terms: evaluate it in FP64, round the direction to FP32
+      D2 H = hodo_d64(g, (double)roots[i]);
+      Psi[n] = atan2f((float)H.y, (float)H.x);
+    } else {
+      Psi[n] = angf(hodo(g, roots[i]));
+    }
+    n++;
+  }
+  p[n] = 1.f;
+  Psi[n] = Psin;
+
+  // Eq. 6: turning of each interval in the direction of the curvature sign
+  for (int k = 0; k < n; ++k) {
+    float pa = p[k], pb = p[k + 1];
+    float sgn = 0.f;
+    float probes[3] = {0.5f * (pa + pb), 0.75f * pa + 0.25f * pb, 0.25f * pa + 0.75f * pb};
+    for (int i = 0; i < 3 && sgn == 0.f; ++i) {
+      float v = MIXED ? (float)Pd.eval((double)probes[i]) : Pf.eval(probes[i]);
+      sgn = v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f);
+    }
+    float delta = 0.f;
+    if (sgn != 0.f) {
+      delta = sgn * wrap2pi(sgn * (Psi[k + 1] - Psi[k]));
+      bool redo = false;
+      if (MIXED) {
+        float ad = fabsf(delta);
+        redo = near_integer(ad / q) || near_integer(0.5f * ad / q) ||
+               fabsf(ad - PS_PI_F) < 1e-4f || ad > PS_TWO_PI_F - 1e-4f || ad < 1e-4f;
+      }
+      if (redo) {
+        // FP64 island: end angles from FP64 gradients (exact differences of the
+        // FP32 inputs), turning and its direction in FP64
+        D2 a0, a1;
+        if (k == 0) {
+          float2 e0 = end_grad0(g);
+          a0 = D2{(double)e0.x, (double)e0.y};
+        } else {
+          a0 = hodo_d64(g, (double)p[k]);
+        }
+        if (k == n - 1) {
+          float2 e1 = end_grad1(g);
+          a1 = D2{(double)e1.x, (double)e1.y};
+        } else {
+          a1 = hodo_d64(g, (double)p[k + 1]);
+        }
+        double d = (double)sgn * (atan2(a1.y, a1.x) - atan2(a0.y, a0.x));
+        d = fmod(d, PS_TWO_PI_D);
+        if (d < 0) d += PS_TWO_PI_D;
+        if (d > PS_TWO_PI_D - 1e-9) d = 0.0;
+        double dd_ = (double)sgn * d;
+        delta = (float)dd_;
+        // store counts computed from the FP64 turning
+        double ad = fabs(dd_);
+        if (ad >= PS_PI_D) {
+          int Dh = ceil_steps_d(0.5 * ad, (double)q);
+          float psi_s = Psi[k] + 0.5f * delta;
+          float ps_ = solve_t<MIXED>(g, psi_s, pa, pb);
+          if (M + 2 > 6) return -1;
+          L.p[M] = pa; L.psi[M] = Psi[k]; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh; M++;
+          L.p[M] = ps_; L.psi[M] = psi_s; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh; M++;
+        } else {
+          int D = ad == 0.0 ? 1 : ceil_steps_d(ad, (double)q);
+          if (M + 1 > 6) return -1;
+          L.p[M] = pa; L.psi[M] = Psi[k]; L.step[M] = delta / (float)D; L.dsum[M + 1] = (uint16_t)D; M++;
+        }
+        continue;
+      }
+      if (fabsf(delta) > PS_TWO_PI_F - 1e-5f) delta = 0.f;
+    }
+    float ad = fabsf(delta);
+    if (ad >= PS_PI_F) {
+      // Sec. 3.3.5: split at half the turning, p by Eq. 11
+      float psi_s = Psi[k] + 0.5f * delta;
+      float ps_ = solve_t<MIXED>(g, psi_s, pa, pb);
+      int Dh = ceil_steps(0.5f * ad, q);
+      if (M + 2 > 6) return -1;
+      L.p[M] = pa; L.psi[M] = Psi[k]; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh; M++;
+      L.p[M] = ps_; L.psi[M] = psi_s; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh; M++;
+    } else {
+      int D = ad == 0.f ? (pb > pa ? 1 : 0) : ceil_steps(ad, q);
+      if (M + 1 > 6) return -1;
+      L.p[M] = pa; L.psi[M] = Psi[k]; L.step[M] = D ? delta / (float)D : 0.f; L.dsum[M + 1] = (uint16_t)D; M++;
+    }
+  }
+  L.p[M] = 1.f;
+  L.psi[M] = Psin;
+  // dsum[k+1] holds Delta_k so far: accumulate into Delta_Sigma
+  int N = 0;
+  L.dsum[0] = 0;
+  for (int k = 0; k < M; ++k) {
+    N += L.dsum[k + 1];
+    L.dsum[k + 1] = (uint16_t)N;
+  }
+  L.meta |= ((uint32_t)M << 4);
+  return N;
+}
+
+__device__ __forceinline__ float ominus_f(float a, float b) {
+  float d = a - b;
+  if (d > PS_PI_F) return d - PS_TWO_PI_F;
+  if (d < -PS_PI_F) return d + PS_TWO_PI_F;
+  return d;
+}
+
+// Join / cap pivot (Sec. 4.3): generator fixed at `at`, psi from Psi0 through
+// delta in J steps; the outer side is N for delta > 0, P for delta < 0 and the
+// inner radius is zero.
+template <bool MIXED>
+__device__ int pivot_setup(float2 at, float Psi0, float delta, int kind, int style, float r,
+                           float miter, float q, LinkRec& L, float2 g_in = make_float2(0.f, 0.f),
+                           float2 g_out = make_float2(0.f, 0.f)) {
+  int J = 0;
+  float ad = fabsf(delta);
+  if (kind == LK_JOIN) {
+    if (delta == 0.f) return 0;
+    switch (style) {
+      case PS_JOIN_BEVEL: J = 1; break;
+      case PS_JOIN_TRIANGLE: J = 2; break;
+      case PS_JOIN_MITER:
+      case PS_JOIN_MITER_TRUNCATE: J = 3; break;
+      case PS_JOIN_ROUND: J = ceil_steps(ad, q); break;
+      default: J = 0;
+    }
+  } else {
+    switch (style) {
+      case PS_CAP_TRIANGLE: J = 2; break;
+      case PS_CAP_SQUARE: J = 4; break;
+      case PS_CAP_ROUND: J = ceil_steps(PS_PI_F, q); break;
+      default: J = 0;
+    }
+  }
+  if (J == 0) return 0;
+  L.P[0] = at;
+  L.rN = delta > 0.f ? r : 0.f;
+  L.rP = delta > 0.f ? 0.f : r;
+  L.psi[0] = Psi0;
+  L.psi[1] = Psi0 + delta;
+  L.step[0] = delta / (float)J;
+  L.dsum[0] = 0;
+  L.dsum[1] = (uint16_t)J;
+  L.p[0] = 0.f;
+  L.p[1] = 1.f;
+  L.meta |= (1u << 4) | ((uint32_t)style << 16);
+  if (kind == LK_CAP && style == PS_CAP_SQUARE) L.meta |= META_FLAG_SQUARE;
+  if (kind == LK_JOIN && (style == PS_JOIN_MITER || style == PS_JOIN_MITER_TRUNCATE)) {
+    float sd = delta > 0.f ? -1.f : 1.f;  // outer offset = at + sd * r * n
+    float s0, c0, s1, c1, sh, ch;
+    sincosf(Psi0, &s0, &c0);
+    sincosf(Psi0 + delta, &s1, &c1);
+    sincosf(Psi0 + 0.5f * delta, &sh, &ch);
+    float2 O0 = at + mk(-s0, c0) * (sd * r);
+    float2 O3 = at + mk(-s1, c1) * (sd * r);
+    // miter ratio 1/sin(phi/2), phi = pi - |delta|; infinite at a reversal
+    float cm = cosf(0.5f * ad);
+    float ratio = cm > 0.f ? 1.f / cm : INFINITY;
+    bool accept = ratio <= miter;
+    if (MIXED && fabsf(ratio - miter) < 1e-4f * miter) {
+      // FP64 island: the miter decision sits on the limit; decide it from the
+      // turning computed in FP64 from the end gradients
+      double d = atan2((double)g_out.y, (double)g_out.x) - atan2((double)g_in.y, (double)g_in.x);
+      if (d > PS_PI_D) d -= PS_TWO_PI_D;
+      if (d < -PS_PI_D) d += PS_TWO_PI_D;
+      double cd = cos(0.5 * fabs(d));
+      accept = cd > 0.0 && 1.0 / cd <= (double)miter;
+    }
+    float2 v1, v2;
+    if (accept) {
+      float2 tip = at + mk(-sh, ch) * (sd * r * ratio);
+      v1 = tip;
+      v2 = tip;
+    } else if (style == PS_JOIN_MITER) {
+      v1 = O0;
+      v2 = O3;
+    } else {
+      float lam = (miter * r - r * cosf(0.5f * ad)) / sinf(0.5f * ad);
+      lam = fmaxf(lam, 0.f);
+      v1 = O0 + mk(c0, s0) * lam;
+      v2 = O3 - mk(c1, s1) * lam;
+    }
+    L.v1 = v1;
+    L.v2 = v2;
+    L.meta |= META_FLAG_OVERRIDE;
+  }
+  return J;
+}
+
+// Full setup of link k of path p.  Returns the number of ribs (N+1 or 0).
+template <bool MIXED>
+__device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, int32_t s0, int n,
+                          int k, float r, int join, int cap, float miter, bool closed, float q,
+                          LinkRec& L) {
+  L.meta = 0;
+  L.w = 1.f;
+  L.rN = L.rP = r;
+  int nrib = 0;
+  if (n <= 0) return 0;
+  if (k & 1) {
+    int i = (k - 1) >> 1;
+    Seg g = load_seg(st, sp, sw, s0 + i);
+    if (zero_length(g)) return 0;
+    L.P[0] = g.A; L.P[1] = g.B; L.P[2] = g.C; L.P[3] = g.D;
+    L.w = g.w;
+    L.meta = LK_SEG | ((uint32_t)g.type << 2);
+    int N = seg_intervals<MIXED>(g, q, L);
+    if (N < 0) return -1;
+    nrib = N > 0 ? N + 1 : 0;
+  } else if (k == 0 || k == 2 * n) {
+    // first / last non-degenerate segment
+    int first = -1, last = -1;
+    if (k == 0 || closed) {
+      for (int i = 0; i < n; ++i) {
+        Seg g = load_seg(st, sp, sw, s0 + i);
+        if (!zero_length(g)) { first = i; break; }
+      }
+    }
+    if (k == 2 * n) {
+      for (int i = n - 1; i >= 0; --i) {
+        Seg g = load_seg(st, sp, sw, s0 + i);
+        if (!zero_length(g)) { last = i; break; }
+      }
+    }
+    if (!closed) {
+      int i = (k == 0) ? first : last;
+      if (i < 0) return 0;
+      Seg c = load_seg(st, sp, sw, s0 + i);
+      L.meta = LK_CAP;
+      float Psi0 = (k == 0) ? angf(end_grad0(c)) + PS_PI_F : angf(end_grad1(c));
+      int J = pivot_setup<MIXED>(k == 0 ? c.A : c.D, Psi0, PS_PI_F, LK_CAP, cap, r, miter, q, L);
+      nrib = J > 0 ? J + 1 : 0;
+    } else if (k == 2 * n) {
+      if (first < 0 || last < 0) return 0;
+      Seg a = load_seg(st, sp, sw, s0 + last), b = load_seg(st, sp, sw, s0 + first);
+      L.meta = LK_JOIN;
+      float Psi0 = angf(end_grad1(a));
+      float delta = ominus_f(angf(end_grad0(b)), Psi0);
+      if (delta == -PS_PI_F) delta = PS_PI_F;
+      int J = pivot_setup<MIXED>(b.A, Psi0, delta, LK_JOIN, join, r, miter, q, L, end_grad1(a),
+                                 end_grad0(b));
+      nrib = J > 0 ? J + 1 : 0;
+    }
+  } else {
+    int i = k / 2 - 1;
+    Seg b = load_seg(st, sp, sw, s0 + i + 1);
+    if (zero_length(b)) return 0;
+    int inc = -1;
+    for (int m = i; m >= 0; --m) {
+      Seg a = load_seg(st, sp, sw, s0 + m);
+      if (!zero_length(a)) { inc = m; break; }
+    }
+    if (inc < 0) return 0;
+    Seg a = load_seg(st, sp, sw, s0 + inc);
+    L.meta = LK_JOIN;
+    float Psi0 = angf(end_grad1(a));
+    float delta = ominus_f(angf(end_grad0(b)), Psi0);
+    if (delta == -PS_PI_F) delta = PS_PI_F;
+    if (MIXED && join == PS_JOIN_ROUND && delta != 0.f && near_integer(fabsf(delta) / q)) {
+      float2 e1 = end_grad1(a), e0 = end_grad0(b);
+      double d = atan2((double)e0.y, (double)e0.x) - atan2((double)e1.y, (double)e1.x);
+      if (d > PS_PI_D) d -= PS_TWO_PI_D;
+      if (d < -PS_PI_D) d += PS_TWO_PI_D;
+      int J = ceil_steps_d(fabs(d), (double)q);
+      int J0 = pivot_setup<MIXED>(b.A, Psi0, delta, LK_JOIN, join, r, miter, q, L, e1, e0);
+      if (J0 > 0 && J > 0 && J != J0) {
+        L.step[0] = delta / (float)J;
+        L.dsum[1] = (uint16_t)J;
+      }
+      nrib = J0 > 0 ? (J > 0 ? J : J0) + 1 : 0;
+    } else {
+      int J = pivot_setup<MIXED>(b.A, Psi0, delta, LK_JOIN, join, r, miter, q, L, end_grad1(a),
+                                 end_grad0(b));
+      nrib = J > 0 ? J + 1 : 0;
+    }
+  }
+  if (nrib == 0) L.meta = 0;
+  return nrib;
+}
+
+// Path of link l: the p with lbase(p) <= l < lbase(p+1), lbase(p) = 2 seg_off[p] + p.
+__device__ __forceinline__ int find_path(const int32_t* seg_off, int n_path, int64_t l) {
+  int lo = 0, hi = n_path;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    int64_t lb = 2 * (int64_t)__ldg(seg_off + mid) + mid;
+    if (lb <= l) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---- block scans (256 threads) ---------------------------------------------------
+template <int NT>
+__device__ __forceinline__ long long block_excl_sum(long long v, long long& total, long long* sm) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sm[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    long long w = lane < NT / 32 ? sm[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < NT / 32) sm[lane] = w;
+  }
+  __syncthreads();
+  total = sm[NT / 32 - 1];
+  long long excl = x - v + (wid > 0 ? sm[wid - 1] : 0);
+  __syncthreads();
+  return excl;
+}
+
+// ---------------------------------------------------------------------------
+// K1: link setup + rib counts + single-pass exclusive scan into link offsets.
+constexpr int SETUP_NT = 256;
+constexpr int SETUP_IPT = 2;
+constexpr int SETUP_TILE = SETUP_NT * SETUP_IPT;
+
+template <bool MIXED>
+__global__ void __launch_bounds__(SETUP_NT) k_link_setup(
+    const uint8_t* __restrict__ st, const float* __restrict__ sp, const float* __restrict__ sw,
+    const int32_t* __restrict__ seg_off, const float* __restrict__ width,
+    const uint8_t* __restrict__ join, const uint8_t* __restrict__ cap,
+    const float* __restrict__ miter, const uint8_t* __restrict__ closed, int n_path,
+    int64_t n_link, float q, LinkRec* __restrict__ recs, int32_t* __restrict__ link_off,
+    int32_t* __restrict__ path_off, int64_t* __restrict__ n_rib_out, int64_t capacity,
+    uint32_t* tflag, long long* tagg, long long* tincl, int32_t* counters, int32_t* status,
+    int64_t n_tiles) {
+  __shared__ long long sm[SETUP_NT / 32 + 1];
+  __shared__ long long s_prefix;
+  __shared__ int s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&counters[0], 1);
+  __syncthreads();
+  int64_t tile = s_tile;
+  if (tile >= n_tiles) return;
+  int cnt[SETUP_IPT];
+  int pth[SETUP_IPT];
+  int kk[SETUP_IPT];
+  long long local = 0;
+  for (int i = 0; i < SETUP_IPT; ++i) {
+    int64_t l = tile * SETUP_TILE + (int64_t)threadIdx.x * SETUP_IPT + i;
+    cnt[i] = 0;
+    pth[i] = -1;
+    kk[i] = -1;
+    if (l < n_link) {
+      int p = find_path(seg_off, n_path, l);
+      int32_t s0 = __ldg(seg_off + p), s1 = __ldg(seg_off + p + 1);
+      int k = (int)(l - (2 * (int64_t)s0 + p));
+      LinkRec L = {};
+      int nr = link_setup<MIXED>(st, sp, sw, s0, s1 - s0, k, 0.5f * __ldg(width + p), join[p],
+                                 cap[p], __ldg(miter + p), closed[p] != 0, q, L);
+      if (nr < 0) {
+        ps_record_error(status, PS_ERR_INVALID);
+        nr = 0;
+        L.meta = 0;
+      }
+      L.pad = 0;
+      recs[l] = L;
+      cnt[i] = nr;
+      pth[i] = p;
+      kk[i] = k;
+      local += nr;
+    }
+  }
+  long long total;
+  long long excl = block_excl_sum<SETUP_NT>(local, total, sm);
+  if (threadIdx.x == 0) s_prefix = lookback_sum(tflag, tagg, tincl, total, tile, status);
+  __syncthreads();
+  long long off = s_prefix + excl;
+  for (int i = 0; i < SETUP_IPT; ++i) {
+    int64_t l = tile * SETUP_TILE + (int64_t)threadIdx.x * SETUP_IPT + i;
+    if (l < n_link) {
+      if (off > 0x7fffffffLL) ps_record_error(status, PS_ERR_CAPACITY);
+      link_off[l] = (int32_t)off;
+      if (kk[i] == 0) path_off[pth[i]] = (int32_t)off;
+      off += cnt[i];
+      if (l == n_link - 1) {
+        link_off[n_link] = (int32_t)off;
+        path_off[n_path] = (int32_t)off;
+        *n_rib_out = off;
+        if (off > capacity) ps_record_error(status, PS_ERR_CAPACITY);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: ribs.  A CTA takes tiles of EMIT_TILE consecutive ribs; each thread finds
+// its rib's link by binary search over the tile's link range, evaluates psi(j),
+// t(j), g(t(j)) and n(j), and writes the rib, its tag and the chord to the
+// previous rib of the same link.
+constexpr int EMIT_NT = 256;
+constexpr int EMIT_K = 4;
+constexpr int EMIT_TILE = EMIT_NT * EMIT_K;
+
+struct RibEval {
+  float4 v;      // N.x N.y P.x P.y
+  float2 grel;   // g(t) - A (segments) for the chord
+  float t;
+  bool seg;
+};
+
+template <bool MIXED>
+__device__ __forceinline__ RibEval eval_rib(const LinkRec& L, int j) {
+  RibEval R;
+  uint32_t meta = L.meta;
+  int kind = META_KIND(meta);
+  int M = META_M(meta);
+  if (kind == LK_SEG) {
+    Seg g;
+    g.type = META_TYPE(meta);
+    g.A = L.P[0]; g.B = L.P[1]; g.C = L.P[2]; g.D = L.P[3];
+    g.w = L.w;
+    int k = 0;
+    while (k < M && j >= (int)L.dsum[k + 1]) ++k;
+    // k == M only for j == N; boundary when j == dsum[k]
+    float t, psi;
+    if (j == (int)L.dsum[k]) {
+      t = L.p[k];
+      psi = L.psi[k];
+    } else {
+      psi = L.psi[k] + L.step[k] * (float)(j - (int)L.dsum[k]);
+      if (META_PIVOT(meta, k)) t = L.p[k];
+      else t = solve_t<MIXED>(g, psi, L.p[k], L.p[k + 1]);
+    }
+    float sn, cs;
+    sincosf(psi, &sn, &cs);
+    float2 n = mk(-sn, cs);
+    float2 gr = MIXED ? g_rel_comp(g, t) : g_rel(g, t);
+    float2 Nv = gr - n * L.rN, Pv = gr + n * L.rP;
+    R.v = make_float4(g.A.x + Nv.x, g.A.y + Nv.y, g.A.x + Pv.x, g.A.y + Pv.y);
+    R.grel = gr;
+    R.t = t;
+    R.seg = true;
+  } else {
+    int J = (int)L.dsum[1];
+    float psi = (j == J) ? L.psi[1] : L.psi[0] + L.step[0] * (float)j;
+    float sn, cs;
+    sincosf(psi, &sn, &cs);
+    float2 n = mk(-sn, cs);
+    float rn = L.rN, rp = L.rP;
+    if ((meta & META_FLAG_SQUARE) && (j == 1 || j == 3)) {
+      rn *= 1.41421356237309515f;
+      rp *= 1.41421356237309515f;
+    }
+    float2 at = L.P[0];
+    float2 Nv = at - n * rn, Pv = at + n * rp;
+    if ((meta & META_FLAG_OVERRIDE) && (j == 1 || j == 2)) {
+      float2 v = j == 1 ? L.v1 : L.v2;
+      if (L.rN > 0.f) Nv = v; else Pv = v;
+    }
+    R.v = make_float4(Nv.x, Nv.y, Pv.x, Pv.y);
+    R.grel = mk(0.f, 0.f);
+    R.t = 0.f;
+    R.seg = false;
+  }
+  return R;
+}
+
+__device__ __forceinline__ int64_t find_link(const int32_t* off, int64_t lo, int64_t hi, int64_t r) {
+  // last l in [lo, hi] with off[l] <= r  (off non-decreasing)
+  while (hi > lo) {
+    int64_t mid = (lo + hi + 1) >> 1;
+    if ((int64_t)__ldg(off + mid) <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(EMIT_NT) k_emit(
+    const LinkRec* __restrict__ recs, const int32_t* __restrict__ link_off,
+    const int32_t* __restrict__ link_path, int64_t n_link, const int64_t* __restrict__ n_rib,
+    int64_t capacity, float4* __restrict__ rib, uint32_t* __restrict__ tag,
+    float* __restrict__ chord, float* __restrict__ tout) {
+  __shared__ int64_t s_l0, s_l1;
+  __shared__ float2 s_g[EMIT_NT];
+  __shared__ int64_t s_lk[EMIT_NT];
+  __shared__ float s_t[EMIT_NT];
+  int64_t R = *n_rib;
+  if (R > capacity) R = capacity;
+  int64_t n_tiles = (R + EMIT_TILE - 1) / EMIT_TILE;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    int64_t r0 = tile * EMIT_TILE;
+    int64_t r1 = r0 + EMIT_TILE;
+    if (r1 > R) r1 = R;
+    if (threadIdx.x == 0) {
+      s_l0 = find_link(link_off, 0, n_link - 1, r0);
+      s_l1 = find_link(link_off, 0, n_link - 1, r1 - 1);
+    }
+    __syncthreads();
+    int64_t l0 = s_l0, l1 = s_l1;
+    float2 prev_g = mk(0.f, 0.f);
+    int64_t prev_l = -1;
+    float prev_t = 0.f;
+    for (int kslab = 0; kslab < EMIT_K; ++kslab) {
+      int64_t r = r0 + (int64_t)kslab * EMIT_NT + threadIdx.x;
+      bool active = r < r1;
+      int64_t l = -1;
+      RibEval E;
+      E.grel = mk(0.f, 0.f);
+      E.t = 0.f;
+      E.seg = false;
+      int j = 0;
+      if (active) {
+        l = find_link(link_off, l0, l1, r);
+        j = (int)(r - __ldg(link_off + l));
+        LinkRec L = recs[l];
+        E = eval_rib<MIXED>(L, j);
+        rib[r] = E.v;
+        uint32_t p = (uint32_t)__ldg(link_path + l);
+        tag[r] = (p << 2) | (E.seg ? PS_TAG_SEGMENT : 0u) | (j == 0 ? PS_TAG_LINK_START : 0u);
+        if (tout) tout[r] = E.t;
+      }
+      if (chord) {
+        // previous rib's centreline point: neighbour in this slab, the last
+        // thread of the previous slab, or (first rib of the tile) recomputed
+        s_g[threadIdx.x] = E.grel;
+        s_lk[threadIdx.x] = l;
+        s_t[threadIdx.x] = E.t;
+        __syncthreads();
+        if (active) {
+          float c = 0.f;
+          if (E.seg && j > 0) {
+            float2 pg;
+            float pt;
+            bool have = false;
+            if (threadIdx.x > 0) {
+              pg = s_g[threadIdx.x - 1];
+              pt = s_t[threadIdx.x - 1];
+              have = true;
+            } else if (kslab > 0 && prev_l == l) {
+              pg = prev_g;
+              pt = prev_t;
+              have = true;
+            }
+            if (!have) {
+              LinkRec L = recs[l];
+              RibEval Ep = eval_rib<MIXED>(L, j - 1);
+              pg = Ep.grel;
+              pt = Ep.t;
+            }
+            if (E.t >= pt) {
+              float dx = E.grel.x - pg.x, dy = E.grel.y - pg.y;
+              c = sqrtf(dx * dx + dy * dy);
+            }
+          }
+          chord[r] = c;
+        }
+        // carry the last thread's value into the next slab
+        prev_g = s_g[EMIT_NT - 1];
+        prev_l = s_lk[EMIT_NT - 1];
+        prev_t = s_t[EMIT_NT - 1];
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Path index of every link (for the rib tags).
+__global__ void k_link_path(const int32_t* __restrict__ seg_off, int n_path, int64_t n_link,
+                            int32_t* __restrict__ link_path) {
+  int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= n_link) return;
+  link_path[l] = find_path(seg_off, n_path, l);
+}
+
+// ---------------------------------------------------------------------------
+// K3: segmented inclusive scan of per-rib chords into cumulative arc length
+// (Eq. 18), restarting at every path's first rib; FP64 accumulation.
+constexpr int SCAN_NT = 256;
+constexpr int SCAN_IPT = 8;
+constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
+
+__global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
+    const float* __restrict__ chord_in, const uint32_t* __restrict__ tag,
+    const int64_t* __restrict__ n_rib, int64_t capacity, float* __restrict__ s_out,
+    float* __restrict__ path_len, uint32_t* tflag, double* tagg, double* tincl,
+    int32_t* counters, int32_t* status) {
+  __shared__ double sv[SCAN_NT / 32];
+  __shared__ int sh[SCAN_NT / 32];
+  __shared__ double s_carry;
+  __shared__ int s_tile;
+  int64_t R = *n_rib;
+  if (R > capacity) R = capacity;
+  int64_t n_tiles = (R + SCAN_TILE - 1) / SCAN_TILE;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&counters[1], 1);
+    __syncthreads();
+    int64_t tile = s_tile;
+    __syncthreads();
+    if (tile >= n_tiles) return;
+    int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_IPT;
+    float c[SCAN_IPT];
+    uint32_t pth[SCAN_IPT];
+    bool head[SCAN_IPT];
+    double acc = 0.0;
+    bool th = false;
+    for (int i = 0; i < SCAN_IPT; ++i) {
+      int64_t r = base + i;
+      if (r < R) {
+        c[i] = chord_in[r];
+        pth[i] = tag[r] >> 2;
+        head[i] = (r == 0) || ((tag[r - 1] >> 2) != pth[i]);
+      } else {
+        c[i] = 0.f;
+        pth[i] = 0xffffffffu;
+        head[i] = false;
+      }
+      if (head[i]) {
+        acc = 0.0;
+        th = true;
+      }
+      acc += (double)c[i];
+    }
+    // segmented warp scan of (th, acc)
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double v = acc;
+    int h = th;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      double vy = __shfl_up_sync(0xffffffffu, v, o);
+      int hy = __shfl_up_sync(0xffffffffu, h, o);
+      if (lane >= o) {
+        if (!h) v += vy;
+        h |= hy;
+      }
+    }
+    if (lane == 31) {
+      sv[wid] = v;
+      sh[wid] = h;
+    }
+    __syncthreads();
+    // exclusive carry from earlier warps of the block
+    double wcarry = 0.0;
+    int whead = 0;
+    for (int w = wid - 1; w >= 0; --w) {
+      wcarry += sv[w];
+      if (sh[w]) { whead = 1; break; }
+    }
+    double tile_v = 0.0;
+    int tile_h = 0;
+    for (int w = SCAN_NT / 32 - 1; w >= 0; --w) {
+      tile_v += sv[w];
+      if (sh[w]) { tile_h = 1; break; }
+    }
+    for (int w = 0; w < SCAN_NT / 32; ++w) tile_h |= sh[w];
+    if (threadIdx.x == 0)
+      s_carry = lookback_segsum(tflag, tagg, tincl, tile_v, tile_h != 0, tile, status);
+    __syncthreads();
+    // exclusive prefix for this thread = inclusive(v,h) of lane-1 ...
+    double vprev = __shfl_up_sync(0xffffffffu, v, 1);
+    int hprev = __shfl_up_sync(0xffffffffu, h, 1);
+    if (lane == 0) {
+      vprev = 0.0;
+      hprev = 0;
+    }
+    double run;
+    if (hprev) run = vprev;
+    else {
+      run = vprev + wcarry;
+      if (!whead) run += s_carry;
+    }
+    for (int i = 0; i < SCAN_IPT; ++i) {
+      int64_t r = base + i;
+      if (r >= R) break;
+      if (head[i]) run = 0.0;
+      run += (double)c[i];
+      s_out[r] = (float)run;
+      bool last = (r == R - 1) || ((tag[r + 1] >> 2) != pth[i]);
+      if (last && path_len) path_len[pth[i]] = (float)run;
+    }
+    __syncthreads();
+  }
+}
+
+// Chords from rib midpoints (standalone arc length of any rib stream).
+__global__ void k_midpoint_chords(const float4* __restrict__ rib, const uint32_t* __restrict__ tag,
+                                  const int64_t* __restrict__ n_rib, int64_t capacity,
+                                  float* __restrict__ chord) {
+  int64_t R = *n_rib;
+  if (R > capacity) R = capacity;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t tg = tag[r];
+    float c = 0.f;
+    if ((tg & PS_TAG_SEGMENT) && !(tg & PS_TAG_LINK_START) && r > 0) {
+      float4 a = rib[r - 1], b = rib[r];
+      float dx = 0.5f * ((b.x + b.z) - (a.x + a.z)), dy = 0.5f * ((b.y + b.w) - (a.y + a.w));
+      c = sqrtf(dx * dx + dy * dy);
+    }
+    chord[r] = c;
+  }
+}
+
+}  // namespace ps
+
+using namespace ps;
+
+// ===========================================================================
+// host entry points
+static int launch_tessellate(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
+                             float dtheta, int precision, uint32_t flags, ps_tess_out* out,
+                             cudaStream_t st) {
+  int64_t S = seg->n_seg;
+  int P = paths->n_path;
+  int64_t L = 2 * S + P;
+  if (P <= 0) return PS_ERR_INVALID;
+  int64_t n_tiles = (L + SETUP_TILE - 1) / SETUP_TILE;
+  int rc;
+  if ((rc = ps_ensure_tiles(ctx, n_tiles + (out->capacity + SCAN_TILE - 1) / SCAN_TILE + 2)) != PS_OK)
+    return rc;
+  if ((rc = ps_ensure_recs(ctx, L)) != PS_OK) return rc;
+  // link path indices live after the records
+  int32_t* link_path = reinterpret_cast<int32_t*>(ctx->d_recs + ctx->rec_cap);
+  cudaMemsetAsync(ctx->d_tile_flag, 0, sizeof(uint32_t) * n_tiles, st);
+  cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
+  // a count-only call has no rib buffers to overflow
+  int64_t count_cap = (flags & PS_TESS_COUNT_ONLY) ? INT64_MAX : out->capacity;
+  { ProfScope ps_(ctx, PK_LINK_PATH, st);
+  k_link_path<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(paths->d_seg_off, P, L, link_path); }
+  {
+  ProfScope ps_(ctx, PK_LINK_SETUP, st);
+  if (precision == PS_PREC_MIXED)
+    k_link_setup<true><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
+        seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
+        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->d_recs,
+        out->d_link_rib_off, out->d_path_rib_off, out->d_n_rib, count_cap, ctx->d_tile_flag,
+        ctx->d_tile_agg, ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles);
+  else
+    k_link_setup<false><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
+        seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
+        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->d_recs,
+        out->d_link_rib_off, out->d_path_rib_off, out->d_n_rib, count_cap, ctx->d_tile_flag,
+        ctx->d_tile_agg, ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles);
+  }
+  if ((rc = ps_cuda_check(cudaGetLastError())) != PS_OK) return rc;
+  if (flags & PS_TESS_COUNT_ONLY) return PS_OK;
+
+  bool arc = (flags & PS_TESS_ARCLENGTH) && out->d_s;
+  int grid = ps_persistent_grid(ctx, precision == PS_PREC_MIXED ? (const void*)k_emit<true>
+                                                                 : (const void*)k_emit<false>,
+                                EMIT_NT, 0);
+  {
+  ProfScope ps_(ctx, PK_EMIT, st);
+  if (precision == PS_PREC_MIXED)
+    k_emit<true><<<grid, EMIT_NT, 0, st>>>(ctx->d_recs, out->d_link_rib_off, link_path, L,
+                                           out->d_n_rib, out->capacity,
+                                           reinterpret_cast<float4*>(out->d_rib), out->d_tag,
+                                           arc ? out->d_s : nullptr, out->d_t);
+  else
+    k_emit<false><<<grid, EMIT_NT, 0, st>>>(ctx->d_recs, out->d_link_rib_off, link_path, L,
+                                            out->d_n_rib, out->capacity,
+                                            reinterpret_cast<float4*>(out->d_rib), out->d_tag,
+                                            arc ? out->d_s : nullptr, out->d_t);
+  }
+  if ((rc = ps_cuda_check(cudaGetLastError())) != PS_OK) return rc;
+  if (arc) {
+    int64_t scan_tiles = (out->capacity + SCAN_TILE - 1) / SCAN_TILE;
+    cudaMemsetAsync(ctx->d_tile_flag + n_tiles + 1, 0, sizeof(uint32_t) * (scan_tiles + 1), st);
+    if (out->d_path_len) cudaMemsetAsync(out->d_path_len, 0, sizeof(float) * P, st);
+    int g2 = ps_persistent_grid(ctx, (const void*)k_arclen_scan, SCAN_NT, 0);
+    ProfScope ps_(ctx, PK_ARCLEN, st);
+    k_arclen_scan<<<g2, SCAN_NT, 0, st>>>(out->d_s, out->d_tag, out->d_n_rib, out->capacity,
+                                          out->d_s, out->d_path_len,
+                                          ctx->d_tile_flag + n_tiles + 1,
+                                          ctx->d_tile_aggd + n_tiles + 1,
+                                          ctx->d_tile_incld + n_tiles + 1, ctx->d_counters,
+                                          ctx->d_status);
+    if ((rc = ps_cuda_check(cudaGetLastError())) != PS_OK) return rc;
+  }
+  return PS_OK;
+}
+
+extern "C" int ps_tessellate_strokes(ps_context* ctx, const ps_segments* seg,
+                                     const ps_paths* paths, float dtheta, int precision,
+                                     uint32_t flags, ps_tess_out* out, void* stream) {
+  if (!ctx || !seg || !paths || !out) return PS_ERR_INVALID;
+  if (!(dtheta >= 1e-4f && dtheta <= 3.14159265f)) return PS_ERR_INVALID;
+  if (precision != PS_PREC_FP32 && precision != PS_PREC_MIXED) return PS_ERR_INVALID;
+  if (seg->n_seg < 0 || paths->n_path <= 0 || seg->n_seg > (int64_t)1 << 29) return PS_ERR_INVALID;
+  if (seg->n_seg > 0 && (!seg->d_type || !seg->d_pts)) return PS_ERR_INVALID;
+  if (!paths->d_seg_off || !paths->d_width || !paths->d_join || !paths->d_cap ||
+      !paths->d_miter || !paths->d_closed)
+    return PS_ERR_INVALID;
+  if (!out->d_link_rib_off || !out->d_path_rib_off || !out->d_n_rib) return PS_ERR_INVALID;
+  if (!(flags & PS_TESS_COUNT_ONLY) && (!out->d_rib || !out->d_tag || out->capacity < 0))
+    return PS_ERR_INVALID;
+  if ((flags & PS_TESS_ARCLENGTH) && !(flags & PS_TESS_COUNT_ONLY) && !out->d_s)
+    return PS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = stream;
+  return launch_tessellate(ctx, seg, paths, dtheta, precision, flags, out, st);
+}
+
+extern "C" int ps_count_ribs_sync(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
+                                  float dtheta, int precision, ps_tess_out* out, void* stream,
+                                  int64_t* h_n_rib) {
+  if (!h_n_rib) return PS_ERR_INVALID;
+  int rc = ps_tessellate_strokes(ctx, seg, paths, dtheta, precision, PS_TESS_COUNT_ONLY, out,
+                                 stream);
+  if (rc != PS_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = ps_cuda_check(cudaMemcpyAsync(h_n_rib, out->d_n_rib, sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, st));
+  if (rc != PS_OK) return rc;
+  return ps_cuda_check(cudaStreamSynchronize(st));
+}
+
+extern "C" int ps_arclength_scan(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
+                                 const int64_t* d_n_rib, int64_t capacity, float* d_s,
+                                 float* d_path_len, int32_t n_path, void* stream) {
+  if (!ctx || !d_rib || !d_tag || !d_n_rib || !d_s || capacity < 0 || n_path < 0)
+    return PS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = stream;
+  int64_t scan_tiles = (capacity + SCAN_TILE - 1) / SCAN_TILE;
+  int rc = ps_ensure_tiles(ctx, scan_tiles + 2);
+  if (rc != PS_OK) return rc;
+  cudaMemsetAsync(ctx->d_tile_flag, 0, sizeof(uint32_t) * (scan_tiles + 1), st);
+  cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
+  if (d_path_len && n_path > 0) cudaMemsetAsync(d_path_len, 0, sizeof(float) * n_path, st);
+  int g = ps_persistent_grid(ctx, (const void*)k_midpoint_chords, 256, 0);
+  { ProfScope ps_(ctx, PK_MIDCHORD, st);
+  k_midpoint_chords<<<g, 256, 0, st>>>(reinterpret_cast<const float4*>(d_rib), d_tag, d_n_rib,
+                                       capacity, d_s); }
+  int g2 = ps_persistent_grid(ctx, (const void*)k_arclen_scan, SCAN_NT, 0);
+  ProfScope ps_(ctx, PK_ARCLEN, st);
+  k_arclen_scan<<<g2, SCAN_NT, 0, st>>>(d_s, d_tag, d_n_rib, capacity, d_s, d_path_len,
+                                        ctx->d_tile_flag, ctx->d_tile_aggd, ctx->d_tile_incld,
+                                        ctx->d_counters, ctx->d_status);
+  return ps_cuda_check(cudaGetLastError());
+}

@@ -117,10 +117,11 @@ def test_c4_precision_subset_mixed_beats_fp32():
     res = {}
     for prec in (PLAIN, MIXED):
         g = gpu_tessellate(b, prec)
-        stats, fails = compare_tess(o, g, b, FRAG[prec], 1.0, s_rel=1.0)
+        stats, fails = compare_tess(o, g, b, FRAG[prec], EPS_ANG[prec])
         res[prec] = stats
         print("c4 prec", prec, stats)
     assert res[MIXED]["count_mismatch_nonfragile"] == 0
+    assert res[MIXED]["vertex_ratio_max"] <= 1.0 and res[MIXED]["s_ratio_max"] <= 1.0
     assert res[MIXED]["count_mismatch_nonfragile"] + res[MIXED]["count_mismatch_fragile"] <= \
         res[PLAIN]["count_mismatch_nonfragile"] + res[PLAIN]["count_mismatch_fragile"]
 
