@@ -169,6 +169,29 @@ int ps_tessellate_strokes(ps_context* ctx, const ps_segments* seg, const ps_path
                           float dtheta, int precision, uint32_t flags, ps_tess_out* out,
                           void* stream);
 
+/* Allocation-free variant of ps_tessellate_strokes (the paper has no
+ * counterpart; this is an interface for callers that cannot allocate device
+ * memory when they stroke -- for example code running during a global-mode
+ * stream capture, or under an allocator that owns the device's memory).
+ * Same arguments, outputs and semantics as ps_tessellate_strokes, except:
+ *   - no context: the workspace is a fixed array inside the library image
+ *     (about 2.9 MB on every device that loads the library, kept until exit);
+ *     the call makes no cudaMalloc, cudaFree or other allocating call;
+ *   - d_status: caller-owned device int32 that kernels set to the first
+ *     PS_ERR_* they meet (the caller zeroes it and reads it back);
+ *   - limits: at most 16384 links (2 n_seg + n_path) and, with
+ *     PS_TESS_ARCLENGTH, a rib capacity of at most 4194304; larger problems
+ *     return PS_ERR_CAPACITY before any launch;
+ *   - the first call on a device looks up the array's device address (with
+ *     that device current); make that first call outside any stream capture;
+ *   - every call uses the same array, which keeps the previous call's
+ *     contents (the call clears what must start at zero): calls that may run
+ *     at the same time on the GPU -- on different streams, or different host
+ *     threads -- race and must be serialized by the caller. */
+int ps_tessellate_strokes_noalloc(const ps_segments* seg, const ps_paths* paths, float dtheta,
+                                  int precision, uint32_t flags, ps_tess_out* out,
+                                  int32_t* d_status, void* stream);
+
 /* Convenience: run the count phase and return R on the host.  SYNCHRONIZES. */
 int ps_count_ribs_sync(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
                        float dtheta, int precision, ps_tess_out* out, void* stream,

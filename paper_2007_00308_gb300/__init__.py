@@ -23,7 +23,7 @@ TAG_LINK_START, TAG_SEGMENT = 1, 2
 EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_status",
            "ps_error_string", "ps_tessellate_strokes", "ps_count_ribs_sync", "ps_arclength_scan",
            "ps_dash", "ps_rasterize_coverage", "ps_profile_enable", "ps_profile_read",
-           "ps_profile_slot_name", "ps_raster_pair_count"]
+           "ps_profile_slot_name", "ps_raster_pair_count", "ps_tessellate_strokes_noalloc"]
 PS_PROF_SLOTS = 10
 
 
@@ -88,6 +88,10 @@ def lib():
         L.ps_profile_slot_name.argtypes = [ctypes.c_int]
         L.ps_profile_slot_name.restype = ctypes.c_char_p
         L.ps_raster_pair_count.argtypes = [P, ctypes.POINTER(I64)]
+        L.ps_tessellate_strokes_noalloc.argtypes = [ctypes.POINTER(_Segments),
+                                                    ctypes.POINTER(_Paths), ctypes.c_float,
+                                                    ctypes.c_int, ctypes.c_uint32,
+                                                    ctypes.POINTER(_TessOut), P, P]
         _lib = L
     return _lib
 
@@ -225,6 +229,19 @@ def ps_tessellate_strokes(ctx: Context, db: DeviceBatch, out: TessOutput, precis
     rc = lib().ps_tessellate_strokes(ctx.handle, ctypes.byref(seg), ctypes.byref(paths), q,
                                      int(precision), int(flags), ctypes.byref(o), _stream(stream))
     _check(rc, "ps_tessellate_strokes")
+
+
+def ps_tessellate_strokes_noalloc(db: DeviceBatch, out: TessOutput, status, precision=PS_PREC_FP32,
+                                  flags=PS_TESS_ARCLENGTH, dtheta=None, stream=None):
+    """Allocation-free tessellation: workspace from the library's fixed device
+    array; ``status`` is a caller-owned int32 device tensor for kernel errors.
+    Returns the host return code (0, or PS_ERR_* without raising)."""
+    seg, paths = db._structs()
+    o = out._struct()
+    q = db.dtheta if dtheta is None else float(dtheta)
+    return lib().ps_tessellate_strokes_noalloc(ctypes.byref(seg), ctypes.byref(paths), q,
+                                               int(precision), int(flags), ctypes.byref(o),
+                                               _ptr(status), _stream(stream))
 
 
 def ps_count_ribs_sync(ctx: Context, db: DeviceBatch, out: TessOutput, precision=PS_PREC_FP32,

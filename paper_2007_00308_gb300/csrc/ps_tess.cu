@@ -1212,3 +1212,140 @@ extern "C" int ps_arclength_scan(ps_context* ctx, const float* d_rib, const uint
                                         ctx->d_counters, ctx->d_status);
   return ps_cuda_check(cudaGetLastError());
 }
+
+// ===========================================================================
+// Allocation-free tessellation.
+//
+// ps_tessellate_strokes keeps its workspace (per-link records, scan tile states)
+// in a context that grows it with cudaMalloc.  Some callers cannot allocate
+// device memory at the point where they stroke: code that runs while a stream is
+// being captured into a CUDA graph in global capture mode, code that runs where
+// another allocator owns the device's memory budget, or code that must not risk
+// a failed or blocking allocation in the middle of its work.  For them this
+// variant takes its workspace from a fixed array that is part of the loaded
+// library image, so it makes no allocation of any kind.
+namespace {
+constexpr int64_t NOALLOC_MAX_LINKS = 16384;
+constexpr int64_t NOALLOC_MAX_RIBS = 4194304;
+constexpr int64_t NOALLOC_SETUP_TILES = NOALLOC_MAX_LINKS / SETUP_TILE + 1;
+constexpr int64_t NOALLOC_SCAN_TILES = NOALLOC_MAX_RIBS / SCAN_TILE + 1;
+constexpr int64_t NOALLOC_TILES = NOALLOC_SETUP_TILES + 1 + NOALLOC_SCAN_TILES + 1;
+// byte offsets of the workspace parts (each 256-byte aligned)
+constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t NA_RECS = 0;
+constexpr size_t NA_PATH = al256(NA_RECS + sizeof(LinkRec) * NOALLOC_MAX_LINKS);
+constexpr size_t NA_FLAG = al256(NA_PATH + sizeof(int32_t) * NOALLOC_MAX_LINKS);
+constexpr size_t NA_AGG = al256(NA_FLAG + sizeof(uint32_t) * NOALLOC_TILES);
+constexpr size_t NA_INCL = al256(NA_AGG + sizeof(long long) * NOALLOC_TILES);
+constexpr size_t NA_AGGD = al256(NA_INCL + sizeof(long long) * NOALLOC_TILES);
+constexpr size_t NA_INCLD = al256(NA_AGGD + sizeof(double) * NOALLOC_TILES);
+constexpr size_t NA_CNT = al256(NA_INCLD + sizeof(double) * NOALLOC_TILES);
+constexpr size_t NA_BYTES = al256(NA_CNT + sizeof(int32_t) * 16);
+}  // namespace
+
+// The workspace: about 2.9 MB held by every device that loads the library until
+// the process exits.  Host code must not take this name as a device address; it
+// asks the runtime for the address on each device (below).
+static __device__ __align__(256) unsigned char ps_noalloc_scratch[NA_BYTES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+unsigned char* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+int g_noalloc_sms[NOALLOC_MAX_DEVICES];
+}  // namespace
+
+extern "C" int ps_tessellate_strokes_noalloc(const ps_segments* seg, const ps_paths* paths,
+                                             float dtheta, int precision, uint32_t flags,
+                                             ps_tess_out* out, int32_t* d_status, void* stream) {
+  if (!seg || !paths || !out || !d_status) return PS_ERR_INVALID;
+  if (!(dtheta >= 1e-4f && dtheta <= 3.14159265f)) return PS_ERR_INVALID;
+  if (precision != PS_PREC_FP32 && precision != PS_PREC_MIXED) return PS_ERR_INVALID;
+  if (seg->n_seg < 0 || paths->n_path <= 0) return PS_ERR_INVALID;
+  if (seg->n_seg > 0 && (!seg->d_type || !seg->d_pts)) return PS_ERR_INVALID;
+  if (!paths->d_seg_off || !paths->d_width || !paths->d_join || !paths->d_cap ||
+      !paths->d_miter || !paths->d_closed)
+    return PS_ERR_INVALID;
+  if (!out->d_link_rib_off || !out->d_path_rib_off || !out->d_n_rib) return PS_ERR_INVALID;
+  bool count_only = (flags & PS_TESS_COUNT_ONLY) != 0;
+  if (!count_only && (!out->d_rib || !out->d_tag || out->capacity < 0)) return PS_ERR_INVALID;
+  bool arc = !count_only && (flags & PS_TESS_ARCLENGTH);
+  if (arc && !out->d_s) return PS_ERR_INVALID;
+  int64_t L = 2 * seg->n_seg + paths->n_path;
+  // the fixed workspace bounds the problem size
+  if (L > NOALLOC_MAX_LINKS) return PS_ERR_CAPACITY;
+  if (arc && out->capacity > NOALLOC_MAX_RIBS) return PS_ERR_CAPACITY;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PS_ERR_CUDA;
+  if (!g_noalloc_ptr[dev]) {
+    // one-time set-up on this device (with it current): the device address of
+    // the workspace, and the SM count for the persistent grids
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, ps_noalloc_scratch) != cudaSuccess || !p) return PS_ERR_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      return PS_ERR_CUDA;
+    g_noalloc_sms[dev] = sms;
+    g_noalloc_ptr[dev] = (unsigned char*)p;
+  }
+  unsigned char* base = g_noalloc_ptr[dev];
+  LinkRec* recs = reinterpret_cast<LinkRec*>(base + NA_RECS);
+  int32_t* link_path = reinterpret_cast<int32_t*>(base + NA_PATH);
+  uint32_t* tflag = reinterpret_cast<uint32_t*>(base + NA_FLAG);
+  long long* tagg = reinterpret_cast<long long*>(base + NA_AGG);
+  long long* tincl = reinterpret_cast<long long*>(base + NA_INCL);
+  double* taggd = reinterpret_cast<double*>(base + NA_AGGD);
+  double* tincld = reinterpret_cast<double*>(base + NA_INCLD);
+  int32_t* counters = reinterpret_cast<int32_t*>(base + NA_CNT);
+
+  cudaStream_t st = (cudaStream_t)stream;
+  int P = paths->n_path;
+  int64_t n_tiles = (L + SETUP_TILE - 1) / SETUP_TILE;
+  // the array keeps the previous call's contents: reset what must start at zero
+  if (cudaMemsetAsync(tflag, 0, sizeof(uint32_t) * NOALLOC_TILES, st) != cudaSuccess ||
+      cudaMemsetAsync(counters, 0, sizeof(int32_t) * 16, st) != cudaSuccess)
+    return PS_ERR_CUDA;
+  int64_t count_cap = count_only ? INT64_MAX : out->capacity;
+  k_link_path<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(paths->d_seg_off, P, L, link_path);
+  if (precision == PS_PREC_MIXED)
+    k_link_setup<true><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
+        seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
+        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, recs, out->d_link_rib_off,
+        out->d_path_rib_off, out->d_n_rib, count_cap, tflag, tagg, tincl, counters, d_status,
+        n_tiles);
+  else
+    k_link_setup<false><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
+        seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
+        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, recs, out->d_link_rib_off,
+        out->d_path_rib_off, out->d_n_rib, count_cap, tflag, tagg, tincl, counters, d_status,
+        n_tiles);
+  if (cudaGetLastError() != cudaSuccess) return PS_ERR_CUDA;
+  if (count_only) return PS_OK;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, precision == PS_PREC_MIXED ? (const void*)k_emit<true> : (const void*)k_emit<false>,
+      EMIT_NT, 0);
+  int grid = g_noalloc_sms[dev] * (per_sm > 0 ? per_sm : 1);
+  if (precision == PS_PREC_MIXED)
+    k_emit<true><<<grid, EMIT_NT, 0, st>>>(recs, out->d_link_rib_off, link_path, L, out->d_n_rib,
+                                           out->capacity, reinterpret_cast<float4*>(out->d_rib),
+                                           out->d_tag, arc ? out->d_s : nullptr, out->d_t);
+  else
+    k_emit<false><<<grid, EMIT_NT, 0, st>>>(recs, out->d_link_rib_off, link_path, L, out->d_n_rib,
+                                            out->capacity, reinterpret_cast<float4*>(out->d_rib),
+                                            out->d_tag, arc ? out->d_s : nullptr, out->d_t);
+  if (cudaGetLastError() != cudaSuccess) return PS_ERR_CUDA;
+  if (arc) {
+    if (out->d_path_len && cudaMemsetAsync(out->d_path_len, 0, sizeof(float) * P, st) != cudaSuccess)
+      return PS_ERR_CUDA;
+    int per_sm2 = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, (const void*)k_arclen_scan, SCAN_NT, 0);
+    int g2 = g_noalloc_sms[dev] * (per_sm2 > 0 ? per_sm2 : 1);
+    int64_t o = NOALLOC_SETUP_TILES + 1;
+    k_arclen_scan<<<g2, SCAN_NT, 0, st>>>(out->d_s, out->d_tag, out->d_n_rib, out->capacity,
+                                          out->d_s, out->d_path_len, tflag + o, taggd + o,
+                                          tincld + o, counters, d_status);
+    if (cudaGetLastError() != cudaSuccess) return PS_ERR_CUDA;
+  }
+  return PS_OK;
+}
