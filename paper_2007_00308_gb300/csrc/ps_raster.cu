@@ -58,7 +58,30 @@ __device__ __forceinline__ void quad_pixels(const QuadFix& q, int W, int H, int&
   pix_range(mny, mxy, H, py0, py1);
 }
 
-// pass 0: count (quad, tile) pairs per tile; pass 1: scatter rib ids into bins
+// Can triangle (x0,y0)-(x1,y1)-(x2,y2) cover a sample of the tile whose samples
+// lie in [rx0, rx1] x [ry0, ry1]?  Separating-axis test on the triangle's edges
+// (the rectangle's own axes are settled by the bounding-box range).
+__device__ __forceinline__ bool tri_meets_rect(int x0, int y0, int x1, int y1, int x2, int y2,
+                                               int rx0, int ry0, int rx1, int ry1) {
+  long long area = (long long)(x1 - x0) * (y2 - y0) - (long long)(y1 - y0) * (x2 - x0);
+  if (area == 0) return false;
+  if (area < 0) {
+    int t = x1; x1 = x2; x2 = t;
+    t = y1; y1 = y2; y2 = t;
+  }
+  int vx[3] = {x0, x1, x2}, vy[3] = {y0, y1, y2};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    long long A = (long long)vy[i] - vy[(i + 1) % 3], B = (long long)vx[(i + 1) % 3] - vx[i];
+    // the rectangle corner maximizing A x + B y
+    long long cx = A >= 0 ? rx1 : rx0, cy = B >= 0 ? ry1 : ry0;
+    if (A * (cx - vx[i]) + B * (cy - vy[i]) < 0) return false;
+  }
+  return true;
+}
+
+// pass 0: count (quad, tile) pairs per tile; pass 1: scatter rib ids into bins.
+// Lanes of a warp that hit the same tile are grouped: one atomic per group.
 template <int PASS>
 __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rib,
                                              const uint32_t* __restrict__ tag,
@@ -70,30 +93,57 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rib,
                                              int32_t* status) {
   int64_t R = *n_rib;
   if (R > capacity) R = capacity;
-  for (int64_t r = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    if (__ldg(tag + r) & PS_TAG_LINK_START) continue;
+  int lane = threadIdx.x & 31;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < R; base += stride) {
+    int64_t r = base + threadIdx.x;
+    bool act = r >= 1 && r < R && !(__ldg(tag + r) & PS_TAG_LINK_START);
     QuadFix q;
-    if (!snap_quad(__ldg(rib + r - 1), __ldg(rib + r), q)) {
-      ps_record_error(status, PS_ERR_RANGE);
-      continue;
+    int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+    if (act) {
+      if (!snap_quad(__ldg(rib + r - 1), __ldg(rib + r), q)) {
+        ps_record_error(status, PS_ERR_RANGE);
+      } else {
+        int px0, px1, py0, py1;
+        quad_pixels(q, W, H, px0, px1, py0, py1);
+        if (px0 <= px1 && py0 <= py1) {
+          tx0 = px0 / TILE_PX; tx1 = px1 / TILE_PX; ty0 = py0 / TILE_PX; ty1 = py1 / TILE_PX;
+        }
+      }
     }
-    int px0, px1, py0, py1;
-    quad_pixels(q, W, H, px0, px1, py0, py1);
-    if (px0 > px1 || py0 > py1) continue;
-    int tx0 = px0 / TILE_PX, tx1 = px1 / TILE_PX, ty0 = py0 / TILE_PX, ty1 = py1 / TILE_PX;
-    for (int ty = ty0; ty <= ty1; ++ty)
-      for (int tx = tx0; tx <= tx1; ++tx) {
-        int t = ty * tiles_x + tx;
+    int ntx = tx1 - tx0 + 1, n = (tx1 >= tx0 && ty1 >= ty0) ? ntx * (ty1 - ty0 + 1) : 0;
+    int nmax = n;
+    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    for (int i = 0; i < nmax; ++i) {
+      int t = -1;
+      if (i < n) {
+        int tx = tx0 + i % ntx, ty = ty0 + i / ntx;
+        // sample rectangle of the tile (1/256 px), clipped to the canvas
+        int rx0 = tx * TILE_UNITS + 8, ry0 = ty * TILE_UNITS + 8;
+        int rx1 = min(tx * TILE_UNITS + TILE_UNITS, W * 256) - 8;
+        int ry1 = min(ty * TILE_UNITS + TILE_UNITS, H * 256) - 8;
+        bool hit = n == 1 ||
+                   tri_meets_rect(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], rx0, ry0, rx1, ry1) ||
+                   tri_meets_rect(q.x[0], q.y[0], q.x[3], q.y[3], q.x[2], q.y[2], rx0, ry0, rx1, ry1);
+        if (hit) t = ty * tiles_x + tx;
+      }
+      unsigned peers = __match_any_sync(0xffffffffu, t);
+      int leader = __ffs(peers) - 1;
+      int cntg = __popc(peers);
+      if (t >= 0) {
         if (PASS == 0) {
-          atomicAdd(count + t, 1);
+          if (lane == leader) atomicAdd(count + t, cntg);
         } else {
-          int pos = atomicAdd(cursor + t, 1);
+          int basepos = 0;
+          if (lane == leader) basepos = atomicAdd(cursor + t, cntg);
+          basepos = __shfl_sync(peers, basepos, leader);
+          int pos = basepos + __popc(peers & ((1u << lane) - 1u));
           int64_t at = (int64_t)off[t] + pos;
           if (at < pair_cap && at < off[t + 1]) bin[at] = (uint32_t)r;
           else ps_record_error(status, PS_ERR_CAPACITY);
         }
       }
+    }
   }
 }
 
@@ -143,19 +193,17 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int32_t* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Coverage.  One CTA per tile (persistent over tiles).  Per tile:
-//  A. bin entries in chunks of CHUNK: one thread per entry assigns the entry's
-//     path a mask slot (shared hash), builds the two triangles' edge functions
-//     relative to the tile origin and the pixel span of every pixel row of the
-//     tile that the triangles can reach;
-//  B. the (entry, pixel) items of the chunk are flattened with a block scan and
-//     shared by all threads; each item ORs the pixel's 16-sample mask of both
-//     triangles into the path's mask;
-//  C. per-path popcounts, the canvas OR, and the masks are cleared.
-// Paths beyond SLOTS per tile are handled in further passes over the bin.
+// Coverage.  One 512-thread CTA per SM, persistent over tiles.  Per tile each
+// warp runs its own queue: it takes the next 32 bin entries, each lane sets one
+// up (the path's mask slot from a shared hash, the edge functions relative to
+// the tile, the pixel span of every pixel row the quad can reach), a warp scan
+// flattens the entries' pixels so that every lane gets one pixel at a time, and
+// each pixel's 16-sample mask is ORed into the path's mask in shared memory.
+// Block-wide barriers only open and close a tile: per-path popcounts and the
+// canvas OR are taken there.  Paths beyond SLOTS per tile take further passes.
 constexpr int CV_NT = 512;
-constexpr int CHUNK = 256;
-constexpr int SLOTS = 256;           // per-path masks resident in shared memory
+constexpr int CV_WARPS = CV_NT / 32;
+constexpr int SLOTS = 224;           // per-path masks resident in shared memory
 constexpr int HKEYS = 2048;          // hash of path ids (max distinct paths per tile)
 constexpr int MASK_WORDS = TILE_PX * TILE_PX / 2;
 
@@ -165,11 +213,12 @@ struct Edge {
 };
 
 struct EntrySetup {
-  Edge e[6];               // triangle 0: e[0..2], triangle 1: e[3..5]
-  uint16_t rowpre[17];     // prefix of span widths over the tile's 16 rows
+  Edge e[6];               // convex quad: e[0..3]; else triangle 0: e[0..2], triangle 1: e[3..5]
+  uint16_t rowpre[17];     // prefix of span widths over rows row0 ..
   uint8_t x0[16];          // first pixel of each row's span
-  uint16_t slot;           // mask slot (0xffff: not this pass)
-  uint8_t valid;           // bit0 tri 0 non-degenerate, bit1 tri 1, bit2 needs int64 path
+  uint16_t slot;           // mask slot of this pass
+  uint8_t valid;           // bit0 tri 0, bit1 tri 1, bit2 int64 path, bit3 convex quad
+  uint8_t row0;
 };
 
 __device__ __forceinline__ void make_edges(int x0, int y0, int x1, int y1, int x2, int y2, Edge* e,
@@ -210,36 +259,148 @@ __device__ __forceinline__ void seg_strip(float ax, float ay, float bx, float by
   xmax = fmaxf(xmax, fmaxf(xa, xb));
 }
 
-// 16-sample mask of one triangle at tile pixel (lx, ly)
-__device__ __forceinline__ uint32_t tri_pixel_mask(const Edge* e, bool big, int lx, int ly) {
-  uint32_t m = 0xffffu;
-  int cx = lx * 256, cy = ly * 256;
+// 16-sample mask of one edge given its value Ec at the pixel corner: sample k
+// passes iff Ec + A (16k+8) + B (16((5k) mod 16)+8) >= 0.
+__device__ __forceinline__ uint32_t edge_mask(const Edge& e, long long Ec, bool big) {
+  if (!big) {
+    long long D = 248ll * (llabs((long long)e.A) + llabs((long long)e.B));
+    if (Ec - D >= 0) return 0xffffu;
+    if (Ec + D < 0) return 0u;
+    int E0 = (int)Ec, A = e.A, B = e.B;  // |E0| < D < 2^30: sums fit in int32
+    uint32_t em = 0;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    long long Ec = (long long)e[i].A * cx + (long long)e[i].B * cy + e[i].C;
-    if (!big) {
-      long long D = 248ll * (llabs((long long)e[i].A) + llabs((long long)e[i].B));
-      if (Ec - D >= 0) continue;          // every sample inside this edge
-      if (Ec + D < 0) return 0u;          // none
-      int E0 = (int)Ec, A = e[i].A, B = e[i].B;
-      uint32_t em = 0;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        int v = E0 + A * (16 * k + 8) + B * (16 * ((5 * k) & 15) + 8);
-        em |= (v >= 0 ? 1u : 0u) << k;
-      }
-      m &= em;
-    } else {
-      uint32_t em = 0;
-      for (int k = 0; k < 16; ++k) {
-        long long v = Ec + (long long)e[i].A * (16 * k + 8) + (long long)e[i].B * (16 * ((5 * k) & 15) + 8);
-        em |= (v >= 0 ? 1u : 0u) << k;
-      }
-      m &= em;
+    for (int k = 0; k < 16; ++k) {
+      int v = E0 + A * (16 * k + 8) + B * (16 * ((5 * k) & 15) + 8);
+      em |= (v >= 0 ? 1u : 0u) << k;
     }
-    if (!m) return 0u;
+    return em;
   }
-  return m;
+  uint32_t em = 0;
+  for (int k = 0; k < 16; ++k) {
+    long long v = Ec + (long long)e.A * (16 * k + 8) + (long long)e.B * (16 * ((5 * k) & 15) + 8);
+    em |= (v >= 0 ? 1u : 0u) << k;
+  }
+  return em;
+}
+
+// Set up entry r (rib id) of tile (ox, oy); returns its pixel count.
+__device__ __forceinline__ int setup_entry(const float4* __restrict__ rib, uint32_t r, int slot,
+                                           int ox, int oy, int tw, int th, EntrySetup& E) {
+  E.slot = (uint16_t)slot;
+  E.valid = 0;
+  E.row0 = 0;
+  E.rowpre[0] = 0;
+  QuadFix q;
+  if (!snap_quad(__ldg(rib + r - 1), __ldg(rib + r), q)) return 0;
+  for (int v = 0; v < 4; ++v) {
+    q.x[v] -= ox;
+    q.y[v] -= oy;
+  }
+  bool v0, v1, big = false;
+  make_edges(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], E.e, v0, big);      // N0 P0 P1
+  make_edges(q.x[0], q.y[0], q.x[3], q.y[3], q.x[2], q.y[2], E.e + 3, v1, big);  // N0 P1 N1
+  if (!v0 && !v1) return 0;
+  uint8_t flags = (v0 ? 1 : 0) | (v1 ? 2 : 0);
+  if (v0 && v1) {
+    // both triangles real and the polygon N0 P0 P1 N1 convex (no turn of the
+    // opposite sense): their union is the polygon, four edges instead of six
+    int px_[4] = {q.x[0], q.x[1], q.x[3], q.x[2]}, py_[4] = {q.y[0], q.y[1], q.y[3], q.y[2]};
+    bool pos = true, neg = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int j = (i + 1) & 3, k2 = (i + 2) & 3;
+      long long c = (long long)(px_[j] - px_[i]) * (py_[k2] - py_[j]) -
+                    (long long)(py_[j] - py_[i]) * (px_[k2] - px_[j]);
+      pos = pos && c >= 0;
+      neg = neg && c <= 0;
+    }
+    if (pos || neg) {
+      bool bigq = false;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        int a0 = neg ? (4 - i) & 3 : i, a1 = neg ? (3 - i) & 3 : (i + 1) & 3;
+        long long A = (long long)py_[a0] - py_[a1], B = (long long)px_[a1] - px_[a0];
+        E.e[i].A = (int)A;
+        E.e[i].B = (int)B;
+        E.e[i].C = -(A * px_[a0] + B * py_[a0]);
+        if (llabs(A) + llabs(B) >= (1ll << 22)) bigq = true;
+      }
+      big = bigq;
+      flags |= 8;
+    }
+  }
+  E.valid = flags | (big ? 4 : 0);
+  // per-row pixel spans over the 5 segments bounding both triangles
+  float fx[4] = {(float)q.x[0], (float)q.x[1], (float)q.x[2], (float)q.x[3]};
+  float fy[4] = {(float)q.y[0], (float)q.y[1], (float)q.y[2], (float)q.y[3]};
+  float ymin = fminf(fminf(fy[0], fy[1]), fminf(fy[2], fy[3]));
+  float ymax = fmaxf(fmaxf(fy[0], fy[1]), fmaxf(fy[2], fy[3]));
+  float mag = fmaxf(fmaxf(fabsf(fx[0]), fabsf(fx[1])), fmaxf(fabsf(fx[2]), fabsf(fx[3])));
+  mag = fmaxf(mag, fmaxf(fabsf(ymin), fabsf(ymax)));
+  float eps = 4.f + mag * 1e-6f;  // float error of the clipped extents, 1/256 px
+  int ly0 = max(0, (int)ceilf((ymin - 248.f - eps) / 256.f));
+  int ly1 = min(th - 1, (int)floorf((ymax - 8.f + eps) / 256.f));
+  int first = -1, tot = 0;
+  for (int ly = ly0; ly <= ly1; ++ly) {
+    float ylo = 256.f * ly + 8.f - eps, yhi = 256.f * ly + 248.f + eps;
+    float xmin = 3.4e38f, xmax = -3.4e38f;
+    seg_strip(fx[0], fy[0], fx[1], fy[1], ylo, yhi, xmin, xmax);  // N0 P0
+    seg_strip(fx[1], fy[1], fx[3], fy[3], ylo, yhi, xmin, xmax);  // P0 P1
+    seg_strip(fx[3], fy[3], fx[2], fy[2], ylo, yhi, xmin, xmax);  // P1 N1
+    seg_strip(fx[2], fy[2], fx[0], fy[0], ylo, yhi, xmin, xmax);  // N1 N0
+    seg_strip(fx[0], fy[0], fx[3], fy[3], ylo, yhi, xmin, xmax);  // N0 P1
+    int w = 0, a = 0;
+    if (xmax >= xmin) {
+      a = max(0, (int)ceilf((xmin - 248.f - eps) / 256.f));
+      int bb = min(tw - 1, (int)floorf((xmax - 8.f + eps) / 256.f));
+      if (bb >= a) w = bb - a + 1;
+    }
+    if (first < 0) {
+      if (w == 0) continue;
+      first = ly;
+    }
+    int k = ly - first;
+    E.x0[k] = (uint8_t)a;
+    tot += w;
+    E.rowpre[k + 1] = (uint16_t)tot;
+  }
+  if (first < 0) return 0;
+  E.row0 = (uint8_t)first;
+  // rows after the last one repeat the final prefix: the row search below takes
+  // the last row whose prefix is <= the item index, which skips empty rows
+  for (int k = ly1 - first + 1; k < 16; ++k) E.rowpre[k + 1] = (uint16_t)tot;
+  return tot;
+}
+
+__device__ __forceinline__ uint32_t pixel_mask(const EntrySetup& E, int lx, int ly) {
+  int cx = lx * 256, cy = ly * 256;
+  bool big = (E.valid & 4) != 0;
+  if (E.valid & 8) {
+    uint32_t m = 0xffffu;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      long long Ec = (long long)E.e[i].A * cx + (long long)E.e[i].B * cy + E.e[i].C;
+      m &= edge_mask(E.e[i], Ec, big);
+      if (!m) return 0u;
+    }
+    return m;
+  }
+  uint32_t m0 = 0, m1 = 0;
+  if (E.valid & 1) {
+    m0 = 0xffffu;
+    for (int i = 0; i < 3 && m0; ++i) {
+      long long Ec = (long long)E.e[i].A * cx + (long long)E.e[i].B * cy + E.e[i].C;
+      m0 &= edge_mask(E.e[i], Ec, big);
+    }
+  }
+  if ((E.valid & 2) && m0 != 0xffffu) {
+    m1 = 0xffffu;
+    for (int i = 3; i < 6 && m1; ++i) {
+      long long Ec = (long long)E.e[i].A * cx + (long long)E.e[i].B * cy + E.e[i].C;
+      m1 &= edge_mask(E.e[i], Ec, big);
+    }
+  }
+  return m0 | m1;
 }
 
 __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
@@ -248,17 +409,17 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
     int H, int tiles_x, int n_tile, uint16_t* __restrict__ canvas,
     unsigned long long* __restrict__ covered, int n_path, int32_t* counters, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem);                       // SLOTS*MASK_WORDS
-  EntrySetup* s_ent = reinterpret_cast<EntrySetup*>(s_mask + SLOTS * MASK_WORDS);  // CHUNK
-  uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_ent + CHUNK);              // HKEYS
-  uint16_t* s_slot_of = reinterpret_cast<uint16_t*>(s_keys + HKEYS);          // HKEYS
-  uint32_t* s_slot_path = reinterpret_cast<uint32_t*>(s_slot_of + HKEYS);     // HKEYS
-  uint32_t* s_pre = s_slot_path + HKEYS;                                      // CHUNK + 1
-  __shared__ int s_tile, s_nslot, s_total;
-  __shared__ uint32_t s_wsum[CV_NT / 32];
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem);                          // SLOTS*MASK_WORDS
+  EntrySetup* s_ent = reinterpret_cast<EntrySetup*>(s_mask + SLOTS * MASK_WORDS);  // CV_NT
+  uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_ent + CV_NT);                 // HKEYS
+  uint16_t* s_slot_of = reinterpret_cast<uint16_t*>(s_keys + HKEYS);             // HKEYS
+  uint32_t* s_slot_path = reinterpret_cast<uint32_t*>(s_slot_of + HKEYS);        // HKEYS
+  __shared__ int s_tile, s_nslot, s_next;
+  __shared__ uint32_t s_pre[CV_WARPS][33];
 
   for (int i = threadIdx.x; i < SLOTS * MASK_WORDS; i += CV_NT) s_mask[i] = 0u;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  EntrySetup* my = s_ent + wid * 32;
   for (;;) {
     if (threadIdx.x == 0) {
       s_tile = atomicAdd(&counters[2], 1);
@@ -275,22 +436,22 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
     int ox = tx * TILE_UNITS, oy = ty * TILE_UNITS;
     int64_t b0 = off[t], b1 = off[t + 1];
     if (b1 > pair_cap) b1 = pair_cap;
-    int64_t n = b1 > b0 ? b1 - b0 : 0;
-    // valid pixels of this tile (canvas edge)
+    int n = (int)(b1 > b0 ? b1 - b0 : 0);
     int tw = min(TILE_PX, W - tx * TILE_PX), th = min(TILE_PX, H - ty * TILE_PX);
     for (int pass = 0;; ++pass) {
       int slot_lo = pass * SLOTS;
-      for (int64_t c0 = 0; c0 < n; c0 += CHUNK) {
-        int ne = (int)(n - c0 < (int64_t)CHUNK ? n - c0 : (int64_t)CHUNK);
-        // ---- A: per-entry setup
-        uint32_t cnt = 0;
-        if (threadIdx.x < ne) {
-          EntrySetup& E = s_ent[threadIdx.x];
-          E.slot = 0xffff;
-          E.valid = 0;
-          uint32_t r = bin[b0 + c0 + threadIdx.x];
+      if (threadIdx.x == 0) s_next = 0;
+      __syncthreads();
+      for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&s_next, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n) break;
+        int e = base + lane;
+        int cnt = 0;
+        if (e < n) {
+          uint32_t r = bin[b0 + e];
           uint32_t key = (__ldg(tag + r) >> 2) + 1u;
-          // slot of the path (insert on the first pass)
           uint32_t h = (key * 2654435761u) & (HKEYS - 1);
           int slot = -1;
           for (int it = 0; it < HKEYS; ++it) {
@@ -303,10 +464,9 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
               break;
             }
             if (prev == key) {
-              // the inserting thread may not have published the slot yet
               uint16_t so;
               int spin = 0;
-              do {
+              do {  // the inserting lane may not have published the slot yet
                 so = ((volatile uint16_t*)s_slot_of)[h];
               } while (so == 0xffffu && ++spin < (1 << 20));
               slot = so;
@@ -315,106 +475,45 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
             if (prev == 0u) break;
             h = (h + 1) & (HKEYS - 1);
           }
-          QuadFix q;
-          if (slot >= slot_lo && slot < slot_lo + SLOTS &&
-              snap_quad(__ldg(rib + r - 1), __ldg(rib + r), q)) {
-            for (int v = 0; v < 4; ++v) {
-              q.x[v] -= ox;
-              q.y[v] -= oy;
-            }
-            bool v0, v1, big = false;
-            make_edges(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], E.e, v0, big);  // N0 P0 P1
-            make_edges(q.x[0], q.y[0], q.x[3], q.y[3], q.x[2], q.y[2], E.e + 3, v1, big);  // N0 P1 N1
-            E.valid = (v0 ? 1 : 0) | (v1 ? 2 : 0) | (big ? 4 : 0);
-            E.slot = (uint16_t)(slot - slot_lo);
-            // per-row spans over the 5 segments bounding both triangles
-            float fx[4] = {(float)q.x[0], (float)q.x[1], (float)q.x[2], (float)q.x[3]};
-            float fy[4] = {(float)q.y[0], (float)q.y[1], (float)q.y[2], (float)q.y[3]};
-            float ymin = fminf(fminf(fy[0], fy[1]), fminf(fy[2], fy[3]));
-            float ymax = fmaxf(fmaxf(fy[0], fy[1]), fmaxf(fy[2], fy[3]));
-            E.rowpre[0] = 0;
-            for (int ly = 0; ly < TILE_PX; ++ly) {
-              int w = 0;
-              if (ly < th && (v0 || v1)) {
-                // sample rows of pixel row ly: y in [256 ly + 8, 256 ly + 248]; pad 1/256
-                float ylo = 256.f * ly + 7.f, yhi = 256.f * ly + 249.f;
-                if (!(ymax < ylo || ymin > yhi)) {
-                  float xmin = 3.4e38f, xmax = -3.4e38f;
-                  seg_strip(fx[0], fy[0], fx[1], fy[1], ylo, yhi, xmin, xmax);  // N0 P0
-                  seg_strip(fx[1], fy[1], fx[3], fy[3], ylo, yhi, xmin, xmax);  // P0 P1
-                  seg_strip(fx[3], fy[3], fx[2], fy[2], ylo, yhi, xmin, xmax);  // P1 N1
-                  seg_strip(fx[2], fy[2], fx[0], fy[0], ylo, yhi, xmin, xmax);  // N1 N0
-                  seg_strip(fx[0], fy[0], fx[3], fy[3], ylo, yhi, xmin, xmax);  // N0 P1
-                  if (xmax >= xmin) {
-                    // conservative by one pixel on each side of the float extent
-                    int a = (int)floorf((xmin - 248.f) / 256.f), bb = (int)floorf((xmax - 8.f) / 256.f) + 1;
-                    a = max(a, 0);
-                    bb = min(bb, tw - 1);
-                    if (bb >= a) {
-                      w = bb - a + 1;
-                      E.x0[ly] = (uint8_t)a;
-                    }
-                  }
-                }
-              }
-              E.rowpre[ly + 1] = (uint16_t)(E.rowpre[ly] + w);
-            }
-            cnt = E.rowpre[TILE_PX];
-          } else {
-            E.rowpre[TILE_PX] = 0;
-          }
+          if (slot >= slot_lo && slot < slot_lo + SLOTS && slot < HKEYS)
+            cnt = setup_entry(rib, r, slot - slot_lo, ox, oy, tw, th, my[lane]);
         }
-        // block exclusive scan of item counts
+        // warp scan of the pixel counts
         uint32_t x = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
           if (lane >= o) x += y;
         }
-        if (lane == 31) s_wsum[wid] = x;
-        __syncthreads();
-        if (wid == 0) {
-          uint32_t v = lane < CV_NT / 32 ? s_wsum[lane] : 0u;
+        s_pre[wid][lane + 1] = x;
+        if (lane == 0) s_pre[wid][0] = 0;
+        int total = __shfl_sync(0xffffffffu, (int)x, 31);
+        __syncwarp();
+        for (int it = lane; it < total; it += 32) {
+          int lo = 0, hi = 31;  // last entry with pre <= it
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
-          }
-          if (lane < CV_NT / 32) s_wsum[lane] = v;
-          if (lane == CV_NT / 32 - 1) s_total = (int)v;
-        }
-        __syncthreads();
-        if (threadIdx.x < CHUNK) s_pre[threadIdx.x] = x - cnt + (wid > 0 ? s_wsum[wid - 1] : 0u);
-        if (threadIdx.x == 0) s_pre[CHUNK] = 0x7fffffffu;
-        __syncthreads();
-        int total = s_total;
-        // ---- B: items
-        for (int it = threadIdx.x; it < total; it += CV_NT) {
-          int lo = 0, hi = ne - 1;  // last entry with pre <= it
-          while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if ((int)s_pre[mid] <= it) lo = mid; else hi = mid - 1;
-          }
-          const EntrySetup& E = s_ent[lo];
-          int li = it - (int)s_pre[lo];
-          int ly = 0;
-          while ((int)E.rowpre[ly + 1] <= li) ++ly;
-          int lx = E.x0[ly] + (li - (int)E.rowpre[ly]);
-          bool big = (E.valid & 4) != 0;
-          uint32_t m = 0;
-          if (E.valid & 1) m |= tri_pixel_mask(E.e, big, lx, ly);
-          if ((E.valid & 2) && m != 0xffffu) m |= tri_pixel_mask(E.e + 3, big, lx, ly);
+          for (int st = 16; st > 0; st >>= 1)
+            if (lo + st <= hi && (int)s_pre[wid][lo + st] <= it) lo += st;
+          const EntrySetup& E = my[lo];
+          int li = it - (int)s_pre[wid][lo];
+          int k = 0;  // row: the last one with rowpre[k] <= li
+#pragma unroll
+          for (int st = 8; st > 0; st >>= 1)
+            if ((int)E.rowpre[k + st] <= li) k += st;
+          int ly = E.row0 + k, lx = E.x0[k] + (li - (int)E.rowpre[k]);
+          uint32_t m = pixel_mask(E, lx, ly);
           if (m) {
             int lp = ly * TILE_PX + lx;
             atomicOr(&s_mask[E.slot * MASK_WORDS + (lp >> 1)], m << (16 * (lp & 1)));
           }
         }
-        __syncthreads();
+        __syncwarp();
       }
-      // ---- C: popcounts and canvas for this pass's slots
+      __syncthreads();
+      // per-path popcounts and the canvas for this pass's slots
       int nslot = min(s_nslot, HKEYS);
       int nhere = min(SLOTS, nslot - slot_lo);
-      for (int s2 = wid; s2 < nhere; s2 += CV_NT / 32) {
+      for (int s2 = wid; s2 < nhere; s2 += CV_WARPS) {
         unsigned c = 0;
         for (int w = lane; w < MASK_WORDS; w += 32) c += __popc(s_mask[s2 * MASK_WORDS + w]);
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
@@ -425,39 +524,30 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
       }
       for (int w = threadIdx.x; w < MASK_WORDS; w += CV_NT) {
         uint32_t v = 0;
-        for (int s2 = 0; s2 < nhere; ++s2) {
-          v |= s_mask[s2 * MASK_WORDS + w];
-        }
+        for (int s2 = 0; s2 < nhere; ++s2) v |= s_mask[s2 * MASK_WORDS + w];
         int lp = 2 * w;
         int py = ty * TILE_PX + lp / TILE_PX, px = tx * TILE_PX + lp % TILE_PX;
         if (py < H) {
-          // later passes OR into what earlier passes wrote
-          uint32_t prevv = 0;
-          if (pass > 0) {
-            if (px < W) prevv |= canvas[(int64_t)py * W + px];
-            if (px + 1 < W) prevv |= (uint32_t)canvas[(int64_t)py * W + px + 1] << 16;
+          if (pass > 0) {  // later passes OR into what earlier passes wrote
+            if (px < W) v |= canvas[(int64_t)py * W + px];
+            if (px + 1 < W) v |= (uint32_t)canvas[(int64_t)py * W + px + 1] << 16;
           }
-          v |= prevv;
           if (px < W) canvas[(int64_t)py * W + px] = (uint16_t)(v & 0xffffu);
           if (px + 1 < W) canvas[(int64_t)py * W + px + 1] = (uint16_t)(v >> 16);
         }
       }
       __syncthreads();
       for (int i = threadIdx.x; i < nhere * MASK_WORDS; i += CV_NT) s_mask[i] = 0u;
+      if (threadIdx.x == 0 && s_nslot > HKEYS) ps_record_error(status, PS_ERR_CAPACITY);
       __syncthreads();
-      if (nslot > HKEYS) {
-        if (threadIdx.x == 0) ps_record_error(status, PS_ERR_CAPACITY);
-      }
       if (slot_lo + SLOTS >= nslot) break;
     }
-    __syncthreads();
   }
 }
 
 size_t coverage_smem_bytes() {
-  return sizeof(uint32_t) * SLOTS * MASK_WORDS + sizeof(EntrySetup) * CHUNK +
-         sizeof(uint32_t) * HKEYS + sizeof(uint16_t) * HKEYS + sizeof(uint32_t) * HKEYS +
-         sizeof(uint32_t) * (CHUNK + 1);
+  return sizeof(uint32_t) * SLOTS * MASK_WORDS + sizeof(EntrySetup) * CV_NT +
+         sizeof(uint32_t) * HKEYS + sizeof(uint16_t) * HKEYS + sizeof(uint32_t) * HKEYS;
 }
 
 }  // namespace

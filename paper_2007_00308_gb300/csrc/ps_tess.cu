@@ -782,53 +782,60 @@ struct RibEval {
 };
 
 template <bool MIXED>
-__device__ __forceinline__ RibEval eval_rib(const LinkRec& L, int j) {
+__device__ __forceinline__ RibEval eval_rib(const LinkRec* __restrict__ L, int j) {
+  // fields are read where needed (L1-cached) instead of copying the record
   RibEval R;
-  uint32_t meta = L.meta;
+  uint32_t meta = __ldg(&L->meta);
   int kind = META_KIND(meta);
   int M = META_M(meta);
+  float4 p01 = __ldg(reinterpret_cast<const float4*>(L->P));
+  float rN = __ldg(&L->rN), rP = __ldg(&L->rP);
   if (kind == LK_SEG) {
     Seg g;
+    float4 p23 = __ldg(reinterpret_cast<const float4*>(L->P) + 1);
     g.type = META_TYPE(meta);
-    g.A = L.P[0]; g.B = L.P[1]; g.C = L.P[2]; g.D = L.P[3];
-    g.w = L.w;
+    g.A = mk(p01.x, p01.y); g.B = mk(p01.z, p01.w); g.C = mk(p23.x, p23.y); g.D = mk(p23.z, p23.w);
+    g.w = __ldg(&L->w);
     int k = 0;
-    while (k < M && j >= (int)L.dsum[k + 1]) ++k;
+    while (k < M && j >= (int)__ldg(&L->dsum[k + 1])) ++k;
     // k == M only for j == N; boundary when j == dsum[k]
     float t, psi;
-    if (j == (int)L.dsum[k]) {
-      t = L.p[k];
-      psi = L.psi[k];
+    int dk = (int)__ldg(&L->dsum[k]);
+    if (j == dk) {
+      t = __ldg(&L->p[k]);
+      psi = __ldg(&L->psi[k]);
     } else {
-      psi = L.psi[k] + L.step[k] * (float)(j - (int)L.dsum[k]);
-      if (META_PIVOT(meta, k)) t = L.p[k];
-      else t = solve_t<MIXED>(g, psi, L.p[k], L.p[k + 1]);
+      psi = __ldg(&L->psi[k]) + __ldg(&L->step[k]) * (float)(j - dk);
+      float pa = __ldg(&L->p[k]);
+      if (META_PIVOT(meta, k)) t = pa;
+      else t = solve_t<MIXED>(g, psi, pa, __ldg(&L->p[k + 1]));
     }
     float sn, cs;
     sincosf(psi, &sn, &cs);
     float2 n = mk(-sn, cs);
     float2 gr = MIXED ? g_rel_comp(g, t) : g_rel(g, t);
-    float2 Nv = gr - n * L.rN, Pv = gr + n * L.rP;
+    float2 Nv = gr - n * rN, Pv = gr + n * rP;
     R.v = make_float4(g.A.x + Nv.x, g.A.y + Nv.y, g.A.x + Pv.x, g.A.y + Pv.y);
     R.grel = gr;
     R.t = t;
     R.seg = true;
   } else {
-    int J = (int)L.dsum[1];
-    float psi = (j == J) ? L.psi[1] : L.psi[0] + L.step[0] * (float)j;
+    int J = (int)__ldg(&L->dsum[1]);
+    float psi = (j == J) ? __ldg(&L->psi[1]) : __ldg(&L->psi[0]) + __ldg(&L->step[0]) * (float)j;
     float sn, cs;
     sincosf(psi, &sn, &cs);
     float2 n = mk(-sn, cs);
-    float rn = L.rN, rp = L.rP;
+    float rn = rN, rp = rP;
     if ((meta & META_FLAG_SQUARE) && (j == 1 || j == 3)) {
       rn *= 1.41421356237309515f;
       rp *= 1.41421356237309515f;
     }
-    float2 at = L.P[0];
+    float2 at = mk(p01.x, p01.y);
     float2 Nv = at - n * rn, Pv = at + n * rp;
     if ((meta & META_FLAG_OVERRIDE) && (j == 1 || j == 2)) {
-      float2 v = j == 1 ? L.v1 : L.v2;
-      if (L.rN > 0.f) Nv = v; else Pv = v;
+      float4 vv = __ldg(reinterpret_cast<const float4*>(&L->v1));
+      float2 v = j == 1 ? mk(vv.x, vv.y) : mk(vv.z, vv.w);
+      if (rN > 0.f) Nv = v; else Pv = v;
     }
     R.v = make_float4(Nv.x, Nv.y, Pv.x, Pv.y);
     R.grel = mk(0.f, 0.f);
@@ -885,8 +892,7 @@ __global__ void __launch_bounds__(EMIT_NT) k_emit(
       if (active) {
         l = find_link(link_off, l0, l1, r);
         j = (int)(r - __ldg(link_off + l));
-        LinkRec L = recs[l];
-        E = eval_rib<MIXED>(L, j);
+        E = eval_rib<MIXED>(recs + l, j);
         rib[r] = E.v;
         uint32_t p = (uint32_t)__ldg(link_path + l);
         tag[r] = (p << 2) | (E.seg ? PS_TAG_SEGMENT : 0u) | (j == 0 ? PS_TAG_LINK_START : 0u);
@@ -915,8 +921,7 @@ __global__ void __launch_bounds__(EMIT_NT) k_emit(
               have = true;
             }
             if (!have) {
-              LinkRec L = recs[l];
-              RibEval Ep = eval_rib<MIXED>(L, j - 1);
+              RibEval Ep = eval_rib<MIXED>(recs + l, j - 1);
               pg = Ep.grel;
               pt = Ep.t;
             }
@@ -958,7 +963,9 @@ __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
     const int64_t* __restrict__ n_rib, int64_t capacity, float* __restrict__ s_out,
     float* __restrict__ path_len, uint32_t* tflag, double* tagg, double* tincl,
     int32_t* counters, int32_t* status) {
-  __shared__ double sv[SCAN_NT / 32];
+  // Within a tile (2048 ribs) sums are FP32 (relative error ~1e-6 of s); the
+  // carry between tiles, which runs over a whole path, is FP64.
+  __shared__ float sv[SCAN_NT / 32];
   __shared__ int sh[SCAN_NT / 32];
   __shared__ double s_carry;
   __shared__ int s_tile;
@@ -975,32 +982,34 @@ __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
     float c[SCAN_IPT];
     uint32_t pth[SCAN_IPT];
     bool head[SCAN_IPT];
-    double acc = 0.0;
+    float acc = 0.f;
     bool th = false;
+    uint32_t prevp = base > 0 && base <= R ? (tag[base - 1] >> 2) : 0xffffffffu;
+#pragma unroll
     for (int i = 0; i < SCAN_IPT; ++i) {
       int64_t r = base + i;
       if (r < R) {
         c[i] = chord_in[r];
         pth[i] = tag[r] >> 2;
-        head[i] = (r == 0) || ((tag[r - 1] >> 2) != pth[i]);
+        head[i] = (r == 0) || (prevp != pth[i]);
+        prevp = pth[i];
       } else {
         c[i] = 0.f;
         pth[i] = 0xffffffffu;
         head[i] = false;
       }
       if (head[i]) {
-        acc = 0.0;
+        acc = 0.f;
         th = true;
       }
-      acc += (double)c[i];
+      acc += c[i];
     }
-    // segmented warp scan of (th, acc)
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double v = acc;
+    float v = acc;
     int h = th;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      double vy = __shfl_up_sync(0xffffffffu, v, o);
+      float vy = __shfl_up_sync(0xffffffffu, v, o);
       int hy = __shfl_up_sync(0xffffffffu, h, o);
       if (lane >= o) {
         if (!h) v += vy;
@@ -1012,44 +1021,47 @@ __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
       sh[wid] = h;
     }
     __syncthreads();
-    // exclusive carry from earlier warps of the block
-    double wcarry = 0.0;
+    float wcarry = 0.f;
     int whead = 0;
     for (int w = wid - 1; w >= 0; --w) {
       wcarry += sv[w];
       if (sh[w]) { whead = 1; break; }
     }
-    double tile_v = 0.0;
-    int tile_h = 0;
-    for (int w = SCAN_NT / 32 - 1; w >= 0; --w) {
-      tile_v += sv[w];
-      if (sh[w]) { tile_h = 1; break; }
-    }
-    for (int w = 0; w < SCAN_NT / 32; ++w) tile_h |= sh[w];
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
+      double tile_v = 0.0;
+      int tile_h = 0;
+      for (int w = SCAN_NT / 32 - 1; w >= 0; --w) {
+        tile_v += (double)sv[w];
+        if (sh[w]) { tile_h = 1; break; }
+      }
+      for (int w = 0; w < SCAN_NT / 32; ++w) tile_h |= sh[w];
       s_carry = lookback_segsum(tflag, tagg, tincl, tile_v, tile_h != 0, tile, status);
+    }
     __syncthreads();
-    // exclusive prefix for this thread = inclusive(v,h) of lane-1 ...
-    double vprev = __shfl_up_sync(0xffffffffu, v, 1);
+    float vprev = __shfl_up_sync(0xffffffffu, v, 1);
     int hprev = __shfl_up_sync(0xffffffffu, h, 1);
     if (lane == 0) {
-      vprev = 0.0;
+      vprev = 0.f;
       hprev = 0;
     }
-    double run;
-    if (hprev) run = vprev;
-    else {
-      run = vprev + wcarry;
-      if (!whead) run += s_carry;
-    }
+    // ribs before this thread's first head continue the running total
+    float carry_f = hprev ? vprev : vprev + wcarry;
+    float tile_carry = (hprev || whead) ? 0.f : (float)s_carry;
+    float run = carry_f;
+    bool after_head = false;
+#pragma unroll
     for (int i = 0; i < SCAN_IPT; ++i) {
       int64_t r = base + i;
       if (r >= R) break;
-      if (head[i]) run = 0.0;
-      run += (double)c[i];
-      s_out[r] = (float)run;
+      if (head[i]) {
+        run = 0.f;
+        after_head = true;
+      }
+      run += c[i];
+      float sv_out = after_head ? run : tile_carry + run;
+      s_out[r] = sv_out;
       bool last = (r == R - 1) || ((tag[r + 1] >> 2) != pth[i]);
-      if (last && path_len) path_len[pth[i]] = (float)run;
+      if (last && path_len) path_len[pth[i]] = sv_out;
     }
     __syncthreads();
   }
