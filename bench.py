@@ -169,18 +169,33 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
-# Algorithmic bytes per unit of each kernel (what the method must move).
+# Algorithmic work per launch of each kernel: bytes the method must move for
+# the HBM-class kernels; sample tests for the coverage kernel (ALU-bound).
+# Per unit: link setup reads 40 B/segment + 24 B/path and writes a 160 B record
+# + 4 B offset per link; the emitter writes 16 B rib + 4 B tag + 4 B chord per
+# rib and reads its link's record (168 B/link); the arc-length scan reads
+# chord + tag and writes s (12 B/rib); binning reads a quad (two ribs, shared
+# with the next quad: 16 B/rib + 4 B tag) per pass and the scatter writes 4 B
+# per bin entry; coverage tests 16 samples per span pixel.
 def algorithmic(kernel, c):
     R, L, S, P, pairs, px = c["R"], c["L"], c["S"], c["P"], c["pairs"], c["px"]
     table = {
         "k_link_setup": ("hbm", 40 * S + 24 * P + (160 + 4) * L),
-        "k_emit": ("hbm", 24 * R + (160 + 4 + 4) * L),
-        "k_arclen_scan": ("hbm", 12 * R + 4 * P),
+        "k_emit": ("hbm", 24 * R + 168 * L),
+        "k_arclen_scan": ("hbm", 12 * R),
         "k_bin_count": ("hbm", 20 * R),
         "k_bin_scatter": ("hbm", 20 * R + 4 * pairs),
-        "k_coverage": ("hbm", 40 * pairs + 2 * px + 8 * P),
+        "k_coverage": ("alu", 16 * c["span_px"]),
     }
     return table.get(kernel)
+
+
+# ALU peak for the coverage kernel: one sample test evaluates, per edge, a
+# multiply-add and a compare; a quad has 4 edges when convex, 6 when drawn as
+# two triangles: 12 lane operations per sample test (upper figure).  Lane
+# operations per second = 152 SMs x 128 lanes x SM clock.
+def alu_peak_tests(sm_mhz):
+    return 152 * 128 * sm_mhz * 1e6 / 12.0
 
 
 def run_ours(args, rank, world, local_rank):
@@ -281,18 +296,40 @@ def run_ours(args, rank, world, local_rank):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     kmean = {k: statistics.mean(v) for k, v in kern.items()}
     dom = max(kmean, key=kmean.get)
-    n_tile = ((Wd + 15) // 16) * ((Ht + 15) // 16)
+    pairs, span_px = ps.ps_raster_stats(ctx)
     counts = {"R": R_now, "L": db.n_link, "S": segs, "P": db.n_path, "px": Wd * Ht,
-              "pairs": int(ps_bin_pairs(ctx, ps, n_tile))}
-    alg = algorithmic(dom, counts)
-    roof = None
-    if alg:
-        bound, nbytes = alg
-        achieved = nbytes / (kmean[dom] * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+              "pairs": pairs, "span_px": span_px}
+    sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    kernels = {}
+    for k, ms in kmean.items():
+        alg = algorithmic(k, counts)
+        if not alg:
+            kernels[k] = {"ms": ms}
+            continue
+        bound, work = alg
+        if bound == "hbm":
+            ach = work / (ms * 1e-3) / 1e9
+            kernels[k] = {"ms": ms, "bound": "hbm", "algorithmic_bytes": work,
+                          "achieved_gbs": ach, "frac": ach / hbm_peak}
+        else:
+            ach = work / (ms * 1e-3) / 1e9
+            pk = alu_peak_tests(sm_mhz) / 1e9
+            kernels[k] = {"ms": ms, "bound": "alu", "sample_tests": work,
+                          "achieved_gtests": ach, "peak_gtests": pk, "frac": ach / pk}
+    kd = kernels[dom]
+    if kd.get("bound") == "alu":
+        roof = {"kernel": dom, "bound": "alu", "achieved": kd["achieved_gtests"],
+                "peak": kd["peak_gtests"], "unit": "Gsample-tests/s", "frac": kd["frac"],
+                "traffic": None,
+                "peak_source": f"derived: 152 SMs x 128 lanes x {sm_mhz:.0f} MHz / 12 lane ops per test",
+                "algorithmic_work": kd["sample_tests"]}
+    elif kd.get("bound") == "hbm":
+        roof = {"kernel": dom, "bound": "hbm", "achieved": kd["achieved_gbs"], "peak": hbm_peak,
+                "unit": "GB/s", "frac": kd["frac"], "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
-                "algorithmic_bytes": nbytes}
+                "algorithmic_bytes": kd["algorithmic_bytes"]}
+    else:
+        roof = None
 
     # end to end through the C ABI with host buffers
     e2e = run_e2e(args, ps, batch, ctx, db, out, canvas, covered, prec, dev)
@@ -312,6 +349,8 @@ def run_ours(args, rank, world, local_rank):
         "covered_samples_per_s": world * cov_samples / (ms_per_step * 1e-3),
         "covered_samples": cov_samples,
         "kernel_ms": kmean,
+        "kernels": kernels,
+        "raster_work": {"bin_entries": pairs, "span_pixels": span_px},
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": 8 * args.steps,
@@ -323,11 +362,6 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         print(json.dumps(line))
     return 0
-
-
-def ps_bin_pairs(ctx, ps, n_tile):
-    """Total raster bin entries of the last step (read from the context's workspace)."""
-    return ps.ps_raster_pair_count(ctx)
 
 
 def run_e2e(args, ps, batch, ctx, db, out, canvas, covered, prec, dev):

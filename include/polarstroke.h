@@ -246,9 +246,10 @@ int ps_profile_enable(ps_context* ctx, int enable);
 int ps_profile_read(ps_context* ctx, float* h_ms /* [PS_PROF_SLOTS] */);
 const char* ps_profile_slot_name(int slot);
 
-/* Number of (quad, tile) bin entries of the context's most recent
- * ps_rasterize_coverage call, read from its device workspace.  SYNCHRONIZES. */
-int ps_raster_pair_count(ps_context* ctx, int64_t* h_pairs);
+/* Work counts of the context's most recent ps_rasterize_coverage call, read from
+ * its device workspace: (quad, tile) bin entries, and the pixels of the per-row
+ * spans the coverage kernel tested (16 samples each).  SYNCHRONIZES. */
+int ps_raster_stats(ps_context* ctx, int64_t* h_pairs, int64_t* h_span_pixels);
 
 #ifdef __cplusplus
 }

@@ -60,6 +60,9 @@ def _load():
             _lib.orc_tessellate.argtypes = [I64, P, P, P, I32, P, P, P, P, P, P, D, P, P, I64, P, P,
                                             P, P, P, P, P, P]
             _lib.orc_tessellate.restype = ctypes.c_int
+            _lib.orc_tessellate_f64.argtypes = [I64, P, P, P, I32, P, P, P, P, P, P, D, P, P, I64,
+                                                P, P, P, P, P, P, P, P]
+            _lib.orc_tessellate_f64.restype = ctypes.c_int
             _lib.orc_segment_intervals.argtypes = [ctypes.c_int, P, ctypes.c_float, D, P, P, P, P, P, P]
             _lib.orc_segment_intervals.restype = ctypes.c_int
             _lib.orc_segment_probe.argtypes = [ctypes.c_int, P, ctypes.c_float, ctypes.c_int, ctypes.c_int, P, P]
@@ -86,20 +89,22 @@ class OracleError(RuntimeError):
     pass
 
 
-def tessellate(batch, dtheta=None):
+def tessellate(batch, dtheta=None, seg_pts64=None, width64=None):
     """Tessellate every path of ``batch`` (FP64).  Returns a dict of numpy arrays:
     link_nrib[L], link_info[L], rib[R,4], s[R], t[R], psi[R], rho[R], tag[R],
-    path_len[P], link_rib_off[L+1], path_rib_off[P+1]."""
+    path_len[P], link_rib_off[L+1], path_rib_off[P+1].
+    seg_pts64 / width64 (optional) replace the batch's FP32 control points /
+    widths with FP64 values (finite differences)."""
     lib = _load()
     q = float(np.float32(batch.dtheta if dtheta is None else dtheta))
     st = _c(batch.seg_type, np.uint8)
-    sp = _c(batch.seg_pts, np.float32).reshape(-1)
-    sw = _c(batch.seg_w, np.float32)
+    sp = _c(batch.seg_pts if seg_pts64 is None else seg_pts64, np.float64).reshape(-1)
+    sw = _c(batch.seg_w, np.float64)
     off = _c(batch.path_seg_off, np.int32)
-    pw = _c(batch.path_width, np.float32)
+    pw = _c(batch.path_width if width64 is None else width64, np.float64)
     pj = _c(batch.path_join, np.uint8)
     pc = _c(batch.path_cap, np.uint8)
-    pm = _c(batch.path_miter, np.float32)
+    pm = _c(batch.path_miter, np.float64)
     pcl = _c(batch.path_closed, np.uint8)
     S, P = len(st), len(pw)
     L = 2 * S + P
@@ -107,8 +112,8 @@ def tessellate(batch, dtheta=None):
     link_info = np.zeros(L, np.uint8)
     total = ctypes.c_int64(0)
     args = (S, _p(st), _p(sp), _p(sw), P, _p(off), _p(pw), _p(pj), _p(pc), _p(pm), _p(pcl), q)
-    rc = lib.orc_tessellate(*args, _p(link_nrib), _p(link_info), 0, None, None, None, None, None,
-                            None, None, ctypes.byref(total))
+    rc = lib.orc_tessellate_f64(*args, _p(link_nrib), _p(link_info), 0, None, None, None, None,
+                                None, None, None, ctypes.byref(total))
     if rc not in (0, -2):
         raise OracleError(f"orc_tessellate count failed: {rc}")
     R = int(total.value)
@@ -119,8 +124,8 @@ def tessellate(batch, dtheta=None):
     rho = np.zeros(R, np.float64)
     tag = np.zeros(R, np.uint32)
     plen = np.zeros(P, np.float64)
-    rc = lib.orc_tessellate(*args, _p(link_nrib), _p(link_info), R, _p(rib), _p(s), _p(t),
-                            _p(psi), _p(rho), _p(tag), _p(plen), ctypes.byref(total))
+    rc = lib.orc_tessellate_f64(*args, _p(link_nrib), _p(link_info), R, _p(rib), _p(s), _p(t),
+                                _p(psi), _p(rho), _p(tag), _p(plen), ctypes.byref(total))
     if rc != 0:
         raise OracleError(f"orc_tessellate failed: {rc}")
     link_off = np.zeros(L + 1, np.int64)

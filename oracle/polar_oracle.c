@@ -566,15 +566,15 @@ typedef struct {
   double miter_limit;
 } Link;
 
-static Seg load_seg(int64_t i, const uint8_t* type, const float* pts, const float* wts) {
+static Seg load_seg(int64_t i, const uint8_t* type, const double* pts, const double* wts) {
   Seg g;
   g.type = type[i];
-  const float* q = pts + 8 * i;
+  const double* q = pts + 8 * i;
   g.A = mk(q[0], q[1]);
   g.B = mk(q[2], q[3]);
   g.C = mk(q[4], q[5]);
   g.D = mk(q[6], q[7]);
-  g.w = wts ? (double)wts[i] : 1.0;
+  g.w = wts ? wts[i] : 1.0;
   return g;
 }
 
@@ -671,13 +671,14 @@ static void emit_pivot(const Link* L, int J, double r, V2* Nv, V2* Pv, double* p
  *   tag[R]         link start / segment bits and path index
  *   path_len[P]    total arc length per path
  */
-int orc_tessellate(int64_t n_seg, const uint8_t* seg_type, const float* seg_pts,
-                   const float* seg_w, int32_t n_path, const int32_t* path_seg_off,
-                   const float* path_width, const uint8_t* path_join, const uint8_t* path_cap,
-                   const float* path_miter, const uint8_t* path_closed, double q,
-                   int64_t* link_nrib, uint8_t* link_info, int64_t rib_cap, double* rib,
-                   double* s_out, double* t_out, double* psi_out, double* rho_out,
-                   uint32_t* tag_out, double* path_len, int64_t* n_rib_total) {
+int orc_tessellate_f64(int64_t n_seg, const uint8_t* seg_type, const double* seg_pts,
+                       const double* seg_w, int32_t n_path, const int32_t* path_seg_off,
+                       const double* path_width, const uint8_t* path_join,
+                       const uint8_t* path_cap, const double* path_miter,
+                       const uint8_t* path_closed, double q, int64_t* link_nrib,
+                       uint8_t* link_info, int64_t rib_cap, double* rib, double* s_out,
+                       double* t_out, double* psi_out, double* rho_out, uint32_t* tag_out,
+                       double* path_len, int64_t* n_rib_total) {
   if (!(q > 0.0) || n_seg < 0 || n_path < 0) return ORC_ERR_INVALID;
   int64_t R = 0;
   int overflow = 0;
@@ -689,7 +690,7 @@ int orc_tessellate(int64_t n_seg, const uint8_t* seg_type, const float* seg_pts,
     int32_t s0 = path_seg_off[p], s1 = path_seg_off[p + 1];
     int n = s1 - s0;
     if (n < 0 || s0 < 0 || s1 > n_seg) return ORC_ERR_INVALID;
-    double r = 0.5 * (double)path_width[p];
+    double r = 0.5 * path_width[p];
     int closed = path_closed ? path_closed[p] : 0;
     int64_t lbase = 2 * (int64_t)s0 + p;
     double s_run = 0.0;
@@ -760,7 +761,7 @@ int orc_tessellate(int64_t n_seg, const uint8_t* seg_type, const float* seg_pts,
         }
       }
       if (L.kind == 2 && L.delta == -PI) L.delta = PI;
-      L.miter_limit = path_miter ? (double)path_miter[p] : 4.0;
+      L.miter_limit = path_miter ? path_miter[p] : 4.0;
 
       int nrib = 0;
       uint8_t info = 0;
@@ -863,6 +864,32 @@ int orc_tessellate(int64_t n_seg, const uint8_t* seg_type, const float* seg_pts,
   }
   if (n_rib_total) *n_rib_total = R;
   return overflow ? ORC_ERR_CAPACITY : ORC_OK;
+}
+
+/* The library's FP32 input layout: converted exactly to FP64 and tessellated. */
+int orc_tessellate(int64_t n_seg, const uint8_t* seg_type, const float* seg_pts,
+                   const float* seg_w, int32_t n_path, const int32_t* path_seg_off,
+                   const float* path_width, const uint8_t* path_join, const uint8_t* path_cap,
+                   const float* path_miter, const uint8_t* path_closed, double q,
+                   int64_t* link_nrib, uint8_t* link_info, int64_t rib_cap, double* rib,
+                   double* s_out, double* t_out, double* psi_out, double* rho_out,
+                   uint32_t* tag_out, double* path_len, int64_t* n_rib_total) {
+  double* pts = (double*)malloc(sizeof(double) * (size_t)(8 * n_seg + 1));
+  double* w = (double*)malloc(sizeof(double) * (size_t)(n_seg + 1));
+  double* wid = (double*)malloc(sizeof(double) * (size_t)(n_path + 1));
+  double* mit = (double*)malloc(sizeof(double) * (size_t)(n_path + 1));
+  if (!pts || !w || !wid || !mit) { free(pts); free(w); free(wid); free(mit); return ORC_ERR_INVALID; }
+  for (int64_t i = 0; i < 8 * n_seg; ++i) pts[i] = seg_pts[i];
+  for (int64_t i = 0; i < n_seg; ++i) w[i] = seg_w ? seg_w[i] : 1.0;
+  for (int32_t p = 0; p < n_path; ++p) {
+    wid[p] = path_width[p];
+    mit[p] = path_miter ? path_miter[p] : 4.0;
+  }
+  int rc = orc_tessellate_f64(n_seg, seg_type, pts, w, n_path, path_seg_off, wid, path_join,
+                              path_cap, mit, path_closed, q, link_nrib, link_info, rib_cap, rib,
+                              s_out, t_out, psi_out, rho_out, tag_out, path_len, n_rib_total);
+  free(pts); free(w); free(wid); free(mit);
+  return rc;
 }
 
 /* Interval table of one segment (for tests). Returns M; fills p, Psi, delta,
@@ -1110,7 +1137,10 @@ int orc_centreline_distance(int64_t n_seg, const uint8_t* seg_type, const float*
   if (!dense) return ORC_ERR_INVALID;
   Seg* segs = (Seg*)malloc(sizeof(Seg) * (size_t)(n_seg ? n_seg : 1));
   for (int64_t i = 0; i < n_seg; ++i) {
-    segs[i] = load_seg(i, seg_type, seg_pts, seg_w);
+    double q8[8];
+    for (int c = 0; c < 8; ++c) q8[c] = seg_pts[8 * i + c];
+    double wi = seg_w ? (double)seg_w[i] : 1.0;
+    segs[i] = load_seg(0, seg_type + i, q8, &wi);
     for (int m = 0; m <= n_dense; ++m)
       dense[i * (n_dense + 1) + m] = seg_eval(&segs[i], (double)m / n_dense);
   }

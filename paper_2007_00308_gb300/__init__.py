@@ -23,7 +23,7 @@ TAG_LINK_START, TAG_SEGMENT = 1, 2
 EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_status",
            "ps_error_string", "ps_tessellate_strokes", "ps_count_ribs_sync", "ps_arclength_scan",
            "ps_dash", "ps_rasterize_coverage", "ps_profile_enable", "ps_profile_read",
-           "ps_profile_slot_name", "ps_raster_pair_count", "ps_tessellate_strokes_noalloc"]
+           "ps_profile_slot_name", "ps_raster_stats", "ps_tessellate_strokes_noalloc"]
 PS_PROF_SLOTS = 10
 
 
@@ -87,7 +87,7 @@ def lib():
         L.ps_profile_read.argtypes = [P, P]
         L.ps_profile_slot_name.argtypes = [ctypes.c_int]
         L.ps_profile_slot_name.restype = ctypes.c_char_p
-        L.ps_raster_pair_count.argtypes = [P, ctypes.POINTER(I64)]
+        L.ps_raster_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
         L.ps_tessellate_strokes_noalloc.argtypes = [ctypes.POINTER(_Segments),
                                                     ctypes.POINTER(_Paths), ctypes.c_float,
                                                     ctypes.c_int, ctypes.c_uint32,
@@ -209,10 +209,11 @@ class TessOutput:
                         p(self.path_rib_off), p(self.path_len), p(self.n_rib), self.capacity)
 
 
-def ps_raster_pair_count(ctx: Context) -> int:
-    n = ctypes.c_int64(0)
-    _check(lib().ps_raster_pair_count(ctx.handle, ctypes.byref(n)), "ps_raster_pair_count")
-    return n.value
+def ps_raster_stats(ctx: Context):
+    """(bin entries, span pixels) of the context's most recent raster call."""
+    n, sp = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().ps_raster_stats(ctx.handle, ctypes.byref(n), ctypes.byref(sp)), "ps_raster_stats")
+    return n.value, sp.value
 
 
 def ps_max_ribs(n_seg, n_path, dtheta) -> int:

@@ -91,7 +91,7 @@ extern "C" void ps_destroy(ps_context* ctx) {
   void* ptrs[] = {ctx->d_status, ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
                   ctx->d_tile_aggd, ctx->d_tile_incld, ctx->d_counters, ctx->d_recs,
                   ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor, ctx->d_bin,
-                  ctx->d_scratch64, ctx->d_mask_scratch};
+                  ctx->d_scratch64, ctx->d_mask_scratch, ctx->d_adj};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free(ctx);

@@ -45,6 +45,9 @@ static_assert(sizeof(LinkRec) == 160, "LinkRec layout");
 #define META_STYLE(m) (((m) >> 16) & 15u)
 #define META_FLAG_OVERRIDE (1u << 20)  // ribs 1,2 outer vertex = v1, v2 (miter)
 #define META_FLAG_SQUARE (1u << 21)    // square cap: ribs 1,3 outer radius * sqrt(2)
+// interior boundary k (1..6) is a split point (Sec. 3.3.5) rather than an inflection
+#define META_SPLIT_BIT(k) (1u << (21 + (k)))
+#define META_SPLIT(m, k) (((m) >> (21 + (k))) & 1u)
 
 // Profiling slots (one per kernel).
 enum {
@@ -83,6 +86,8 @@ struct ps_context {
   int64_t last_n_tile;      // tiles of the most recent raster call
   uint32_t* d_mask_scratch; // per-CTA per-path tile masks beyond shared memory
   size_t d_scratch_words;
+  void* d_adj;              // adjoint workspace
+  size_t adj_bytes;
   int num_sms;
 };
 
@@ -213,6 +218,15 @@ int ps_ensure_recs(ps_context* ctx, int64_t n_link);
 int ps_ensure_raster(ps_context* ctx, int64_t n_tile, int64_t n_pair);
 int ps_cuda_check(cudaError_t e);
 int ps_persistent_grid(ps_context* ctx, const void* kernel, int block, size_t smem);
+// Link setup (records in ctx->d_recs, link path indices after them) into the given
+// offset arrays; used by the adjoint to rebuild the forward's interval records.
+int ps_run_link_setup(ps_context* ctx, const ps_segments* seg, const ps_paths* paths, float dtheta,
+                      int precision, int32_t* d_link_off, int32_t* d_path_off, int64_t* d_n_rib,
+                      cudaStream_t st);
+// Segmented (by path) inclusive prefix of per-rib values, in place, with per-path totals.
+int ps_run_segmented_prefix(ps_context* ctx, float* d_vals, const uint32_t* d_tag,
+                            const int64_t* d_n_rib, int64_t capacity, float* d_path_tot,
+                            int32_t n_path, cudaStream_t st);
 void ps_prof_mark(ps_context* ctx, int slot, int end, cudaStream_t st);
 struct ProfScope {
   ps_context* c;

@@ -407,7 +407,8 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
     const float4* __restrict__ rib, const uint32_t* __restrict__ tag,
     const int32_t* __restrict__ off, const uint32_t* __restrict__ bin, int64_t pair_cap, int W,
     int H, int tiles_x, int n_tile, uint16_t* __restrict__ canvas,
-    unsigned long long* __restrict__ covered, int n_path, int32_t* counters, int32_t* status) {
+    unsigned long long* __restrict__ covered, int n_path, int32_t* counters, int32_t* status,
+    unsigned long long* __restrict__ stats) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem);                          // SLOTS*MASK_WORDS
   EntrySetup* s_ent = reinterpret_cast<EntrySetup*>(s_mask + SLOTS * MASK_WORDS);  // CV_NT
@@ -488,6 +489,7 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
         s_pre[wid][lane + 1] = x;
         if (lane == 0) s_pre[wid][0] = 0;
         int total = __shfl_sync(0xffffffffu, (int)x, 31);
+        if (lane == 0 && stats) atomicAdd(stats, (unsigned long long)total);
         __syncwarp();
         for (int it = lane; it < total; it += 32) {
           int lo = 0, hi = 31;  // last entry with pre <= it
@@ -583,6 +585,7 @@ extern "C" int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const 
   cudaMemsetAsync(ctx->d_tile_count, 0, sizeof(int32_t) * (n_tile + 1), st);
   cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
   cudaMemsetAsync(d_covered, 0, sizeof(uint64_t) * (size_t)n_path, st);
+  cudaMemsetAsync(ctx->d_scratch64, 0, sizeof(int64_t), st);
   int grid_bin = ps_persistent_grid(ctx, (const void*)k_bin<0>, 256, 0);
   const float4* rib = reinterpret_cast<const float4*>(d_rib);
   { ProfScope ps_(ctx, PK_BIN_COUNT, st);
@@ -600,19 +603,25 @@ extern "C" int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const 
   k_coverage<<<grid_cov, CV_NT, cov_smem, st>>>(
       rib, d_tag, ctx->d_tile_off, ctx->d_bin, ctx->pair_cap, width, height, tiles_x, (int)n_tile,
       d_canvas, reinterpret_cast<unsigned long long*>(d_covered), n_path, ctx->d_counters,
-      ctx->d_status); }
+      ctx->d_status, reinterpret_cast<unsigned long long*>(ctx->d_scratch64)); }
   return ps_cuda_check(cudaGetLastError());
 }
 
-extern "C" int ps_raster_pair_count(ps_context* ctx, int64_t* h_pairs) {
-  if (!ctx || !h_pairs) return PS_ERR_INVALID;
+extern "C" int ps_raster_stats(ps_context* ctx, int64_t* h_pairs, int64_t* h_span_pixels) {
+  if (!ctx || !h_pairs || !h_span_pixels) return PS_ERR_INVALID;
   *h_pairs = 0;
+  *h_span_pixels = 0;
   if (!ctx->d_tile_off || ctx->last_n_tile <= 0) return PS_OK;
   int32_t v = 0;
+  int64_t sp = 0;
   cudaStream_t st = (cudaStream_t)ctx->last_stream;
   int rc = ps_cuda_check(cudaMemcpyAsync(&v, ctx->d_tile_off + ctx->last_n_tile, sizeof(int32_t),
                                          cudaMemcpyDeviceToHost, st));
+  if (rc == PS_OK)
+    rc = ps_cuda_check(cudaMemcpyAsync(&sp, ctx->d_scratch64, sizeof(int64_t),
+                                       cudaMemcpyDeviceToHost, st));
   if (rc == PS_OK) rc = ps_cuda_check(cudaStreamSynchronize(st));
   *h_pairs = v;
+  *h_span_pixels = sp;
   return rc;
 }

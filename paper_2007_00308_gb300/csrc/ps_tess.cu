@@ -434,7 +434,9 @@ __device__ int seg_intervals(const Seg& g, float q, LinkRec& L) {
           float ps_ = solve_t<MIXED>(g, psi_s, pa, pb);
           if (M + 2 > 6) return -1;
           L.p[M] = pa; L.psi[M] = Psi[k]; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh; M++;
-          L.p[M] = ps_; L.psi[M] = psi_s; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh; M++;
+          L.p[M] = ps_; L.psi[M] = psi_s; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh;
+          L.meta |= META_SPLIT_BIT(M);
+          M++;
         } else {
           int D = ad == 0.0 ? 1 : ceil_steps_d(ad, (double)q);
           if (M + 1 > 6) return -1;
@@ -452,7 +454,9 @@ __device__ int seg_intervals(const Seg& g, float q, LinkRec& L) {
       int Dh = ceil_steps(0.5f * ad, q);
       if (M + 2 > 6) return -1;
       L.p[M] = pa; L.psi[M] = Psi[k]; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh; M++;
-      L.p[M] = ps_; L.psi[M] = psi_s; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh; M++;
+      L.p[M] = ps_; L.psi[M] = psi_s; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh;
+      L.meta |= META_SPLIT_BIT(M);
+      M++;
     } else {
       int D = ad == 0.f ? (pb > pa ? 1 : 0) : ceil_steps(ad, q);
       if (M + 1 > 6) return -1;
@@ -1360,4 +1364,50 @@ extern "C" int ps_tessellate_strokes_noalloc(const ps_segments* seg, const ps_pa
     if (cudaGetLastError() != cudaSuccess) return PS_ERR_CUDA;
   }
   return PS_OK;
+}
+
+// ---------------------------------------------------------------------------
+int ps_run_link_setup(ps_context* ctx, const ps_segments* seg, const ps_paths* paths, float dtheta,
+                      int precision, int32_t* d_link_off, int32_t* d_path_off, int64_t* d_n_rib,
+                      cudaStream_t st) {
+  int64_t S = seg->n_seg;
+  int P = paths->n_path;
+  int64_t L = 2 * S + P;
+  int64_t n_tiles = (L + SETUP_TILE - 1) / SETUP_TILE;
+  int rc;
+  if ((rc = ps_ensure_tiles(ctx, n_tiles + 2)) != PS_OK) return rc;
+  if ((rc = ps_ensure_recs(ctx, L)) != PS_OK) return rc;
+  int32_t* link_path = reinterpret_cast<int32_t*>(ctx->d_recs + ctx->rec_cap);
+  cudaMemsetAsync(ctx->d_tile_flag, 0, sizeof(uint32_t) * n_tiles, st);
+  cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
+  k_link_path<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(paths->d_seg_off, P, L, link_path);
+  if (precision == PS_PREC_MIXED)
+    k_link_setup<true><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
+        seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
+        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->d_recs, d_link_off,
+        d_path_off, d_n_rib, INT64_MAX, ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
+        ctx->d_counters, ctx->d_status, n_tiles);
+  else
+    k_link_setup<false><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
+        seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
+        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->d_recs, d_link_off,
+        d_path_off, d_n_rib, INT64_MAX, ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
+        ctx->d_counters, ctx->d_status, n_tiles);
+  return ps_cuda_check(cudaGetLastError());
+}
+
+int ps_run_segmented_prefix(ps_context* ctx, float* d_vals, const uint32_t* d_tag,
+                            const int64_t* d_n_rib, int64_t capacity, float* d_path_tot,
+                            int32_t n_path, cudaStream_t st) {
+  int64_t scan_tiles = (capacity + SCAN_TILE - 1) / SCAN_TILE;
+  int rc = ps_ensure_tiles(ctx, scan_tiles + 2);
+  if (rc != PS_OK) return rc;
+  cudaMemsetAsync(ctx->d_tile_flag, 0, sizeof(uint32_t) * (scan_tiles + 1), st);
+  cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
+  if (d_path_tot && n_path > 0) cudaMemsetAsync(d_path_tot, 0, sizeof(float) * n_path, st);
+  int g2 = ps_persistent_grid(ctx, (const void*)k_arclen_scan, SCAN_NT, 0);
+  k_arclen_scan<<<g2, SCAN_NT, 0, st>>>(d_vals, d_tag, d_n_rib, capacity, d_vals, d_path_tot,
+                                        ctx->d_tile_flag, ctx->d_tile_aggd, ctx->d_tile_incld,
+                                        ctx->d_counters, ctx->d_status);
+  return ps_cuda_check(cudaGetLastError());
 }
