@@ -54,6 +54,23 @@ def parse():
 
 
 # ---------------------------------------------------------------------------
+def max_over_ranks(value: float, device) -> float:
+    """Maximum of a per-rank scalar over the process group (the slowest rank's
+    timed region bounds the whole job's throughput)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job units/s: every rank processes its own batch (weak scaling)."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
 
@@ -270,18 +287,15 @@ def run_ours(args, rank, world, local_rank):
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(sum(step_ms), dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     st = ctx.status()
     if st != 0:
         raise RuntimeError(f"device status {st}: {ps.error_string(st)}")
     ms_per_step = total_ms / args.steps
     segs = batch.n_seg
-    value = world * segs / (ms_per_step * 1e-3)
+    value = job_throughput(segs, world, ms_per_step)
     cov_samples = int(covered.sum().item())
     R_now = int(out.n_rib.item())
 

@@ -192,6 +192,22 @@ int ps_tessellate_strokes_noalloc(const ps_segments* seg, const ps_paths* paths,
                                   int precision, uint32_t flags, ps_tess_out* out,
                                   int32_t* d_status, void* stream);
 
+/* Adjoint of ps_tessellate_strokes at the forward pass's fixed step counts.
+ * Given dL/d(rib vertices) (d_grad_rib, [R*4]) and optionally dL/ds
+ * (d_grad_s, [R]), writes dL/d(control points) (d_grad_pts, [n_seg*8], zeroed
+ * by the call; a quadratic's or conic's middle point gets its gradient in the B
+ * slot) and dL/d(stroke width) (d_grad_width, [n_path]).  `fwd` is the forward
+ * call's output with d_t filled (the forward must request t).  Each rib's t(j)
+ * solves Eq. 11 and is differentiated implicitly; normal angles interpolate
+ * their interval's boundary angles; arc length is the chord sum of Eq. 18.
+ * Not followed (gradient contribution omitted): conic weights, miter tips
+ * (their vertices move with the join point only), collinear pivots.  The
+ * paper has no differentiation; this is the library's extension. */
+int ps_tessellate_backward(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
+                           float dtheta, int precision, const ps_tess_out* fwd,
+                           const float* d_grad_rib, const float* d_grad_s, float* d_grad_pts,
+                           float* d_grad_width, void* stream);
+
 /* Convenience: run the count phase and return R on the host.  SYNCHRONIZES. */
 int ps_count_ribs_sync(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
                        float dtheta, int precision, ps_tess_out* out, void* stream,

@@ -23,7 +23,8 @@ TAG_LINK_START, TAG_SEGMENT = 1, 2
 EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_status",
            "ps_error_string", "ps_tessellate_strokes", "ps_count_ribs_sync", "ps_arclength_scan",
            "ps_dash", "ps_rasterize_coverage", "ps_profile_enable", "ps_profile_read",
-           "ps_profile_slot_name", "ps_raster_stats", "ps_tessellate_strokes_noalloc"]
+           "ps_profile_slot_name", "ps_raster_stats", "ps_tessellate_strokes_noalloc",
+           "ps_tessellate_backward"]
 PS_PROF_SLOTS = 10
 
 
@@ -88,6 +89,9 @@ def lib():
         L.ps_profile_slot_name.argtypes = [ctypes.c_int]
         L.ps_profile_slot_name.restype = ctypes.c_char_p
         L.ps_raster_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
+        L.ps_tessellate_backward.argtypes = [P, ctypes.POINTER(_Segments), ctypes.POINTER(_Paths),
+                                             ctypes.c_float, ctypes.c_int,
+                                             ctypes.POINTER(_TessOut), P, P, P, P, P]
         L.ps_tessellate_strokes_noalloc.argtypes = [ctypes.POINTER(_Segments),
                                                     ctypes.POINTER(_Paths), ctypes.c_float,
                                                     ctypes.c_int, ctypes.c_uint32,
@@ -243,6 +247,20 @@ def ps_tessellate_strokes_noalloc(db: DeviceBatch, out: TessOutput, status, prec
     return lib().ps_tessellate_strokes_noalloc(ctypes.byref(seg), ctypes.byref(paths), q,
                                                int(precision), int(flags), ctypes.byref(o),
                                                _ptr(status), _stream(stream))
+
+
+def ps_tessellate_backward(ctx: Context, db: DeviceBatch, fwd: TessOutput, grad_rib, grad_s,
+                           grad_pts, grad_width, precision=PS_PREC_MIXED, dtheta=None,
+                           stream=None):
+    """Adjoint of a forward call (which must have requested t)."""
+    seg, paths = db._structs()
+    o = fwd._struct()
+    q = db.dtheta if dtheta is None else float(dtheta)
+    rc = lib().ps_tessellate_backward(ctx.handle, ctypes.byref(seg), ctypes.byref(paths), q,
+                                      int(precision), ctypes.byref(o), _ptr(grad_rib),
+                                      _ptr(grad_s), _ptr(grad_pts), _ptr(grad_width),
+                                      _stream(stream))
+    _check(rc, "ps_tessellate_backward")
 
 
 def ps_count_ribs_sync(ctx: Context, db: DeviceBatch, out: TessOutput, precision=PS_PREC_FP32,
