@@ -310,7 +310,8 @@ def run_ours(args, rank, world, local_rank):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     kmean = {k: statistics.mean(v) for k, v in kern.items()}
     dom = max(kmean, key=kmean.get)
-    pairs, span_px = ps.ps_raster_stats(ctx)
+    rstat = ps.ps_raster_stats(ctx)
+    pairs, span_px = rstat["pairs"], rstat["span_pixels"]
     counts = {"R": R_now, "L": db.n_link, "S": segs, "P": db.n_path, "px": Wd * Ht,
               "pairs": pairs, "span_px": span_px}
     sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
@@ -364,7 +365,7 @@ def run_ours(args, rank, world, local_rank):
         "covered_samples": cov_samples,
         "kernel_ms": kmean,
         "kernels": kernels,
-        "raster_work": {"bin_entries": pairs, "span_pixels": span_px},
+        "raster_work": rstat,
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": 8 * args.steps,

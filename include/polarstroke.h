@@ -263,9 +263,31 @@ int ps_profile_read(ps_context* ctx, float* h_ms /* [PS_PROF_SLOTS] */);
 const char* ps_profile_slot_name(int slot);
 
 /* Work counts of the context's most recent ps_rasterize_coverage call, read from
- * its device workspace: (quad, tile) bin entries, and the pixels of the per-row
- * spans the coverage kernel tested (16 samples each).  SYNCHRONIZES. */
-int ps_raster_stats(ps_context* ctx, int64_t* h_pairs, int64_t* h_span_pixels);
+ * its device workspace into h_counts[0 .. n_counts-1] (entries past
+ * PS_RSTAT_COUNT are zeroed):
+ *   PS_RSTAT_PAIRS          (quad, tile) bin entries
+ *   PS_RSTAT_SPAN_PIXELS    pixels of the per-row spans the coverage kernel
+ *                           tested (16 samples each), the sum of the next three
+ *   PS_RSTAT_CONVEX_PIXELS  ... of quads that are convex (or one triangle)
+ *   PS_RSTAT_TWO_TRI_PIXELS ... of non-convex quads (two triangles)
+ *   PS_RSTAT_GENERAL_PIXELS ... of quads with an edge longer than 1024 px
+ *   PS_RSTAT_TILE_PATHS     sum over tiles of the distinct paths met there
+ *   PS_RSTAT_TILE_PASSES    sum over tiles of the passes over the tile's bin
+ *                           (one per 224 distinct paths)
+ *   PS_RSTAT_SPAN_ROWS      (bin entry, pixel row) pairs whose span was computed
+ * SYNCHRONIZES. */
+enum {
+  PS_RSTAT_PAIRS = 0,
+  PS_RSTAT_SPAN_PIXELS = 1,
+  PS_RSTAT_CONVEX_PIXELS = 2,
+  PS_RSTAT_TWO_TRI_PIXELS = 3,
+  PS_RSTAT_GENERAL_PIXELS = 4,
+  PS_RSTAT_TILE_PATHS = 5,
+  PS_RSTAT_TILE_PASSES = 6,
+  PS_RSTAT_SPAN_ROWS = 7,
+  PS_RSTAT_COUNT = 8
+};
+int ps_raster_stats(ps_context* ctx, int64_t* h_counts, int n_counts);
 
 #ifdef __cplusplus
 }

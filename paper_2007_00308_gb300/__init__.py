@@ -88,7 +88,7 @@ def lib():
         L.ps_profile_read.argtypes = [P, P]
         L.ps_profile_slot_name.argtypes = [ctypes.c_int]
         L.ps_profile_slot_name.restype = ctypes.c_char_p
-        L.ps_raster_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
+        L.ps_raster_stats.argtypes = [P, P, ctypes.c_int]
         L.ps_tessellate_backward.argtypes = [P, ctypes.POINTER(_Segments), ctypes.POINTER(_Paths),
                                              ctypes.c_float, ctypes.c_int,
                                              ctypes.POINTER(_TessOut), P, P, P, P, P]
@@ -213,11 +213,16 @@ class TessOutput:
                         p(self.path_rib_off), p(self.path_len), p(self.n_rib), self.capacity)
 
 
-def ps_raster_stats(ctx: Context):
-    """(bin entries, span pixels) of the context's most recent raster call."""
-    n, sp = ctypes.c_int64(0), ctypes.c_int64(0)
-    _check(lib().ps_raster_stats(ctx.handle, ctypes.byref(n), ctypes.byref(sp)), "ps_raster_stats")
-    return n.value, sp.value
+RSTAT_NAMES = ("pairs", "span_pixels", "convex_pixels", "two_triangle_pixels", "general_pixels",
+               "tile_paths", "tile_passes", "span_rows")
+
+
+def ps_raster_stats(ctx: Context) -> dict:
+    """Work counts of the context's most recent raster call (``RSTAT_NAMES``)."""
+    buf = (ctypes.c_int64 * len(RSTAT_NAMES))()
+    _check(lib().ps_raster_stats(ctx.handle, ctypes.cast(buf, ctypes.c_void_p), len(RSTAT_NAMES)),
+           "ps_raster_stats")
+    return dict(zip(RSTAT_NAMES, (int(v) for v in buf)))
 
 
 def ps_max_ribs(n_seg, n_path, dtheta) -> int:

@@ -208,18 +208,31 @@ constexpr int HKEYS = 2048;          // hash of path ids (max distinct paths per
 constexpr int MASK_WORDS = TILE_PX * TILE_PX / 2;
 
 struct Edge {
-  int A, B;       // E(x, y) = A x + B y + C, tile-relative 1/256 px
-  long long C;
+  int A, B;       // E(x, y) = A (x - ex) + B (y - ey), tile-relative 1/256 px
+  int ex, ey;     // the edge's start vertex
 };
 
-struct EntrySetup {
-  Edge e[6];               // convex quad: e[0..3]; else triangle 0: e[0..2], triangle 1: e[3..5]
-  uint16_t rowpre[17];     // prefix of span widths over rows row0 ..
-  uint8_t x0[16];          // first pixel of each row's span
+// General form: convex quad in e[0..3], else triangle 0 in e[0..2] and
+// triangle 1 in e[3..5], each edge as {A, B, ex, ey}.  Fast forms: one convex
+// polygon of at most four edges in e[0..3] (bit5), or the union of two
+// triangles e[0..2], e[3..5] (bit6), each edge stored as {A, B, C', i1} with
+// A (x - 8) + B (y - 8) + C' the edge function (C' clamped, see to_fast_edge)
+// and i1 = 16 A + 80 B the step between consecutive samples whose sample row
+// advances by 5.
+struct __align__(16) EntrySetup {
+  Edge e[6];               // 16 bytes each, read as int4
+  int dm;                  // fast form: 240 * max(|A| + |B|) over the edges
+  uint8_t x0[16];          // first pixel of each row's span (rows row0 ..)
+  uint8_t w[16];           // span width of each row
+  uint16_t rowpre[17];     // prefix of span widths
   uint16_t slot;           // mask slot of this pass
-  uint8_t valid;           // bit0 tri 0, bit1 tri 1, bit2 int64 path, bit3 convex quad
-  uint8_t row0;
+  uint8_t valid;           // bit0 tri 0, bit1 tri 1, bit2 int64 path, bit3 convex quad,
+                           // bit4 int32 path, bit5 fast convex form, bit6 fast two-triangle form
+  uint8_t row0, nrow;
 };
+
+static_assert(sizeof(Edge) == 16 && sizeof(EntrySetup) % 16 == 0 && offsetof(EntrySetup, e) == 0,
+              "edges are loaded as int4 from shared memory");
 
 __device__ __forceinline__ void make_edges(int x0, int y0, int x1, int y1, int x2, int y2, Edge* e,
                                            bool& valid, bool& big) {
@@ -233,30 +246,13 @@ __device__ __forceinline__ void make_edges(int x0, int y0, int x1, int y1, int x
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     int ax = vx[i], ay = vy[i], bx = vx[(i + 1) % 3], by = vy[(i + 1) % 3];
-    long long A = (long long)ay - by, B = (long long)bx - ax;
+    long long A = (long long)ay - by, B = (long long)bx - ax;  // E = (bx-ax)(y-ay) - (by-ay)(x-ax)
     e[i].A = (int)A;
     e[i].B = (int)B;
-    e[i].C = -(A * ax + B * ay);  // E = (bx-ax)(y-ay) - (by-ay)(x-ax)
+    e[i].ex = ax;
+    e[i].ey = ay;
     if (llabs(A) + llabs(B) >= (1ll << 22)) big = true;
   }
-}
-
-// x-extent of segment (ax,ay)-(bx,by) clipped to the strip y in [ylo, yhi]
-__device__ __forceinline__ void seg_strip(float ax, float ay, float bx, float by, float ylo,
-                                          float yhi, float& xmin, float& xmax) {
-  if (ay > by) {
-    float t = ax; ax = bx; bx = t;
-    t = ay; ay = by; by = t;
-  }
-  if (by < ylo || ay > yhi) return;
-  float xa = ax, xb = bx;
-  if (by > ay) {
-    float k = (bx - ax) / (by - ay);
-    if (ay < ylo) xa = ax + k * (ylo - ay);
-    if (by > yhi) xb = ax + k * (yhi - ay);
-  }
-  xmin = fminf(xmin, fminf(xa, xb));
-  xmax = fmaxf(xmax, fmaxf(xa, xb));
 }
 
 // 16-sample mask of one edge given its value Ec at the pixel corner: sample k
@@ -283,18 +279,220 @@ __device__ __forceinline__ uint32_t edge_mask(const Edge& e, long long Ec, bool 
   return em;
 }
 
-// Set up entry r (rib id) of tile (ox, oy); returns its pixel count.
-__device__ __forceinline__ int setup_entry(const float4* __restrict__ rib, uint32_t r, int slot,
-                                           int ox, int oy, int tw, int th, EntrySetup& E) {
+// Same with every quantity known to fit in int32 (edges shorter than 64 px whose
+// start vertices lie within 128 px of the tile).
+__device__ __forceinline__ uint32_t edge_mask32(const Edge& e, int Ec) {
+  int D = 248 * (abs(e.A) + abs(e.B));
+  if (Ec - D >= 0) return 0xffffu;
+  if (Ec + D < 0) return 0u;
+  uint32_t em = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    int v = Ec + e.A * (16 * k + 8) + e.B * (16 * ((5 * k) & 15) + 8);
+    em |= (v >= 0 ? 1u : 0u) << k;
+  }
+  return em;
+}
+
+// {A, B, ex, ey} -> fast form {A, B, C', i1} (requires |A| + |B| < 2^18).
+__device__ __forceinline__ void to_fast_edge(Edge& ed) {
+  long long A = ed.A, B = ed.B, S = llabs(A) + llabs(B);
+  // value at sample 0 of the tile's first pixel: A (8 - ex) + B (8 - ey)
+  long long c = A * (8ll - ed.ex) + B * (8ll - ed.ey);
+  // Over the tile the value moves by at most 3840 S between pixel corners and
+  // 240 S between samples: beyond +-(4080 S + 1) the sign of every sample is
+  // fixed, so clamping there changes no sample.
+  long long lim = 4080ll * S + 1;
+  c = c > lim ? lim : (c < -lim ? -lim : c);
+  ed.ex = (int)c;
+  ed.ey = (int)(16 * A + 80 * B);
+}
+
+// Pixel rows whose sample band [256 ly + 8, 256 ly + 248] meets [ymin, ymax].
+__device__ __forceinline__ int entry_rows(int ymin, int ymax, int th, EntrySetup& E) {
+  int64_t c0 = ceil_div((int64_t)ymin - 248, 256), c1 = floor_div((int64_t)ymax - 8, 256);
+  int ly0 = (int)(c0 < 0 ? 0 : c0);
+  int ly1 = (int)(c1 > th - 1 ? th - 1 : c1);
+  if (ly1 < ly0) return 0;
+  E.row0 = (uint8_t)ly0;
+  E.nrow = (uint8_t)(ly1 - ly0 + 1);
+  return ly1 - ly0 + 1;
+}
+
+// Edge lists of the fast forms as pairs of polygon vertex indices (polygon
+// order N0 P0 P1 N1 = 0 1 2 3), 4 bits per edge (start | end << 2), six edges;
+// 0x0 (start = end) is the always-true edge A = B = 0.
+constexpr uint32_t EL_CONVEX_POS = 0x4u | 0x9u << 4 | 0xEu << 8 | 0x3u << 12;  // 0->1 1->2 2->3 3->0
+constexpr uint32_t EL_CONVEX_NEG = 0xCu | 0xBu << 4 | 0x6u << 8 | 0x1u << 12;  // 0->3 3->2 2->1 1->0
+constexpr uint32_t EL_TRI0_POS = 0x4u | 0x9u << 4 | 0x2u << 8;   // 0->1 1->2 2->0
+constexpr uint32_t EL_TRI0_NEG = 0x8u | 0x6u << 4 | 0x1u << 8;   // 0->2 2->1 1->0
+constexpr uint32_t EL_TRI1_POS = 0x8u | 0xEu << 4 | 0x3u << 8;   // 0->2 2->3 3->0
+constexpr uint32_t EL_TRI1_NEG = 0xCu | 0xBu << 4 | 0x2u << 8;   // 0->3 3->2 2->0
+
+// Setup of a quad whose extent is below 2^14 (64 px) on both axes: every
+// cross product and fast-form constant fits in int32, and one code path serves
+// all classes.  Vertex coordinates are tile-relative and the quad meets the
+// tile, so |8 - x| < 2^14 + 4104 and |A (8 - x) + B (8 - y)| < 2^30.
+__device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax, int tw, int th,
+                                           EntrySetup& E) {
+  const int X0 = q.x[0], Y0 = q.y[0], X1 = q.x[1], Y1 = q.y[1];  // N0 P0
+  const int X2 = q.x[3], Y2 = q.y[3], X3 = q.x[2], Y3 = q.y[2];  // P1 N1
+  int a0 = (X1 - X0) * (Y2 - Y0) - (Y1 - Y0) * (X2 - X0);          // N0 P0 P1
+  int a1 = (X2 - X0) * (Y3 - Y0) - (Y2 - Y0) * (X3 - X0);          // N0 P1 N1
+  if (a0 == 0 && a1 == 0) return 0;
+  // turns at the four corners of N0 P0 P1 N1
+  int c0 = (X1 - X0) * (Y2 - Y1) - (Y1 - Y0) * (X2 - X1);
+  int c1 = (X2 - X1) * (Y3 - Y2) - (Y2 - Y1) * (X3 - X2);
+  int c2 = (X3 - X2) * (Y0 - Y3) - (Y3 - Y2) * (X0 - X3);
+  int c3 = (X0 - X3) * (Y1 - Y0) - (Y0 - Y3) * (X1 - X0);
+  bool pos = c0 >= 0 && c1 >= 0 && c2 >= 0 && c3 >= 0;
+  bool neg = c0 <= 0 && c1 <= 0 && c2 <= 0 && c3 <= 0;
+  uint32_t el0 = a0 > 0 ? EL_TRI0_POS : EL_TRI0_NEG;
+  uint32_t el1 = a1 > 0 ? EL_TRI1_POS : EL_TRI1_NEG;
+  uint32_t el;
+  uint8_t cls;
+  if (a0 != 0 && a1 != 0 && (pos || neg)) {
+    el = pos ? EL_CONVEX_POS : EL_CONVEX_NEG;
+    cls = 8 | 32;
+  } else if (a0 != 0 && a1 != 0) {
+    el = el0 | el1 << 12;
+    cls = 64;
+  } else {
+    el = a0 != 0 ? el0 : el1;
+    cls = 32;
+  }
+  const bool two = cls == 64;
+  // Per edge, the line A X + B Y + C' = 0 (X = x - 8, Y = y - 8) as X = k Y + u.
+  // An edge with A > 0 bounds X from below: over a row's sample band
+  // Y in [Y0, Y0 + 240] by k Y0 + u + min(0, 240 k) - eps, kept as wl(Y0) =
+  // fma(k, Y0, ul).  A < 0 bounds X from above; its bound is kept negated,
+  // wh(Y0) = fma(-k, Y0, uh), so both kinds reduce with max.  Edges with A = 0
+  // (horizontal, or the always-true edge) bound nothing here.  eps covers the
+  // float rounding of k, u and the fma (a few 2^-24 relative to |u| + 4096 |k|).
+  float kq[6], uq[6];
+  uint32_t lo_side = 0;
+  int smax = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    int ia = (el >> (4 * i)) & 3, ib = (el >> (4 * i + 2)) & 3;
+    int xa = ia == 0 ? X0 : ia == 1 ? X1 : ia == 2 ? X2 : X3;
+    int ya = ia == 0 ? Y0 : ia == 1 ? Y1 : ia == 2 ? Y2 : Y3;
+    int xb = ib == 0 ? X0 : ib == 1 ? X1 : ib == 2 ? X2 : X3;
+    int yb = ib == 0 ? Y0 : ib == 1 ? Y1 : ib == 2 ? Y2 : Y3;
+    int A = ya - yb, B = xb - xa, S = abs(A) + abs(B);
+    int c = A * (8 - xa) + B * (8 - ya);
+    int lim = 4080 * S + 1;
+    c = min(max(c, -lim), lim);
+    smax = max(smax, S);
+    *reinterpret_cast<int4*>(&E.e[i]) = make_int4(A, B, c, 16 * A + 80 * B);
+    float fa = (float)A;
+    float k = __fdividef((float)-B, fa), u = __fdividef((float)-c, fa);
+    float eps = 4.f + 1e-6f * (fabsf(u) + 4096.f * fabsf(k));
+    float k240 = 240.f * k;
+    if (A > 0) {
+      kq[i] = k;
+      uq[i] = u + fminf(0.f, k240) - eps;
+      lo_side |= 1u << i;
+    } else if (A < 0) {
+      kq[i] = -k;
+      uq[i] = -(u + fmaxf(0.f, k240) + eps);
+    } else {
+      kq[i] = 0.f;
+      uq[i] = -INFINITY;
+    }
+  }
+  E.dm = 240 * smax;
+  E.valid = cls | (a0 != 0 ? 1 : 0) | (a1 != 0 ? 2 : 0);
+  if (entry_rows(ymin, ymax, th, E) == 0) return 0;
+  // row spans: group 0 = edges 0..3 (triangle 0 and, for a convex quad, the
+  // fourth edge), group 1 = edges 3..5 of the two-triangle form; union of groups
+  const bool e3g1 = two;
+  int tot = 0;
+  E.rowpre[0] = 0;
+  const int nrow = E.nrow;
+  for (int j = 0; j < 16; ++j) {
+    int wj = 0, aj = 0;
+    if (j < nrow) {
+      const float Yb = 256.f * (float)(E.row0 + j);
+      float L0 = -INFINITY, M0 = -INFINITY, L1 = -INFINITY, M1 = -INFINITY;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        float w = fmaf(kq[i], Yb, uq[i]);
+        bool lo = (lo_side >> i) & 1u;
+        bool g1 = i >= 4 || (i == 3 && e3g1);
+        if (g1) {
+          L1 = lo ? fmaxf(L1, w) : L1;
+          M1 = lo ? M1 : fmaxf(M1, w);
+        } else {
+          L0 = lo ? fmaxf(L0, w) : L0;
+          M0 = lo ? M0 : fmaxf(M0, w);
+        }
+      }
+      float lo0 = L0, hi0 = -M0, lo1 = L1, hi1 = -M1;
+      bool ok0 = lo0 <= hi0, ok1 = two && lo1 <= hi1;
+      float lo = ok0 ? (ok1 ? fminf(lo0, lo1) : lo0) : lo1;
+      float hi = ok0 ? (ok1 ? fmaxf(hi0, hi1) : hi0) : hi1;
+      if (ok0 || ok1) {
+        lo = fmaxf(lo, -1e9f);
+        hi = fminf(hi, 1e9f);
+        int pa = max(0, (int)ceilf((lo - 240.f) * (1.f / 256.f)));
+        int pb = min(tw - 1, (int)floorf(hi * (1.f / 256.f)));
+        if (pb >= pa) {
+          aj = pa;
+          wj = pb - pa + 1;
+        }
+      }
+      E.x0[j] = (uint8_t)aj;
+      E.w[j] = (uint8_t)wj;
+    }
+    tot += wj;
+    E.rowpre[j + 1] = (uint16_t)tot;
+  }
+  return tot;
+}
+
+__device__ __forceinline__ void row_span(const EntrySetup& E, int ly, int tw, int& a, int& w);
+__device__ __forceinline__ void row_span_fast(const EntrySetup& E, int ly, int tw, int& a, int& w);
+
+// Row spans of an entry set up by the general path (per row, as above).
+__device__ __forceinline__ int finish_spans(EntrySetup& E, int tw) {
+  int tot = 0;
+  E.rowpre[0] = 0;
+  for (int j = 0; j < 16; ++j) {
+    if (j < E.nrow) {
+      int a0, w0;
+      if (E.valid & 96) row_span_fast(E, E.row0 + j, tw, a0, w0);
+      else row_span(E, E.row0 + j, tw, a0, w0);
+      E.x0[j] = (uint8_t)a0;
+      E.w[j] = (uint8_t)w0;
+      tot += w0;
+    }
+    E.rowpre[j + 1] = (uint16_t)tot;
+  }
+  return tot;
+}
+
+// Edges and row spans of the quad between ribs ra, rb in tile (ox, oy);
+// returns the number of pixels in its spans (0: nothing to draw).
+__device__ __forceinline__ int setup_edges(const float4 ra, const float4 rb, int slot, int ox,
+                                           int oy, int tw, int th, EntrySetup& E) {
   E.slot = (uint16_t)slot;
   E.valid = 0;
   E.row0 = 0;
-  E.rowpre[0] = 0;
+  E.nrow = 0;
   QuadFix q;
-  if (!snap_quad(__ldg(rib + r - 1), __ldg(rib + r), q)) return 0;
+  if (!snap_quad(ra, rb, q)) return 0;
   for (int v = 0; v < 4; ++v) {
     q.x[v] -= ox;
     q.y[v] -= oy;
+  }
+  {
+    int mnx = min(min(q.x[0], q.x[1]), min(q.x[2], q.x[3]));
+    int mxx = max(max(q.x[0], q.x[1]), max(q.x[2], q.x[3]));
+    int mny = min(min(q.y[0], q.y[1]), min(q.y[2], q.y[3]));
+    int mxy = max(max(q.y[0], q.y[1]), max(q.y[2], q.y[3]));
+    if (mxx - mnx < (1 << 14) && mxy - mny < (1 << 14))
+      return setup_small(q, mny, mxy, tw, th, E);
   }
   bool v0, v1, big = false;
   make_edges(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], E.e, v0, big);      // N0 P0 P1
@@ -322,65 +520,281 @@ __device__ __forceinline__ int setup_entry(const float4* __restrict__ rib, uint3
         long long A = (long long)py_[a0] - py_[a1], B = (long long)px_[a1] - px_[a0];
         E.e[i].A = (int)A;
         E.e[i].B = (int)B;
-        E.e[i].C = -(A * px_[a0] + B * py_[a0]);
+        E.e[i].ex = px_[a0];
+        E.e[i].ey = py_[a0];
         if (llabs(A) + llabs(B) >= (1ll << 22)) bigq = true;
       }
       big = bigq;
       flags |= 8;
     }
   }
-  E.valid = flags | (big ? 4 : 0);
-  // per-row pixel spans over the 5 segments bounding both triangles
-  float fx[4] = {(float)q.x[0], (float)q.x[1], (float)q.x[2], (float)q.x[3]};
-  float fy[4] = {(float)q.y[0], (float)q.y[1], (float)q.y[2], (float)q.y[3]};
-  float ymin = fminf(fminf(fy[0], fy[1]), fminf(fy[2], fy[3]));
-  float ymax = fmaxf(fmaxf(fy[0], fy[1]), fmaxf(fy[2], fy[3]));
-  float mag = fmaxf(fmaxf(fabsf(fx[0]), fabsf(fx[1])), fmaxf(fabsf(fx[2]), fabsf(fx[3])));
-  mag = fmaxf(mag, fmaxf(fabsf(ymin), fabsf(ymax)));
-  float eps = 4.f + mag * 1e-6f;  // float error of the clipped extents, 1/256 px
-  int ly0 = max(0, (int)ceilf((ymin - 248.f - eps) / 256.f));
-  int ly1 = min(th - 1, (int)floorf((ymax - 8.f + eps) / 256.f));
-  int first = -1, tot = 0;
-  for (int ly = ly0; ly <= ly1; ++ly) {
-    float ylo = 256.f * ly + 8.f - eps, yhi = 256.f * ly + 248.f + eps;
-    float xmin = 3.4e38f, xmax = -3.4e38f;
-    seg_strip(fx[0], fy[0], fx[1], fy[1], ylo, yhi, xmin, xmax);  // N0 P0
-    seg_strip(fx[1], fy[1], fx[3], fy[3], ylo, yhi, xmin, xmax);  // P0 P1
-    seg_strip(fx[3], fy[3], fx[2], fy[2], ylo, yhi, xmin, xmax);  // P1 N1
-    seg_strip(fx[2], fy[2], fx[0], fy[0], ylo, yhi, xmin, xmax);  // N1 N0
-    seg_strip(fx[0], fy[0], fx[3], fy[3], ylo, yhi, xmin, xmax);  // N0 P1
-    int w = 0, a = 0;
-    if (xmax >= xmin) {
-      a = max(0, (int)ceilf((xmin - 248.f - eps) / 256.f));
-      int bb = min(tw - 1, (int)floorf((xmax - 8.f + eps) / 256.f));
-      if (bb >= a) w = bb - a + 1;
-    }
-    if (first < 0) {
-      if (w == 0) continue;
-      first = ly;
-    }
-    int k = ly - first;
-    E.x0[k] = (uint8_t)a;
-    tot += w;
-    E.rowpre[k + 1] = (uint16_t)tot;
+  // int32 evaluation is exact when |A|,|B| < 2^14 and every start vertex is
+  // within 2^15 (128 px) of the tile: |A (x - ex)| + |B (y - ey)| < 2^31
+  bool small = !big;
+  int ne = (flags & 8) ? 4 : 6;
+  for (int i = 0; i < ne; ++i) {
+    const Edge& ed = E.e[i];
+    if ((i < 3 && !(flags & 1) && !(flags & 8)) || (i >= 3 && !(flags & 2))) continue;
+    small = small && abs(ed.A) < (1 << 14) && abs(ed.B) < (1 << 14) && ed.ex > -(1 << 15) &&
+            ed.ex < (1 << 15) + TILE_UNITS && ed.ey > -(1 << 15) && ed.ey < (1 << 15) + TILE_UNITS;
   }
-  if (first < 0) return 0;
-  E.row0 = (uint8_t)first;
-  // rows after the last one repeat the final prefix: the row search below takes
-  // the last row whose prefix is <= the item index, which skips empty rows
-  for (int k = ly1 - first + 1; k < 16; ++k) E.rowpre[k + 1] = (uint16_t)tot;
-  return tot;
+  E.valid = flags | (big ? 4 : 0) | (small ? 16 : 0);
+  // fast form: a convex quad or a single triangle whose edges all have
+  // |A| + |B| < 2^18 (shorter than 1024 px); every value of fast_mask then
+  // fits in int32 (see fast_mask)
+  int nf = (flags & 8) ? 4 : ((flags & 3) == 1 || (flags & 3) == 2) ? 3 : 0;
+  if (!nf && flags == 3 && !big) {
+    // both triangles real, polygon not convex: two-triangle fast form
+    long long smax = 0;
+    for (int i = 0; i < 6; ++i) smax = max(smax, llabs((long long)E.e[i].A) + llabs((long long)E.e[i].B));
+    if (smax < (1ll << 18)) {
+      for (int i = 0; i < 6; ++i) to_fast_edge(E.e[i]);
+      E.dm = (int)(240 * smax);
+      E.valid |= 64;
+    }
+  }
+  if (nf && !big) {
+    const Edge* src = (flags & 8) || (flags & 1) ? E.e : E.e + 3;
+    long long smax = 0;
+    for (int i = 0; i < nf; ++i) smax = max(smax, llabs((long long)src[i].A) + llabs((long long)src[i].B));
+    if (smax < (1ll << 18)) {
+      Edge f[4];
+      for (int i = 0; i < nf; ++i) {
+        f[i] = src[i];
+        to_fast_edge(f[i]);
+      }
+      if (nf == 3) {  // always-true fourth edge
+        f[3].A = 0;
+        f[3].B = 0;
+        f[3].ex = 1;
+        f[3].ey = 0;
+      }
+      for (int i = 0; i < 4; ++i) E.e[i] = f[i];
+      E.dm = (int)(240 * smax);
+      E.valid |= 32;
+    }
+  }
+  int ymin = min(min(q.y[0], q.y[1]), min(q.y[2], q.y[3]));
+  int ymax = max(max(q.y[0], q.y[1]), max(q.y[2], q.y[3]));
+  if (entry_rows(ymin, ymax, th, E) == 0) return 0;
+  return finish_spans(E, tw);
 }
 
-__device__ __forceinline__ uint32_t pixel_mask(const EntrySetup& E, int lx, int ly) {
+// x-extent of the region where the given edges are all >= 0, over the sample
+// band of pixel row ly (conservative: float, widened by eps).  Each edge with
+// A != 0 bounds x on one side: x >= xe(y) for A > 0, x <= xe(y) for A < 0, with
+// xe(y) = ex - (B / A)(y - ey); over the band the weakest bound is taken.
+__device__ __forceinline__ bool band_extent(const Edge* e, int ne, int ly, float& lo, float& hi) {
+  float ylo = 256.f * ly + 8.f, yhi = 256.f * ly + 248.f;
+  lo = -3.4e38f;
+  hi = 3.4e38f;
+  for (int i = 0; i < ne; ++i) {
+    float A = (float)e[i].A, B = (float)e[i].B, ex = (float)e[i].ex, ey = (float)e[i].ey;
+    if (e[i].A == 0) {
+      // E = B (y - ey): some sample row of the band must have E >= 0
+      float m = fmaxf(B * (ylo - ey), B * (yhi - ey));
+      if (m < -4.f * fabsf(B) - 1.f) return false;
+      continue;
+    }
+    float k = B / A;
+    float xa = ex - k * (ylo - ey), xb = ex - k * (yhi - ey);
+    float eps = 4.f + 1e-6f * (fabsf(ex) + fabsf(xa) + fabsf(xb) + fabsf(ey) + 4096.f);
+    if (e[i].A > 0) lo = fmaxf(lo, fminf(xa, xb) - eps);
+    else hi = fminf(hi, fmaxf(xa, xb) + eps);
+  }
+  return hi >= lo;
+}
+
+__device__ __forceinline__ void row_span(const EntrySetup& E, int ly, int tw, int& a, int& w) {
+  float lo, hi;
+  bool ok;
+  if (E.valid & 8) {
+    ok = band_extent(E.e, 4, ly, lo, hi);
+  } else {
+    float l0 = 3.4e38f, h0 = -3.4e38f, l1, h1;
+    ok = false;
+    if ((E.valid & 1) && band_extent(E.e, 3, ly, l1, h1)) {
+      l0 = fminf(l0, l1);
+      h0 = fmaxf(h0, h1);
+      ok = true;
+    }
+    if ((E.valid & 2) && band_extent(E.e + 3, 3, ly, l1, h1)) {
+      l0 = fminf(l0, l1);
+      h0 = fmaxf(h0, h1);
+      ok = true;
+    }
+    lo = l0;
+    hi = h0;
+  }
+  a = 0;
+  w = 0;
+  if (!ok) return;
+  // pixels whose samples x in [256 lx + 8, 256 lx + 248] can lie in [lo, hi]
+  lo = fmaxf(lo, -1e9f);
+  hi = fminf(hi, 1e9f);
+  int pa = max(0, (int)ceilf((lo - 248.f) / 256.f));
+  int pb = min(tw - 1, (int)floorf((hi - 8.f) / 256.f));
+  if (pb >= pa) {
+    a = pa;
+    w = pb - pa + 1;
+  }
+}
+
+// 16-sample mask of a fast-form entry at pixel corner (cx, cy) (tile-relative,
+// 1/256 px).  Per edge, v = C' + A cx + B cy is the value at sample 0; with
+// S = |A| + |B| < 2^18, |C'| <= 4080 S + 1 and cx, cy <= 3840 it stays below
+// 2^31.  Clamped to [-dm - 1, dm] (dm >= 240 S) it keeps the sign of every
+// sample value v + A 16 k + B 16 ((5 k) mod 16), and those sums stay within
+// +-(2 dm + 1) < 2^31.  A sample is covered iff no edge is negative there: the
+// sign bit of the OR of the four values.
+__device__ __forceinline__ uint32_t fast_mask(const EntrySetup& E, int cx, int cy) {
+  const int dm = E.dm;
+  int v[4], i1[4], i2[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int4 ed = *reinterpret_cast<const int4*>(&E.e[i]);
+    int t = ed.z + ed.x * cx + ed.y * cy;
+    v[i] = min(max(t, -dm - 1), dm);
+    i1[i] = ed.w;                 // sample row + 5
+    i2[i] = ed.w - ed.y * 256;    // sample row - 11
+  }
+  uint32_t neg = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    uint32_t o = (uint32_t)(v[0] | v[1] | v[2] | v[3]);
+    neg |= (o >> 31) << k;
+    if (k < 15) {
+      const bool up = ((5 * k) & 15) <= 10;  // next sample row is 5 further
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] += up ? i1[i] : i2[i];
+    }
+  }
+  return ~neg & 0xffffu;
+}
+
+// Two-triangle fast form: a sample is covered iff one of the triangles has no
+// negative edge there (same bounds as fast_mask).
+__device__ __forceinline__ uint32_t fast_mask2(const EntrySetup& E, int cx, int cy) {
+  const int dm = E.dm;
+  int v[6], i1[6], i2[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const int4 ed = *reinterpret_cast<const int4*>(&E.e[i]);
+    int t = ed.z + ed.x * cx + ed.y * cy;
+    v[i] = min(max(t, -dm - 1), dm);
+    i1[i] = ed.w;
+    i2[i] = ed.w - ed.y * 256;
+  }
+  uint32_t neg = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    uint32_t o = (uint32_t)(v[0] | v[1] | v[2]) & (uint32_t)(v[3] | v[4] | v[5]);
+    neg |= (o >> 31) << k;
+    if (k < 15) {
+      const bool up = ((5 * k) & 15) <= 10;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) v[i] += up ? i1[i] : i2[i];
+    }
+  }
+  return ~neg & 0xffffu;
+}
+
+// Conservative pixel span of a fast-form entry on pixel row ly: each edge with
+// A != 0 bounds x on one side over the row's sample band, x >= or <= 8 - (B
+// (y - 8) + C') / A; an edge with A == 0 rules the row out when it is negative
+// on the whole band.  Float, widened by eps.
+template <int N>
+__device__ __forceinline__ bool band_extent_fast(const Edge* e, float y0, float& lo, float& hi) {
+  float y1 = y0 + 240.f;  // sample rows y - 8 of the band: [y0, y0 + 240]
+  lo = -3.4e38f;
+  hi = 3.4e38f;
+  bool dead = false;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int4 ed = *reinterpret_cast<const int4*>(&e[i]);
+    float A = (float)ed.x, B = (float)ed.y, C = (float)ed.z;
+    float n0 = fmaf(B, y0, C), n1 = fmaf(B, y1, C);
+    float mag = fabsf(C) + 4096.f * fabsf(B);
+    if (ed.x == 0) {
+      dead = dead || fmaxf(n0, n1) < -(4.f + 1e-6f * mag);
+      continue;
+    }
+    float r = __frcp_rn(A);
+    float xa = 8.f - n0 * r, xb = 8.f - n1 * r;
+    float eps = 4.f + 1e-6f * (mag * fabsf(r) + fabsf(xa) + fabsf(xb));
+    if (ed.x > 0) lo = fmaxf(lo, fminf(xa, xb) - eps);
+    else hi = fminf(hi, fmaxf(xa, xb) + eps);
+  }
+  return !dead && hi >= lo;
+}
+
+__device__ __forceinline__ void row_span_fast(const EntrySetup& E, int ly, int tw, int& a, int& w) {
+  float y0 = 256.f * ly;
+  float lo, hi;
+  bool ok;
+  if (E.valid & 64) {
+    float l1, h1;
+    bool ok0 = band_extent_fast<3>(E.e, y0, lo, hi);
+    bool ok1 = band_extent_fast<3>(E.e + 3, y0, l1, h1);
+    if (!ok0) {
+      lo = l1;
+      hi = h1;
+    } else if (ok1) {
+      lo = fminf(lo, l1);
+      hi = fmaxf(hi, h1);
+    }
+    ok = ok0 || ok1;
+  } else {
+    ok = band_extent_fast<4>(E.e, y0, lo, hi);
+  }
+  a = 0;
+  w = 0;
+  if (!ok) return;
+  lo = fmaxf(lo, -1e9f);
+  hi = fminf(hi, 1e9f);
+  int pa = max(0, (int)ceilf((lo - 248.f) * (1.f / 256.f)));
+  int pb = min(tw - 1, (int)floorf((hi - 8.f) * (1.f / 256.f)));
+  if (pb >= pa) {
+    a = pa;
+    w = pb - pa + 1;
+  }
+}
+
+__device__ __forceinline__ uint32_t tri_or_quad_mask(const EntrySetup& E, int lx, int ly) {
   int cx = lx * 256, cy = ly * 256;
   bool big = (E.valid & 4) != 0;
+  if (E.valid & 16) {  // int32 path
+    if (E.valid & 8) {
+      uint32_t m = 0xffffu;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        int Ec = E.e[i].A * (cx - E.e[i].ex) + E.e[i].B * (cy - E.e[i].ey);
+        m &= edge_mask32(E.e[i], Ec);
+        if (!m) return 0u;
+      }
+      return m;
+    }
+    uint32_t m0 = 0, m1 = 0;
+    if (E.valid & 1) {
+      m0 = 0xffffu;
+      for (int i = 0; i < 3 && m0; ++i)
+        m0 &= edge_mask32(E.e[i], E.e[i].A * (cx - E.e[i].ex) + E.e[i].B * (cy - E.e[i].ey));
+    }
+    if ((E.valid & 2) && m0 != 0xffffu) {
+      m1 = 0xffffu;
+      for (int i = 3; i < 6 && m1; ++i)
+        m1 &= edge_mask32(E.e[i], E.e[i].A * (cx - E.e[i].ex) + E.e[i].B * (cy - E.e[i].ey));
+    }
+    return m0 | m1;
+  }
+  auto ev = [&](const Edge& ed) {
+    return (long long)ed.A * (cx - ed.ex) + (long long)ed.B * (cy - ed.ey);
+  };
   if (E.valid & 8) {
     uint32_t m = 0xffffu;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      long long Ec = (long long)E.e[i].A * cx + (long long)E.e[i].B * cy + E.e[i].C;
-      m &= edge_mask(E.e[i], Ec, big);
+      m &= edge_mask(E.e[i], ev(E.e[i]), big);
       if (!m) return 0u;
     }
     return m;
@@ -388,17 +802,11 @@ __device__ __forceinline__ uint32_t pixel_mask(const EntrySetup& E, int lx, int 
   uint32_t m0 = 0, m1 = 0;
   if (E.valid & 1) {
     m0 = 0xffffu;
-    for (int i = 0; i < 3 && m0; ++i) {
-      long long Ec = (long long)E.e[i].A * cx + (long long)E.e[i].B * cy + E.e[i].C;
-      m0 &= edge_mask(E.e[i], Ec, big);
-    }
+    for (int i = 0; i < 3 && m0; ++i) m0 &= edge_mask(E.e[i], ev(E.e[i]), big);
   }
   if ((E.valid & 2) && m0 != 0xffffu) {
     m1 = 0xffffu;
-    for (int i = 3; i < 6 && m1; ++i) {
-      long long Ec = (long long)E.e[i].A * cx + (long long)E.e[i].B * cy + E.e[i].C;
-      m1 &= edge_mask(E.e[i], Ec, big);
-    }
+    for (int i = 3; i < 6 && m1; ++i) m1 &= edge_mask(E.e[i], ev(E.e[i]), big);
   }
   return m0 | m1;
 }
@@ -412,15 +820,37 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem);                          // SLOTS*MASK_WORDS
   EntrySetup* s_ent = reinterpret_cast<EntrySetup*>(s_mask + SLOTS * MASK_WORDS);  // CV_NT
+  static_assert((sizeof(uint32_t) * SLOTS * MASK_WORDS) % 16 == 0, "entry array alignment");
   uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_ent + CV_NT);                 // HKEYS
   uint16_t* s_slot_of = reinterpret_cast<uint16_t*>(s_keys + HKEYS);             // HKEYS
   uint32_t* s_slot_path = reinterpret_cast<uint32_t*>(s_slot_of + HKEYS);        // HKEYS
   __shared__ int s_tile, s_nslot, s_next;
-  __shared__ uint32_t s_pre[CV_WARPS][33];
+  __shared__ unsigned long long s_pre[CV_WARPS][33];
+  __shared__ uint32_t s_canvas[MASK_WORDS];
 
   for (int i = threadIdx.x; i < SLOTS * MASK_WORDS; i += CV_NT) s_mask[i] = 0u;
+  for (int i = threadIdx.x; i < MASK_WORDS; i += CV_NT) s_canvas[i] = 0u;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   EntrySetup* my = s_ent + wid * 32;
+  // work counters (items: per warp, the same in every lane; rows: per lane),
+  // added to the global ones at tile ends: one atomic per warp and tile
+  unsigned long long st_items = 0, st_rows = 0;
+  int st_batches = 0;
+  auto flush_stats = [&]() {
+    for (int o = 16; o > 0; o >>= 1) st_rows += __shfl_xor_sync(0xffffffffu, st_rows, o);
+    if (lane == 0 && stats && (st_items | st_rows)) {
+      unsigned long long f0 = st_items & 0x1fffffu, f1 = (st_items >> 21) & 0x1fffffu,
+                         f2 = st_items >> 42;
+      atomicAdd(stats, f0 + f1 + f2);
+      atomicAdd(stats + 1, f0);
+      atomicAdd(stats + 2, f1);
+      atomicAdd(stats + 3, f2);
+      atomicAdd(stats + 6, st_rows);
+    }
+    st_items = 0;
+    st_rows = 0;
+    st_batches = 0;
+  };
   for (;;) {
     if (threadIdx.x == 0) {
       s_tile = atomicAdd(&counters[2], 1);
@@ -432,6 +862,7 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
     }
     __syncthreads();
     int t = s_tile;
+    flush_stats();
     if (t >= n_tile) return;
     int tx = t % tiles_x, ty = t / tiles_x;
     int ox = tx * TILE_UNITS, oy = ty * TILE_UNITS;
@@ -443,18 +874,36 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
       int slot_lo = pass * SLOTS;
       if (threadIdx.x == 0) s_next = 0;
       __syncthreads();
+      // batches of 32 bin entries per warp; the next batch's entries are
+      // fetched while this one is processed, and each entry's tag and two ribs
+      // are gathered together
+      int base_next = 0;
+      if (lane == 0) base_next = atomicAdd(&s_next, 32);
+      base_next = __shfl_sync(0xffffffffu, base_next, 0);
+      uint32_t r_next = base_next + lane < n ? bin[b0 + base_next + lane] : 0u;
       for (;;) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&s_next, 32);
-        base = __shfl_sync(0xffffffffu, base, 0);
+        const int base = base_next;
+        const uint32_t r = r_next;
         if (base >= n) break;
-        int e = base + lane;
-        int cnt = 0;
-        if (e < n) {
-          uint32_t r = bin[b0 + e];
-          uint32_t key = (__ldg(tag + r) >> 2) + 1u;
+        const int e = base + lane;
+        const bool valid = e < n;
+        uint32_t tg = 0u;
+        float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
+        if (valid) {
+          tg = __ldg(tag + r);
+          ra = __ldg(rib + r - 1);
+          rb = __ldg(rib + r);
+        }
+        if (lane == 0) base_next = atomicAdd(&s_next, 32);
+        base_next = __shfl_sync(0xffffffffu, base_next, 0);
+        if (base_next + lane < n) r_next = bin[b0 + base_next + lane];
+        // slot of the entry's path: one hash probe per distinct path in the warp
+        const uint32_t key = valid ? (tg >> 2) + 1u : 0u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        int slot = -1;
+        if (valid && lane == leader) {
           uint32_t h = (key * 2654435761u) & (HKEYS - 1);
-          int slot = -1;
           for (int it = 0; it < HKEYS; ++it) {
             uint32_t prev = pass == 0 ? atomicCAS(&s_keys[h], 0u, key) : s_keys[h];
             if (prev == 0u && pass == 0) {
@@ -467,7 +916,7 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
             if (prev == key) {
               uint16_t so;
               int spin = 0;
-              do {  // the inserting lane may not have published the slot yet
+              do {  // the inserting warp may not have published the slot yet
                 so = ((volatile uint16_t*)s_slot_of)[h];
               } while (so == 0xffffu && ++spin < (1 << 20));
               slot = so;
@@ -476,57 +925,94 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
             if (prev == 0u) break;
             h = (h + 1) & (HKEYS - 1);
           }
-          if (slot >= slot_lo && slot < slot_lo + SLOTS && slot < HKEYS)
-            cnt = setup_entry(rib, r, slot - slot_lo, ox, oy, tw, th, my[lane]);
         }
-        // warp scan of the pixel counts
-        uint32_t x = cnt;
+        slot = __shfl_sync(0xffffffffu, slot, leader);
+        unsigned long long packed = 0;
+        if (valid && slot >= slot_lo && slot < slot_lo + SLOTS && slot < HKEYS) {
+          EntrySetup& E = my[lane];
+          int tot = setup_edges(ra, rb, slot - slot_lo, ox, oy, tw, th, E);
+          if (tot > 0) {
+            st_rows += E.nrow;
+            // pixel items per class in 21-bit fields (at most 32 x 256 each):
+            // convex fast form, two-triangle fast form, general form
+            int cls = (E.valid & 32) ? 0 : (E.valid & 64) ? 1 : 2;
+            packed = (unsigned long long)tot << (21 * cls);
+          }
+        }
+        __syncwarp();
+        unsigned long long xp = packed;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-          if (lane >= o) x += y;
+          unsigned long long y = __shfl_up_sync(0xffffffffu, xp, o);
+          if (lane >= o) xp += y;
         }
-        s_pre[wid][lane + 1] = x;
+        s_pre[wid][lane + 1] = xp;
         if (lane == 0) s_pre[wid][0] = 0;
-        int total = __shfl_sync(0xffffffffu, (int)x, 31);
-        if (lane == 0 && stats) atomicAdd(stats, (unsigned long long)total);
+        unsigned long long tot3 = __shfl_sync(0xffffffffu, xp, 31);
+        st_items += tot3;  // three 21-bit fields of at most 8192 per batch
+        if (++st_batches == 200) flush_stats();
         __syncwarp();
-        for (int it = lane; it < total; it += 32) {
-          int lo = 0, hi = 31;  // last entry with pre <= it
+#pragma unroll 1
+        for (int cls = 0; cls < 3; ++cls) {
+          const int sh = 21 * cls;
+          const int total = (int)((tot3 >> sh) & 0x1fffffu);
+          for (int it = lane; it < total; it += 32) {
+            int lo = 0;  // last entry whose prefix in this class is <= it
 #pragma unroll
-          for (int st = 16; st > 0; st >>= 1)
-            if (lo + st <= hi && (int)s_pre[wid][lo + st] <= it) lo += st;
-          const EntrySetup& E = my[lo];
-          int li = it - (int)s_pre[wid][lo];
-          int k = 0;  // row: the last one with rowpre[k] <= li
+            for (int st = 16; st > 0; st >>= 1)
+              if (lo + st <= 31 && (int)((s_pre[wid][lo + st] >> sh) & 0x1fffffu) <= it) lo += st;
+            const EntrySetup& E = my[lo];
+            int li = it - (int)((s_pre[wid][lo] >> sh) & 0x1fffffu);
+            int k = 0;
 #pragma unroll
-          for (int st = 8; st > 0; st >>= 1)
-            if ((int)E.rowpre[k + st] <= li) k += st;
-          int ly = E.row0 + k, lx = E.x0[k] + (li - (int)E.rowpre[k]);
-          uint32_t m = pixel_mask(E, lx, ly);
-          if (m) {
-            int lp = ly * TILE_PX + lx;
-            atomicOr(&s_mask[E.slot * MASK_WORDS + (lp >> 1)], m << (16 * (lp & 1)));
+            for (int st = 8; st > 0; st >>= 1)
+              if ((int)E.rowpre[k + st] <= li) k += st;
+            int ly = E.row0 + k, lx = E.x0[k] + (li - (int)E.rowpre[k]);
+            uint32_t m = cls == 0 ? fast_mask(E, lx * 256, ly * 256)
+                         : cls == 1 ? fast_mask2(E, lx * 256, ly * 256)
+                                    : tri_or_quad_mask(E, lx, ly);
+            if (m) {
+              int lp = ly * TILE_PX + lx;
+              atomicOr(&s_mask[E.slot * MASK_WORDS + (lp >> 1)], m << (16 * (lp & 1)));
+            }
           }
         }
         __syncwarp();
       }
       __syncthreads();
-      // per-path popcounts and the canvas for this pass's slots
+      // per-path popcounts, OR into the tile's canvas words, and clear: one
+      // warp per slot
       int nslot = min(s_nslot, HKEYS);
       int nhere = min(SLOTS, nslot - slot_lo);
       for (int s2 = wid; s2 < nhere; s2 += CV_WARPS) {
+        uint32_t* ms = s_mask + s2 * MASK_WORDS;
         unsigned c = 0;
-        for (int w = lane; w < MASK_WORDS; w += 32) c += __popc(s_mask[s2 * MASK_WORDS + w]);
+#pragma unroll
+        for (int w = lane; w < MASK_WORDS; w += 32) {
+          uint32_t v = ms[w];
+          if (v) {
+            ms[w] = 0u;
+            c += __popc(v);
+            atomicOr(&s_canvas[w], v);
+          }
+        }
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if (lane == 0 && c) {
           uint32_t p = s_slot_path[slot_lo + s2];
           if ((int)p < n_path) atomicAdd(covered + p, (unsigned long long)c);
         }
       }
+      if (threadIdx.x == 0) {
+        if (s_nslot > HKEYS) ps_record_error(status, PS_ERR_CAPACITY);
+        if (stats) {
+          atomicAdd(stats + 5, 1ull);
+          if (pass == 0) atomicAdd(stats + 4, (unsigned long long)nslot);
+        }
+      }
+      __syncthreads();
       for (int w = threadIdx.x; w < MASK_WORDS; w += CV_NT) {
-        uint32_t v = 0;
-        for (int s2 = 0; s2 < nhere; ++s2) v |= s_mask[s2 * MASK_WORDS + w];
+        uint32_t v = s_canvas[w];
+        s_canvas[w] = 0u;
         int lp = 2 * w;
         int py = ty * TILE_PX + lp / TILE_PX, px = tx * TILE_PX + lp % TILE_PX;
         if (py < H) {
@@ -538,10 +1024,6 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
           if (px + 1 < W) canvas[(int64_t)py * W + px + 1] = (uint16_t)(v >> 16);
         }
       }
-      __syncthreads();
-      for (int i = threadIdx.x; i < nhere * MASK_WORDS; i += CV_NT) s_mask[i] = 0u;
-      if (threadIdx.x == 0 && s_nslot > HKEYS) ps_record_error(status, PS_ERR_CAPACITY);
-      __syncthreads();
       if (slot_lo + SLOTS >= nslot) break;
     }
   }
@@ -585,7 +1067,7 @@ extern "C" int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const 
   cudaMemsetAsync(ctx->d_tile_count, 0, sizeof(int32_t) * (n_tile + 1), st);
   cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
   cudaMemsetAsync(d_covered, 0, sizeof(uint64_t) * (size_t)n_path, st);
-  cudaMemsetAsync(ctx->d_scratch64, 0, sizeof(int64_t), st);
+  cudaMemsetAsync(ctx->d_scratch64, 0, 7 * sizeof(int64_t), st);
   int grid_bin = ps_persistent_grid(ctx, (const void*)k_bin<0>, 256, 0);
   const float4* rib = reinterpret_cast<const float4*>(d_rib);
   { ProfScope ps_(ctx, PK_BIN_COUNT, st);
@@ -607,21 +1089,21 @@ extern "C" int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const 
   return ps_cuda_check(cudaGetLastError());
 }
 
-extern "C" int ps_raster_stats(ps_context* ctx, int64_t* h_pairs, int64_t* h_span_pixels) {
-  if (!ctx || !h_pairs || !h_span_pixels) return PS_ERR_INVALID;
-  *h_pairs = 0;
-  *h_span_pixels = 0;
-  if (!ctx->d_tile_off || ctx->last_n_tile <= 0) return PS_OK;
-  int32_t v = 0;
-  int64_t sp = 0;
-  cudaStream_t st = (cudaStream_t)ctx->last_stream;
-  int rc = ps_cuda_check(cudaMemcpyAsync(&v, ctx->d_tile_off + ctx->last_n_tile, sizeof(int32_t),
-                                         cudaMemcpyDeviceToHost, st));
-  if (rc == PS_OK)
-    rc = ps_cuda_check(cudaMemcpyAsync(&sp, ctx->d_scratch64, sizeof(int64_t),
+extern "C" int ps_raster_stats(ps_context* ctx, int64_t* h_counts, int n_counts) {
+  if (!ctx || !h_counts || n_counts < 0) return PS_ERR_INVALID;
+  int64_t v[PS_RSTAT_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int rc = PS_OK;
+  if (ctx->d_tile_off && ctx->last_n_tile > 0) {
+    int32_t pairs = 0;
+    cudaStream_t st = (cudaStream_t)ctx->last_stream;
+    rc = ps_cuda_check(cudaMemcpyAsync(&pairs, ctx->d_tile_off + ctx->last_n_tile, sizeof(int32_t),
                                        cudaMemcpyDeviceToHost, st));
-  if (rc == PS_OK) rc = ps_cuda_check(cudaStreamSynchronize(st));
-  *h_pairs = v;
-  *h_span_pixels = sp;
+    if (rc == PS_OK)
+      rc = ps_cuda_check(cudaMemcpyAsync(v + 1, ctx->d_scratch64, 7 * sizeof(int64_t),
+                                         cudaMemcpyDeviceToHost, st));
+    if (rc == PS_OK) rc = ps_cuda_check(cudaStreamSynchronize(st));
+    v[0] = pairs;
+  }
+  for (int i = 0; i < n_counts; ++i) h_counts[i] = i < PS_RSTAT_COUNT ? v[i] : 0;
   return rc;
 }
