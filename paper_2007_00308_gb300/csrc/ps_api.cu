@@ -55,6 +55,15 @@ int ps_ensure_raster(ps_context* ctx, int64_t n_tile, int64_t n_pair) {
   return PS_OK;
 }
 
+int ps_ensure_quad_hits(ps_context* ctx, int64_t n_rib) {
+  if (n_rib <= ctx->quad_hits_cap) return PS_OK;
+  int64_t cap = n_rib + n_rib / 8 + 1024;
+  int rc = grow((void**)&ctx->d_quad_hits, sizeof(uint32_t) * cap);
+  if (rc != PS_OK) return rc;
+  ctx->quad_hits_cap = cap;
+  return PS_OK;
+}
+
 int ps_persistent_grid(ps_context* ctx, const void* kernel, int block, size_t smem) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess ||
@@ -91,7 +100,7 @@ extern "C" void ps_destroy(ps_context* ctx) {
   void* ptrs[] = {ctx->d_status, ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
                   ctx->d_tile_aggd, ctx->d_tile_incld, ctx->d_counters, ctx->d_recs,
                   ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor, ctx->d_bin,
-                  ctx->d_scratch64, ctx->d_mask_scratch, ctx->d_adj};
+                  ctx->d_scratch64, ctx->d_mask_scratch, ctx->d_adj, ctx->d_quad_hits};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free(ctx);

@@ -81,6 +81,8 @@ struct ps_context {
   int32_t* d_tile_cursor;   // [n_tile]
   int64_t raster_tile_cap;
   uint32_t* d_bin;          // [pair_cap]
+  uint32_t* d_quad_hits;    // [quad_hits_cap] per-rib tile-hit masks of the binning passes
+  int64_t quad_hits_cap;
   int64_t pair_cap;
   int64_t* d_scratch64;     // 16 int64 of per-call scalars
   int64_t last_n_tile;      // tiles of the most recent raster call
@@ -216,6 +218,7 @@ __device__ __forceinline__ double lookback_segsum(uint32_t* flag, double* agg, d
 int ps_ensure_tiles(ps_context* ctx, int64_t n_tile);
 int ps_ensure_recs(ps_context* ctx, int64_t n_link);
 int ps_ensure_raster(ps_context* ctx, int64_t n_tile, int64_t n_pair);
+int ps_ensure_quad_hits(ps_context* ctx, int64_t n_rib);
 int ps_cuda_check(cudaError_t e);
 int ps_persistent_grid(ps_context* ctx, const void* kernel, int block, size_t smem);
 // Link setup (records in ctx->d_recs, link path indices after them) into the given

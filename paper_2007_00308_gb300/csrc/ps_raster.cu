@@ -15,10 +15,9 @@ constexpr int TILE_PX = 16;                 // tile edge in pixels
 constexpr int TILE_UNITS = TILE_PX * 256;   // in 1/256 px
 constexpr int COORD_LIMIT = 1 << 29;        // |v * 256| < 2^29, i.e. |v| < 2^21 px
 
-__device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {
-  return a >= 0 ? a / b : -((-a + b - 1) / b);
-}
-__device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return -floor_div(-a, b); }
+// floor(a / 256) and ceil(a / 256) (arithmetic shifts round toward -inf)
+__device__ __forceinline__ int64_t floor256(int64_t a) { return a >> 8; }
+__device__ __forceinline__ int64_t ceil256(int64_t a) { return -((-a) >> 8); }
 
 struct QuadFix {
   int x[4], y[4];  // N0 P0 N1 P1 in 1/256 px
@@ -41,21 +40,11 @@ __device__ __forceinline__ bool snap_quad(const float4 a, const float4 b, QuadFi
 
 // Pixel range whose sample window [256p + 8, 256p + 248] meets [lo, hi].
 __device__ __forceinline__ void pix_range(int lo, int hi, int n, int& p0, int& p1) {
-  int64_t a = ceil_div((int64_t)lo - 248, 256), b = floor_div((int64_t)hi - 8, 256);
+  int64_t a = ceil256((int64_t)lo - 248), b = floor256((int64_t)hi - 8);
   if (a < 0) a = 0;
   if (b > n - 1) b = n - 1;
   p0 = (int)a;
   p1 = (int)b;
-}
-
-__device__ __forceinline__ void quad_pixels(const QuadFix& q, int W, int H, int& px0, int& px1,
-                                            int& py0, int& py1) {
-  int mnx = min(min(q.x[0], q.x[1]), min(q.x[2], q.x[3]));
-  int mxx = max(max(q.x[0], q.x[1]), max(q.x[2], q.x[3]));
-  int mny = min(min(q.y[0], q.y[1]), min(q.y[2], q.y[3]));
-  int mxy = max(max(q.y[0], q.y[1]), max(q.y[2], q.y[3]));
-  pix_range(mnx, mxx, W, px0, px1);
-  pix_range(mny, mxy, H, py0, py1);
 }
 
 // Can triangle (x0,y0)-(x1,y1)-(x2,y2) cover a sample of the tile whose samples
@@ -80,52 +69,154 @@ __device__ __forceinline__ bool tri_meets_rect(int x0, int y0, int x1, int y1, i
   return true;
 }
 
-// pass 0: count (quad, tile) pairs per tile; pass 1: scatter rib ids into bins.
-// Lanes of a warp that hit the same tile are grouped: one atomic per group.
+// Same test in int32, for triangles whose extent is below 2^14 on both axes
+// and rectangles within 2^14 + 4096 of them: every product stays below 2^29.
+__device__ __forceinline__ bool tri_meets_rect32(int x0, int y0, int x1, int y1, int x2, int y2,
+                                                 int rx0, int ry0, int rx1, int ry1) {
+  int area = (x1 - x0) * (y2 - y0) - (y1 - y0) * (x2 - x0);
+  if (area == 0) return false;
+  if (area < 0) {
+    int t = x1; x1 = x2; x2 = t;
+    t = y1; y1 = y2; y2 = t;
+  }
+  int vx[3] = {x0, x1, x2}, vy[3] = {y0, y1, y2};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    int A = vy[i] - vy[(i + 1) % 3], B = vx[(i + 1) % 3] - vx[i];
+    int cx = A >= 0 ? rx1 : rx0, cy = B >= 0 ? ry1 : ry0;
+    if (A * (cx - vx[i]) + B * (cy - vy[i]) < 0) return false;
+  }
+  return true;
+}
+
+// Does quad q (triangles N0 P0 P1 and N0 P1 N1) meet tile (tx, ty)'s sample
+// rectangle, clipped to the canvas?
+__device__ __forceinline__ bool quad_meets_tile(const QuadFix& q, bool small, int tx, int ty,
+                                                int W, int H) {
+  int rx0 = tx * TILE_UNITS + 8, ry0 = ty * TILE_UNITS + 8;
+  int rx1 = min(tx * TILE_UNITS + TILE_UNITS, W * 256) - 8;
+  int ry1 = min(ty * TILE_UNITS + TILE_UNITS, H * 256) - 8;
+  if (small)
+    return tri_meets_rect32(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], rx0, ry0, rx1, ry1) ||
+           tri_meets_rect32(q.x[0], q.y[0], q.x[3], q.y[3], q.x[2], q.y[2], rx0, ry0, rx1, ry1);
+  return tri_meets_rect(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], rx0, ry0, rx1, ry1) ||
+         tri_meets_rect(q.x[0], q.y[0], q.x[3], q.y[3], q.x[2], q.y[2], rx0, ry0, rx1, ry1);
+}
+
+// pass 0: count (quad, tile) pairs per tile and keep, per quad with at most 31
+// candidate tiles (those of its pixel bounding box), the bit mask of the tiles
+// its triangles meet; pass 1: scatter rib ids into bins from those masks
+// (re-testing only quads with more candidates).  A warp takes 32 quads, one
+// per lane, and flattens their (quad, candidate) pairs with a warp scan so that
+// each lane tests one pair at a time; lanes of the warp that hit the same tile
+// are grouped: one atomic per group.
+constexpr uint32_t HITS_RETEST = 0xffffffffu;
+constexpr int BIN_NT = 256;
+
+struct BinQuad {
+  int x[4], y[4];
+  int tx0, ty0, ntx, n;  // candidate tiles: ntx columns from (tx0, ty0), n in all
+  uint32_t mask;         // pass 1: hit mask from pass 0; pass 0: hits found
+  int small;
+};
+
 template <int PASS>
-__global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rib,
-                                             const uint32_t* __restrict__ tag,
-                                             const int64_t* __restrict__ n_rib, int64_t capacity,
-                                             int W, int H, int tiles_x, int32_t* __restrict__ count,
-                                             const int32_t* __restrict__ off,
-                                             int32_t* __restrict__ cursor,
-                                             uint32_t* __restrict__ bin, int64_t pair_cap,
-                                             int32_t* status) {
+__global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
+                                                const uint32_t* __restrict__ tag,
+                                                const int64_t* __restrict__ n_rib, int64_t capacity,
+                                                int W, int H, int tiles_x,
+                                                int32_t* __restrict__ count,
+                                                const int32_t* __restrict__ off,
+                                                int32_t* __restrict__ cursor,
+                                                uint32_t* __restrict__ bin, int64_t pair_cap,
+                                                uint32_t* __restrict__ hits, int32_t* status) {
+  __shared__ BinQuad s_q[BIN_NT];
+  __shared__ int s_pre[BIN_NT / 32][33];
   int64_t R = *n_rib;
   if (R > capacity) R = capacity;
-  int lane = threadIdx.x & 31;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < R; base += stride) {
-    int64_t r = base + threadIdx.x;
-    bool act = r >= 1 && r < R && !(__ldg(tag + r) & PS_TAG_LINK_START);
-    QuadFix q;
-    int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  BinQuad* wq = s_q + wid * 32;
+  int64_t stride = (int64_t)gridDim.x * BIN_NT;
+  for (int64_t base = (int64_t)blockIdx.x * BIN_NT; base < R; base += stride) {
+    const int64_t r = base + threadIdx.x;
+    const bool act = r >= 1 && r < R && !(__ldg(tag + r) & PS_TAG_LINK_START);
+    BinQuad& Q = wq[lane];
+    int cnt = 0;
+    Q.n = 0;
+    Q.mask = 0;
     if (act) {
+      QuadFix q;
       if (!snap_quad(__ldg(rib + r - 1), __ldg(rib + r), q)) {
-        ps_record_error(status, PS_ERR_RANGE);
+        if (PASS == 0) ps_record_error(status, PS_ERR_RANGE);
       } else {
+        int mnx = min(min(q.x[0], q.x[1]), min(q.x[2], q.x[3]));
+        int mxx = max(max(q.x[0], q.x[1]), max(q.x[2], q.x[3]));
+        int mny = min(min(q.y[0], q.y[1]), min(q.y[2], q.y[3]));
+        int mxy = max(max(q.y[0], q.y[1]), max(q.y[2], q.y[3]));
         int px0, px1, py0, py1;
-        quad_pixels(q, W, H, px0, px1, py0, py1);
+        pix_range(mnx, mxx, W, px0, px1);
+        pix_range(mny, mxy, H, py0, py1);
         if (px0 <= px1 && py0 <= py1) {
-          tx0 = px0 / TILE_PX; tx1 = px1 / TILE_PX; ty0 = py0 / TILE_PX; ty1 = py1 / TILE_PX;
+          int tx0 = px0 / TILE_PX, tx1 = px1 / TILE_PX, ty0 = py0 / TILE_PX, ty1 = py1 / TILE_PX;
+          for (int v = 0; v < 4; ++v) {
+            Q.x[v] = q.x[v];
+            Q.y[v] = q.y[v];
+          }
+          Q.tx0 = tx0;
+          Q.ty0 = ty0;
+          Q.ntx = tx1 - tx0 + 1;
+          Q.n = Q.ntx * (ty1 - ty0 + 1);
+          Q.small = mxx - mnx < (1 << 14) && mxy - mny < (1 << 14);
+          if (PASS == 1) {
+            uint32_t m = __ldg(hits + r);
+            Q.mask = m;
+            cnt = Q.n <= 31 ? __popc(m) : Q.n;
+          } else {
+            cnt = Q.n;
+          }
         }
       }
     }
-    int ntx = tx1 - tx0 + 1, n = (tx1 >= tx0 && ty1 >= ty0) ? ntx * (ty1 - ty0 + 1) : 0;
-    int nmax = n;
-    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
-    for (int i = 0; i < nmax; ++i) {
-      int t = -1;
-      if (i < n) {
-        int tx = tx0 + i % ntx, ty = ty0 + i / ntx;
-        // sample rectangle of the tile (1/256 px), clipped to the canvas
-        int rx0 = tx * TILE_UNITS + 8, ry0 = ty * TILE_UNITS + 8;
-        int rx1 = min(tx * TILE_UNITS + TILE_UNITS, W * 256) - 8;
-        int ry1 = min(ty * TILE_UNITS + TILE_UNITS, H * 256) - 8;
-        bool hit = n == 1 ||
-                   tri_meets_rect(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], rx0, ry0, rx1, ry1) ||
-                   tri_meets_rect(q.x[0], q.y[0], q.x[3], q.y[3], q.x[2], q.y[2], rx0, ry0, rx1, ry1);
-        if (hit) t = ty * tiles_x + tx;
+    // warp scan of the pair counts
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    s_pre[wid][lane + 1] = x;
+    if (lane == 0) s_pre[wid][0] = 0;
+    const int total = __shfl_sync(0xffffffffu, x, 31);
+    __syncwarp();
+    for (int it0 = 0; it0 < total; it0 += 32) {
+      const int it = it0 + lane;
+      int t = -1, e = 0, i = 0;
+      if (it < total) {
+        int lo = 0;  // last quad whose prefix is <= it
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1)
+          if (lo + st <= 31 && s_pre[wid][lo + st] <= it) lo += st;
+        e = lo;
+        const BinQuad& B = wq[e];
+        int k = it - s_pre[wid][e];
+        bool hit;
+        if (PASS == 1 && B.n <= 31) {
+          i = __fns(B.mask, 0, k + 1);  // position of the (k+1)-th set bit
+          hit = true;
+        } else {
+          i = k;
+          int tx = B.tx0 + i % B.ntx, ty = B.ty0 + i / B.ntx;
+          QuadFix q;
+          for (int v = 0; v < 4; ++v) {
+            q.x[v] = B.x[v];
+            q.y[v] = B.y[v];
+          }
+          hit = B.n == 1 || quad_meets_tile(q, B.small != 0, tx, ty, W, H);
+        }
+        if (hit) {
+          t = (B.ty0 + i / B.ntx) * tiles_x + (B.tx0 + i % B.ntx);
+          if (PASS == 0 && i < 31) atomicOr(&wq[e].mask, 1u << i);
+        }
       }
       unsigned peers = __match_any_sync(0xffffffffu, t);
       int leader = __ffs(peers) - 1;
@@ -139,11 +230,14 @@ __global__ void __launch_bounds__(256) k_bin(const float4* __restrict__ rib,
           basepos = __shfl_sync(peers, basepos, leader);
           int pos = basepos + __popc(peers & ((1u << lane) - 1u));
           int64_t at = (int64_t)off[t] + pos;
-          if (at < pair_cap && at < off[t + 1]) bin[at] = (uint32_t)r;
+          if (at < pair_cap && at < off[t + 1]) bin[at] = (uint32_t)(base + wid * 32 + e);
           else ps_record_error(status, PS_ERR_CAPACITY);
         }
       }
     }
+    __syncwarp();
+    if (PASS == 0 && act) hits[r] = Q.n <= 31 ? Q.mask : HITS_RETEST;
+    __syncwarp();
   }
 }
 
@@ -310,7 +404,7 @@ __device__ __forceinline__ void to_fast_edge(Edge& ed) {
 
 // Pixel rows whose sample band [256 ly + 8, 256 ly + 248] meets [ymin, ymax].
 __device__ __forceinline__ int entry_rows(int ymin, int ymax, int th, EntrySetup& E) {
-  int64_t c0 = ceil_div((int64_t)ymin - 248, 256), c1 = floor_div((int64_t)ymax - 8, 256);
+  int64_t c0 = ceil256((int64_t)ymin - 248), c1 = floor256((int64_t)ymax - 8);
   int ly0 = (int)(c0 < 0 ? 0 : c0);
   int ly1 = (int)(c1 > th - 1 ? th - 1 : c1);
   if (ly1 < ly0) return 0;
@@ -1053,6 +1147,7 @@ extern "C" int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const 
   int64_t want_pairs = ctx->pair_cap > 0 ? ctx->pair_cap : 4 * capacity + 1024;
   int rc = ps_ensure_raster(ctx, n_tile, want_pairs);
   if (rc != PS_OK) return rc;
+  if ((rc = ps_ensure_quad_hits(ctx, capacity)) != PS_OK) return rc;
   size_t cov_smem = coverage_smem_bytes();
   static int attr_done = 0;
   if (!attr_done) {
@@ -1068,19 +1163,21 @@ extern "C" int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const 
   cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
   cudaMemsetAsync(d_covered, 0, sizeof(uint64_t) * (size_t)n_path, st);
   cudaMemsetAsync(ctx->d_scratch64, 0, 7 * sizeof(int64_t), st);
-  int grid_bin = ps_persistent_grid(ctx, (const void*)k_bin<0>, 256, 0);
+  int grid_bin = ps_persistent_grid(ctx, (const void*)k_bin<0>, BIN_NT, 0);
   const float4* rib = reinterpret_cast<const float4*>(d_rib);
   { ProfScope ps_(ctx, PK_BIN_COUNT, st);
-  k_bin<0><<<grid_bin, 256, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, tiles_x,
+  k_bin<0><<<grid_bin, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, tiles_x,
                                       ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor,
-                                      ctx->d_bin, ctx->pair_cap, ctx->d_status); }
+                                      ctx->d_bin, ctx->pair_cap, ctx->d_quad_hits,
+                                      ctx->d_status); }
   { ProfScope ps_(ctx, PK_TILE_SCAN, st);
   k_tile_scan<<<1, 1024, 0, st>>>(ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor,
                                   (int)n_tile, ctx->pair_cap, ctx->d_status); }
   { ProfScope ps_(ctx, PK_BIN_SCATTER, st);
-  k_bin<1><<<grid_bin, 256, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, tiles_x,
+  k_bin<1><<<grid_bin, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, tiles_x,
                                       ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor,
-                                      ctx->d_bin, ctx->pair_cap, ctx->d_status); }
+                                      ctx->d_bin, ctx->pair_cap, ctx->d_quad_hits,
+                                      ctx->d_status); }
   { ProfScope ps_(ctx, PK_COVERAGE, st);
   k_coverage<<<grid_cov, CV_NT, cov_smem, st>>>(
       rib, d_tag, ctx->d_tile_off, ctx->d_bin, ctx->pair_cap, width, height, tiles_x, (int)n_tile,

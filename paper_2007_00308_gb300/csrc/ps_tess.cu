@@ -77,10 +77,8 @@ __device__ __forceinline__ void solve_coeffs(const Seg& g, V N, R& a, R& b, R& c
 // small slack), the one whose tangent points along psi (largest H.T(psi)), else
 // the endpoint with the smaller |H.N|.  MIXED redoes near-double roots in FP64.
 template <bool MIXED>
-__device__ float solve_t(const Seg& g, float psi, float pa, float pb) {
+__device__ float solve_t(const Seg& g, float psi, float sn, float cs, float pa, float pb) {
   if (g.type == PS_LINE) return pa;
-  float sn, cs;
-  sincosf(psi, &sn, &cs);
   float2 N = mk(-sn, cs), T = mk(cs, sn);
   float a, b, c;
   solve_coeffs<float>(g, N, a, b, c);
@@ -128,6 +126,13 @@ __device__ float solve_t(const Seg& g, float psi, float pa, float pb) {
   if (found) return best;
   float fa = fabsf(dot2(hodo(g, pa), N)), fb = fabsf(dot2(hodo(g, pb), N));
   return fa < fb ? pa : pb;
+}
+
+template <bool MIXED>
+__device__ __forceinline__ float solve_t(const Seg& g, float psi, float pa, float pb) {
+  float sn, cs;
+  sincosf(psi, &sn, &cs);
+  return solve_t<MIXED>(g, psi, sn, cs, pa, pb);
 }
 
 // ---------------------------------------------------------------------------
@@ -770,13 +775,16 @@ __global__ void __launch_bounds__(SETUP_NT) k_link_setup(
 }
 
 // ---------------------------------------------------------------------------
-// K2: ribs.  A CTA takes tiles of EMIT_TILE consecutive ribs; each thread finds
-// its rib's link by binary search over the tile's link range, evaluates psi(j),
-// t(j), g(t(j)) and n(j), and writes the rib, its tag and the chord to the
-// previous rib of the same link.
+// K2: ribs.  Each warp takes chunks of EMIT_CHUNK consecutive ribs and works
+// through them in slabs of 32, one rib per lane: the lane's link advances
+// monotonically from the chunk's first link (found by a 32-way search), the
+// rib's psi(j), t(j), g(t(j)) and n(j) are evaluated, and the rib, its tag and
+// the chord to the previous rib of the same link (the previous lane, the last
+// lane of the previous slab, or for the chunk's first rib a re-evaluation) are
+// written.  No block-wide synchronisation.
 constexpr int EMIT_NT = 256;
-constexpr int EMIT_K = 4;
-constexpr int EMIT_TILE = EMIT_NT * EMIT_K;
+constexpr int EMIT_K = 16;
+constexpr int EMIT_CHUNK = 32 * EMIT_K;
 
 struct RibEval {
   float4 v;      // N.x N.y P.x P.y
@@ -805,17 +813,13 @@ __device__ __forceinline__ RibEval eval_rib(const LinkRec* __restrict__ L, int j
     // k == M only for j == N; boundary when j == dsum[k]
     float t, psi;
     int dk = (int)__ldg(&L->dsum[k]);
-    if (j == dk) {
-      t = __ldg(&L->p[k]);
-      psi = __ldg(&L->psi[k]);
-    } else {
-      psi = __ldg(&L->psi[k]) + __ldg(&L->step[k]) * (float)(j - dk);
-      float pa = __ldg(&L->p[k]);
-      if (META_PIVOT(meta, k)) t = pa;
-      else t = solve_t<MIXED>(g, psi, pa, __ldg(&L->p[k + 1]));
-    }
+    bool bnd = j == dk;
+    psi = bnd ? __ldg(&L->psi[k]) : __ldg(&L->psi[k]) + __ldg(&L->step[k]) * (float)(j - dk);
     float sn, cs;
     sincosf(psi, &sn, &cs);
+    float pa = __ldg(&L->p[k]);
+    if (bnd || META_PIVOT(meta, k)) t = pa;
+    else t = solve_t<MIXED>(g, psi, sn, cs, pa, __ldg(&L->p[k + 1]));
     float2 n = mk(-sn, cs);
     float2 gr = MIXED ? g_rel_comp(g, t) : g_rel(g, t);
     float2 Nv = gr - n * rN, Pv = gr + n * rP;
@@ -858,43 +862,55 @@ __device__ __forceinline__ int64_t find_link(const int32_t* off, int64_t lo, int
   return lo;
 }
 
+// Warp-cooperative find_link over [0, n - 1] (off[0] <= r): 32 probes per round.
+__device__ __forceinline__ int64_t find_link_warp(const int32_t* off, int64_t n, int64_t r,
+                                                  int lane) {
+  int64_t lo = 0, hi = n - 1;  // off[lo] <= r, answer in [lo, hi]
+  while (hi - lo > 31) {
+    int64_t step = (hi - lo + 31) / 32;
+    int64_t cand = lo + lane * step;
+    bool ok = cand <= hi && (int64_t)__ldg(off + cand) <= r;
+    uint32_t b = __ballot_sync(0xffffffffu, ok);
+    int m = __popc(b);  // lanes 0 .. m-1 ok (lane 0 always)
+    int64_t nlo = lo + (int64_t)(m - 1) * step;
+    int64_t nhi = m < 32 ? lo + (int64_t)m * step - 1 : hi;
+    lo = nlo;
+    hi = nhi < hi ? nhi : hi;
+  }
+  int64_t cand = lo + lane;
+  bool ok = cand <= hi && (int64_t)__ldg(off + cand) <= r;
+  uint32_t b = __ballot_sync(0xffffffffu, ok);
+  return lo + __popc(b) - 1;
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(EMIT_NT) k_emit(
     const LinkRec* __restrict__ recs, const int32_t* __restrict__ link_off,
     const int32_t* __restrict__ link_path, int64_t n_link, const int64_t* __restrict__ n_rib,
     int64_t capacity, float4* __restrict__ rib, uint32_t* __restrict__ tag,
     float* __restrict__ chord, float* __restrict__ tout) {
-  __shared__ int64_t s_l0, s_l1;
-  __shared__ float2 s_g[EMIT_NT];
-  __shared__ int64_t s_lk[EMIT_NT];
-  __shared__ float s_t[EMIT_NT];
   int64_t R = *n_rib;
   if (R > capacity) R = capacity;
-  int64_t n_tiles = (R + EMIT_TILE - 1) / EMIT_TILE;
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    int64_t r0 = tile * EMIT_TILE;
-    int64_t r1 = r0 + EMIT_TILE;
-    if (r1 > R) r1 = R;
-    if (threadIdx.x == 0) {
-      s_l0 = find_link(link_off, 0, n_link - 1, r0);
-      s_l1 = find_link(link_off, 0, n_link - 1, r1 - 1);
-    }
-    __syncthreads();
-    int64_t l0 = s_l0, l1 = s_l1;
-    float2 prev_g = mk(0.f, 0.f);
-    int64_t prev_l = -1;
-    float prev_t = 0.f;
-    for (int kslab = 0; kslab < EMIT_K; ++kslab) {
-      int64_t r = r0 + (int64_t)kslab * EMIT_NT + threadIdx.x;
-      bool active = r < r1;
-      int64_t l = -1;
+  const int lane = threadIdx.x & 31;
+  const int64_t n_chunks = (R + EMIT_CHUNK - 1) / EMIT_CHUNK;
+  const int64_t warp0 = ((int64_t)blockIdx.x * EMIT_NT + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * EMIT_NT) >> 5;
+  for (int64_t c = warp0; c < n_chunks; c += n_warps) {
+    const int64_t r0 = c * EMIT_CHUNK;
+    int64_t l = find_link_warp(link_off, n_link, r0, lane);
+    float2 carry_g = mk(0.f, 0.f);
+    float carry_t = 0.f;
+#pragma unroll 1
+    for (int s = 0; s < EMIT_K; ++s) {
+      const int64_t r = r0 + (int64_t)s * 32 + lane;
+      const bool active = r < R;
       RibEval E;
       E.grel = mk(0.f, 0.f);
       E.t = 0.f;
       E.seg = false;
       int j = 0;
       if (active) {
-        l = find_link(link_off, l0, l1, r);
+        while (l + 1 < n_link && (int64_t)__ldg(link_off + l + 1) <= r) ++l;
         j = (int)(r - __ldg(link_off + l));
         E = eval_rib<MIXED>(recs + l, j);
         rib[r] = E.v;
@@ -903,47 +919,35 @@ __global__ void __launch_bounds__(EMIT_NT) k_emit(
         if (tout) tout[r] = E.t;
       }
       if (chord) {
-        // previous rib's centreline point: neighbour in this slab, the last
-        // thread of the previous slab, or (first rib of the tile) recomputed
-        s_g[threadIdx.x] = E.grel;
-        s_lk[threadIdx.x] = l;
-        s_t[threadIdx.x] = E.t;
-        __syncthreads();
+        // rib r - 1 is in the same link iff j > 0
+        float2 pg;
+        pg.x = __shfl_up_sync(0xffffffffu, E.grel.x, 1);
+        pg.y = __shfl_up_sync(0xffffffffu, E.grel.y, 1);
+        float pt = __shfl_up_sync(0xffffffffu, E.t, 1);
+        if (lane == 0) {
+          pg = carry_g;
+          pt = carry_t;
+        }
+        carry_g.x = __shfl_sync(0xffffffffu, E.grel.x, 31);
+        carry_g.y = __shfl_sync(0xffffffffu, E.grel.y, 31);
+        carry_t = __shfl_sync(0xffffffffu, E.t, 31);
         if (active) {
-          float c = 0.f;
+          float cl = 0.f;
           if (E.seg && j > 0) {
-            float2 pg;
-            float pt;
-            bool have = false;
-            if (threadIdx.x > 0) {
-              pg = s_g[threadIdx.x - 1];
-              pt = s_t[threadIdx.x - 1];
-              have = true;
-            } else if (kslab > 0 && prev_l == l) {
-              pg = prev_g;
-              pt = prev_t;
-              have = true;
-            }
-            if (!have) {
+            if (lane == 0 && s == 0) {
               RibEval Ep = eval_rib<MIXED>(recs + l, j - 1);
               pg = Ep.grel;
               pt = Ep.t;
             }
             if (E.t >= pt) {
               float dx = E.grel.x - pg.x, dy = E.grel.y - pg.y;
-              c = sqrtf(dx * dx + dy * dy);
+              cl = sqrtf(dx * dx + dy * dy);
             }
           }
-          chord[r] = c;
+          chord[r] = cl;
         }
-        // carry the last thread's value into the next slab
-        prev_g = s_g[EMIT_NT - 1];
-        prev_l = s_lk[EMIT_NT - 1];
-        prev_t = s_t[EMIT_NT - 1];
-        __syncthreads();
       }
     }
-    __syncthreads();
   }
 }
 
