@@ -321,7 +321,8 @@ struct __align__(16) EntrySetup {
   uint16_t rowpre[17];     // prefix of span widths
   uint16_t slot;           // mask slot of this pass
   uint8_t valid;           // bit0 tri 0, bit1 tri 1, bit2 int64 path, bit3 convex quad,
-                           // bit4 int32 path, bit5 fast convex form, bit6 fast two-triangle form
+                           // bit4 int32 path, bit5 fast convex form, bit6 fast two-triangle
+                           // form
   uint8_t row0, nrow;
 };
 
@@ -423,10 +424,11 @@ constexpr uint32_t EL_TRI0_NEG = 0x8u | 0x6u << 4 | 0x1u << 8;   // 0->2 2->1 1-
 constexpr uint32_t EL_TRI1_POS = 0x8u | 0xEu << 4 | 0x3u << 8;   // 0->2 2->3 3->0
 constexpr uint32_t EL_TRI1_NEG = 0xCu | 0xBu << 4 | 0x2u << 8;   // 0->3 3->2 2->0
 
-// Setup of a quad whose extent is below 2^14 (64 px) on both axes: every
-// cross product and fast-form constant fits in int32, and one code path serves
-// all classes.  Vertex coordinates are tile-relative and the quad meets the
-// tile, so |8 - x| < 2^14 + 4104 and |A (8 - x) + B (8 - y)| < 2^30.
+// Setup of a quad whose extent is below 2^15 (128 px) on both axes: every
+// cross product of vertex differences is below 2^30 in magnitude and their
+// differences fit in int32; the fast-form constant A (8 - x) + B (8 - y) is
+// formed in int64 (|8 - x| < 2^15 + 4104, as the quad meets the tile) and
+// clamped into int32.  One code path serves all classes.
 __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax, int tw, int th,
                                            EntrySetup& E) {
   const int X0 = q.x[0], Y0 = q.y[0], X1 = q.x[1], Y1 = q.y[1];  // N0 P0
@@ -449,7 +451,14 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
     el = pos ? EL_CONVEX_POS : EL_CONVEX_NEG;
     cls = 8 | 32;
   } else if (a0 != 0 && a1 != 0) {
-    el = el0 | el1 << 12;
+    // diagonal first (as triangle 0 orients it), then the other two edges of
+    // each triangle; slot 5 unused
+    uint32_t d0 = a0 > 0 ? 0x2u : 0x8u;            // 2->0 or 0->2
+    uint32_t t0 = a0 > 0 ? (0x4u | 0x9u << 4)      // 0->1 1->2
+                         : (0x6u | 0x1u << 4);     // 2->1 1->0
+    uint32_t t1 = a1 > 0 ? (0xEu | 0x3u << 4)      // 2->3 3->0
+                         : (0xCu | 0xBu << 4);     // 0->3 3->2
+    el = d0 | t0 << 4 | t1 << 12;
     cls = 64;
   } else {
     el = a0 != 0 ? el0 : el1;
@@ -466,6 +475,8 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
   float kq[6], uq[6];
   uint32_t lo_side = 0;
   int smax = 0;
+  float k0 = 0.f, u0 = 0.f, eps0 = 0.f;
+  bool apos0 = false, anz0 = false;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     int ia = (el >> (4 * i)) & 3, ib = (el >> (4 * i + 2)) & 3;
@@ -474,15 +485,22 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
     int xb = ib == 0 ? X0 : ib == 1 ? X1 : ib == 2 ? X2 : X3;
     int yb = ib == 0 ? Y0 : ib == 1 ? Y1 : ib == 2 ? Y2 : Y3;
     int A = ya - yb, B = xb - xa, S = abs(A) + abs(B);
-    int c = A * (8 - xa) + B * (8 - ya);
+    long long c64 = (long long)A * (8 - xa) + (long long)B * (8 - ya);
     int lim = 4080 * S + 1;
-    c = min(max(c, -lim), lim);
+    int c = (int)(c64 > lim ? lim : (c64 < -lim ? -lim : c64));
     smax = max(smax, S);
     *reinterpret_cast<int4*>(&E.e[i]) = make_int4(A, B, c, 16 * A + 80 * B);
     float fa = (float)A;
     float k = __fdividef((float)-B, fa), u = __fdividef((float)-c, fa);
     float eps = 4.f + 1e-6f * (fabsf(u) + 4096.f * fabsf(k));
     float k240 = 240.f * k;
+    if (i == 0) {
+      k0 = k;
+      u0 = u;
+      eps0 = eps;
+      apos0 = A > 0;
+      anz0 = A != 0;
+    }
     if (A > 0) {
       kq[i] = k;
       uq[i] = u + fminf(0.f, k240) - eps;
@@ -497,7 +515,33 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
   }
   E.dm = 240 * smax;
   E.valid = cls | (a0 != 0 ? 1 : 0) | (a1 != 0 ? 2 : 0);
+  if (two) {
+    // With F(p) = cross(P1 - N0, p - N0), triangle 0's diagonal edge is
+    // -sgn(a0) F and triangle 1's is sgn(a1) F.  When a0 and a1 have the same
+    // sign the triangles lie on opposite sides and triangle 1 needs e[0] <= 0,
+    // taken as e[0] < 0 (the sign bit of ~e[0]): a sample on the diagonal inside
+    // triangle 1 lies on the segment N0 P1, which triangle 0 also covers.
+    // Otherwise triangle 1 needs e[0] >= 0 like triangle 0.  e[5].A holds the
+    // word XORed into e[0] for triangle 1's test.
+    E.e[5].A = (a0 > 0) == (a1 > 0) ? -1 : 0;
+  }
   if (entry_rows(ymin, ymax, th, E) == 0) return 0;
+  if (two && anz0) {
+    // slot 5 for spans: triangle 1's diagonal bound (e[0] reversed when the
+    // triangles lie on opposite sides, else e[0] itself); a horizontal diagonal
+    // bounds no x and leaves slot 5 as the always-true edge
+    bool lo5 = ((a0 > 0) == (a1 > 0)) ? !apos0 : apos0;
+    float k240 = 240.f * k0;
+    if (lo5) {
+      kq[5] = k0;
+      uq[5] = u0 + fminf(0.f, k240) - eps0;
+      lo_side |= 1u << 5;
+    } else {
+      kq[5] = -k0;
+      uq[5] = -(u0 + fmaxf(0.f, k240) + eps0);
+      lo_side &= ~(1u << 5);
+    }
+  }
   // row spans: group 0 = edges 0..3 (triangle 0 and, for a convex quad, the
   // fourth edge), group 1 = edges 3..5 of the two-triangle form; union of groups
   const bool e3g1 = two;
@@ -555,7 +599,7 @@ __device__ __forceinline__ int finish_spans(EntrySetup& E, int tw) {
   for (int j = 0; j < 16; ++j) {
     if (j < E.nrow) {
       int a0, w0;
-      if (E.valid & 96) row_span_fast(E, E.row0 + j, tw, a0, w0);
+      if (E.valid & 32) row_span_fast(E, E.row0 + j, tw, a0, w0);
       else row_span(E, E.row0 + j, tw, a0, w0);
       E.x0[j] = (uint8_t)a0;
       E.w[j] = (uint8_t)w0;
@@ -585,7 +629,7 @@ __device__ __forceinline__ int setup_edges(const float4 ra, const float4 rb, int
     int mxx = max(max(q.x[0], q.x[1]), max(q.x[2], q.x[3]));
     int mny = min(min(q.y[0], q.y[1]), min(q.y[2], q.y[3]));
     int mxy = max(max(q.y[0], q.y[1]), max(q.y[2], q.y[3]));
-    if (mxx - mnx < (1 << 14) && mxy - mny < (1 << 14))
+    if (mxx - mnx < (1 << 15) && mxy - mny < (1 << 15))
       return setup_small(q, mny, mxy, tw, th, E);
   }
   bool v0, v1, big = false;
@@ -637,16 +681,6 @@ __device__ __forceinline__ int setup_edges(const float4 ra, const float4 rb, int
   // |A| + |B| < 2^18 (shorter than 1024 px); every value of fast_mask then
   // fits in int32 (see fast_mask)
   int nf = (flags & 8) ? 4 : ((flags & 3) == 1 || (flags & 3) == 2) ? 3 : 0;
-  if (!nf && flags == 3 && !big) {
-    // both triangles real, polygon not convex: two-triangle fast form
-    long long smax = 0;
-    for (int i = 0; i < 6; ++i) smax = max(smax, llabs((long long)E.e[i].A) + llabs((long long)E.e[i].B));
-    if (smax < (1ll << 18)) {
-      for (int i = 0; i < 6; ++i) to_fast_edge(E.e[i]);
-      E.dm = (int)(240 * smax);
-      E.valid |= 64;
-    }
-  }
   if (nf && !big) {
     const Edge* src = (flags & 8) || (flags & 1) ? E.e : E.e + 3;
     long long smax = 0;
@@ -766,13 +800,17 @@ __device__ __forceinline__ uint32_t fast_mask(const EntrySetup& E, int cx, int c
   return ~neg & 0xffffu;
 }
 
-// Two-triangle fast form: a sample is covered iff one of the triangles has no
-// negative edge there (same bounds as fast_mask).
+// Two-triangle fast form: e[0] is the shared diagonal (as triangle 0 orients
+// it), e[1], e[2] triangle 0's other edges, e[3], e[4] triangle 1's, and
+// e[5].A the word XORed into e[0] for triangle 1 (see setup_small).  A sample
+// is covered iff one triangle has no failing edge there (same bounds as
+// fast_mask).
 __device__ __forceinline__ uint32_t fast_mask2(const EntrySetup& E, int cx, int cy) {
   const int dm = E.dm;
-  int v[6], i1[6], i2[6];
+  const uint32_t x1 = (uint32_t)E.e[5].A;
+  int v[5], i1[5], i2[5];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < 5; ++i) {
     const int4 ed = *reinterpret_cast<const int4*>(&E.e[i]);
     int t = ed.z + ed.x * cx + ed.y * cy;
     v[i] = min(max(t, -dm - 1), dm);
@@ -782,12 +820,13 @@ __device__ __forceinline__ uint32_t fast_mask2(const EntrySetup& E, int cx, int 
   uint32_t neg = 0;
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
-    uint32_t o = (uint32_t)(v[0] | v[1] | v[2]) & (uint32_t)(v[3] | v[4] | v[5]);
-    neg |= (o >> 31) << k;
+    uint32_t f0 = (uint32_t)(v[0] | v[1] | v[2]);
+    uint32_t f1 = ((uint32_t)v[0] ^ x1) | (uint32_t)(v[3] | v[4]);
+    neg |= ((f0 & f1) >> 31) << k;
     if (k < 15) {
       const bool up = ((5 * k) & 15) <= 10;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) v[i] += up ? i1[i] : i2[i];
+      for (int i = 0; i < 5; ++i) v[i] += up ? i1[i] : i2[i];
     }
   }
   return ~neg & 0xffffu;
@@ -826,21 +865,7 @@ __device__ __forceinline__ void row_span_fast(const EntrySetup& E, int ly, int t
   float y0 = 256.f * ly;
   float lo, hi;
   bool ok;
-  if (E.valid & 64) {
-    float l1, h1;
-    bool ok0 = band_extent_fast<3>(E.e, y0, lo, hi);
-    bool ok1 = band_extent_fast<3>(E.e + 3, y0, l1, h1);
-    if (!ok0) {
-      lo = l1;
-      hi = h1;
-    } else if (ok1) {
-      lo = fminf(lo, l1);
-      hi = fmaxf(hi, h1);
-    }
-    ok = ok0 || ok1;
-  } else {
-    ok = band_extent_fast<4>(E.e, y0, lo, hi);
-  }
+  ok = band_extent_fast<4>(E.e, y0, lo, hi);  // convex fast form (general path)
   a = 0;
   w = 0;
   if (!ok) return;
@@ -919,7 +944,7 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
   uint16_t* s_slot_of = reinterpret_cast<uint16_t*>(s_keys + HKEYS);             // HKEYS
   uint32_t* s_slot_path = reinterpret_cast<uint32_t*>(s_slot_of + HKEYS);        // HKEYS
   __shared__ int s_tile, s_nslot, s_next;
-  __shared__ unsigned long long s_pre[CV_WARPS][33];
+  __shared__ uint8_t s_own[CV_WARPS][32];
   __shared__ uint32_t s_canvas[MASK_WORDS];
 
   for (int i = threadIdx.x; i < SLOTS * MASK_WORDS; i += CV_NT) s_mask[i] = 0u;
@@ -1040,34 +1065,57 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
           unsigned long long y = __shfl_up_sync(0xffffffffu, xp, o);
           if (lane >= o) xp += y;
         }
-        s_pre[wid][lane + 1] = xp;
-        if (lane == 0) s_pre[wid][0] = 0;
-        unsigned long long tot3 = __shfl_sync(0xffffffffu, xp, 31);
+        const unsigned long long tot3 = __shfl_sync(0xffffffffu, xp, 31);
+        const unsigned long long excl3 = xp - packed;
         st_items += tot3;  // three 21-bit fields of at most 8192 per batch
         if (++st_batches == 200) flush_stats();
-        __syncwarp();
 #pragma unroll 1
         for (int cls = 0; cls < 3; ++cls) {
           const int sh = 21 * cls;
           const int total = (int)((tot3 >> sh) & 0x1fffffu);
-          for (int it = lane; it < total; it += 32) {
-            int lo = 0;  // last entry whose prefix in this class is <= it
+          // this lane's entry: first item and item count in the class
+          const int pe = (int)((excl3 >> sh) & 0x1fffffu);
+          const int ce = (int)((packed >> sh) & 0x1fffffu);
+          for (int it0 = 0; it0 < total; it0 += 32) {
+            // Items it0 .. it0 + 31 go one per lane.  Entries whose first item
+            // falls inside the round (after its first position) mark their
+            // start bit; the item's entry is the last start at or before the
+            // lane, else the entry holding item it0.
+            __syncwarp();
+            const int sp = pe - it0;
+            const bool starts_here = ce > 0 && sp > 0 && sp < 32;
+            const uint32_t starts = __reduce_or_sync(0xffffffffu, starts_here ? 1u << sp : 0u);
+            if (starts_here) s_own[wid][sp] = (uint8_t)lane;
+            const uint32_t held = __ballot_sync(0xffffffffu, ce > 0 && pe <= it0);
+            const int ebase = 31 - __clz(held);
+            const int pebase = __shfl_sync(0xffffffffu, pe, ebase);
+            __syncwarp();
+            const int it = it0 + lane;
+            if (it < total) {
+              const uint32_t sm = starts & ((2u << lane) - 1u);
+              int e, first;
+              if (sm) {
+                const int p = 31 - __clz(sm);
+                e = s_own[wid][p];
+                first = it0 + p;
+              } else {
+                e = ebase;
+                first = pebase;
+              }
+              const EntrySetup& E = my[e];
+              const int li = it - first;
+              int k = 0;
 #pragma unroll
-            for (int st = 16; st > 0; st >>= 1)
-              if (lo + st <= 31 && (int)((s_pre[wid][lo + st] >> sh) & 0x1fffffu) <= it) lo += st;
-            const EntrySetup& E = my[lo];
-            int li = it - (int)((s_pre[wid][lo] >> sh) & 0x1fffffu);
-            int k = 0;
-#pragma unroll
-            for (int st = 8; st > 0; st >>= 1)
-              if ((int)E.rowpre[k + st] <= li) k += st;
-            int ly = E.row0 + k, lx = E.x0[k] + (li - (int)E.rowpre[k]);
-            uint32_t m = cls == 0 ? fast_mask(E, lx * 256, ly * 256)
-                         : cls == 1 ? fast_mask2(E, lx * 256, ly * 256)
-                                    : tri_or_quad_mask(E, lx, ly);
-            if (m) {
-              int lp = ly * TILE_PX + lx;
-              atomicOr(&s_mask[E.slot * MASK_WORDS + (lp >> 1)], m << (16 * (lp & 1)));
+              for (int st = 8; st > 0; st >>= 1)
+                if ((int)E.rowpre[k + st] <= li) k += st;
+              const int ly = E.row0 + k, lx = E.x0[k] + (li - (int)E.rowpre[k]);
+              uint32_t m = cls == 0 ? fast_mask(E, lx * 256, ly * 256)
+                           : cls == 1 ? fast_mask2(E, lx * 256, ly * 256)
+                                      : tri_or_quad_mask(E, lx, ly);
+              if (m) {
+                int lp = ly * TILE_PX + lx;
+                atomicOr(&s_mask[E.slot * MASK_WORDS + (lp >> 1)], m << (16 * (lp & 1)));
+              }
             }
           }
         }
