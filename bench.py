@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--n-paths", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c2 (default) is the configuration the metric is quoted on; the "
+                         "others print their own line for the per-configuration table")
     return ap.parse_args()
 
 
@@ -207,12 +210,31 @@ def algorithmic(kernel, c):
     return table.get(kernel)
 
 
-# ALU peak for the coverage kernel: one sample test evaluates, per edge, a
-# multiply-add and a compare; a quad has 4 edges when convex, 6 when drawn as
-# two triangles: 12 lane operations per sample test (upper figure).  Lane
-# operations per second = 152 SMs x 128 lanes x SM clock.
-def alu_peak_tests(sm_mhz):
-    return 152 * 128 * sm_mhz * 1e6 / 12.0
+# ALU peak for the coverage kernel.  One sample test is one sample against one
+# quad.  The branch-free masks step every edge value from sample to sample with
+# one add and combine sign bits with three-input logic ops: a convex quad (or
+# single triangle) takes 4 adds + 2 logic ops + 1 op to gather the sign bit,
+# 7 lane ops; a non-convex quad (two triangles sharing the diagonal) 5 adds +
+# 3 logic ops + 2, 10 lane ops; the general path (edges over 1024 px) ~12.  The
+# SM issues at most 128 lane ops per clock (4 schedulers x 32 lanes).
+OPS_PER_TEST = {"convex_pixels": 7.0, "two_triangle_pixels": 10.0, "general_pixels": 12.0}
+
+
+def ops_per_test(rstat):
+    n = sum(rstat.get(k, 0) for k in OPS_PER_TEST)
+    if n <= 0:
+        return 12.0
+    return sum(OPS_PER_TEST[k] * rstat.get(k, 0) for k in OPS_PER_TEST) / n
+
+
+def alu_peak_tests(sm_mhz, ops):
+    return 152 * 128 * sm_mhz * 1e6 / ops
+
+
+# DRAM traffic of one k_coverage launch per bin entry, from the ncu capture in
+# profiles/k_coverage_c2_1000paths.md (dram__bytes_read.sum + write.sum =
+# 124.3 MB over 8,351,880 bin entries); scaled to the launch by its bin entries.
+COVERAGE_TRAFFIC_PER_PAIR = (117.389824e6 + 6.917888e6) / 8351880
 
 
 def run_ours(args, rank, world, local_rank):
@@ -328,16 +350,20 @@ def run_ours(args, rank, world, local_rank):
                           "achieved_gbs": ach, "frac": ach / hbm_peak}
         else:
             ach = work / (ms * 1e-3) / 1e9
-            pk = alu_peak_tests(sm_mhz) / 1e9
+            opt = ops_per_test(rstat)
+            pk = alu_peak_tests(sm_mhz, opt) / 1e9
             kernels[k] = {"ms": ms, "bound": "alu", "sample_tests": work,
                           "achieved_gtests": ach, "peak_gtests": pk, "frac": ach / pk}
     kd = kernels[dom]
     if kd.get("bound") == "alu":
+        opt = ops_per_test(rstat)
         roof = {"kernel": dom, "bound": "alu", "achieved": kd["achieved_gtests"],
                 "peak": kd["peak_gtests"], "unit": "Gsample-tests/s", "frac": kd["frac"],
-                "traffic": None,
-                "peak_source": f"derived: 152 SMs x 128 lanes x {sm_mhz:.0f} MHz / 12 lane ops per test",
-                "algorithmic_work": kd["sample_tests"]}
+                "traffic": int(COVERAGE_TRAFFIC_PER_PAIR * pairs) if dom == "k_coverage" else None,
+                "peak_source": (f"derived: 152 SMs x 128 lane ops/clock x {sm_mhz:.0f} MHz / "
+                                f"{opt:.2f} lane ops per sample test (pixel-class mix)"),
+                "algorithmic_work": kd["sample_tests"],
+                "traffic_source": "ncu capture of 1,000 paths scaled by bin entries"}
     elif kd.get("bound") == "hbm":
         roof = {"kernel": dom, "bound": "hbm", "achieved": kd["achieved_gbs"], "peak": hbm_peak,
                 "unit": "GB/s", "frac": kd["frac"], "traffic": None,
@@ -436,6 +462,142 @@ def run_plain(ps, batch, dev, max_paths=2000):
             "one path per launch, FP32, host-synchronous count", "s": dt}
 
 
+CONFIG_DESC = {
+    "c1": "c1 plain small: one path of 64 chained cubics in [0,512]^2, width 8 px, round joins "
+          "and caps, dtheta 2 deg, 512x512 at 16 samples/pixel; step = tessellation + coverage",
+    "c3": "c3 large single path: 5,031 chained cubics on a random walk, width 2 px, round joins "
+          "and caps, dtheta 0.5 deg, dash [12 on, 6 off], 4096x4096 at 16 samples/pixel; step = "
+          "tessellation + arc length + dash + coverage of the dashed quads",
+    "c4": "c4 precision stress: 1,000,000 single-cubic paths near cusps and near collinearity, "
+          "coordinates up to 1e6 px, width 1 px, butt caps, dtheta 1 deg; step = tessellation "
+          "(no raster)",
+    "c5": "c5 differentiation: 4,096 paths x 32 chained cubics in [0,1024]^2, widths 1-16 px, "
+          "round joins and caps, dtheta 2 deg; step = forward tessellation + adjoint",
+}
+
+
+def run_config(args, rank, world, local_rank):
+    """One line for a configuration other than the headline one (same timing rules:
+    graph-captured step, L2 flushed before every step, CUDA events on the stream)."""
+    import torch
+    import paper_2007_00308_gb300 as ps
+    from paper_2007_00308_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = args.workload
+    batch = {"c1": W.c1_plain_small, "c3": W.c3_large_path, "c4": W.c4_precision,
+             "c5": W.c5_differentiation}[wl]()
+    ctx = ps.Context()
+    db = ps.DeviceBatch(batch, device=dev)
+    prec = ps.PS_PREC_MIXED
+    probe = ps.TessOutput(db.n_link, db.n_path, 0, arclength=False, device=dev)
+    R = ps.ps_count_ribs_sync(ctx, db, probe, prec)
+    out = ps.TessOutput(db.n_link, db.n_path, R, arclength=True, want_t=(wl == "c5"), device=dev)
+    raster = wl in ("c1", "c3")
+    Wd, Ht = batch.canvas if raster else (0, 0)
+    extra = {}
+    if raster:
+        canvas = torch.zeros((Ht, Wd), dtype=torch.int16, device=dev)
+        covered = torch.zeros(db.n_path, dtype=torch.int64, device=dev)
+    if wl == "c3":
+        pattern, offset = batch.dash
+        cap = 3 * R + 4096
+        d_rib = torch.empty((cap, 4), dtype=torch.float32, device=dev)
+        d_s = torch.empty(cap, dtype=torch.float32, device=dev)
+        d_tag = torch.empty(cap, dtype=torch.int32, device=dev)
+        d_src = torch.empty(cap, dtype=torch.int32, device=dev)
+        d_n = torch.zeros(1, dtype=torch.int64, device=dev)
+    if wl == "c5":
+        gen = torch.Generator(device="cpu").manual_seed(20200705)
+        g_rib = torch.randn((R, 4), generator=gen).to(dev)
+        g_s = torch.randn(R, generator=gen).to(dev)
+        g_pts = torch.zeros((db.n_seg, 4, 2), dtype=torch.float32, device=dev)
+        g_w = torch.zeros(db.n_path, dtype=torch.float32, device=dev)
+    if raster:
+        n_tile = ((Wd + 15) // 16) * ((Ht + 15) // 16)
+        ctx.reserve(n_link=db.n_link, n_rib=R, n_tile=n_tile, n_pair=6 * (3 * R if wl == "c3" else R))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(stream=None):
+        ps.ps_tessellate_strokes(ctx, db, out, prec, ps.PS_TESS_ARCLENGTH, stream=stream)
+        if wl == "c1":
+            ps.ps_rasterize_coverage(ctx, out.rib, out.tag, out.n_rib, out.capacity, db.n_path,
+                                     Wd, Ht, canvas, covered, stream=stream)
+        elif wl == "c3":
+            ps.ps_dash(ctx, out.rib, out.s, out.tag, out.n_rib, out.capacity, pattern, offset,
+                       d_rib, d_s, d_tag, d_src, d_n, cap, stream=stream)
+            ps.ps_rasterize_coverage(ctx, d_rib, d_tag, d_n, cap, db.n_path, Wd, Ht, canvas,
+                                     covered, stream=stream)
+        elif wl == "c5":
+            g_pts.zero_()
+            g_w.zero_()
+            ps.ps_tessellate_backward(ctx, db, out, g_rib, g_s, g_pts, g_w, prec, stream=stream)
+
+    step()
+    torch.cuda.synchronize()
+    st = ctx.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st}: {ps.error_string(st)}")
+    ctx.profile(True)
+    g = torch.cuda.CUDAGraph()
+    sside = torch.cuda.Stream(device=dev)
+    sside.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(sside):
+        step(stream=sside)
+    torch.cuda.current_stream().wait_stream(sside)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        step()
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        g.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kern = {}
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record()
+        g.replay()
+        ev[i][1].record()
+        for k, v in ctx.profile_read().items():
+            kern.setdefault(k, []).append(v)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_per_step = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev) / args.steps
+    st = ctx.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st}: {ps.error_string(st)}")
+    line = {
+        "metric": METRIC, "value": job_throughput(batch.n_seg, world, ms_per_step),
+        "unit": "segments/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": CONFIG_DESC[wl], "variant": "batched+mixed, one CUDA graph per step",
+                   "n_segments": int(batch.n_seg), "n_paths": int(batch.n_path),
+                   "n_ribs": int(out.n_rib.item()),
+                   "l2": "flushed before every timed step (256 MiB write)"},
+        "kernel_ms": {k: statistics.mean(v) for k, v in kern.items()},
+        "clocks": clk,
+    }
+    if raster:
+        cs = int(covered.sum().item())
+        line["covered_samples"] = cs
+        line["covered_samples_per_s"] = world * cs / (ms_per_step * 1e-3)
+        line["raster_work"] = ps.ps_raster_stats(ctx)
+    if wl == "c3":
+        line["config"]["n_dashed_ribs"] = int(d_n.item())
+    if not args.no_plain and wl != "c5":
+        line["plain"] = run_plain(ps, batch, dev, max_paths=2000 if wl == "c4" else batch.n_path)
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -449,6 +611,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
+        if args.workload != "c2":
+            return run_config(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
