@@ -237,6 +237,33 @@ def alu_peak_tests(sm_mhz, ops):
 COVERAGE_TRAFFIC_PER_PAIR = (117.389824e6 + 6.917888e6) / 8351880
 
 
+def tune_step(ps, ctx, step, n_tile, R, key, flush, raster=True):
+    """Size the bins from the step's own count, then autotune the launch
+    parameters (cached per device and workload signature)."""
+    import torch
+    from paper_2007_00308_gb300 import autotune as AT
+    pairs_reserved = None
+    step()
+    torch.cuda.synchronize()
+    st = ctx.status()
+    if raster and st == ps.PS_ERR_CAPACITY:
+        pairs = ps.ps_raster_stats(ctx)["pairs"]
+        pairs_reserved = AT.reserve_bins(ctx, n_tile, pairs)
+        step()
+        torch.cuda.synchronize()
+        st = ctx.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st}: {ps.error_string(st)}")
+    res = AT.tuned(ctx, step, key, flush=flush.zero_ if flush is not None else None)
+    torch.cuda.synchronize()
+    st = ctx.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st}: {ps.error_string(st)}")
+    res = {k: v for k, v in res.items() if k != "trials"}
+    res["bin_entries_reserved"] = pairs_reserved
+    return res
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -258,8 +285,9 @@ def run_ours(args, rank, world, local_rank):
     out = ps.TessOutput(db.n_link, db.n_path, R, arclength=True, device=dev)
     canvas = torch.zeros((Ht, Wd), dtype=torch.int16, device=dev)
     covered = torch.zeros(db.n_path, dtype=torch.int64, device=dev)
-    ctx.reserve(n_link=db.n_link, n_rib=R, n_tile=((Wd + 15) // 16) * ((Ht + 15) // 16),
-                n_pair=6 * R)
+    n_tile = ((Wd + 15) // 16) * ((Ht + 15) // 16)
+    # bins start at one entry per rib; the first step's count sizes them
+    ctx.reserve(n_link=db.n_link, n_rib=R, n_tile=n_tile, n_pair=R)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(stream=None):
@@ -267,12 +295,12 @@ def run_ours(args, rank, world, local_rank):
         ps.ps_rasterize_coverage(ctx, out.rib, out.tag, out.n_rib, out.capacity, db.n_path, Wd, Ht,
                                  canvas, covered, stream=stream)
 
-    # eager warm-up (allocates workspace), then capture one step in a graph
-    step()
-    torch.cuda.synchronize()
-    st = ctx.status()
-    if st != 0:
-        raise RuntimeError(f"device status {st}: {ps.error_string(st)}")
+    # eager steps: bin sizing and autotuning (allocates workspace), then one
+    # step captured in a graph
+    from paper_2007_00308_gb300 import autotune as AT
+    tuning = tune_step(ps, ctx, step, n_tile, R,
+                       AT.signature(torch.cuda.get_device_name(dev), batch.n_seg, db.n_path, R,
+                                    (Wd, Ht)), flush)
     ctx.profile(True)
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream(device=dev)
@@ -386,7 +414,7 @@ def run_ours(args, rank, world, local_rank):
                    "FP32 with compensated g(t) and FP64 islands", "n_segments": segs,
                    "n_paths": db.n_path, "n_ribs": R_now, "canvas": [Wd, Ht], "spp": 16,
                    "l2": "flushed before every timed step (256 MiB write)",
-                   "wall_s_timed_region": t_wall},
+                   "wall_s_timed_region": t_wall, "autotune": tuning},
         "covered_samples_per_s": world * cov_samples / (ms_per_step * 1e-3),
         "covered_samples": cov_samples,
         "kernel_ms": kmean,
@@ -514,9 +542,9 @@ def run_config(args, rank, world, local_rank):
         g_s = torch.randn(R, generator=gen).to(dev)
         g_pts = torch.zeros((db.n_seg, 4, 2), dtype=torch.float32, device=dev)
         g_w = torch.zeros(db.n_path, dtype=torch.float32, device=dev)
+    n_tile = ((Wd + 15) // 16) * ((Ht + 15) // 16)
     if raster:
-        n_tile = ((Wd + 15) // 16) * ((Ht + 15) // 16)
-        ctx.reserve(n_link=db.n_link, n_rib=R, n_tile=n_tile, n_pair=6 * (3 * R if wl == "c3" else R))
+        ctx.reserve(n_link=db.n_link, n_rib=R, n_tile=n_tile, n_pair=R)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(stream=None):
@@ -534,11 +562,10 @@ def run_config(args, rank, world, local_rank):
             g_w.zero_()
             ps.ps_tessellate_backward(ctx, db, out, g_rib, g_s, g_pts, g_w, prec, stream=stream)
 
-    step()
-    torch.cuda.synchronize()
-    st = ctx.status()
-    if st != 0:
-        raise RuntimeError(f"device status {st}: {ps.error_string(st)}")
+    from paper_2007_00308_gb300 import autotune as AT
+    tuning = tune_step(ps, ctx, step, n_tile, R,
+                       AT.signature(torch.cuda.get_device_name(dev), batch.n_seg, db.n_path, R,
+                                    (Wd, Ht)) + f"|{wl}", flush, raster=raster)
     ctx.profile(True)
     g = torch.cuda.CUDAGraph()
     sside = torch.cuda.Stream(device=dev)
@@ -580,7 +607,7 @@ def run_config(args, rank, world, local_rank):
         "config": {"workload": CONFIG_DESC[wl], "variant": "batched+mixed, one CUDA graph per step",
                    "n_segments": int(batch.n_seg), "n_paths": int(batch.n_path),
                    "n_ribs": int(out.n_rib.item()),
-                   "l2": "flushed before every timed step (256 MiB write)"},
+                   "l2": "flushed before every timed step (256 MiB write)", "autotune": tuning},
         "kernel_ms": {k: statistics.mean(v) for k, v in kern.items()},
         "clocks": clk,
     }

@@ -262,6 +262,25 @@ int ps_profile_enable(ps_context* ctx, int enable);
 int ps_profile_read(ps_context* ctx, float* h_ms /* [PS_PROF_SLOTS] */);
 const char* ps_profile_slot_name(int slot);
 
+/* Launch parameters of a context, for autotuning.  They change how work is
+ * split over threads, never what is computed.
+ *   PS_TUNE_EMIT_SLABS   ribs per warp task in the rib kernel, in slabs of 32:
+ *                        4, 8, 16 (default) or 32
+ *   PS_TUNE_SETUP_LINKS  links per thread in the link-setup kernel: 1, 2
+ *                        (default) or 4
+ *   PS_TUNE_BIN_BLOCKS   CTAs per SM of the two binning passes: 0 (default: as
+ *                        many as fit) or 1..16
+ * ps_set_tuning returns PS_ERR_INVALID for an unknown key or value; the
+ * allocation-free entry point always uses the defaults. */
+enum {
+  PS_TUNE_EMIT_SLABS = 0,
+  PS_TUNE_SETUP_LINKS = 1,
+  PS_TUNE_BIN_BLOCKS = 2,
+  PS_TUNE_COUNT = 3
+};
+int ps_set_tuning(ps_context* ctx, int key, int value);
+int ps_get_tuning(ps_context* ctx, int key, int* value);
+
 /* Work counts of the context's most recent ps_rasterize_coverage call, read from
  * its device workspace into h_counts[0 .. n_counts-1] (entries past
  * PS_RSTAT_COUNT are zeroed):

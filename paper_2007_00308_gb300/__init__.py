@@ -24,8 +24,13 @@ EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_statu
            "ps_error_string", "ps_tessellate_strokes", "ps_count_ribs_sync", "ps_arclength_scan",
            "ps_dash", "ps_rasterize_coverage", "ps_profile_enable", "ps_profile_read",
            "ps_profile_slot_name", "ps_raster_stats", "ps_tessellate_strokes_noalloc",
-           "ps_tessellate_backward"]
+           "ps_tessellate_backward", "ps_set_tuning", "ps_get_tuning"]
 PS_PROF_SLOTS = 10
+PS_TUNE_EMIT_SLABS, PS_TUNE_SETUP_LINKS, PS_TUNE_BIN_BLOCKS = 0, 1, 2
+TUNE_CANDIDATES = {PS_TUNE_EMIT_SLABS: (4, 8, 16, 32), PS_TUNE_SETUP_LINKS: (1, 2, 4),
+                   PS_TUNE_BIN_BLOCKS: (0, 2, 4, 8)}
+TUNE_NAMES = {PS_TUNE_EMIT_SLABS: "emit_slabs", PS_TUNE_SETUP_LINKS: "setup_links",
+              PS_TUNE_BIN_BLOCKS: "bin_blocks"}
 
 
 class PolarStrokeError(RuntimeError):
@@ -89,6 +94,8 @@ def lib():
         L.ps_profile_slot_name.argtypes = [ctypes.c_int]
         L.ps_profile_slot_name.restype = ctypes.c_char_p
         L.ps_raster_stats.argtypes = [P, P, ctypes.c_int]
+        L.ps_set_tuning.argtypes = [P, ctypes.c_int, ctypes.c_int]
+        L.ps_get_tuning.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.ps_tessellate_backward.argtypes = [P, ctypes.POINTER(_Segments), ctypes.POINTER(_Paths),
                                              ctypes.c_float, ctypes.c_int,
                                              ctypes.POINTER(_TessOut), P, P, P, P, P]
@@ -152,6 +159,14 @@ class Context:
         _check(lib().ps_profile_read(self.handle, ctypes.cast(ms, ctypes.c_void_p)), "ps_profile_read")
         return {lib().ps_profile_slot_name(i).decode(): ms[i] for i in range(PS_PROF_SLOTS)
                 if ms[i] >= 0}
+
+    def set_tuning(self, key: int, value: int):
+        _check(lib().ps_set_tuning(self.handle, int(key), int(value)), "ps_set_tuning")
+
+    def get_tuning(self, key: int) -> int:
+        v = ctypes.c_int(0)
+        _check(lib().ps_get_tuning(self.handle, int(key), ctypes.byref(v)), "ps_get_tuning")
+        return v.value
 
     def status(self) -> int:
         """Read and clear the device status word (synchronizes)."""

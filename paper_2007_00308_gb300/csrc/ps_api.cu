@@ -90,7 +90,35 @@ extern "C" int ps_create(ps_context** out) {
   }
   cudaMemset(ctx->d_status, 0, 64);
   cudaMemset(ctx->d_counters, 0, sizeof(int32_t) * 16);
+  ctx->tune[PS_TUNE_EMIT_SLABS] = 16;
+  ctx->tune[PS_TUNE_SETUP_LINKS] = 2;
+  ctx->tune[PS_TUNE_BIN_BLOCKS] = 0;
   *out = ctx;
+  return PS_OK;
+}
+
+extern "C" int ps_set_tuning(ps_context* ctx, int key, int value) {
+  if (!ctx) return PS_ERR_INVALID;
+  switch (key) {
+    case PS_TUNE_EMIT_SLABS:
+      if (value != 4 && value != 8 && value != 16 && value != 32) return PS_ERR_INVALID;
+      break;
+    case PS_TUNE_SETUP_LINKS:
+      if (value != 1 && value != 2 && value != 4) return PS_ERR_INVALID;
+      break;
+    case PS_TUNE_BIN_BLOCKS:
+      if (value < 0 || value > 16) return PS_ERR_INVALID;
+      break;
+    default:
+      return PS_ERR_INVALID;
+  }
+  ctx->tune[key] = value;
+  return PS_OK;
+}
+
+extern "C" int ps_get_tuning(ps_context* ctx, int key, int* value) {
+  if (!ctx || !value || key < 0 || key >= PS_TUNE_COUNT) return PS_ERR_INVALID;
+  *value = ctx->tune[key];
   return PS_OK;
 }
 

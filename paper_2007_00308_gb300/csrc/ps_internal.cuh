@@ -91,6 +91,7 @@ struct ps_context {
   void* d_adj;              // adjoint workspace
   size_t adj_bytes;
   int num_sms;
+  int tune[PS_TUNE_COUNT];  // launch parameters (ps_set_tuning)
 };
 
 // ---- status -----------------------------------------------------------------

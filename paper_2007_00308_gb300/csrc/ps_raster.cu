@@ -1211,7 +1211,9 @@ extern "C" int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const 
   cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
   cudaMemsetAsync(d_covered, 0, sizeof(uint64_t) * (size_t)n_path, st);
   cudaMemsetAsync(ctx->d_scratch64, 0, 7 * sizeof(int64_t), st);
-  int grid_bin = ps_persistent_grid(ctx, (const void*)k_bin<0>, BIN_NT, 0);
+  int grid_bin = ctx->tune[PS_TUNE_BIN_BLOCKS] > 0
+                     ? ctx->num_sms * ctx->tune[PS_TUNE_BIN_BLOCKS]
+                     : ps_persistent_grid(ctx, (const void*)k_bin<0>, BIN_NT, 0);
   const float4* rib = reinterpret_cast<const float4*>(d_rib);
   { ProfScope ps_(ctx, PK_BIN_COUNT, st);
   k_bin<0><<<grid_bin, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, tiles_x,

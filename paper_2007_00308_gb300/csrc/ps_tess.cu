@@ -703,10 +703,10 @@ __device__ __forceinline__ long long block_excl_sum(long long v, long long& tota
 // ---------------------------------------------------------------------------
 // K1: link setup + rib counts + single-pass exclusive scan into link offsets.
 constexpr int SETUP_NT = 256;
-constexpr int SETUP_IPT = 2;
+constexpr int SETUP_IPT = 2;  // links per thread by default (tunable: 1, 2, 4)
 constexpr int SETUP_TILE = SETUP_NT * SETUP_IPT;
 
-template <bool MIXED>
+template <bool MIXED, int SETUP_IPT>
 __global__ void __launch_bounds__(SETUP_NT) k_link_setup(
     const uint8_t* __restrict__ st, const float* __restrict__ sp, const float* __restrict__ sw,
     const int32_t* __restrict__ seg_off, const float* __restrict__ width,
@@ -728,7 +728,7 @@ __global__ void __launch_bounds__(SETUP_NT) k_link_setup(
   int kk[SETUP_IPT];
   long long local = 0;
   for (int i = 0; i < SETUP_IPT; ++i) {
-    int64_t l = tile * SETUP_TILE + (int64_t)threadIdx.x * SETUP_IPT + i;
+    int64_t l = tile * (SETUP_NT * SETUP_IPT) + (int64_t)threadIdx.x * SETUP_IPT + i;
     cnt[i] = 0;
     pth[i] = -1;
     kk[i] = -1;
@@ -758,7 +758,7 @@ __global__ void __launch_bounds__(SETUP_NT) k_link_setup(
   __syncthreads();
   long long off = s_prefix + excl;
   for (int i = 0; i < SETUP_IPT; ++i) {
-    int64_t l = tile * SETUP_TILE + (int64_t)threadIdx.x * SETUP_IPT + i;
+    int64_t l = tile * (SETUP_NT * SETUP_IPT) + (int64_t)threadIdx.x * SETUP_IPT + i;
     if (l < n_link) {
       if (off > 0x7fffffffLL) ps_record_error(status, PS_ERR_CAPACITY);
       link_off[l] = (int32_t)off;
@@ -783,8 +783,7 @@ __global__ void __launch_bounds__(SETUP_NT) k_link_setup(
 // lane of the previous slab, or for the chunk's first rib a re-evaluation) are
 // written.  No block-wide synchronisation.
 constexpr int EMIT_NT = 256;
-constexpr int EMIT_K = 16;
-constexpr int EMIT_CHUNK = 32 * EMIT_K;
+constexpr int EMIT_K = 16;  // slabs of 32 ribs per chunk by default (tunable: 4, 8, 16, 32)
 
 struct RibEval {
   float4 v;      // N.x N.y P.x P.y
@@ -888,20 +887,21 @@ __global__ void __launch_bounds__(EMIT_NT) k_emit(
     const LinkRec* __restrict__ recs, const int32_t* __restrict__ link_off,
     const int32_t* __restrict__ link_path, int64_t n_link, const int64_t* __restrict__ n_rib,
     int64_t capacity, float4* __restrict__ rib, uint32_t* __restrict__ tag,
-    float* __restrict__ chord, float* __restrict__ tout) {
+    float* __restrict__ chord, float* __restrict__ tout, int emit_k) {
   int64_t R = *n_rib;
   if (R > capacity) R = capacity;
   const int lane = threadIdx.x & 31;
-  const int64_t n_chunks = (R + EMIT_CHUNK - 1) / EMIT_CHUNK;
+  const int64_t chunk = 32 * (int64_t)emit_k;
+  const int64_t n_chunks = (R + chunk - 1) / chunk;
   const int64_t warp0 = ((int64_t)blockIdx.x * EMIT_NT + threadIdx.x) >> 5;
   const int64_t n_warps = ((int64_t)gridDim.x * EMIT_NT) >> 5;
   for (int64_t c = warp0; c < n_chunks; c += n_warps) {
-    const int64_t r0 = c * EMIT_CHUNK;
+    const int64_t r0 = c * chunk;
     int64_t l = find_link_warp(link_off, n_link, r0, lane);
     float2 carry_g = mk(0.f, 0.f);
     float carry_t = 0.f;
 #pragma unroll 1
-    for (int s = 0; s < EMIT_K; ++s) {
+    for (int s = 0; s < emit_k; ++s) {
       const int64_t r = r0 + (int64_t)s * 32 + lane;
       const bool active = r < R;
       RibEval E;
@@ -1107,7 +1107,8 @@ static int launch_tessellate(ps_context* ctx, const ps_segments* seg, const ps_p
   int P = paths->n_path;
   int64_t L = 2 * S + P;
   if (P <= 0) return PS_ERR_INVALID;
-  int64_t n_tiles = (L + SETUP_TILE - 1) / SETUP_TILE;
+  const int ipt = ctx->tune[PS_TUNE_SETUP_LINKS];
+  int64_t n_tiles = (L + SETUP_NT * ipt - 1) / (SETUP_NT * ipt);
   int rc;
   if ((rc = ps_ensure_tiles(ctx, n_tiles + (out->capacity + SCAN_TILE - 1) / SCAN_TILE + 2)) != PS_OK)
     return rc;
@@ -1122,18 +1123,24 @@ static int launch_tessellate(ps_context* ctx, const ps_segments* seg, const ps_p
   k_link_path<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(paths->d_seg_off, P, L, link_path); }
   {
   ProfScope ps_(ctx, PK_LINK_SETUP, st);
-  if (precision == PS_PREC_MIXED)
-    k_link_setup<true><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
-        seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
-        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->d_recs,
-        out->d_link_rib_off, out->d_path_rib_off, out->d_n_rib, count_cap, ctx->d_tile_flag,
-        ctx->d_tile_agg, ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles);
-  else
-    k_link_setup<false><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
-        seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
-        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->d_recs,
-        out->d_link_rib_off, out->d_path_rib_off, out->d_n_rib, count_cap, ctx->d_tile_flag,
-        ctx->d_tile_agg, ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles);
+#define PS_SETUP_ARGS                                                                          \
+  seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,         \
+      paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->d_recs,               \
+      out->d_link_rib_off, out->d_path_rib_off, out->d_n_rib, count_cap, ctx->d_tile_flag,    \
+      ctx->d_tile_agg, ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles
+  const unsigned g = (unsigned)n_tiles;
+  const bool mx = precision == PS_PREC_MIXED;
+  if (ipt == 1) {
+    if (mx) k_link_setup<true, 1><<<g, SETUP_NT, 0, st>>>(PS_SETUP_ARGS);
+    else k_link_setup<false, 1><<<g, SETUP_NT, 0, st>>>(PS_SETUP_ARGS);
+  } else if (ipt == 4) {
+    if (mx) k_link_setup<true, 4><<<g, SETUP_NT, 0, st>>>(PS_SETUP_ARGS);
+    else k_link_setup<false, 4><<<g, SETUP_NT, 0, st>>>(PS_SETUP_ARGS);
+  } else {
+    if (mx) k_link_setup<true, 2><<<g, SETUP_NT, 0, st>>>(PS_SETUP_ARGS);
+    else k_link_setup<false, 2><<<g, SETUP_NT, 0, st>>>(PS_SETUP_ARGS);
+  }
+#undef PS_SETUP_ARGS
   }
   if ((rc = ps_cuda_check(cudaGetLastError())) != PS_OK) return rc;
   if (flags & PS_TESS_COUNT_ONLY) return PS_OK;
@@ -1148,12 +1155,13 @@ static int launch_tessellate(ps_context* ctx, const ps_segments* seg, const ps_p
     k_emit<true><<<grid, EMIT_NT, 0, st>>>(ctx->d_recs, out->d_link_rib_off, link_path, L,
                                            out->d_n_rib, out->capacity,
                                            reinterpret_cast<float4*>(out->d_rib), out->d_tag,
-                                           arc ? out->d_s : nullptr, out->d_t);
+                                           arc ? out->d_s : nullptr, out->d_t, ctx->tune[PS_TUNE_EMIT_SLABS]);
   else
     k_emit<false><<<grid, EMIT_NT, 0, st>>>(ctx->d_recs, out->d_link_rib_off, link_path, L,
                                             out->d_n_rib, out->capacity,
                                             reinterpret_cast<float4*>(out->d_rib), out->d_tag,
-                                            arc ? out->d_s : nullptr, out->d_t);
+                                            arc ? out->d_s : nullptr, out->d_t,
+                                            ctx->tune[PS_TUNE_EMIT_SLABS]);
   }
   if ((rc = ps_cuda_check(cudaGetLastError())) != PS_OK) return rc;
   if (arc) {
@@ -1328,13 +1336,13 @@ extern "C" int ps_tessellate_strokes_noalloc(const ps_segments* seg, const ps_pa
   int64_t count_cap = count_only ? INT64_MAX : out->capacity;
   k_link_path<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(paths->d_seg_off, P, L, link_path);
   if (precision == PS_PREC_MIXED)
-    k_link_setup<true><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
+    k_link_setup<true, SETUP_IPT><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
         paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, recs, out->d_link_rib_off,
         out->d_path_rib_off, out->d_n_rib, count_cap, tflag, tagg, tincl, counters, d_status,
         n_tiles);
   else
-    k_link_setup<false><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
+    k_link_setup<false, SETUP_IPT><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
         paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, recs, out->d_link_rib_off,
         out->d_path_rib_off, out->d_n_rib, count_cap, tflag, tagg, tincl, counters, d_status,
@@ -1349,11 +1357,11 @@ extern "C" int ps_tessellate_strokes_noalloc(const ps_segments* seg, const ps_pa
   if (precision == PS_PREC_MIXED)
     k_emit<true><<<grid, EMIT_NT, 0, st>>>(recs, out->d_link_rib_off, link_path, L, out->d_n_rib,
                                            out->capacity, reinterpret_cast<float4*>(out->d_rib),
-                                           out->d_tag, arc ? out->d_s : nullptr, out->d_t);
+                                           out->d_tag, arc ? out->d_s : nullptr, out->d_t, EMIT_K);
   else
     k_emit<false><<<grid, EMIT_NT, 0, st>>>(recs, out->d_link_rib_off, link_path, L, out->d_n_rib,
                                             out->capacity, reinterpret_cast<float4*>(out->d_rib),
-                                            out->d_tag, arc ? out->d_s : nullptr, out->d_t);
+                                            out->d_tag, arc ? out->d_s : nullptr, out->d_t, EMIT_K);
   if (cudaGetLastError() != cudaSuccess) return PS_ERR_CUDA;
   if (arc) {
     if (out->d_path_len && cudaMemsetAsync(out->d_path_len, 0, sizeof(float) * P, st) != cudaSuccess)
@@ -1386,13 +1394,13 @@ int ps_run_link_setup(ps_context* ctx, const ps_segments* seg, const ps_paths* p
   cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
   k_link_path<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(paths->d_seg_off, P, L, link_path);
   if (precision == PS_PREC_MIXED)
-    k_link_setup<true><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
+    k_link_setup<true, SETUP_IPT><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
         paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->d_recs, d_link_off,
         d_path_off, d_n_rib, INT64_MAX, ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
         ctx->d_counters, ctx->d_status, n_tiles);
   else
-    k_link_setup<false><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
+    k_link_setup<false, SETUP_IPT><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
         paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->d_recs, d_link_off,
         d_path_off, d_n_rib, INT64_MAX, ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
