@@ -262,6 +262,21 @@ int ps_profile_enable(ps_context* ctx, int enable);
 int ps_profile_read(ps_context* ctx, float* h_ms /* [PS_PROF_SLOTS] */);
 const char* ps_profile_slot_name(int slot);
 
+/* SVG elliptical arc -> conic segments (host function, no device work).
+ * The arc runs from (x0, y0) to (x1, y1) on the ellipse with radii rx, ry whose
+ * x axis is rotated by phi_deg, the large-arc and sweep flags choosing among the
+ * four candidate arcs as in SVG 1.1 (radii too small for the chord are scaled
+ * up; negative radii count as their absolute values).  The paper takes arcs in
+ * through its rational conic form (Table 1): each output piece spans at most 90
+ * degrees of the ellipse and is written as a PS_CONIC segment, h_pts[8 i .. 8 i
+ * + 7] = A, B, B, D (the layout of d_pts) and h_w[i] = w_B.  The first A and
+ * the last D are the given end points exactly.
+ * Returns the number of pieces (0 when the end points coincide, 1 flat piece
+ * when a radius is zero, else 1..4), or PS_ERR_INVALID (null pointers,
+ * non-finite input).  h_pts holds 32 floats, h_w 4. */
+int ps_svg_arc_to_conics(float x0, float y0, float rx, float ry, float phi_deg, int large_arc,
+                         int sweep, float x1, float y1, float* h_pts, float* h_w);
+
 /* Launch parameters of a context, for autotuning.  They change how work is
  * split over threads, never what is computed.
  *   PS_TUNE_EMIT_SLABS   ribs per warp task in the rib kernel, in slabs of 32:

@@ -766,6 +766,12 @@ int orc_tessellate_f64(int64_t n_seg, const uint8_t* seg_type, const double* seg
       int nrib = 0;
       uint8_t info = 0;
       if (L.kind == 1) {
+        /* A conic with w_B <= -1 is an external parabola (w = -1) or hyperbola
+         * (w < -1): its denominator (1-t)^2 + 2w(1-t)t + t^2 vanishes at
+         * t = 1/2 +- sqrt(w^2-1)/(2(1-w)) in [0,1] (Sec. 3.3.3 with the
+         * corrected root formula), where the curve passes through infinity and
+         * its stroke is unbounded.  Such a segment is rejected. */
+        if (g.type == ORC_CONIC && !(g.w > -1.0)) return ORC_ERR_INVALID;
         seg_intervals(&g, q, &I);
         if (I.N > 0) nrib = I.N + 1;
         info |= (I.fragile64 ? INFO_FRAGILE64 : 0) | (I.fragile32 ? INFO_FRAGILE32 : 0);

@@ -24,7 +24,7 @@ EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_statu
            "ps_error_string", "ps_tessellate_strokes", "ps_count_ribs_sync", "ps_arclength_scan",
            "ps_dash", "ps_rasterize_coverage", "ps_profile_enable", "ps_profile_read",
            "ps_profile_slot_name", "ps_raster_stats", "ps_tessellate_strokes_noalloc",
-           "ps_tessellate_backward", "ps_set_tuning", "ps_get_tuning"]
+           "ps_tessellate_backward", "ps_set_tuning", "ps_get_tuning", "ps_svg_arc_to_conics"]
 PS_PROF_SLOTS = 10
 PS_TUNE_EMIT_SLABS, PS_TUNE_SETUP_LINKS, PS_TUNE_BIN_BLOCKS = 0, 1, 2
 TUNE_CANDIDATES = {PS_TUNE_EMIT_SLABS: (4, 8, 16, 32), PS_TUNE_SETUP_LINKS: (1, 2, 4),
@@ -95,6 +95,8 @@ def lib():
         L.ps_profile_slot_name.restype = ctypes.c_char_p
         L.ps_raster_stats.argtypes = [P, P, ctypes.c_int]
         L.ps_set_tuning.argtypes = [P, ctypes.c_int, ctypes.c_int]
+        F = ctypes.c_float
+        L.ps_svg_arc_to_conics.argtypes = [F, F, F, F, F, ctypes.c_int, ctypes.c_int, F, F, P, P]
         L.ps_get_tuning.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.ps_tessellate_backward.argtypes = [P, ctypes.POINTER(_Segments), ctypes.POINTER(_Paths),
                                              ctypes.c_float, ctypes.c_int,
@@ -238,6 +240,21 @@ def ps_raster_stats(ctx: Context) -> dict:
     _check(lib().ps_raster_stats(ctx.handle, ctypes.cast(buf, ctypes.c_void_p), len(RSTAT_NAMES)),
            "ps_raster_stats")
     return dict(zip(RSTAT_NAMES, (int(v) for v in buf)))
+
+
+def svg_arc_to_conics(x0, y0, rx, ry, phi_deg, large_arc, sweep, x1, y1):
+    """SVG elliptical arc -> conic segments: (pts float32[n, 4, 2] as A, B, B, D;
+    w float32[n]).  Host only."""
+    import numpy as np
+    pts = np.zeros(32, np.float32)
+    w = np.zeros(4, np.float32)
+    n = lib().ps_svg_arc_to_conics(float(x0), float(y0), float(rx), float(ry), float(phi_deg),
+                                   int(bool(large_arc)), int(bool(sweep)), float(x1), float(y1),
+                                   pts.ctypes.data_as(ctypes.c_void_p),
+                                   w.ctypes.data_as(ctypes.c_void_p))
+    if n < 0:
+        _check(n, "ps_svg_arc_to_conics")
+    return pts[:8 * n].reshape(n, 4, 2), w[:n]
 
 
 def ps_max_ribs(n_seg, n_path, dtheta) -> int:

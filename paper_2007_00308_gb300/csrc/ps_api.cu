@@ -1,3 +1,4 @@
+#include <cmath>
 // Context, workspace and status handling of the C ABI.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -225,4 +226,85 @@ extern "C" const char* ps_error_string(int code) {
     case PS_ERR_RANGE: return "vertex coordinate out of the rasterizer's range";
     default: return "unknown error";
   }
+}
+
+// ---------------------------------------------------------------------------
+// SVG elliptical arc (endpoint parameterization) -> conic segments.  Host code.
+// Steps (SVG 1.1 arc implementation notes, restated): move the chord midpoint
+// to the origin and undo the rotation phi; scale the radii up when the
+// endpoints are too far apart for them; the centre follows from the chord and
+// the radii, on the side the two flags select; the start angle and the signed
+// sweep are taken on the unit circle of the ellipse's own axes.  The sweep is
+// cut into n <= 4 equal pieces of at most 90 degrees; a piece [a, b] of the
+// unit circle is the rational quadratic with end points at angles a and b,
+// middle control point at angle (a+b)/2 and distance 1/cos h (h = (b-a)/2, where
+// the end tangents meet), and weight cos h.  An affine map (scale by rx, ry,
+// rotate by phi, translate to the centre) keeps the weight.
+extern "C" int ps_svg_arc_to_conics(float x0, float y0, float rx, float ry, float phi_deg,
+                                    int large_arc, int sweep, float x1, float y1,
+                                    float* h_pts, float* h_w) {
+  if (!h_pts || !h_w) return PS_ERR_INVALID;
+  if (!(std::isfinite(x0) && std::isfinite(y0) && std::isfinite(x1) && std::isfinite(y1) &&
+        std::isfinite(rx) && std::isfinite(ry) && std::isfinite(phi_deg)))
+    return PS_ERR_INVALID;
+  if (x0 == x1 && y0 == y1) return 0;  // no arc at all
+  double Rx = std::fabs((double)rx), Ry = std::fabs((double)ry);
+  auto put = [&](int i, double ax, double ay, double bx, double by, double dx, double dy,
+                 double w) {
+    float* o = h_pts + 8 * i;
+    o[0] = (float)ax; o[1] = (float)ay; o[2] = (float)bx; o[3] = (float)by;
+    o[4] = (float)bx; o[5] = (float)by; o[6] = (float)dx; o[7] = (float)dy;
+    h_w[i] = (float)w;
+  };
+  if (Rx == 0.0 || Ry == 0.0) {  // a straight segment: a flat conic
+    put(0, x0, y0, 0.5 * ((double)x0 + x1), 0.5 * ((double)y0 + y1), x1, y1, 1.0);
+    return 1;
+  }
+  const double PI = 3.14159265358979323846;
+  double phi = (double)phi_deg * PI / 180.0, cp = std::cos(phi), sp = std::sin(phi);
+  double hx = 0.5 * ((double)x0 - x1), hy = 0.5 * ((double)y0 - y1);
+  double xp = cp * hx + sp * hy, yp = -sp * hx + cp * hy;
+  double lam = (xp * xp) / (Rx * Rx) + (yp * yp) / (Ry * Ry);
+  if (lam > 1.0) {
+    double k = std::sqrt(lam);
+    Rx *= k;
+    Ry *= k;
+  }
+  double num = Rx * Rx * Ry * Ry - Rx * Rx * yp * yp - Ry * Ry * xp * xp;
+  double den = Rx * Rx * yp * yp + Ry * Ry * xp * xp;
+  double f = (num > 0.0 && den > 0.0) ? std::sqrt(num / den) : 0.0;
+  if ((large_arc != 0) == (sweep != 0)) f = -f;
+  double cxp = f * Rx * yp / Ry, cyp = -f * Ry * xp / Rx;
+  double cx = cp * cxp - sp * cyp + 0.5 * ((double)x0 + x1);
+  double cy = sp * cxp + cp * cyp + 0.5 * ((double)y0 + y1);
+  double ux = (xp - cxp) / Rx, uy = (yp - cyp) / Ry, vx = (-xp - cxp) / Rx, vy = (-yp - cyp) / Ry;
+  double th0 = std::atan2(uy, ux);
+  double dth = std::atan2(ux * vy - uy * vx, ux * vx + uy * vy);
+  if (!sweep && dth > 0.0) dth -= 2.0 * PI;
+  if (sweep && dth < 0.0) dth += 2.0 * PI;
+  int n = (int)std::ceil(std::fabs(dth) / (0.5 * PI) - 1e-12);
+  if (n < 1) n = 1;
+  if (n > 4) n = 4;
+  auto map = [&](double px, double py, double& X, double& Y) {
+    double ex = Rx * px, ey = Ry * py;
+    X = cx + cp * ex - sp * ey;
+    Y = cy + sp * ex + cp * ey;
+  };
+  double step = dth / n, hh = 0.5 * step, wv = std::cos(hh);
+  double px = (double)x0, py = (double)y0;
+  for (int i = 0; i < n; ++i) {
+    double a = th0 + step * i, m = a + hh, b = a + step;
+    double bx, by, dx, dy;
+    map(std::cos(m) / wv, std::sin(m) / wv, bx, by);
+    if (i == n - 1) {
+      dx = x1;
+      dy = y1;
+    } else {
+      map(std::cos(b), std::sin(b), dx, dy);
+    }
+    put(i, px, py, bx, by, dx, dy, wv);
+    px = dx;
+    py = dy;
+  }
+  return n;
 }

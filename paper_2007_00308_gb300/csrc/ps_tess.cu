@@ -584,6 +584,10 @@ __device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, i
     int i = (k - 1) >> 1;
     Seg g = load_seg(st, sp, sw, s0 + i);
     if (zero_length(g)) return 0;
+    // A conic with w_B <= -1 (external parabola / hyperbola) passes through
+    // infinity where its denominator vanishes, t = 1/2 +- sqrt(w^2-1)/(2(1-w)):
+    // its stroke is unbounded, so it is rejected (an error, no ribs).
+    if (g.type == PS_CONIC && !(g.w > -1.f)) return -1;
     L.P[0] = g.A; L.P[1] = g.B; L.P[2] = g.C; L.P[3] = g.D;
     L.w = g.w;
     L.meta = LK_SEG | ((uint32_t)g.type << 2);

@@ -57,6 +57,13 @@ def _edge_batches():
                                          [[100, 0], [150, -50], [150, -50], [200, 0]],
                                          [[200, 0], [250, 60], [250, 60], [300, 0]]],
                              w=[0.7, 3.0, -0.5], width=4, dtheta_deg=1)
+    # external ellipses (-1 < w < 0, the complementary arcs), and w = 0 (the chord)
+    R = 60.0
+    ext = [[[R, 0], [R, R], [R, R], [0, R]], [[0, R], [-40, 90], [-40, 90], [-80, 20]],
+           [[-80, 20], [-60, -30], [-60, -30], [-20, -40]],
+           [[-20, -40], [10, -10], [10, -10], [30, -60]], [[30, -60], [60, -20], [60, -20], [90, -50]]]
+    out["external_conics"] = W.single([K] * 5, ext, w=[-math.cos(math.pi / 4), -0.05, -0.5, -0.95, 0.0],
+                                      width=5, join=W.JOIN_ROUND, cap=W.CAP_ROUND, dtheta_deg=1)
     out["coincident"] = W.single([C, C, Q], [[[0, 0], [0, 0], [40, 30], [60, 0]],
                                              [[60, 0], [80, 10], [90, 0], [90, 0]],
                                              [[90, 0], [90, 0], [90, 0], [120, 40]]], width=4)
@@ -91,6 +98,21 @@ def test_edge_cases(name, prec):
     if name == "collinear_backtrack" and prec == PLAIN:
         pytest.skip("exact collinearity is not decidable in FP32 differences")
     _check(EDGES[name], prec)
+
+
+def test_external_parabola_and_hyperbola_are_rejected():
+    """w_B <= -1: the curve passes through infinity; the link is an error (status
+    PS_ERR_INVALID) and emits nothing, and the oracle refuses the batch."""
+    import paper_2007_00308_gb300 as ps
+    b = W.single([W.LINE, W.CONIC], [[[0, 0], [0, 0], [50, 0], [50, 0]],
+                                     [[50, 0], [100, 60], [100, 60], [150, 0]]],
+                 w=[1.0, -1.5], width=4)
+    with pytest.raises(oracle.OracleError):
+        oracle.tessellate(b)
+    for prec in (PLAIN, MIXED):
+        g = gpu_tessellate(b, prec)
+        assert g["status"] == ps.PS_ERR_INVALID
+        assert np.diff(g["link_rib_off"])[3] == 0  # the conic's link
 
 
 def test_empty_and_degenerate_paths():
