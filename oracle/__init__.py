@@ -16,6 +16,8 @@ Parity status per function (see the tests under ``tests/test_oracle_*.py``):
   raster           pinned (axis-aligned rectangles and triangles against a
                    point-in-polygon count written with a different predicate)
   centreline_distance  pinned (distance to a line and a circle in closed form)
+  uniform_ribs     pinned (parabola chords against the midpoint tangent, closed form)
+  facet_angles     pinned (circle arc: every facet equals the polar step)
 """
 from __future__ import annotations
 
@@ -74,6 +76,10 @@ def _load():
             _lib.orc_centreline_distance.argtypes = [I64, P, P, P, ctypes.c_int, ctypes.c_int,
                                                      ctypes.c_int, P]
             _lib.orc_centreline_distance.restype = ctypes.c_int
+            _lib.orc_uniform_ribs.argtypes = [ctypes.c_int, P, D, ctypes.c_int, D, P]
+            _lib.orc_uniform_ribs.restype = ctypes.c_int
+            _lib.orc_facet_angles.argtypes = [I64, P, D, P, P]
+            _lib.orc_facet_angles.restype = ctypes.c_int
     return _lib
 
 
@@ -211,6 +217,33 @@ def centreline_distance(batch, width, height, n_dense=2000):
     if rc != 0:
         raise OracleError(f"orc_centreline_distance failed: {rc}")
     return out
+
+
+def uniform_ribs(seg_type, pts, w, n_quads, width):
+    """Uniform parametric ribs of one segment (Sec. 8.1): float64[n_quads + 1, 4]."""
+    lib = _load()
+    p = _c(np.asarray(pts, np.float64).reshape(8), np.float64)
+    rib = np.zeros((int(n_quads) + 1, 4))
+    rc = lib.orc_uniform_ribs(int(seg_type), _p(p), float(w), int(n_quads), 0.5 * float(width),
+                              _p(rib))
+    if rc != 0:
+        raise OracleError(f"orc_uniform_ribs failed: {rc}")
+    return rib
+
+
+def facet_angles(rib, slack=1e-12):
+    """Facet angles of one segment's rib run: (angle float64[n, 2] (-1 where
+    undefined), ordinary bool[n, 2]); columns are the N and P sides.  slack:
+    tolerance of the tangent-range test (1e-12 for FP64 ribs)."""
+    lib = _load()
+    rib = _c(rib, np.float64).reshape(-1, 4)
+    n = len(rib)
+    ang = np.zeros((n, 2))
+    ordn = np.zeros((n, 2), np.uint8)
+    rc = lib.orc_facet_angles(n, _p(rib), float(slack), _p(ang), _p(ordn))
+    if rc != 0:
+        raise OracleError(f"orc_facet_angles failed: {rc}")
+    return ang, ordn.astype(bool)
 
 
 def sample_positions(width, height):

@@ -1185,3 +1185,96 @@ int orc_centreline_distance(int64_t n_seg, const uint8_t* seg_type, const float*
   free(segs);
   return ORC_OK;
 }
+
+/* ---- uniform parametric tessellation and facet angles (Sec. 8.1) --------- */
+/* The comparison of Sec. 8.1 strokes a segment with Eq. 1 sampled at uniform
+ * parameters: rib j of N+1 at t_j = j/N is g(t_j) -+ r n(t_j), with n(t) the
+ * unit left normal of g'(t) (the same N/P convention as the polar ribs).  Where
+ * g'(t) = 0 (an exact cusp) the direction of g''(t) stands in for the tangent;
+ * a segment whose hodograph vanishes everywhere uses its chord.  N is set by
+ * the caller (the polar quad count of the same segment). */
+int orc_uniform_ribs(int type, const double* pts8, double w, int N, double r, double* rib) {
+  if (N < 1 || !pts8 || !rib) return ORC_ERR_INVALID;
+  Seg g;
+  g.type = type;
+  g.A = mk(pts8[0], pts8[1]); g.B = mk(pts8[2], pts8[3]);
+  g.C = mk(pts8[4], pts8[5]); g.D = mk(pts8[6], pts8[7]);
+  g.w = w;
+  for (int j = 0; j <= N; ++j) {
+    double t = (double)j / (double)N;
+    V2 p = seg_eval(&g, t);
+    V2 T = hodo(&g, t);
+    double L = sqrt(T.x * T.x + T.y * T.y);
+    if (L == 0.0) {
+      T = hodo_d(&g, t);
+      L = sqrt(T.x * T.x + T.y * T.y);
+    }
+    if (L == 0.0) {
+      T = sub(g.D, g.A);
+      L = sqrt(T.x * T.x + T.y * T.y);
+    }
+    V2 n = L > 0.0 ? mk(-T.y / L, T.x / L) : mk(0.0, 0.0);
+    rib[4 * j + 0] = p.x - r * n.x;
+    rib[4 * j + 1] = p.y - r * n.y;
+    rib[4 * j + 2] = p.x + r * n.x;
+    rib[4 * j + 3] = p.y + r * n.y;
+  }
+  return ORC_OK;
+}
+
+/* Facet angles of one run of ribs (one segment's quads): for each interior rib
+ * j and each side X in {N, P}, the angle in [0, pi] between the boundary edges
+ * X_j - X_{j-1} and X_{j+1} - X_j, where one quad meets the next (Sec. 4.2's
+ * facet angle).  Sec. 4.2 bounds it by 2q except next to offset cusps: an
+ * offset arc without a cusp has its chord direction between the tangent
+ * directions at its ends, and those are the generator's (the offset's tangent
+ * is the generator's, reversed only through a cusp).  So a facet is ordinary
+ * when each of its two edges points within the angle between the tangents of
+ * its end ribs (the rib P - N is the left normal, turned clockwise it is the
+ * tangent), within a slack (unit-vector cross products; 1e-12 for FP64 ribs).
+ * A rib of zero length carries no tangent; there an
+ * edge counts when it advances with the centreline edge ((N+P)/2) of the same
+ * index.  angle[2j+s] is -1 where an edge has zero length (ribs 0 and n-1 have
+ * no facet). */
+static int edge_regular(const double* rib, int64_t i0, int64_t i1, int s, V2 e, double eps) {
+  V2 v0 = mk(rib[4 * i0 + 2] - rib[4 * i0], rib[4 * i0 + 3] - rib[4 * i0 + 1]);
+  V2 v1 = mk(rib[4 * i1 + 2] - rib[4 * i1], rib[4 * i1 + 3] - rib[4 * i1 + 1]);
+  double l0 = sqrt(v0.x * v0.x + v0.y * v0.y), l1 = sqrt(v1.x * v1.x + v1.y * v1.y);
+  double le = sqrt(e.x * e.x + e.y * e.y);
+  if (l0 == 0.0 || l1 == 0.0) {
+    V2 m0 = mk(0.5 * (rib[4 * i0] + rib[4 * i0 + 2]), 0.5 * (rib[4 * i0 + 1] + rib[4 * i0 + 3]));
+    V2 m1 = mk(0.5 * (rib[4 * i1] + rib[4 * i1 + 2]), 0.5 * (rib[4 * i1 + 1] + rib[4 * i1 + 3]));
+    V2 m = sub(m1, m0);
+    (void)s;
+    return e.x * m.x + e.y * m.y > 0.0;
+  }
+  V2 T0 = mk(v0.y / l0, -v0.x / l0), T1 = mk(v1.y / l1, -v1.x / l1);
+  V2 u = mk(e.x / le, e.y / le);
+  double c01 = T0.x * T1.y - T0.y * T1.x;
+  double c0u = T0.x * u.y - T0.y * u.x, cu1 = u.x * T1.y - u.y * T1.x;
+  if (u.x * (T0.x + T1.x) + u.y * (T0.y + T1.y) <= 0.0) return 0;  /* backwards */
+  if (c01 >= 0.0) return c0u >= -eps && cu1 >= -eps;  /* counter-clockwise step */
+  return c0u <= eps && cu1 <= eps;                     /* clockwise step */
+}
+
+int orc_facet_angles(int64_t n, const double* rib, double slack, double* angle,
+                     uint8_t* ordinary) {
+  if (n < 0 || (n > 0 && (!rib || !angle || !ordinary))) return ORC_ERR_INVALID;
+  for (int64_t j = 0; j < n; ++j) {
+    for (int s = 0; s < 2; ++s) {
+      angle[2 * j + s] = -1.0;
+      ordinary[2 * j + s] = 0;
+      if (j == 0 || j == n - 1) continue;
+      V2 a = mk(rib[4 * (j - 1) + 2 * s], rib[4 * (j - 1) + 2 * s + 1]);
+      V2 b = mk(rib[4 * j + 2 * s], rib[4 * j + 2 * s + 1]);
+      V2 c = mk(rib[4 * (j + 1) + 2 * s], rib[4 * (j + 1) + 2 * s + 1]);
+      V2 e0 = sub(b, a), e1 = sub(c, b);
+      if ((e0.x == 0.0 && e0.y == 0.0) || (e1.x == 0.0 && e1.y == 0.0)) continue;
+      angle[2 * j + s] = fabs(atan2(e0.x * e1.y - e0.y * e1.x, e0.x * e1.x + e0.y * e1.y));
+      ordinary[2 * j + s] =
+          (edge_regular(rib, j - 1, j, s, e0, slack) && edge_regular(rib, j, j + 1, s, e1, slack))
+              ? 1 : 0;
+    }
+  }
+  return ORC_OK;
+}
