@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--n-paths", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "facet"],
                     help="c2 (default) is the configuration the metric is quoted on; the "
                          "others print their own line for the per-configuration table")
     return ap.parse_args()
@@ -501,6 +501,10 @@ CONFIG_DESC = {
           "(no raster)",
     "c5": "c5 differentiation: 4,096 paths x 32 chained cubics in [0,1024]^2, widths 1-16 px, "
           "round joins and caps, dtheta 2 deg; step = forward tessellation + adjoint",
+    "facet": "uniform-parametric comparison: 20,000 single cubics (half serpentines, a quarter "
+             "exact cusps, a quarter loops), chords 20-400 px, widths 1-100 px, dtheta 4 deg; "
+             "step = polar tessellation + uniform tessellation at the same counts + facet "
+             "statistics of both",
 }
 
 
@@ -515,7 +519,7 @@ def run_config(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     wl = args.workload
     batch = {"c1": W.c1_plain_small, "c3": W.c3_large_path, "c4": W.c4_precision,
-             "c5": W.c5_differentiation}[wl]()
+             "c5": W.c5_differentiation, "facet": W.facet_comparison}[wl]()
     ctx = ps.Context()
     db = ps.DeviceBatch(batch, device=dev)
     prec = ps.PS_PREC_MIXED
@@ -536,6 +540,10 @@ def run_config(args, rank, world, local_rank):
         d_tag = torch.empty(cap, dtype=torch.int32, device=dev)
         d_src = torch.empty(cap, dtype=torch.int32, device=dev)
         d_n = torch.zeros(1, dtype=torch.int64, device=dev)
+    if wl == "facet":
+        uni = torch.empty_like(out.rib)
+        st_p = torch.empty((db.n_link, 4), dtype=torch.float32, device=dev)
+        st_u = torch.empty_like(st_p)
     if wl == "c5":
         gen = torch.Generator(device="cpu").manual_seed(20200705)
         g_rib = torch.randn((R, 4), generator=gen).to(dev)
@@ -557,6 +565,12 @@ def run_config(args, rank, world, local_rank):
                        d_rib, d_s, d_tag, d_src, d_n, cap, stream=stream)
             ps.ps_rasterize_coverage(ctx, d_rib, d_tag, d_n, cap, db.n_path, Wd, Ht, canvas,
                                      covered, stream=stream)
+        elif wl == "facet":
+            ps.ps_uniform_tessellate(ctx, db, out, uni, stream=stream)
+            ps.ps_facet_stats(ctx, out.rib, out.tag, out.link_rib_off, out.n_rib, out.capacity,
+                              st_p, stream=stream)
+            ps.ps_facet_stats(ctx, uni, out.tag, out.link_rib_off, out.n_rib, out.capacity,
+                              st_u, stream=stream)
         elif wl == "c5":
             g_pts.zero_()
             g_w.zero_()
@@ -618,7 +632,22 @@ def run_config(args, rank, world, local_rank):
         line["raster_work"] = ps.ps_raster_stats(ctx)
     if wl == "c3":
         line["config"]["n_dashed_ribs"] = int(d_n.item())
-    if not args.no_plain and wl != "c5":
+    if wl == "facet":
+        import math
+        sp = st_p.cpu().double().numpy()
+        su = st_u.cpu().double().numpy()
+
+        def summary(a):
+            n = a[:, 3].sum()
+            m = a[:, 1].sum() / n
+            return {"max_deg": math.degrees(a[:, 0].max()), "mean_deg": math.degrees(m),
+                    "sd_deg": math.degrees(math.sqrt(max(a[:, 2].sum() / n - m * m, 0.0))),
+                    "ordinary_facets": int(n)}
+        segs = (sp[:, 3] > 0) & (su[:, 3] > 0)
+        line["facets"] = {"polar": summary(sp), "uniform": summary(su),
+                          "segments_polar_max_smaller": float((sp[segs, 0] < su[segs, 0]).mean()),
+                          "bound_2q_deg": math.degrees(2 * batch.dtheta)}
+    if not args.no_plain and wl not in ("c5", "facet"):
         line["plain"] = run_plain(ps, batch, dev, max_paths=2000 if wl == "c4" else batch.n_path)
     if rank == 0:
         print(json.dumps(line))

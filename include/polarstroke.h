@@ -262,6 +262,32 @@ int ps_profile_enable(ps_context* ctx, int enable);
 int ps_profile_read(ps_context* ctx, float* h_ms /* [PS_PROF_SLOTS] */);
 const char* ps_profile_slot_name(int slot);
 
+/* Uniform parametric comparison (Sec. 8.1).  For every segment link of the
+ * polar tessellation fwd (made from the same seg and paths), writes the same
+ * number of ribs N+1 at uniform parameters t_j = j/N: g(t_j) -+ (w/2) n(t_j)
+ * with n the unit left normal of g'(t_j) (Eq. 1 sampled uniformly; at an exact
+ * cusp the direction of g''(t) stands in for the tangent).  Join and cap links
+ * keep the polar ribs, so fwd's tags, offsets and counts describe the output
+ * too (equal quad counts, as the paper compares).
+ *   d_rib_out  float4[fwd->capacity] (N.x, N.y, P.x, P.y), caller-owned.
+ * Returns PS_ERR_INVALID for null or inconsistent arguments. */
+int ps_uniform_tessellate(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
+                          const ps_tess_out* fwd, float* d_rib_out, void* stream);
+
+/* Facet-angle statistics of a rib stream (Sec. 4.2, 8.1).  A facet is where one
+ * quad's boundary edge meets the next: at every interior rib of a segment link,
+ * on the N and P sides, the angle in [0, pi] between the edges before and after
+ * it.  Only ordinary facets count: each of the two edges points between the
+ * tangents of its end ribs (a rib P - N turned clockwise) within `slack`
+ * (cross products of unit vectors; ~1e-5 suits FP32 ribs), which leaves out
+ * the facets next to offset cusps; ribs of zero length use the centreline.
+ *   d_stats[4 l .. 4 l + 3] = max, sum, sum of squares, count of the ordinary
+ *   facet angles (radians) of link l; zeros for links without any.
+ * The ribs' link structure comes from d_tag and d_link_rib_off[n_link + 1]. */
+int ps_facet_stats(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
+                   const int32_t* d_link_rib_off, int64_t n_link, const int64_t* d_n_rib,
+                   int64_t capacity, float slack, float* d_stats, void* stream);
+
 /* SVG elliptical arc -> conic segments (host function, no device work).
  * The arc runs from (x0, y0) to (x1, y1) on the ellipse with radii rx, ry whose
  * x axis is rotated by phi_deg, the large-arc and sweep flags choosing among the

@@ -24,7 +24,8 @@ EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_statu
            "ps_error_string", "ps_tessellate_strokes", "ps_count_ribs_sync", "ps_arclength_scan",
            "ps_dash", "ps_rasterize_coverage", "ps_profile_enable", "ps_profile_read",
            "ps_profile_slot_name", "ps_raster_stats", "ps_tessellate_strokes_noalloc",
-           "ps_tessellate_backward", "ps_set_tuning", "ps_get_tuning", "ps_svg_arc_to_conics"]
+           "ps_tessellate_backward", "ps_set_tuning", "ps_get_tuning", "ps_svg_arc_to_conics",
+           "ps_uniform_tessellate", "ps_facet_stats"]
 PS_PROF_SLOTS = 10
 PS_TUNE_EMIT_SLABS, PS_TUNE_SETUP_LINKS, PS_TUNE_BIN_BLOCKS = 0, 1, 2
 TUNE_CANDIDATES = {PS_TUNE_EMIT_SLABS: (4, 8, 16, 32), PS_TUNE_SETUP_LINKS: (1, 2, 4),
@@ -97,6 +98,9 @@ def lib():
         L.ps_set_tuning.argtypes = [P, ctypes.c_int, ctypes.c_int]
         F = ctypes.c_float
         L.ps_svg_arc_to_conics.argtypes = [F, F, F, F, F, ctypes.c_int, ctypes.c_int, F, F, P, P]
+        L.ps_uniform_tessellate.argtypes = [P, ctypes.POINTER(_Segments), ctypes.POINTER(_Paths),
+                                            ctypes.POINTER(_TessOut), P, P]
+        L.ps_facet_stats.argtypes = [P, P, P, P, I64, P, I64, F, P, P]
         L.ps_get_tuning.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.ps_tessellate_backward.argtypes = [P, ctypes.POINTER(_Segments), ctypes.POINTER(_Paths),
                                              ctypes.c_float, ctypes.c_int,
@@ -240,6 +244,25 @@ def ps_raster_stats(ctx: Context) -> dict:
     _check(lib().ps_raster_stats(ctx.handle, ctypes.cast(buf, ctypes.c_void_p), len(RSTAT_NAMES)),
            "ps_raster_stats")
     return dict(zip(RSTAT_NAMES, (int(v) for v in buf)))
+
+
+def ps_uniform_tessellate(ctx: Context, db: DeviceBatch, fwd: TessOutput, out_rib, stream=None):
+    """Uniform parametric ribs with the polar tessellation fwd's per-link counts."""
+    seg, paths = db._structs()
+    o = fwd._struct()
+    _check(lib().ps_uniform_tessellate(ctx.handle, ctypes.byref(seg), ctypes.byref(paths),
+                                       ctypes.byref(o), _ptr(out_rib), _stream(stream)),
+           "ps_uniform_tessellate")
+
+
+def ps_facet_stats(ctx: Context, rib, tag, link_rib_off, n_rib, capacity, stats, slack=1e-5,
+                   stream=None):
+    """Per-link (max, sum, sum of squares, count) of ordinary facet angles into
+    stats float32[n_link, 4]."""
+    n_link = int(link_rib_off.numel()) - 1
+    _check(lib().ps_facet_stats(ctx.handle, _ptr(rib), _ptr(tag), _ptr(link_rib_off), n_link,
+                                _ptr(n_rib), int(capacity), float(slack), _ptr(stats),
+                                _stream(stream)), "ps_facet_stats")
 
 
 def svg_arc_to_conics(x0, y0, rx, ry, phi_deg, large_arc, sweep, x1, y1):

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpolarstroke.so")
-SOURCES = ["ps_api.cu", "ps_tess.cu", "ps_raster.cu", "ps_dash.cu", "ps_adjoint.cu"]
+SOURCES = ["ps_api.cu", "ps_tess.cu", "ps_raster.cu", "ps_dash.cu", "ps_adjoint.cu",
+           "ps_facets.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

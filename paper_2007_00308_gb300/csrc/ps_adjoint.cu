@@ -103,7 +103,8 @@ __device__ __forceinline__ void weights(const Seg& g, float t, float* b, float* 
       Hd = (g.D - g.B) - (g.B - g.A);
       break;
     case PS_CONIC: {
-      float w = g.w, den = u * u + 2.f * u * t * w + t * t;
+      // the denominator in its cancellation-free form (as in g_rel)
+      float w = g.w, s12 = 1.f - 2.f * t, den = s12 * s12 + 2.f * (1.f + w) * u * t;
       b[0] = u * u / den; b[1] = 2.f * u * t * w / den; b[2] = 0.f; b[3] = t * t / den;
       beta[0] = -w * u * u - u * t; beta[1] = w * u * u - w * t * t; beta[2] = 0.f;
       beta[3] = u * t + w * t * t;

@@ -136,7 +136,11 @@ __device__ __forceinline__ float2 g_rel(const Seg& g, float t) {
     case PS_QUAD:
       return (g.B - g.A) * (2.f * u * t) + (g.D - g.A) * (t * t);
     case PS_CONIC: {
-      float den = u * u + 2.f * u * t * g.w + t * t;
+      // (1-t)^2 + 2w(1-t)t + t^2 written as (1-2t)^2 + 2(1+w)(1-t)t: for
+      // w > -1 both terms are non-negative, so the sum does not cancel when w
+      // nears -1 (where the denominator itself nears 0 at t = 1/2)
+      float s = 1.f - 2.f * t;
+      float den = s * s + 2.f * (1.f + g.w) * u * t;
       float2 num = (g.B - g.A) * (2.f * u * t * g.w) + (g.D - g.A) * (t * t);
       return num * (1.f / den);
     }

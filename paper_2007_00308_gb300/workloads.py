@@ -315,6 +315,42 @@ def c5_differentiation(n_paths: int = 4096, n_seg: int = 32,
                       canvas=(1024, 1024))
 
 
+def facet_comparison(n_paths: int = 20000, seed: int = SEED_BASE + 6,
+                     dtheta_deg: float = 4.0) -> StrokeBatch:
+    """Single-cubic open paths for the uniform-parametric comparison: half
+    serpentines (B and C on opposite sides of the chord), a quarter exact cusps
+    (C = A + B - D on a 1/64-px grid), a quarter loops (a cusp with C pushed off
+    along the chord); chord length log-uniform 20-400 px at a random angle,
+    widths log-uniform 1-100 px, butt caps, dtheta 4 deg (the paper's figure)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pts = np.zeros((n_paths, 4, 2))
+    kind = rng.uniform(0, 1, n_paths)
+    for i in range(n_paths):
+        L = math.exp(rng.uniform(math.log(20.0), math.log(400.0)))
+        ang = rng.uniform(-math.pi, math.pi)
+        c, s_ = math.cos(ang), math.sin(ang)
+        rot = np.array([[c, -s_], [s_, c]])
+        o = rng.uniform(0, 1024, 2)
+        if kind[i] < 0.5:
+            b = [rng.uniform(0.1, 0.6) * L, rng.uniform(0.2, 1.0) * L]
+            cc = [rng.uniform(0.4, 0.9) * L, -rng.uniform(0.2, 1.0) * L]
+            local = np.array([[0, 0], b, cc, [L, 0]])
+        else:
+            A, D = np.array([0.0, 0.0]), np.array([L, 0.0])
+            B = np.array([rng.uniform(0.2, 1.2) * L, rng.uniform(0.3, 1.0) * L])
+            C = A + B - D
+            if kind[i] >= 0.75:
+                C = C + np.array([rng.uniform(0.05, 0.3) * L, 0.0])
+            local = np.array([A, B, C, D])
+        pts[i] = _grid(local @ rot.T + o)
+        if kind[i] >= 0.5 and kind[i] < 0.75:
+            pts[i, 2] = pts[i, 0] + pts[i, 1] - pts[i, 3]  # exact on the grid
+    widths = np.exp(rng.uniform(math.log(1.0), math.log(100.0), n_paths))
+    return make_batch("facet_comparison", np.full(n_paths, CUBIC), pts, np.ones(n_paths),
+                      np.ones(n_paths, np.int64), widths, JOIN_ROUND, CAP_BUTT,
+                      dtheta_deg=dtheta_deg, canvas=(0, 0))
+
+
 CONFIGS = {
     "c1": c1_plain_small,
     "c2": c2_batching,
