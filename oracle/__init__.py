@@ -13,6 +13,8 @@ Parity status per function (see the tests under ``tests/test_oracle_*.py``):
                    structure, per-step turn, total turning, chord error, joins,
                    caps; coverage against brute force)
   dash             pinned (straight line against the analytic dash pieces)
+  dash_capped      pinned (straight line: caps against the analytic cap shapes;
+                   coverage of a capped dashed line against brute force)
   raster           pinned (axis-aligned rectangles and triangles against a
                    point-in-polygon count written with a different predicate)
   centreline_distance  pinned (distance to a line and a circle in closed form)
@@ -76,6 +78,9 @@ def _load():
             _lib.orc_centreline_distance.argtypes = [I64, P, P, P, ctypes.c_int, ctypes.c_int,
                                                      ctypes.c_int, P]
             _lib.orc_centreline_distance.restype = ctypes.c_int
+            _lib.orc_dash_capped.argtypes = [I64, P, P, P, P, ctypes.c_int, D, P, I64, D, I64, P,
+                                             P, P, P, P]
+            _lib.orc_dash_capped.restype = ctypes.c_int
             _lib.orc_uniform_ribs.argtypes = [ctypes.c_int, P, D, ctypes.c_int, D, P]
             _lib.orc_uniform_ribs.restype = ctypes.c_int
             _lib.orc_facet_angles.argtypes = [I64, P, D, P, P]
@@ -187,6 +192,32 @@ def dash(rib, s, tag, pattern, offset=0.0):
                       _p(os_), _p(otag), _p(osrc), ctypes.byref(n))
     if rc != 0:
         raise OracleError(f"orc_dash failed: {rc}")
+    return dict(rib=orib, s=os_, tag=otag, src=osrc)
+
+
+def dash_capped(rib, s, tag, pattern, offset, path_cap, dtheta):
+    """Dashing with capped dash ends (Sec. 5.2, reading R18): as ``dash`` plus the
+    path's cap style (path_cap[p]) at every stretch end inside the path.
+    Returns dict(rib[n,4], s[n], tag[n], src[n])."""
+    lib = _load()
+    rib = _c(rib, np.float64).reshape(-1)
+    s = _c(s, np.float64)
+    tag = _c(tag, np.uint32)
+    pat = _c(pattern, np.float64)
+    pc = _c(path_cap, np.uint8)
+    q = float(np.float32(dtheta))
+    R = len(s)
+    n = ctypes.c_int64(0)
+    args = (R, _p(rib), _p(s), _p(tag), _p(pat), len(pat), float(offset), _p(pc), len(pc), q)
+    rc = lib.orc_dash_capped(*args, 0, None, None, None, None, ctypes.byref(n))
+    if rc not in (0, -2):
+        raise OracleError(f"orc_dash_capped count failed: {rc}")
+    m = int(n.value)
+    orib = np.zeros((m, 4)); os_ = np.zeros(m); otag = np.zeros(m, np.uint32)
+    osrc = np.zeros(m, np.int64)
+    rc = lib.orc_dash_capped(*args, m, _p(orib), _p(os_), _p(otag), _p(osrc), ctypes.byref(n))
+    if rc != 0:
+        raise OracleError(f"orc_dash_capped failed: {rc}")
     return dict(rib=orib, s=os_, tag=otag, src=osrc)
 
 

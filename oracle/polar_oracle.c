@@ -1278,3 +1278,110 @@ int orc_facet_angles(int64_t n, const double* rib, double slack, double* angle,
   }
   return ORC_OK;
 }
+
+/* ---- dashing with capped dash ends (Sec. 5.2, reading R18) ---------------- */
+/* As orc_dash, and every on-stretch [a, b) gets the path's cap style at its
+ * ends inside the path: a start cap where 0 < a lies in a segment quad
+ * [s_{j-1}, s_j), an end cap where b lies in (s_{j-1}, s_j].  A cap is the
+ * path cap of Sec. 4.3.5 (reading R7) about the boundary rib: centre the rib's
+ * midpoint, radius half its length, tangent the rib turned clockwise; a start
+ * cap pivots from psi + pi, an end cap from psi, both through +pi.  Its J+1
+ * ribs (J from the cap style, none for butt) form a strip of their own at the
+ * boundary's s, written right before the stretch's first piece (start cap) or
+ * right after its last piece (end cap).  path_cap[p] is path p's cap style. */
+static int64_t dash_cap(int64_t n, int64_t cap, const double* rib, int64_t j, double f, double sv,
+                        uint32_t path, int style, double q, int start, double* out_rib,
+                        double* out_s, uint32_t* out_tag, int64_t* out_src) {
+  int J = cap_count(style, q);
+  if (J <= 0) return 0;
+  double v[4];
+  for (int c = 0; c < 4; ++c) {
+    double v0 = rib[4 * (j - 1) + c], v1 = rib[4 * j + c];
+    v[c] = v0 + f * (v1 - v0);
+  }
+  double vx = v[2] - v[0], vy = v[3] - v[1];
+  double r = 0.5 * sqrt(vx * vx + vy * vy);
+  double psi = atan2(-vx, vy); /* the rib is 2r n(psi), n = (-sin psi, cos psi) */
+  Link L;
+  memset(&L, 0, sizeof L);
+  L.kind = 3;
+  L.style = style;
+  L.at = mk(0.5 * (v[0] + v[2]), 0.5 * (v[1] + v[3]));
+  L.Psi0 = start ? psi + PI : psi;
+  L.delta = PI;
+  if (out_rib && n + J + 1 <= cap) {
+    V2* Nv = (V2*)malloc(sizeof(V2) * (size_t)(J + 1));
+    V2* Pv = (V2*)malloc(sizeof(V2) * (size_t)(J + 1));
+    double* ps_ = (double*)malloc(sizeof(double) * (size_t)(J + 1));
+    if (!Nv || !Pv || !ps_) {
+      free(Nv); free(Pv); free(ps_);
+      return 0;
+    }
+    emit_pivot(&L, J, r, Nv, Pv, ps_);
+    for (int k = 0; k <= J; ++k) {
+      out_rib[4 * (n + k) + 0] = Nv[k].x;
+      out_rib[4 * (n + k) + 1] = Nv[k].y;
+      out_rib[4 * (n + k) + 2] = Pv[k].x;
+      out_rib[4 * (n + k) + 3] = Pv[k].y;
+      out_s[n + k] = sv;
+      out_tag[n + k] = (path << 2) | (k == 0 ? TAG_LINK_START : 0u);
+      out_src[n + k] = j;
+    }
+    free(Nv); free(Pv); free(ps_);
+  }
+  return J + 1;
+}
+
+int orc_dash_capped(int64_t R, const double* rib, const double* s, const uint32_t* tag,
+                    const double* pattern, int m, double offset, const uint8_t* path_cap,
+                    int64_t n_path, double q, int64_t cap, double* out_rib, double* out_s,
+                    uint32_t* out_tag, int64_t* out_src, int64_t* n_out) {
+  if (m <= 0 || m > 32 || !(q > 0.0) || (n_path > 0 && !path_cap)) return ORC_ERR_INVALID;
+  int m2 = (m % 2) ? 2 * m : m;
+  double cum[65];
+  cum[0] = 0.0;
+  for (int i = 0; i < m2; ++i) {
+    double d = pattern[i % m];
+    if (!(d >= 0.0)) return ORC_ERR_INVALID;
+    cum[i + 1] = cum[i] + d;
+  }
+  double period = cum[m2];
+  if (!(period > 0.0)) return ORC_ERR_INVALID;
+  int64_t n = 0;
+  for (int64_t j = 1; j < R; ++j) {
+    if (tag[j] & TAG_LINK_START) continue;
+    double sa = s[j - 1], sb = s[j];
+    uint32_t tg = tag[j] & ~TAG_LINK_START;
+    uint32_t path = tag[j] >> 2;
+    if ((int64_t)path >= n_path) return ORC_ERR_INVALID;
+    int style = path_cap[path];
+    double k0 = floor((sa + offset) / period) - 1.0;
+    for (double k = k0;; k += 1.0) {
+      double base = k * period;
+      if (base - offset > sb) break;
+      for (int i = 0; i < m2; i += 2) {
+        double a = (base + cum[i]) - offset, b = (base + cum[i + 1]) - offset;
+        if (!(b > a)) continue;
+        if (sb > sa) {
+          double lo = a > sa ? a : sa, hi = b < sb ? b : sb;
+          if (hi > lo) {
+            double f0 = (lo - sa) / (sb - sa), f1 = (hi - sa) / (sb - sa);
+            if (a >= sa && a < sb && a > 0.0)
+              n += dash_cap(n, cap, rib, j, f0, lo, path, style, q, 1, out_rib, out_s, out_tag,
+                            out_src);
+            dash_put(n, cap, rib, j, f0, f1, lo, hi, tg, out_rib, out_s, out_tag, out_src);
+            n += 2;
+            if (b > sa && b <= sb)
+              n += dash_cap(n, cap, rib, j, f1, hi, path, style, q, 0, out_rib, out_s, out_tag,
+                            out_src);
+          }
+        } else if (sa >= a && sa < b) { /* zero-length quad kept whole */
+          dash_put(n, cap, rib, j, 0.0, 1.0, sa, sb, tg, out_rib, out_s, out_tag, out_src);
+          n += 2;
+        }
+      }
+    }
+  }
+  *n_out = n;
+  return n > cap ? ORC_ERR_CAPACITY : ORC_OK;
+}
