@@ -235,6 +235,24 @@ int ps_dash(ps_context* ctx, const float* d_rib, const float* d_s, const uint32_
             float offset, float* d_out_rib, float* d_out_s, uint32_t* d_out_tag,
             int32_t* d_out_src, int64_t* d_n_out, int64_t out_capacity, void* stream);
 
+/* ps_dash with capped dash ends (Sec. 5.2, reading R18 of the design notes):
+ * every on-stretch also gets its path's cap style (d_path_cap[p], PS_CAP_*;
+ * butt adds nothing) at its ends inside the path -- a start cap where the
+ * stretch begins at 0 < a inside a segment quad [s_{r-1}, s_r), an end cap
+ * where it ends at b in (s_{r-1}, s_r].  A cap is the path cap of Sec. 4.3.5
+ * (pivot through +pi, outer side N, inner radius 0; round caps step by at most
+ * dtheta) about the boundary rib: centre the rib's midpoint, radius half its
+ * length, tangent the rib turned clockwise.  Its J+1 ribs form a strip of their
+ * own (link-start tag on the first, segment bit clear) at the boundary's s,
+ * written right before the stretch's first piece (start cap) or right after its
+ * last piece (end cap).  Counts, offsets and errors as ps_dash; the output
+ * count includes the cap ribs. */
+int ps_dash_capped(ps_context* ctx, const float* d_rib, const float* d_s, const uint32_t* d_tag,
+                   const int64_t* d_n_rib, int64_t capacity, const float* h_pattern, int n_pattern,
+                   float offset, const uint8_t* d_path_cap, int32_t n_path, float dtheta,
+                   float* d_out_rib, float* d_out_s, uint32_t* d_out_tag, int32_t* d_out_src,
+                   int64_t* d_n_out, int64_t out_capacity, void* stream);
+
 /* Coverage of the quads of a rib stream on a width x height canvas with 16
  * samples per pixel (spp must be 16).  Vertices snap to round-half-even(v*256);
  * sample k of pixel (x, y) sits at (x + (16k+8)/256, y + (16((5k) mod 16)+8)/256);

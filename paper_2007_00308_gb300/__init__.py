@@ -25,7 +25,7 @@ EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_statu
            "ps_dash", "ps_rasterize_coverage", "ps_profile_enable", "ps_profile_read",
            "ps_profile_slot_name", "ps_raster_stats", "ps_tessellate_strokes_noalloc",
            "ps_tessellate_backward", "ps_set_tuning", "ps_get_tuning", "ps_svg_arc_to_conics",
-           "ps_uniform_tessellate", "ps_facet_stats"]
+           "ps_uniform_tessellate", "ps_facet_stats", "ps_dash_capped"]
 PS_PROF_SLOTS = 10
 PS_TUNE_EMIT_SLABS, PS_TUNE_SETUP_LINKS, PS_TUNE_BIN_BLOCKS = 0, 1, 2
 TUNE_CANDIDATES = {PS_TUNE_EMIT_SLABS: (4, 8, 16, 32), PS_TUNE_SETUP_LINKS: (1, 2, 4),
@@ -98,6 +98,8 @@ def lib():
         L.ps_set_tuning.argtypes = [P, ctypes.c_int, ctypes.c_int]
         F = ctypes.c_float
         L.ps_svg_arc_to_conics.argtypes = [F, F, F, F, F, ctypes.c_int, ctypes.c_int, F, F, P, P]
+        L.ps_dash_capped.argtypes = [P, P, P, P, P, I64, P, ctypes.c_int, F, P, I32, F, P, P, P,
+                                     P, P, I64, P]
         L.ps_uniform_tessellate.argtypes = [P, ctypes.POINTER(_Segments), ctypes.POINTER(_Paths),
                                             ctypes.POINTER(_TessOut), P, P]
         L.ps_facet_stats.argtypes = [P, P, P, P, I64, P, I64, F, P, P]
@@ -349,6 +351,19 @@ def ps_dash(ctx: Context, rib, s, tag, n_rib, capacity, pattern, offset, out_rib
                        _ptr(out_s), _ptr(out_tag), _ptr(out_src), _ptr(n_out), int(out_capacity),
                        _stream(stream))
     _check(rc, "ps_dash")
+
+
+def ps_dash_capped(ctx: Context, rib, s, tag, n_rib, capacity, pattern, offset, path_cap, dtheta,
+                   out_rib, out_s, out_tag, out_src, n_out, out_capacity, stream=None):
+    """ps_dash with the paths' cap styles (uint8 device tensor path_cap[P]) at
+    every dash end inside a path."""
+    pat = (ctypes.c_float * len(pattern))(*[float(v) for v in pattern])
+    rc = lib().ps_dash_capped(ctx.handle, _ptr(rib), _ptr(s), _ptr(tag), _ptr(n_rib),
+                              int(capacity), ctypes.cast(pat, ctypes.c_void_p), len(pattern),
+                              float(offset), _ptr(path_cap), int(path_cap.numel()), float(dtheta),
+                              _ptr(out_rib), _ptr(out_s), _ptr(out_tag), _ptr(out_src), _ptr(n_out),
+                              int(out_capacity), _stream(stream))
+    _check(rc, "ps_dash_capped")
 
 
 def ps_rasterize_coverage(ctx: Context, rib, tag, n_rib, capacity, n_path, width, height, canvas,

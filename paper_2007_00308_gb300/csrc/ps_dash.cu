@@ -6,6 +6,14 @@
 // an independent 2-rib strip.  A quad of zero length (join, cap, cusp pivot) is
 // kept whole iff its s is "on".  Stretch boundaries are evaluated in FP64 with
 // explicitly rounded operations (no contraction).
+//
+// With cap styles (ps_dash_capped), every stretch also gets its path's cap at
+// its ends inside the path: a start cap where 0 < a lies in [s_{r-1}, s_r), an
+// end cap where b lies in (s_{r-1}, s_r], each the path cap of Sec. 4.3.5
+// (pivot through +pi, outer side N, inner radius 0) about the boundary rib --
+// centre its midpoint, radius half its length, tangent the rib turned
+// clockwise -- as a strip of its own at the boundary's s, written before the
+// stretch's first piece or after its last.
 #include <cuda_runtime.h>
 
 #include "ps_internal.cuh"
@@ -17,7 +25,43 @@ struct DashPattern {
   double period;
   double offset;
   int m2;
+  int j_round;                 // ribs - 1 of a round cap at this dtheta
+  const uint8_t* path_cap;     // cap style per path, or null: butt dash ends
+  int n_path;
 };
+
+__device__ __forceinline__ int cap_steps(const DashPattern& P, uint32_t path) {
+  if (!P.path_cap || (int)path >= P.n_path) return 0;
+  switch (P.path_cap[path]) {
+    case PS_CAP_TRIANGLE: return 2;
+    case PS_CAP_SQUARE: return 4;
+    case PS_CAP_ROUND: return P.j_round;
+    default: return 0;
+  }
+}
+
+// Ribs k = 0..J of a dash cap about boundary rib v (start: pivot from psi + pi,
+// end: from psi; both through +pi).
+__device__ __forceinline__ void emit_cap(float4 v, int J, bool square, bool start, uint32_t tg,
+                                         float sv, int32_t src, int64_t o, float4* out_rib,
+                                         float* out_s, uint32_t* out_tag, int32_t* out_src) {
+  const float PI_F = 3.14159265358979323846f;
+  float cx = 0.5f * (v.x + v.z), cy = 0.5f * (v.y + v.w);
+  float vx = v.z - v.x, vy = v.w - v.y;
+  float r = 0.5f * sqrtf(vx * vx + vy * vy);
+  float psi = atan2f(-vx, vy);  // the rib is 2r n(psi), n = (-sin psi, cos psi)
+  float psi0 = start ? psi + PI_F : psi;
+  for (int k = 0; k <= J; ++k) {
+    float ang = k == J ? psi0 + PI_F : psi0 + PI_F * (float)k / (float)J;
+    float sn, cs;
+    sincosf(ang, &sn, &cs);
+    float rn = (square && (k == 1 || k == 3)) ? r * 1.41421356237309515f : r;
+    out_rib[o + k] = make_float4(cx + rn * sn, cy - rn * cs, cx, cy);
+    out_s[o + k] = sv;
+    out_tag[o + k] = (tg & ~(PS_TAG_SEGMENT | PS_TAG_LINK_START)) | (k == 0 ? PS_TAG_LINK_START : 0u);
+    if (out_src) out_src[o + k] = src;
+  }
+}
 
 constexpr int DASH_NT = 256;
 
@@ -27,7 +71,9 @@ __device__ __forceinline__ int dash_quad(const DashPattern& P, double sa, double
                                          uint32_t tg, int64_t out0, float4* out_rib,
                                          float* out_s, uint32_t* out_tag, int32_t* out_src,
                                          int64_t out_cap, int32_t* status) {
-  int n = 0;
+  int n = 0;  // output ribs
+  const int J = cap_steps(P, tg >> 2);
+  const bool square = J == 4 && P.path_cap && P.path_cap[tg >> 2] == PS_CAP_SQUARE;
   double k0 = floor(__ddiv_rn(__dadd_rn(sa, P.offset), P.period)) - 1.0;
   float4 v0, v1;
   if (EMIT) {
@@ -54,9 +100,12 @@ __device__ __forceinline__ int dash_quad(const DashPattern& P, double sa, double
         keep = (sa >= a && sa < b);
       }
       if (!keep) continue;
+      const bool cap0 = J > 0 && sb > sa && a >= sa && a < sb && a > 0.0;
+      const bool cap1 = J > 0 && sb > sa && b > sa && b <= sb;
+      const int nr = 2 + (cap0 ? J + 1 : 0) + (cap1 ? J + 1 : 0);
       if (EMIT) {
-        int64_t o = out0 + 2 * n;
-        if (o + 2 <= out_cap) {
+        int64_t o = out0 + n + (cap0 ? J + 1 : 0);
+        if (out0 + n + nr <= out_cap) {
           double f0 = 0.0, f1 = 1.0;
           if (sb > sa) {
             double d = __dsub_rn(sb, sa);
@@ -81,11 +130,17 @@ __device__ __forceinline__ int dash_quad(const DashPattern& P, double sa, double
             out_src[o] = (int32_t)r;
             out_src[o + 1] = (int32_t)r;
           }
+          if (cap0)
+            emit_cap(out_rib[o], J, square, true, tg, (float)lo, (int32_t)r, out0 + n, out_rib,
+                     out_s, out_tag, out_src);
+          if (cap1)
+            emit_cap(out_rib[o + 1], J, square, false, tg, (float)hi, (int32_t)r, o + 2, out_rib,
+                     out_s, out_tag, out_src);
         } else {
           ps_record_error(status, PS_ERR_CAPACITY);
         }
       }
-      ++n;
+      n += nr;
     }
   }
   return n;
@@ -125,8 +180,8 @@ __global__ void __launch_bounds__(DASH_NT) k_dash(
     if (active) {
       sa = (double)s[r - 1];
       sb = (double)s[r];
-      cnt = dash_quad<false>(P, sa, sb, r, rib, 0.f, 0.f, 0u, 0, nullptr, nullptr, nullptr, nullptr,
-                             0, status);
+      cnt = dash_quad<false>(P, sa, sb, r, rib, 0.f, 0.f, tg, 0, nullptr, nullptr, nullptr,
+                             nullptr, 0, status);
     }
     long long x = cnt;
     for (int o = 1; o < 32; o <<= 1) {
@@ -143,12 +198,12 @@ __global__ void __launch_bounds__(DASH_NT) k_dash(
     long long excl = x - cnt + wpre;
     if (threadIdx.x == 0) s_prefix = lookback_sum(tflag, tagg, tincl, total, tile, status);
     __syncthreads();
-    int64_t out0 = 2 * (s_prefix + excl);
+    int64_t out0 = s_prefix + excl;
     if (active && cnt)
       dash_quad<true>(P, sa, sb, r, rib, 0.f, 0.f, tg & ~PS_TAG_LINK_START, out0, out_rib, out_s,
                       out_tag, out_src, out_cap, status);
     if (tile == n_tiles - 1 && threadIdx.x == DASH_NT - 1) {
-      long long tot = 2 * (s_prefix + total);
+      long long tot = s_prefix + total;
       *n_out = tot;
       if (tot > out_cap) ps_record_error(status, PS_ERR_CAPACITY);
     }
@@ -158,13 +213,17 @@ __global__ void __launch_bounds__(DASH_NT) k_dash(
 
 }  // namespace
 
-extern "C" int ps_dash(ps_context* ctx, const float* d_rib, const float* d_s,
-                       const uint32_t* d_tag, const int64_t* d_n_rib, int64_t capacity,
-                       const float* h_pattern, int n_pattern, float offset, float* d_out_rib,
-                       float* d_out_s, uint32_t* d_out_tag, int32_t* d_out_src, int64_t* d_n_out,
-                       int64_t out_capacity, void* stream) {
+extern "C" int ps_dash_capped(ps_context* ctx, const float* d_rib, const float* d_s,
+                              const uint32_t* d_tag, const int64_t* d_n_rib, int64_t capacity,
+                              const float* h_pattern, int n_pattern, float offset,
+                              const uint8_t* d_path_cap, int32_t n_path, float dtheta,
+                              float* d_out_rib, float* d_out_s, uint32_t* d_out_tag,
+                              int32_t* d_out_src, int64_t* d_n_out, int64_t out_capacity,
+                              void* stream) {
   if (!ctx || !d_rib || !d_s || !d_tag || !d_n_rib || !h_pattern || !d_out_rib || !d_out_s ||
       !d_out_tag || !d_n_out || capacity < 0 || out_capacity < 0)
+    return PS_ERR_INVALID;
+  if (d_path_cap && (n_path < 0 || !(dtheta >= 1e-4f && dtheta <= 3.14159265f)))
     return PS_ERR_INVALID;
   if (n_pattern < 1 || n_pattern > 32 || !(offset == offset)) return PS_ERR_INVALID;
   DashPattern P;
@@ -177,6 +236,16 @@ extern "C" int ps_dash(ps_context* ctx, const float* d_rib, const float* d_s,
   }
   P.period = P.cum[P.m2];
   P.offset = (double)offset;
+  P.path_cap = d_path_cap;
+  P.n_path = d_path_cap ? n_path : 0;
+  P.j_round = 0;
+  if (d_path_cap) {
+    // a round cap turns pi in steps of at most q (a ratio within 1e-4 step above
+    // an integer takes that integer, as for every turning count)
+    double x = 3.14159265358979323846 / (double)dtheta;
+    int J = (int)ceil(x - 1e-4);
+    P.j_round = J < 1 ? 1 : J;
+  }
   if (!(P.period > 0.0)) return PS_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = stream;
@@ -193,4 +262,14 @@ extern "C" int ps_dash(ps_context* ctx, const float* d_rib, const float* d_s,
                                     ctx->d_tile_agg, ctx->d_tile_incl, ctx->d_counters,
                                     ctx->d_status);
   return ps_cuda_check(cudaGetLastError());
+}
+
+extern "C" int ps_dash(ps_context* ctx, const float* d_rib, const float* d_s,
+                       const uint32_t* d_tag, const int64_t* d_n_rib, int64_t capacity,
+                       const float* h_pattern, int n_pattern, float offset, float* d_out_rib,
+                       float* d_out_s, uint32_t* d_out_tag, int32_t* d_out_src, int64_t* d_n_out,
+                       int64_t out_capacity, void* stream) {
+  return ps_dash_capped(ctx, d_rib, d_s, d_tag, d_n_rib, capacity, h_pattern, n_pattern, offset,
+                        nullptr, 0, 1.f, d_out_rib, d_out_s, d_out_tag, d_out_src, d_n_out,
+                        out_capacity, stream);
 }

@@ -82,3 +82,51 @@ def test_dash_matches_oracle_on_gpu_ribs():
                                512, 1)
     assert np.array_equal(can.cpu().numpy().view(np.uint16), ocan)
     assert int(cov.item()) == int(ocov[0])
+
+
+@pytest.mark.parametrize("cap", [W.CAP_ROUND, W.CAP_SQUARE, W.CAP_TRIANGLE])
+def test_capped_dash_matches_oracle_on_gpu_ribs(cap):
+    """Capped dash ends: same order, pieces bit-identical, cap ribs within the
+    vertex bound (FP32 sincos about the same boundary ribs), tags and s exact."""
+    import torch
+    import paper_2007_00308_gb300 as ps
+    from tests._parity import ulp32
+    b = W.c3_large_path(n_seg=400)
+    b.path_cap[:] = cap
+    g = gpu_tessellate(b, 1)
+    out, ctx = g["out"], g["ctx"]
+    pattern, offset = b.dash
+    od = oracle.dash_capped(g["rib"], g["s"], g["tag"], pattern, offset, b.path_cap, b.dtheta)
+    m = len(od["s"])
+    cap_ = m + 16
+    orib = torch.empty((cap_, 4), dtype=torch.float32, device="cuda")
+    os_ = torch.empty(cap_, dtype=torch.float32, device="cuda")
+    otag = torch.empty(cap_, dtype=torch.int32, device="cuda")
+    osrc = torch.empty(cap_, dtype=torch.int32, device="cuda")
+    n = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pc = torch.from_numpy(b.path_cap.astype(np.uint8)).cuda()
+    ps.ps_dash_capped(ctx, out.rib, out.s, out.tag, out.n_rib, out.capacity, pattern, offset, pc,
+                      b.dtheta, orib, os_, otag, osrc, n, cap_)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    assert int(n.item()) == m
+    gtag = otag[:m].cpu().numpy().view(np.uint32)
+    assert np.array_equal(gtag, od["tag"])
+    assert np.array_equal(osrc[:m].cpu().numpy(), od["src"])
+    assert np.array_equal(os_[:m].cpu().numpy(), od["s"].astype(np.float32))
+    grib = orib[:m].cpu().numpy().astype(np.float64)
+    piece = ((gtag >> 1) & 1) == 1
+    assert np.array_equal(grib[piece], od["rib"].astype(np.float32)[piece].astype(np.float64))
+    capr = ~piece
+    assert capr.sum() > 0 or cap == W.CAP_BUTT
+    err = np.abs(grib[capr] - od["rib"][capr])
+    tol = 1e-4 + 4 * ulp32(np.abs(od["rib"][capr]))
+    assert (err <= tol).all(), float((err / tol).max())
+    # and the capped dashes rasterize identically on both sides
+    can = torch.zeros((512, 512), dtype=torch.int16, device="cuda")
+    cov = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ps.ps_rasterize_coverage(ctx, orib, otag, n, cap_, 1, 512, 512, can, cov)
+    torch.cuda.synchronize()
+    ocan, ocov = oracle.raster(grib, gtag, 512, 512, 1)
+    assert np.array_equal(can.cpu().numpy().view(np.uint16), ocan)
+    assert int(cov.item()) == int(ocov[0])
