@@ -16,7 +16,9 @@ Parity status per function (see the tests under ``tests/test_oracle_*.py``):
   dash_capped      pinned (straight line: caps against the analytic cap shapes;
                    coverage of a capped dashed line against brute force)
   raster           pinned (axis-aligned rectangles and triangles against a
-                   point-in-polygon count written with a different predicate)
+                   point-in-polygon count written with a different predicate);
+                   exact=True pinned (convex quads equal the two-triangle raster
+                   off the boundary, bow-tie lobes against rational geometry)
   centreline_distance  pinned (distance to a line and a circle in closed form)
   uniform_ribs     pinned (parabola chords against the midpoint tangent, closed form)
   facet_angles     pinned (circle arc: every facet equals the polar step)
@@ -75,6 +77,8 @@ def _load():
             _lib.orc_dash.restype = ctypes.c_int
             _lib.orc_raster.argtypes = [I64, P, P, ctypes.c_int, ctypes.c_int, I32, P, P]
             _lib.orc_raster.restype = ctypes.c_int
+            _lib.orc_raster_exact.argtypes = [I64, P, P, ctypes.c_int, ctypes.c_int, I32, P, P]
+            _lib.orc_raster_exact.restype = ctypes.c_int
             _lib.orc_centreline_distance.argtypes = [I64, P, P, P, ctypes.c_int, ctypes.c_int,
                                                      ctypes.c_int, P]
             _lib.orc_centreline_distance.restype = ctypes.c_int
@@ -221,15 +225,18 @@ def dash_capped(rib, s, tag, pattern, offset, path_cap, dtheta):
     return dict(rib=orib, s=os_, tag=otag, src=osrc)
 
 
-def raster(rib, tag, width, height, n_path):
-    """16-sample coverage of a rib stream.  Returns (canvas uint16[H,W], covered uint64[P])."""
+def raster(rib, tag, width, height, n_path, exact=False):
+    """16-sample coverage of a rib stream.  Returns (canvas uint16[H,W], covered uint64[P]).
+    exact: quads filled as polygons by the crossing rule (reading R19) instead of as
+    two triangles."""
     lib = _load()
     rib = _c(rib, np.float64).reshape(-1)
     tag = _c(tag, np.uint32)
     canvas = np.zeros((height, width), np.uint16)
     covered = np.zeros(max(int(n_path), 1), np.uint64)
-    rc = lib.orc_raster(len(tag), _p(rib), _p(tag), int(width), int(height), int(n_path),
-                        _p(canvas), _p(covered))
+    fn = lib.orc_raster_exact if exact else lib.orc_raster
+    rc = fn(len(tag), _p(rib), _p(tag), int(width), int(height), int(n_path), _p(canvas),
+            _p(covered))
     if rc != 0:
         raise OracleError(f"orc_raster failed: {rc}")
     return canvas, covered[:n_path]

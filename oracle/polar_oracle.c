@@ -1068,8 +1068,65 @@ static void raster_tri(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t c
 
 /* rib[4R] in px (any precision; snapped here), tag[R].  canvas[W*H] is ORed
  * into (the caller zeroes it); covered[n_path] is added to. */
+/* Reading R19 (Sec. 4.1, Sec. 7: quads rasterized as quads, bow-ties as such):
+ * the exact coverage of quad (N0, P0, P1, N1) is its polygon N0 -> P0 -> P1 ->
+ * N1 -> N0 filled by the crossing rule: a sample is covered iff the ray from it
+ * towards +x crosses an odd number of the four edges, where edge a -> b is
+ * crossed iff a.y <= y < b.y with the sample strictly left of a -> b, or
+ * b.y <= y < a.y with the sample strictly right of it (integer edge function).
+ * A closed polyline of four edges winds at most once around a point, so odd
+ * crossings = nonzero winding: convex, concave and bow-tie quads alike. */
+static void raster_quad_exact(const int64_t* vx, const int64_t* vy, uint16_t* mask, int64_t x0c,
+                              int64_t y0c, int64_t x1c, int64_t y1c) {
+  int64_t wc = x1c - x0c + 1;
+  int64_t minx = vx[0], maxx = vx[0], miny = vy[0], maxy = vy[0];
+  for (int i = 1; i < 4; ++i) {
+    if (vx[i] < minx) minx = vx[i];
+    if (vx[i] > maxx) maxx = vx[i];
+    if (vy[i] < miny) miny = vy[i];
+    if (vy[i] > maxy) maxy = vy[i];
+  }
+  int64_t px0 = ceil_div(minx - 248, 256), px1 = floor_div(maxx - 8, 256);
+  int64_t py0 = ceil_div(miny - 248, 256), py1 = floor_div(maxy - 8, 256);
+  if (px0 < x0c) px0 = x0c;
+  if (py0 < y0c) py0 = y0c;
+  if (px1 > x1c) px1 = x1c;
+  if (py1 > y1c) py1 = y1c;
+  for (int64_t y = py0; y <= py1; ++y) {
+    for (int64_t x = px0; x <= px1; ++x) {
+      uint16_t m = 0;
+      for (int k = 0; k < 16; ++k) {
+        int64_t sx = 256 * x + 16 * k + 8, sy = 256 * y + 16 * ((5 * k) % 16) + 8;
+        int cross = 0;
+        for (int i = 0; i < 4; ++i) {
+          int64_t ax = vx[i], ay = vy[i], bx = vx[(i + 1) & 3], by = vy[(i + 1) & 3];
+          int64_t e = (bx - ax) * (sy - ay) - (by - ay) * (sx - ax);
+          if (ay <= sy && sy < by && e > 0) cross ^= 1;
+          if (by <= sy && sy < ay && e < 0) cross ^= 1;
+        }
+        if (cross) m |= (uint16_t)(1u << k);
+      }
+      mask[(y - y0c) * wc + (x - x0c)] |= m;
+    }
+  }
+}
+
+static int raster_impl(int64_t R, const double* rib, const uint32_t* tag, int W, int H,
+                       int32_t n_path, int exact, uint16_t* canvas, uint64_t* covered);
+
 int orc_raster(int64_t R, const double* rib, const uint32_t* tag, int W, int H,
                int32_t n_path, uint16_t* canvas, uint64_t* covered) {
+  return raster_impl(R, rib, tag, W, H, n_path, 0, canvas, covered);
+}
+
+/* O2 with the exact quad coverage of reading R19. */
+int orc_raster_exact(int64_t R, const double* rib, const uint32_t* tag, int W, int H,
+                     int32_t n_path, uint16_t* canvas, uint64_t* covered) {
+  return raster_impl(R, rib, tag, W, H, n_path, 1, canvas, covered);
+}
+
+static int raster_impl(int64_t R, const double* rib, const uint32_t* tag, int W, int H,
+                       int32_t n_path, int exact, uint16_t* canvas, uint64_t* covered) {
   if (W <= 0 || H <= 0) return ORC_ERR_INVALID;
   uint16_t* mask = (uint16_t*)calloc((size_t)W * H, sizeof(uint16_t));
   if (!mask) return ORC_ERR_INVALID;
@@ -1103,8 +1160,13 @@ int orc_raster(int64_t R, const double* rib, const uint32_t* tag, int W, int H,
         const double* b = rib + 4 * i;
         int64_t Nax = snap256(a[0]), Nay = snap256(a[1]), Pax = snap256(a[2]), Pay = snap256(a[3]);
         int64_t Nbx = snap256(b[0]), Nby = snap256(b[1]), Pbx = snap256(b[2]), Pby = snap256(b[3]);
-        raster_tri(Nax, Nay, Pax, Pay, Pbx, Pby, mask, x0, y0, x1, y1);
-        raster_tri(Nax, Nay, Pbx, Pby, Nbx, Nby, mask, x0, y0, x1, y1);
+        if (exact) {
+          int64_t qx[4] = {Nax, Pax, Pbx, Nbx}, qy[4] = {Nay, Pay, Pby, Nby};
+          raster_quad_exact(qx, qy, mask, x0, y0, x1, y1);
+        } else {
+          raster_tri(Nax, Nay, Pax, Pay, Pbx, Pby, mask, x0, y0, x1, y1);
+          raster_tri(Nax, Nay, Pbx, Pby, Nbx, Nby, mask, x0, y0, x1, y1);
+        }
       }
       uint64_t cnt = 0;
       for (int yy = 0; yy < hc; ++yy)
