@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--n-paths", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--exact", action="store_true",
+                    help="rasterize quads as polygons (bow-ties as such) instead of two triangles")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "facet"],
                     help="c2 (default) is the configuration the metric is quoted on; the "
                          "others print their own line for the per-configuration table")
@@ -293,7 +295,7 @@ def run_ours(args, rank, world, local_rank):
     def step(stream=None):
         ps.ps_tessellate_strokes(ctx, db, out, prec, ps.PS_TESS_ARCLENGTH, stream=stream)
         ps.ps_rasterize_coverage(ctx, out.rib, out.tag, out.n_rib, out.capacity, db.n_path, Wd, Ht,
-                                 canvas, covered, stream=stream)
+                                 canvas, covered, stream=stream, exact=args.exact)
 
     # eager steps: bin sizing and autotuning (allocates workspace), then one
     # step captured in a graph
@@ -411,7 +413,8 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "variant": "batched+mixed: one CUDA graph per step, "
-                   "FP32 with compensated g(t) and FP64 islands", "n_segments": segs,
+                   "FP32 with compensated g(t) and FP64 islands" +
+                   (", quads rasterized as polygons" if args.exact else ""), "n_segments": segs,
                    "n_paths": db.n_path, "n_ribs": R_now, "canvas": [Wd, Ht], "spp": 16,
                    "l2": "flushed before every timed step (256 MiB write)",
                    "wall_s_timed_region": t_wall, "autotune": tuning},
@@ -454,7 +457,7 @@ def run_e2e(args, ps, batch, ctx, db, out, canvas, covered, prec, dev):
             getattr(db, k).copy_(t, non_blocking=True)
         ps.ps_tessellate_strokes(ctx, db, out, prec, ps.PS_TESS_ARCLENGTH)
         ps.ps_rasterize_coverage(ctx, out.rib, out.tag, out.n_rib, out.capacity, db.n_path, Wd, Ht,
-                                 canvas, covered)
+                                 canvas, covered, exact=args.exact)
         h_canvas.copy_(canvas, non_blocking=True)
         h_cov.copy_(covered, non_blocking=True)
         b.record()

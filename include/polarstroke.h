@@ -268,6 +268,20 @@ int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const uint32_t* d
                           int width, int height, int spp, uint16_t* d_canvas,
                           uint64_t* d_covered, void* stream);
 
+/* ps_rasterize_coverage with every quad filled as its polygon N_{r-1} ->
+ * P_{r-1} -> P_r -> N_r -> N_{r-1} instead of as two triangles (Sec. 4.1:
+ * quads rasterized as quads, bow-tie quads as bow-ties; Sec. 7: two
+ * overlapping triangles exaggerate a bow-tie's coverage).  A sample is covered
+ * by a quad iff the ray from it towards +x crosses an odd number of the
+ * polygon's edges, edge a -> b being crossed iff a.y <= y < b.y with the sample
+ * strictly left of a -> b, or b.y <= y < a.y with it strictly right (integer
+ * edge functions on the same snapped vertices).  Arguments, union and counts as
+ * ps_rasterize_coverage. */
+int ps_rasterize_coverage_exact(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
+                                const int64_t* d_n_rib, int64_t capacity, int32_t n_path,
+                                int width, int height, int spp, uint16_t* d_canvas,
+                                uint64_t* d_covered, void* stream);
+
 /* ---- kernel timing (measurement hooks) ------------------------------------------
  * With profiling enabled the library records a CUDA event pair around each of its
  * kernel launches on the launching stream (as external event-record nodes when

@@ -25,7 +25,8 @@ EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_statu
            "ps_dash", "ps_rasterize_coverage", "ps_profile_enable", "ps_profile_read",
            "ps_profile_slot_name", "ps_raster_stats", "ps_tessellate_strokes_noalloc",
            "ps_tessellate_backward", "ps_set_tuning", "ps_get_tuning", "ps_svg_arc_to_conics",
-           "ps_uniform_tessellate", "ps_facet_stats", "ps_dash_capped"]
+           "ps_uniform_tessellate", "ps_facet_stats", "ps_dash_capped",
+           "ps_rasterize_coverage_exact"]
 PS_PROF_SLOTS = 10
 PS_TUNE_EMIT_SLABS, PS_TUNE_SETUP_LINKS, PS_TUNE_BIN_BLOCKS = 0, 1, 2
 TUNE_CANDIDATES = {PS_TUNE_EMIT_SLABS: (4, 8, 16, 32), PS_TUNE_SETUP_LINKS: (1, 2, 4),
@@ -89,6 +90,8 @@ def lib():
         L.ps_dash.argtypes = [P, P, P, P, P, I64, P, ctypes.c_int, ctypes.c_float, P, P, P, P, P,
                               I64, P]
         L.ps_rasterize_coverage.argtypes = [P, P, P, P, I64, I32, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, P, P, P]
+        L.ps_rasterize_coverage_exact.argtypes = [P, P, P, P, I64, I32, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int, P, P, P]
         L.ps_profile_enable.argtypes = [P, ctypes.c_int]
         L.ps_profile_read.argtypes = [P, P]
@@ -367,8 +370,9 @@ def ps_dash_capped(ctx: Context, rib, s, tag, n_rib, capacity, pattern, offset, 
 
 
 def ps_rasterize_coverage(ctx: Context, rib, tag, n_rib, capacity, n_path, width, height, canvas,
-                          covered, spp=16, stream=None):
-    rc = lib().ps_rasterize_coverage(ctx.handle, _ptr(rib), _ptr(tag), _ptr(n_rib), int(capacity),
+                          covered, spp=16, stream=None, exact=False):
+    fn = lib().ps_rasterize_coverage_exact if exact else lib().ps_rasterize_coverage
+    rc = fn(ctx.handle, _ptr(rib), _ptr(tag), _ptr(n_rib), int(capacity),
                                      int(n_path), int(width), int(height), int(spp), _ptr(canvas),
                                      _ptr(covered), _stream(stream))
     _check(rc, "ps_rasterize_coverage")

@@ -610,8 +610,141 @@ __device__ __forceinline__ int finish_spans(EntrySetup& E, int tw) {
   return tot;
 }
 
+// Exact quad coverage (the crossing rule: a sample is covered iff the ray from
+// it towards +x crosses an odd number of the edges of N0 -> P0 -> P1 -> N1 ->
+// N0; edge a -> b is crossed iff a.y <= y < b.y with the sample strictly left
+// of it, or b.y <= y < a.y with the sample strictly right of it).  Per edge the
+// function is stored sign-normalised, F = -E for edges going up (b.y > a.y)
+// and E otherwise, so that a crossing is F < 0 inside the edge's y-range
+// [ylo, yhi) (empty for horizontal edges).  The y-ranges go to e[4] and e[5];
+// the edges to e[0..3], in the fast form (|A| + |B| < 2^18) or else as
+// {A, B, ex, ey} for the int64 path.  Runs after the spans were taken from the
+// class edges (spans of the two diagonal-split triangles contain the polygon).
+__device__ __forceinline__ void store_exact(const QuadFix& q, EntrySetup& E) {
+  const int px[4] = {q.x[0], q.x[1], q.x[3], q.x[2]}, py[4] = {q.y[0], q.y[1], q.y[3], q.y[2]};
+  long long smax = 0;
+  long long A[4], B[4];
+  int yr[8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int ax = px[i], ay = py[i], bx = px[(i + 1) & 3], by = py[(i + 1) & 3];
+    long long a = (long long)ay - by, b = (long long)bx - ax;
+    if (by > ay) {  // going up: F = -E
+      a = -a;
+      b = -b;
+    }
+    A[i] = a;
+    B[i] = b;
+    smax = max(smax, llabs(a) + llabs(b));
+    yr[2 * i] = min(ay, by);
+    yr[2 * i + 1] = max(ay, by);
+  }
+  if (smax < (1ll << 18)) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      long long S = llabs(A[i]) + llabs(B[i]);
+      long long c = A[i] * (8ll - px[i]) + B[i] * (8ll - py[i]);
+      long long lim = 4080ll * S + 1;
+      c = c > lim ? lim : (c < -lim ? -lim : c);
+      E.e[i].A = (int)A[i];
+      E.e[i].B = (int)B[i];
+      E.e[i].ex = (int)c;
+      E.e[i].ey = (int)(16 * A[i] + 80 * B[i]);
+    }
+    E.dm = (int)(240 * smax);
+    E.valid = (E.valid & ~(64 | 8)) | 32;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      E.e[i].A = (int)A[i];
+      E.e[i].B = (int)B[i];
+      E.e[i].ex = px[i];
+      E.e[i].ey = py[i];
+    }
+    E.valid = E.valid & ~(32 | 64 | 8);
+  }
+  *reinterpret_cast<int4*>(&E.e[4]) = make_int4(yr[0], yr[1], yr[2], yr[3]);
+  *reinterpret_cast<int4*>(&E.e[5]) = make_int4(yr[4], yr[5], yr[6], yr[7]);
+}
+
+// Bits k of the samples whose sample row (5k mod 16) lies in [a, b): the
+// y-range masks of the exact mode, rowmask[17 a + b].
+__device__ __forceinline__ uint32_t row_range_mask(int a, int b) {
+  uint32_t m = 0;
+  for (int k = 0; k < 16; ++k) {
+    int sk = (5 * k) & 15;
+    if (sk >= a && sk < b) m |= 1u << k;
+  }
+  return m;
+}
+
+__device__ __forceinline__ uint32_t exact_yrange(int lo, int hi, int base,
+                                                 const uint16_t* __restrict__ rowmask) {
+  // samples of the row at y = base + 16 s: in range iff ceil((lo-base)/16) <= s < ceil((hi-base)/16)
+  int a = (lo - base + 15) >> 4, b = (hi - base + 15) >> 4;
+  a = min(max(a, 0), 16);
+  b = min(max(b, 0), 16);
+  return rowmask[17 * a + b];
+}
+
+// Fast exact mask: the four sign-normalised edge values stepped from sample to
+// sample as in fast_mask (same clamp and int32 bounds), one sign mask per edge,
+// each limited to its edge's y-range; the parity of the crossings.
+__device__ __forceinline__ uint32_t exact_mask(const EntrySetup& E, int cx, int cy,
+                                               const uint16_t* __restrict__ rowmask) {
+  const int dm = E.dm;
+  int v[4], i1[4], i2[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int4 ed = *reinterpret_cast<const int4*>(&E.e[i]);
+    int t = ed.z + ed.x * cx + ed.y * cy;
+    v[i] = min(max(t, -dm - 1), dm);
+    i1[i] = ed.w;
+    i2[i] = ed.w - ed.y * 256;
+  }
+  uint32_t sg[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sg[i] |= ((uint32_t)v[i] >> 31) << k;
+    if (k < 15) {
+      const bool up = ((5 * k) & 15) <= 10;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] += up ? i1[i] : i2[i];
+    }
+  }
+  const int4 ya = *reinterpret_cast<const int4*>(&E.e[4]);
+  const int4 yb = *reinterpret_cast<const int4*>(&E.e[5]);
+  const int base = cy + 8;
+  uint32_t c = (sg[0] & exact_yrange(ya.x, ya.y, base, rowmask)) ^
+               (sg[1] & exact_yrange(ya.z, ya.w, base, rowmask)) ^
+               (sg[2] & exact_yrange(yb.x, yb.y, base, rowmask)) ^
+               (sg[3] & exact_yrange(yb.z, yb.w, base, rowmask));
+  return c & 0xffffu;
+}
+
+// The same rule in int64 for quads with an edge of |A| + |B| >= 2^18.
+__device__ __forceinline__ uint32_t exact_mask_general(const EntrySetup& E, int lx, int ly) {
+  const int4 ya = *reinterpret_cast<const int4*>(&E.e[4]);
+  const int4 yb = *reinterpret_cast<const int4*>(&E.e[5]);
+  const int lo[4] = {ya.x, ya.z, yb.x, yb.z}, hi[4] = {ya.y, ya.w, yb.y, yb.w};
+  uint32_t m = 0;
+  for (int k = 0; k < 16; ++k) {
+    long long sx = 256ll * lx + 16 * k + 8, sy = 256ll * ly + 16 * ((5 * k) & 15) + 8;
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      long long F = (long long)E.e[i].A * (sx - E.e[i].ex) + (long long)E.e[i].B * (sy - E.e[i].ey);
+      c ^= (sy >= lo[i] && sy < hi[i] && F < 0) ? 1u : 0u;
+    }
+    m |= c << k;
+  }
+  return m;
+}
+
 // Edges and row spans of the quad between ribs ra, rb in tile (ox, oy);
 // returns the number of pixels in its spans (0: nothing to draw).
+template <bool EXACT>
 __device__ __forceinline__ int setup_edges(const float4 ra, const float4 rb, int slot, int ox,
                                            int oy, int tw, int th, EntrySetup& E) {
   E.slot = (uint16_t)slot;
@@ -629,8 +762,11 @@ __device__ __forceinline__ int setup_edges(const float4 ra, const float4 rb, int
     int mxx = max(max(q.x[0], q.x[1]), max(q.x[2], q.x[3]));
     int mny = min(min(q.y[0], q.y[1]), min(q.y[2], q.y[3]));
     int mxy = max(max(q.y[0], q.y[1]), max(q.y[2], q.y[3]));
-    if (mxx - mnx < (1 << 15) && mxy - mny < (1 << 15))
-      return setup_small(q, mny, mxy, tw, th, E);
+    if (mxx - mnx < (1 << 15) && mxy - mny < (1 << 15)) {
+      int tot = setup_small(q, mny, mxy, tw, th, E);
+      if (EXACT && tot > 0) store_exact(q, E);
+      return tot;
+    }
   }
   bool v0, v1, big = false;
   make_edges(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], E.e, v0, big);      // N0 P0 P1
@@ -705,7 +841,9 @@ __device__ __forceinline__ int setup_edges(const float4 ra, const float4 rb, int
   int ymin = min(min(q.y[0], q.y[1]), min(q.y[2], q.y[3]));
   int ymax = max(max(q.y[0], q.y[1]), max(q.y[2], q.y[3]));
   if (entry_rows(ymin, ymax, th, E) == 0) return 0;
-  return finish_spans(E, tw);
+  int tot = finish_spans(E, tw);
+  if (EXACT && tot > 0) store_exact(q, E);
+  return tot;
 }
 
 // x-extent of the region where the given edges are all >= 0, over the sample
@@ -930,6 +1068,7 @@ __device__ __forceinline__ uint32_t tri_or_quad_mask(const EntrySetup& E, int lx
   return m0 | m1;
 }
 
+template <bool EXACT>
 __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
     const float4* __restrict__ rib, const uint32_t* __restrict__ tag,
     const int32_t* __restrict__ off, const uint32_t* __restrict__ bin, int64_t pair_cap, int W,
@@ -946,9 +1085,13 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
   __shared__ int s_tile, s_nslot, s_next;
   __shared__ uint8_t s_own[CV_WARPS][32];
   __shared__ uint32_t s_canvas[MASK_WORDS];
+  __shared__ uint16_t s_rowmask[EXACT ? 17 * 17 : 1];
 
   for (int i = threadIdx.x; i < SLOTS * MASK_WORDS; i += CV_NT) s_mask[i] = 0u;
   for (int i = threadIdx.x; i < MASK_WORDS; i += CV_NT) s_canvas[i] = 0u;
+  if (EXACT)
+    for (int i = threadIdx.x; i < 17 * 17; i += CV_NT)
+      s_rowmask[i] = (uint16_t)row_range_mask(i / 17, i % 17);
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   EntrySetup* my = s_ent + wid * 32;
   // work counters (items: per warp, the same in every lane; rows: per lane),
@@ -1049,7 +1192,7 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
         unsigned long long packed = 0;
         if (valid && slot >= slot_lo && slot < slot_lo + SLOTS && slot < HKEYS) {
           EntrySetup& E = my[lane];
-          int tot = setup_edges(ra, rb, slot - slot_lo, ox, oy, tw, th, E);
+          int tot = setup_edges<EXACT>(ra, rb, slot - slot_lo, ox, oy, tw, th, E);
           if (tot > 0) {
             st_rows += E.nrow;
             // pixel items per class in 21-bit fields (at most 32 x 256 each):
@@ -1109,9 +1252,14 @@ __global__ void __launch_bounds__(CV_NT, 1) k_coverage(
               for (int st = 8; st > 0; st >>= 1)
                 if ((int)E.rowpre[k + st] <= li) k += st;
               const int ly = E.row0 + k, lx = E.x0[k] + (li - (int)E.rowpre[k]);
-              uint32_t m = cls == 0 ? fast_mask(E, lx * 256, ly * 256)
-                           : cls == 1 ? fast_mask2(E, lx * 256, ly * 256)
-                                      : tri_or_quad_mask(E, lx, ly);
+              uint32_t m;
+              if (EXACT)
+                m = cls == 0 ? exact_mask(E, lx * 256, ly * 256, s_rowmask)
+                             : exact_mask_general(E, lx, ly);
+              else
+                m = cls == 0 ? fast_mask(E, lx * 256, ly * 256)
+                    : cls == 1 ? fast_mask2(E, lx * 256, ly * 256)
+                               : tri_or_quad_mask(E, lx, ly);
               if (m) {
                 int lp = ly * TILE_PX + lx;
                 atomicOr(&s_mask[E.slot * MASK_WORDS + (lp >> 1)], m << (16 * (lp & 1)));
@@ -1178,10 +1326,10 @@ size_t coverage_smem_bytes() {
 
 }  // namespace
 
-extern "C" int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
-                                     const int64_t* d_n_rib, int64_t capacity, int32_t n_path,
-                                     int width, int height, int spp, uint16_t* d_canvas,
-                                     uint64_t* d_covered, void* stream) {
+static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
+                     const int64_t* d_n_rib, int64_t capacity, int32_t n_path, int width,
+                     int height, int spp, uint16_t* d_canvas, uint64_t* d_covered, void* stream,
+                     bool exact) {
   if (!ctx || !d_rib || !d_tag || !d_n_rib || !d_canvas || !d_covered) return PS_ERR_INVALID;
   if (spp != 16 || width <= 0 || height <= 0 || capacity < 0 || n_path < 0) return PS_ERR_INVALID;
   if ((int64_t)width * 256 >= COORD_LIMIT || (int64_t)height * 256 >= COORD_LIMIT)
@@ -1197,15 +1345,15 @@ extern "C" int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const 
   if (rc != PS_OK) return rc;
   if ((rc = ps_ensure_quad_hits(ctx, capacity)) != PS_OK) return rc;
   size_t cov_smem = coverage_smem_bytes();
-  static int attr_done = 0;
-  if (!attr_done) {
-    if ((rc = ps_cuda_check(cudaFuncSetAttribute((const void*)k_coverage,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const void* kcov = exact ? (const void*)k_coverage<true> : (const void*)k_coverage<false>;
+  static int attr_done[2] = {0, 0};
+  if (!attr_done[exact]) {
+    if ((rc = ps_cuda_check(cudaFuncSetAttribute(kcov, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)cov_smem))) != PS_OK)
       return rc;
-    attr_done = 1;
+    attr_done[exact] = 1;
   }
-  int grid_cov = ps_persistent_grid(ctx, (const void*)k_coverage, CV_NT, cov_smem);
+  int grid_cov = ps_persistent_grid(ctx, kcov, CV_NT, cov_smem);
   ctx->last_n_tile = n_tile;
   cudaMemsetAsync(ctx->d_tile_count, 0, sizeof(int32_t) * (n_tile + 1), st);
   cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
@@ -1229,11 +1377,32 @@ extern "C" int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const 
                                       ctx->d_bin, ctx->pair_cap, ctx->d_quad_hits,
                                       ctx->d_status); }
   { ProfScope ps_(ctx, PK_COVERAGE, st);
-  k_coverage<<<grid_cov, CV_NT, cov_smem, st>>>(
-      rib, d_tag, ctx->d_tile_off, ctx->d_bin, ctx->pair_cap, width, height, tiles_x, (int)n_tile,
-      d_canvas, reinterpret_cast<unsigned long long*>(d_covered), n_path, ctx->d_counters,
-      ctx->d_status, reinterpret_cast<unsigned long long*>(ctx->d_scratch64)); }
+#define PS_COV_ARGS                                                                              \
+  rib, d_tag, ctx->d_tile_off, ctx->d_bin, ctx->pair_cap, width, height, tiles_x, (int)n_tile,  \
+      d_canvas, reinterpret_cast<unsigned long long*>(d_covered), n_path, ctx->d_counters,      \
+      ctx->d_status, reinterpret_cast<unsigned long long*>(ctx->d_scratch64)
+  if (exact) k_coverage<true><<<grid_cov, CV_NT, cov_smem, st>>>(PS_COV_ARGS);
+  else k_coverage<false><<<grid_cov, CV_NT, cov_smem, st>>>(PS_COV_ARGS);
+#undef PS_COV_ARGS
+  }
   return ps_cuda_check(cudaGetLastError());
+}
+
+extern "C" int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
+                                     const int64_t* d_n_rib, int64_t capacity, int32_t n_path,
+                                     int width, int height, int spp, uint16_t* d_canvas,
+                                     uint64_t* d_covered, void* stream) {
+  return rasterize(ctx, d_rib, d_tag, d_n_rib, capacity, n_path, width, height, spp, d_canvas,
+                   d_covered, stream, false);
+}
+
+extern "C" int ps_rasterize_coverage_exact(ps_context* ctx, const float* d_rib,
+                                           const uint32_t* d_tag, const int64_t* d_n_rib,
+                                           int64_t capacity, int32_t n_path, int width, int height,
+                                           int spp, uint16_t* d_canvas, uint64_t* d_covered,
+                                           void* stream) {
+  return rasterize(ctx, d_rib, d_tag, d_n_rib, capacity, n_path, width, height, spp, d_canvas,
+                   d_covered, stream, true);
 }
 
 extern "C" int ps_raster_stats(ps_context* ctx, int64_t* h_counts, int n_counts) {

@@ -11,32 +11,51 @@ from tests._parity import gpu_tessellate
 pytestmark = pytest.mark.gpu
 
 
-def gpu_raster(g, batch, W_, H_):
+def gpu_raster(g, batch, W_, H_, exact=False):
     import torch
     import paper_2007_00308_gb300 as ps
     canvas = torch.zeros((H_, W_), dtype=torch.int16, device="cuda")
     covered = torch.zeros(batch.n_path, dtype=torch.int64, device="cuda")
     out = g["out"]
     ps.ps_rasterize_coverage(g["ctx"], out.rib, out.tag, out.n_rib, out.capacity, batch.n_path,
-                             W_, H_, canvas, covered)
+                             W_, H_, canvas, covered, exact=exact)
     torch.cuda.synchronize()
     st = g["ctx"].status()
     return canvas.cpu().numpy().view(np.uint16), covered.cpu().numpy().view(np.uint64), st
 
 
-@pytest.mark.parametrize("name", ["c1", "c2_small", "c5_small"])
-def test_coverage_bit_exact_on_gpu_vertices(name):
+def _raster_case(name):
     if name == "c1":
-        b = W.c1_plain_small()
-    elif name == "c2_small":
-        b = W.c2_batching(n_paths=120, canvas=512)
-    else:
-        b = W.c5_differentiation(n_paths=16)
+        return W.c1_plain_small()
+    if name == "c2_small":
+        return W.c2_batching(n_paths=120, canvas=512)
+    if name == "c5_small":
+        return W.c5_differentiation(n_paths=16)
+    if name == "bow_ties":
+        # wide strokes around tight bends: inner sides fold into bow-tie quads
+        pts = [[[20, 100], [220, 20], [-60, 20], [150, 100]],
+               [[150, 100], [300, 200], [100, 200], [250, 120]],
+               [[250, 120], [330, 60], [330, 60], [380, 130]]]
+        return W.single([W.CUBIC, W.CUBIC, W.QUAD], pts, width=46, join=W.JOIN_MITER,
+                        cap=W.CAP_BUTT, dtheta_deg=4.0, canvas=(420, 260))
+    if name == "long_quads":
+        # quads with edges over 1024 px (the int64 path of the exact mode)
+        pts = [[[10, 30], [10, 30], [1500, 200], [1500, 200]],
+               [[1500, 200], [1500, 200], [40, 420], [40, 420]]]
+        return W.single([W.LINE, W.LINE], pts, width=9, join=W.JOIN_BEVEL, cap=W.CAP_SQUARE,
+                        dtheta_deg=2.0, canvas=(1536, 448))
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("exact", [False, True])
+@pytest.mark.parametrize("name", ["c1", "c2_small", "c5_small", "bow_ties", "long_quads"])
+def test_coverage_bit_exact_on_gpu_vertices(name, exact):
+    b = _raster_case(name)
     Wd, Ht = b.canvas
     g = gpu_tessellate(b, 1)
-    can, cov, st = gpu_raster(g, b, Wd, Ht)
+    can, cov, st = gpu_raster(g, b, Wd, Ht, exact=exact)
     assert st == 0
-    ocan, ocov = oracle.raster(g["rib"], g["tag"], Wd, Ht, b.n_path)
+    ocan, ocov = oracle.raster(g["rib"], g["tag"], Wd, Ht, b.n_path, exact=exact)
     diff = can != ocan
     assert not diff.any(), f"{diff.sum()} pixels differ"
     assert np.array_equal(cov, ocov)
