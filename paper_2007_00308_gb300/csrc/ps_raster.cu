@@ -287,7 +287,8 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int32_t* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Coverage.  One 512-thread CTA per SM, persistent over tiles.  Per tile each
+// Coverage.  Two 256-thread CTAs per SM (one's warps issue while the other's
+// wait at a tile barrier), persistent over tiles.  Per tile each
 // warp runs its own queue: it takes the next 32 bin entries, each lane sets one
 // up (the path's mask slot from a shared hash, the edge functions relative to
 // the tile, the pixel span of every pixel row the quad can reach), a warp scan
@@ -295,10 +296,10 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int32_t* __restrict__ 
 // each pixel's 16-sample mask is ORed into the path's mask in shared memory.
 // Block-wide barriers only open and close a tile: per-path popcounts and the
 // canvas OR are taken there.  Paths beyond SLOTS per tile take further passes.
-constexpr int CV_NT = 512;
+constexpr int CV_NT = 256;
 constexpr int CV_WARPS = CV_NT / 32;
-constexpr int SLOTS = 224;           // per-path masks resident in shared memory
-constexpr int HKEYS = 2048;          // hash of path ids (max distinct paths per tile)
+constexpr int SLOTS = 96;            // per-path masks resident in shared memory
+constexpr int HKEYS = 1024;          // hash of path ids (max distinct paths per tile)
 constexpr int MASK_WORDS = TILE_PX * TILE_PX / 2;
 
 struct Edge {
@@ -1069,7 +1070,7 @@ __device__ __forceinline__ uint32_t tri_or_quad_mask(const EntrySetup& E, int lx
 }
 
 template <bool EXACT>
-__global__ void __launch_bounds__(CV_NT, 1) k_coverage(
+__global__ void __launch_bounds__(CV_NT, 2) k_coverage(
     const float4* __restrict__ rib, const uint32_t* __restrict__ tag,
     const int32_t* __restrict__ off, const uint32_t* __restrict__ bin, int64_t pair_cap, int W,
     int H, int tiles_x, int n_tile, uint16_t* __restrict__ canvas,

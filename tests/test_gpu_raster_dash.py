@@ -38,6 +38,10 @@ def _raster_case(name):
                [[250, 120], [330, 60], [330, 60], [380, 130]]]
         return W.single([W.CUBIC, W.CUBIC, W.QUAD], pts, width=46, join=W.JOIN_MITER,
                         cap=W.CAP_BUTT, dtheta_deg=4.0, canvas=(420, 260))
+    if name == "crowded":
+        # 300 paths on four tiles: more paths per tile than the coverage kernel
+        # keeps in shared memory at once (further passes over the tile)
+        return W.c2_batching(n_paths=300, canvas=32, mean_segs=3.0, max_segs=6)
     if name == "long_quads":
         # quads with edges over 1024 px (the int64 path of the exact mode)
         pts = [[[10, 30], [10, 30], [1500, 200], [1500, 200]],
@@ -48,7 +52,8 @@ def _raster_case(name):
 
 
 @pytest.mark.parametrize("exact", [False, True])
-@pytest.mark.parametrize("name", ["c1", "c2_small", "c5_small", "bow_ties", "long_quads"])
+@pytest.mark.parametrize("name", ["c1", "c2_small", "c5_small", "bow_ties", "long_quads",
+                                  "crowded"])
 def test_coverage_bit_exact_on_gpu_vertices(name, exact):
     b = _raster_case(name)
     Wd, Ht = b.canvas
