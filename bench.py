@@ -235,8 +235,8 @@ def alu_peak_tests(sm_mhz, ops):
 
 # DRAM traffic of one k_coverage launch per bin entry, from the ncu capture in
 # profiles/k_coverage_c2_1000paths.md (dram__bytes_read.sum + write.sum =
-# 124.3 MB over 8,351,880 bin entries); scaled to the launch by its bin entries.
-COVERAGE_TRAFFIC_PER_PAIR = (117.389824e6 + 6.917888e6) / 8351880
+# 124.1 MB over 8,351,880 bin entries); scaled to the launch by its bin entries.
+COVERAGE_TRAFFIC_PER_PAIR = (117.455360e6 + 6.630656e6) / 8351880
 
 
 def tune_step(ps, ctx, step, n_tile, R, key, flush, raster=True):
