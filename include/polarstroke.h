@@ -235,7 +235,7 @@ int ps_dash(ps_context* ctx, const float* d_rib, const float* d_s, const uint32_
             float offset, float* d_out_rib, float* d_out_s, uint32_t* d_out_tag,
             int32_t* d_out_src, int64_t* d_n_out, int64_t out_capacity, void* stream);
 
-/* ps_dash with capped dash ends (Sec. 5.2, reading R18 of the design notes):
+/* ps_dash with capped dash ends (Sec. 5.2; the paper leaves their form open):
  * every on-stretch also gets its path's cap style (d_path_cap[p], PS_CAP_*;
  * butt adds nothing) at its ends inside the path -- a start cap where the
  * stretch begins at 0 < a inside a segment quad [s_{r-1}, s_r), an end cap
@@ -262,7 +262,9 @@ int ps_dash_capped(ps_context* ctx, const float* d_rib, const float* d_s, const 
  *   d_canvas[y*width + x]   uint16 sample mask, OR over all paths (overwritten)
  *   d_covered[p]            uint64 samples covered by path p (union of its
  *                           quads; overwritten)
- * Quads with a vertex beyond +-2^21 px are skipped and record PS_ERR_RANGE. */
+ * Quads with a vertex beyond +-2^21 px are skipped and record PS_ERR_RANGE.  A
+ * 16x16-pixel tile met by more than 1024 distinct paths records
+ * PS_ERR_CAPACITY (its coverage is then incomplete). */
 int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
                           const int64_t* d_n_rib, int64_t capacity, int32_t n_path,
                           int width, int height, int spp, uint16_t* d_canvas,
@@ -365,7 +367,7 @@ int ps_get_tuning(ps_context* ctx, int key, int* value);
  *   PS_RSTAT_GENERAL_PIXELS ... of quads with an edge longer than 1024 px
  *   PS_RSTAT_TILE_PATHS     sum over tiles of the distinct paths met there
  *   PS_RSTAT_TILE_PASSES    sum over tiles of the passes over the tile's bin
- *                           (one per 224 distinct paths)
+ *                           (one per 96 distinct paths)
  *   PS_RSTAT_SPAN_ROWS      (bin entry, pixel row) pairs whose span was computed
  * SYNCHRONIZES. */
 enum {

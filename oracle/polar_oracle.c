@@ -17,8 +17,8 @@
  *   O3  orc_centreline_distance   brute-force distance to the generator curves
  *
  * Every step follows the paper's order and notation.  Where the paper is
- * silent or self-contradictory the reading taken is stated at the step
- * (readings R1..R16 are listed with their justification in the design notes).
+ * silent or self-contradictory the reading taken is stated at the step,
+ * numbered R1..R19.
  *
  * Compile with -ffp-contract=off so that no multiply-add is fused behind the
  * source's back: the results are then the same on x86-64 and aarch64.

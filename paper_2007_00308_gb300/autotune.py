@@ -13,7 +13,8 @@ signature.  ``reserve_bins`` sizes the (quad, tile) bin reservation from the
 entries a step actually produced.
 
 The 16x16-pixel tile of the rasterizer is fixed: its per-path sample masks
-(512 B each) are what fits 224 paths of a tile in shared memory.
+(512 B each) are what fits 96 paths of a tile into each of the two coverage
+CTAs an SM holds; a 32x32 tile would fit 24.
 """
 from __future__ import annotations
 
