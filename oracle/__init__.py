@@ -63,11 +63,11 @@ def _load():
             _lib = ctypes.CDLL(build())
             P = ctypes.c_void_p
             I64, I32, D = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
-            _lib.orc_tessellate.argtypes = [I64, P, P, P, I32, P, P, P, P, P, P, D, P, P, I64, P, P,
-                                            P, P, P, P, P, P]
+            _lib.orc_tessellate.argtypes = [I64, P, P, P, I32, P, P, P, P, P, P, D, D, P, P, I64, P,
+                                            P, P, P, P, P, P, P]
             _lib.orc_tessellate.restype = ctypes.c_int
-            _lib.orc_tessellate_f64.argtypes = [I64, P, P, P, I32, P, P, P, P, P, P, D, P, P, I64,
-                                                P, P, P, P, P, P, P, P]
+            _lib.orc_tessellate_f64.argtypes = [I64, P, P, P, I32, P, P, P, P, P, P, D, D, P, P,
+                                                I64, P, P, P, P, P, P, P, P]
             _lib.orc_tessellate_f64.restype = ctypes.c_int
             _lib.orc_segment_intervals.argtypes = [ctypes.c_int, P, ctypes.c_float, D, P, P, P, P, P, P]
             _lib.orc_segment_intervals.restype = ctypes.c_int
@@ -104,14 +104,16 @@ class OracleError(RuntimeError):
     pass
 
 
-def tessellate(batch, dtheta=None, seg_pts64=None, width64=None):
+def tessellate(batch, dtheta=None, seg_pts64=None, width64=None, tau=0.0):
     """Tessellate every path of ``batch`` (FP64).  Returns a dict of numpy arrays:
     link_nrib[L], link_info[L], rib[R,4], s[R], t[R], psi[R], rho[R], tag[R],
     path_len[P], link_rib_off[L+1], path_rib_off[P+1].
     seg_pts64 / width64 (optional) replace the batch's FP32 control points /
-    widths with FP64 values (finite differences)."""
+    widths with FP64 values (finite differences).  tau > 0 is the pixel
+    tolerance of the per-link step boost (reading R21; taken as FP32 like q)."""
     lib = _load()
     q = float(np.float32(batch.dtheta if dtheta is None else dtheta))
+    tau = float(np.float32(tau))
     st = _c(batch.seg_type, np.uint8)
     sp = _c(batch.seg_pts if seg_pts64 is None else seg_pts64, np.float64).reshape(-1)
     sw = _c(batch.seg_w, np.float64)
@@ -126,7 +128,7 @@ def tessellate(batch, dtheta=None, seg_pts64=None, width64=None):
     link_nrib = np.zeros(L, np.int64)
     link_info = np.zeros(L, np.uint8)
     total = ctypes.c_int64(0)
-    args = (S, _p(st), _p(sp), _p(sw), P, _p(off), _p(pw), _p(pj), _p(pc), _p(pm), _p(pcl), q)
+    args = (S, _p(st), _p(sp), _p(sw), P, _p(off), _p(pw), _p(pj), _p(pc), _p(pm), _p(pcl), q, tau)
     rc = lib.orc_tessellate_f64(*args, _p(link_nrib), _p(link_info), 0, None, None, None, None,
                                 None, None, None, ctypes.byref(total))
     if rc not in (0, -2):

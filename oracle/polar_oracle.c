@@ -578,6 +578,54 @@ static Seg load_seg(int64_t i, const uint8_t* type, const double* pts, const dou
   return g;
 }
 
+/* Reading R21 (Sec. 7 leaves a pixel-scale boost of q to heuristics).  With a
+ * pixel tolerance tau > 0 each link steps by its own q_link >= q, the largest
+ * step (up to the bounds below) at which every boundary edge of its quads
+ * stays within tau px of the stroke boundary it replaces; tau = 0 keeps q.
+ *
+ * Round join or cap: the outer boundary is an arc of radius r = w/2, and one
+ * step of phi leaves a gap of r (1 - cos(phi/2)) between arc and chord, so
+ *   q_link = max(q, 2 acos(1 - tau / r))    (pi when tau >= r).
+ *
+ * Segment: the boundary piece of one step is the offset of a curve piece
+ * that turns by phi <= pi/2 in one direction; its length is at most
+ * l + r phi, l the curve piece's length, and l <= L_g, the length of the
+ * control polygon (a polynomial Bezier's or a positive-weight conic's arc is
+ * no longer than its control polygon).  A convex arc turning by phi lies in
+ * the triangle of its chord c and end tangents, at most (c/2) tan(phi/2) from
+ * the chord.  Splitting tau between the two terms of c, and using
+ * tan(x) <= 4x/pi on [0, pi/4]:
+ *   q_link = max(q, min(2 atan(tau / L_g), sqrt(pi tau / (2 r)), pi/2)).
+ * The bound holds on the outer side and on an inner side whose radius of
+ * curvature stays >= r (elsewhere the inner side folds inside the stroke).  A
+ * conic with w_B <= 0 leaves its control hull and keeps q. */
+static double polygon_length(const Seg* g) {
+  switch (g->type) {
+    case ORC_LINE: return len(sub(g->D, g->A));
+    case ORC_QUAD: return len(sub(g->B, g->A)) + len(sub(g->D, g->B));
+    case ORC_CUBIC: return len(sub(g->B, g->A)) + len(sub(g->C, g->B)) + len(sub(g->D, g->C));
+    case ORC_CONIC: return g->w > 0.0 ? len(sub(g->B, g->A)) + len(sub(g->D, g->B)) : -1.0;
+  }
+  return -1.0;
+}
+
+static double seg_step(const Seg* g, double q, double tau, double r) {
+  if (!(tau > 0.0)) return q;
+  double Lg = polygon_length(g);
+  if (Lg < 0.0) return q;
+  double a = Lg > 0.0 ? 2.0 * atan(tau / Lg) : PI;
+  double b = sqrt(PI * tau / (2.0 * r));
+  double qp = a < b ? a : b;
+  if (qp > 0.5 * PI) qp = 0.5 * PI;
+  return qp > q ? qp : q;
+}
+
+static double round_step(double q, double tau, double r) {
+  if (!(tau > 0.0)) return q;
+  double qp = tau >= r ? PI : 2.0 * acos(1.0 - tau / r);
+  return qp > q ? qp : q;
+}
+
 /* Round-style counts J = ceil(|delta|/q) (Sec. 4.3.2, 4.3.4) */
 static int round_count(double delta, double q) {
   double ad = fabs(delta);
@@ -675,11 +723,11 @@ int orc_tessellate_f64(int64_t n_seg, const uint8_t* seg_type, const double* seg
                        const double* seg_w, int32_t n_path, const int32_t* path_seg_off,
                        const double* path_width, const uint8_t* path_join,
                        const uint8_t* path_cap, const double* path_miter,
-                       const uint8_t* path_closed, double q, int64_t* link_nrib,
+                       const uint8_t* path_closed, double q0, double tau, int64_t* link_nrib,
                        uint8_t* link_info, int64_t rib_cap, double* rib, double* s_out,
                        double* t_out, double* psi_out, double* rho_out, uint32_t* tag_out,
                        double* path_len, int64_t* n_rib_total) {
-  if (!(q > 0.0) || n_seg < 0 || n_path < 0) return ORC_ERR_INVALID;
+  if (!(q0 > 0.0) || !(tau >= 0.0) || n_seg < 0 || n_path < 0) return ORC_ERR_INVALID;
   int64_t R = 0;
   int overflow = 0;
   enum { MAXR = 8192 };
@@ -762,6 +810,11 @@ int orc_tessellate_f64(int64_t n_seg, const uint8_t* seg_type, const double* seg
       }
       if (L.kind == 2 && L.delta == -PI) L.delta = PI;
       L.miter_limit = path_miter ? path_miter[p] : 4.0;
+      /* the link's step (R21; q0 itself when tau = 0) */
+      double q = q0;
+      if (L.kind == 1) q = seg_step(&g, q0, tau, r);
+      else if (L.kind == 2 && L.style == ORC_JOIN_ROUND) q = round_step(q0, tau, r);
+      else if (L.kind == 3 && L.style == ORC_CAP_ROUND) q = round_step(q0, tau, r);
 
       int nrib = 0;
       uint8_t info = 0;
@@ -876,7 +929,7 @@ int orc_tessellate_f64(int64_t n_seg, const uint8_t* seg_type, const double* seg
 int orc_tessellate(int64_t n_seg, const uint8_t* seg_type, const float* seg_pts,
                    const float* seg_w, int32_t n_path, const int32_t* path_seg_off,
                    const float* path_width, const uint8_t* path_join, const uint8_t* path_cap,
-                   const float* path_miter, const uint8_t* path_closed, double q,
+                   const float* path_miter, const uint8_t* path_closed, double q, double tau,
                    int64_t* link_nrib, uint8_t* link_info, int64_t rib_cap, double* rib,
                    double* s_out, double* t_out, double* psi_out, double* rho_out,
                    uint32_t* tag_out, double* path_len, int64_t* n_rib_total) {
@@ -892,7 +945,7 @@ int orc_tessellate(int64_t n_seg, const uint8_t* seg_type, const float* seg_pts,
     mit[p] = path_miter ? path_miter[p] : 4.0;
   }
   int rc = orc_tessellate_f64(n_seg, seg_type, pts, w, n_path, path_seg_off, wid, path_join,
-                              path_cap, mit, path_closed, q, link_nrib, link_info, rib_cap, rib,
+                              path_cap, mit, path_closed, q, tau, link_nrib, link_info, rib_cap, rib,
                               s_out, t_out, psi_out, rho_out, tag_out, path_len, n_rib_total);
   free(pts); free(w); free(wid); free(mit);
   return rc;
