@@ -540,6 +540,11 @@ static void seg_intervals(const Seg* g, double q, Intervals* I) {
       if (fabs(delta) > TWO_PI - 1e-9) { delta = 0.0; I->fragile64 = 1; I->fragile32 = 1; }
       if (fabs(delta) > TWO_PI - 1e-4) I->fragile32 = 1;
     }
+    /* the split decision below (|delta| >= pi) is fragile when the turning is
+     * within rounding of pi: splitting or not changes the count unless q
+     * divides pi/2 */
+    if (fabs(fabs(delta) - PI) < 1e-5) I->fragile32 = 1;
+    if (fabs(fabs(delta) - PI) < 1e-12) I->fragile64 = 1;
     if (fabs(delta) >= PI) {
       /* Sec. 3.3.5: split at half the turning (reading R6), p by Eq. 11 */
       double psi_s = Psi[k] + 0.5 * delta;

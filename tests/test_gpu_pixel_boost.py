@@ -1,0 +1,122 @@
+"""Pixel-scale step boost on the GPU (reading R21) against the oracle with the
+same tolerance: exact counts and tags on non-fragile links, vertices and arc
+length within the usual bounds, the count-only pass agreeing with the emitted
+stream, and the adjoint at the boosted counts against FP64 central
+differences."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_00308_gb300 import workloads as W
+from tests._parity import compare_tess, gpu_tessellate
+
+pytestmark = pytest.mark.gpu
+
+PLAIN, MIXED = 0, 1
+EPS_ANG = {PLAIN: 4e-6, MIXED: 4e-6}
+FRAG = {PLAIN: oracle.FRAGILE32, MIXED: oracle.FRAGILE64}
+
+
+def _case(name):
+    if name == "c1":
+        return W.c1_plain_small()
+    if name == "c2_small":
+        return W.c2_batching(n_paths=300, seed=W.SEED_BASE + 2)
+    if name == "c5_small":
+        return W.c5_differentiation(n_paths=32)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("prec", [PLAIN, MIXED])
+@pytest.mark.parametrize("tau", [0.05, 0.25, 2.0])
+@pytest.mark.parametrize("name", ["c1", "c2_small", "c5_small"])
+def test_boosted_tessellation_matches_the_oracle(name, tau, prec):
+    b = _case(name)
+    o = oracle.tessellate(b, tau=tau)
+    g = gpu_tessellate(b, prec, tau=tau)
+    assert g["status"] == 0
+    stats, fails = compare_tess(o, g, b, FRAG[prec], EPS_ANG[prec])
+    print(name, tau, prec, stats)
+    assert not fails, fails
+    assert stats["count_mismatch_fragile"] <= max(2, 2e-3 * stats["links"])
+    o0 = oracle.tessellate(b)
+    assert len(o["s"]) < len(o0["s"])
+
+
+def test_count_only_pass_and_context_setting():
+    import torch
+    import paper_2007_00308_gb300 as ps
+    b = _case("c2_small")
+    ctx = ps.Context()
+    assert ctx.get_pixel_tolerance() == 0.0
+    ctx.set_pixel_tolerance(0.25)
+    assert ctx.get_pixel_tolerance() == 0.25
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(ps.PolarStrokeError):
+            ctx.set_pixel_tolerance(bad)
+    db = ps.DeviceBatch(b)
+    R = ps.ps_count_ribs_sync(ctx, db, ps.TessOutput(db.n_link, db.n_path, 0, arclength=False),
+                              ps.PS_PREC_MIXED)
+    out = ps.tessellate(ctx, db, ps.PS_PREC_MIXED, arclength=True)
+    torch.cuda.synchronize()
+    assert int(out.n_rib.item()) == R == len(oracle.tessellate(b, tau=0.25)["s"])
+    ctx.set_pixel_tolerance(0.0)
+    out0 = ps.tessellate(ctx, db, ps.PS_PREC_MIXED, arclength=True)
+    torch.cuda.synchronize()
+    assert int(out0.n_rib.item()) == len(oracle.tessellate(b)["s"]) > R
+
+
+def test_adjoint_at_boosted_counts():
+    import torch
+    import paper_2007_00308_gb300 as ps
+    from paper_2007_00308_gb300.autograd import PolarStroke
+    tau = 0.3
+    pts = [[[10, 10], [14, 16], [18, 9], [22, 13]],
+           [[22, 13], [24, 17], [24, 17], [27, 12]],
+           [[27, 12], [29, 10], [29, 10], [32, 14]]]
+    b = W.single([W.CUBIC, W.QUAD, W.CONIC], pts, w=[1, 1, 1.7], width=5,
+                 join=W.JOIN_ROUND, cap=W.CAP_ROUND, dtheta_deg=1.0)
+    c = ps.Context()
+    c.set_pixel_tolerance(tau)
+    pts_t = torch.tensor(b.seg_pts, dtype=torch.float32, device="cuda", requires_grad=True)
+    w_t = torch.tensor(b.path_width, dtype=torch.float32, device="cuda", requires_grad=True)
+    rib, s = PolarStroke.apply(pts_t, w_t, b, ps.PS_PREC_MIXED, c)
+    R = rib.shape[0]
+    o0 = oracle.tessellate(b, tau=tau)
+    assert R == len(o0["s"]) < len(oracle.tessellate(b)["s"])
+    rng = np.random.default_rng(3)
+    G_rib = rng.standard_normal((R, 4))
+    G_s = rng.standard_normal(R) * 0.1
+    L = (rib * torch.tensor(G_rib, dtype=torch.float32, device="cuda")).sum() + \
+        (s * torch.tensor(G_s, dtype=torch.float32, device="cuda")).sum()
+    L.backward()
+    g_gpu = pts_t.grad.cpu().numpy().astype(np.float64)
+    counts = o0["link_nrib"]
+    base = b.seg_pts.astype(np.float64)
+    h = 1e-4
+
+    def loss(p):
+        o = oracle.tessellate(b, seg_pts64=p, tau=tau)
+        if not np.array_equal(o["link_nrib"], counts):
+            return None
+        return float((o["rib"] * G_rib).sum() + (o["s"] * G_s).sum())
+
+    g_fd = np.full(base.shape, np.nan)
+    it = np.nditer(base, flags=["multi_index"])
+    for _ in it:
+        i = it.multi_index
+        p1, p2 = base.copy(), base.copy()
+        p1[i] += h
+        p2[i] -= h
+        a, c_ = loss(p1), loss(p2)
+        if a is not None and c_ is not None:
+            g_fd[i] = (a - c_) / (2 * h)
+    for i, t in enumerate(b.seg_type):
+        if t in (W.QUAD, W.CONIC):
+            g_fd[i, 1] = np.nan_to_num(g_fd[i, 1]) + np.nan_to_num(g_fd[i, 2])
+            g_fd[i, 2] = 0.0
+    ok = ~np.isnan(g_fd)
+    assert ok.mean() > 0.8
+    rel = np.linalg.norm((g_gpu - g_fd)[ok]) / np.linalg.norm(g_fd[ok])
+    print("boosted adjoint rel l2", rel)
+    assert rel < 2e-3
