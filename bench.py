@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--exact", action="store_true",
                     help="rasterize quads as polygons (bow-ties as such) instead of two triangles")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch parameters (profiling runs)")
+    ap.add_argument("--pixel-tol", type=float, default=0.0,
+                    help="pixel-scale boost of the angle step per link, tolerance in px "
+                         "(0, the default, keeps the configured dtheta everywhere)")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "facet"],
                     help="c2 (default) is the configuration the metric is quoted on; the "
                          "others print their own line for the per-configuration table")
@@ -239,9 +244,13 @@ def alu_peak_tests(sm_mhz, ops):
 COVERAGE_TRAFFIC_PER_PAIR = (117.455360e6 + 6.630656e6) / 8351880
 
 
+AUTOTUNE = True
+
+
 def tune_step(ps, ctx, step, n_tile, R, key, flush, raster=True):
     """Size the bins from the step's own count, then autotune the launch
-    parameters (cached per device and workload signature)."""
+    parameters (cached per device and workload signature; skipped, keeping the
+    defaults, under --no-autotune)."""
     import torch
     from paper_2007_00308_gb300 import autotune as AT
     pairs_reserved = None
@@ -256,6 +265,8 @@ def tune_step(ps, ctx, step, n_tile, R, key, flush, raster=True):
         st = ctx.status()
     if st != 0:
         raise RuntimeError(f"device status {st}: {ps.error_string(st)}")
+    if not AUTOTUNE:
+        return {"params": AT.current(ctx), "skipped": True, "bin_entries_reserved": pairs_reserved}
     res = AT.tuned(ctx, step, key, flush=flush.zero_ if flush is not None else None)
     torch.cuda.synchronize()
     st = ctx.status()
@@ -279,6 +290,8 @@ def run_ours(args, rank, world, local_rank):
     batch = W.c2_batching(n_paths=args.n_paths)
     Wd, Ht = batch.canvas
     ctx = ps.Context()
+    if args.pixel_tol > 0:
+        ctx.set_pixel_tolerance(args.pixel_tol)
     db = ps.DeviceBatch(batch, device=dev)
     prec = ps.PS_PREC_MIXED
     # exact rib count once at set-up; the step itself never synchronizes
@@ -414,7 +427,9 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "variant": "batched+mixed: one CUDA graph per step, "
                    "FP32 with compensated g(t) and FP64 islands" +
-                   (", quads rasterized as polygons" if args.exact else ""), "n_segments": segs,
+                   (", quads rasterized as polygons" if args.exact else "") +
+                   (f", per-link step boosted to pixel scale (tolerance {args.pixel_tol:g} px)"
+                    if args.pixel_tol > 0 else ""), "n_segments": segs,
                    "n_paths": db.n_path, "n_ribs": R_now, "canvas": [Wd, Ht], "spp": 16,
                    "l2": "flushed before every timed step (256 MiB write)",
                    "wall_s_timed_region": t_wall, "autotune": tuning},
@@ -658,7 +673,9 @@ def run_config(args, rank, world, local_rank):
 
 
 def main():
+    global AUTOTUNE
     args = parse()
+    AUTOTUNE = not args.no_autotune
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -175,7 +175,7 @@ int ps_tessellate_strokes(ps_context* ctx, const ps_segments* seg, const ps_path
  * stream capture, or under an allocator that owns the device's memory).
  * Same arguments, outputs and semantics as ps_tessellate_strokes, except:
  *   - no context: the workspace is a fixed array inside the library image
- *     (about 2.9 MB on every device that loads the library, kept until exit);
+ *     (about 2.7 MB on every device that loads the library, kept until exit);
  *     the call makes no cudaMalloc, cudaFree or other allocating call;
  *   - d_status: caller-owned device int32 that kernels set to the first
  *     PS_ERR_* they meet (the caller zeroes it and reads it back);
@@ -355,6 +355,24 @@ enum {
 };
 int ps_set_tuning(ps_context* ctx, int key, int value);
 int ps_get_tuning(ps_context* ctx, int key, int* value);
+
+/* Pixel-scale boost of the angle step (Sec. 7 suggests boosting q for
+ * segments, joins and caps near the scale of pixels; the rule is this
+ * library's).  With tau > 0 (px) every later tessellation, count and adjoint
+ * call of the context steps each link by its own q_link >= dtheta:
+ *   round join / round cap:  max(dtheta, 2 acos(1 - tau/r)), pi once tau >= r
+ *                            (r = width/2; the largest step whose arc-to-chord
+ *                            gap on the circular boundary is <= tau);
+ *   segment:                 max(dtheta, min(2 atan(tau/L_g), sqrt(pi tau/(2r)),
+ *                            pi/2)), L_g the length of its control polygon
+ *                            (keeps every step's boundary edge within tau of
+ *                            the offset curve on sides that do not fold);
+ *   conic with w_B <= 0, other join and cap styles:  dtheta.
+ * Counts only ever decrease, so ps_max_ribs stays a bound.  tau = 0 (the
+ * default) turns the boost off; the allocation-free entry point never applies
+ * it.  PS_ERR_INVALID for tau < 0 or not finite. */
+int ps_set_pixel_tolerance(ps_context* ctx, float tau);
+int ps_get_pixel_tolerance(ps_context* ctx, float* tau);
 
 /* Work counts of the context's most recent ps_rasterize_coverage call, read from
  * its device workspace into h_counts[0 .. n_counts-1] (entries past

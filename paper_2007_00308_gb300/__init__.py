@@ -26,7 +26,7 @@ EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_statu
            "ps_profile_slot_name", "ps_raster_stats", "ps_tessellate_strokes_noalloc",
            "ps_tessellate_backward", "ps_set_tuning", "ps_get_tuning", "ps_svg_arc_to_conics",
            "ps_uniform_tessellate", "ps_facet_stats", "ps_dash_capped",
-           "ps_rasterize_coverage_exact"]
+           "ps_rasterize_coverage_exact", "ps_set_pixel_tolerance", "ps_get_pixel_tolerance"]
 PS_PROF_SLOTS = 10
 PS_TUNE_EMIT_SLABS, PS_TUNE_SETUP_LINKS, PS_TUNE_BIN_BLOCKS = 0, 1, 2
 TUNE_CANDIDATES = {PS_TUNE_EMIT_SLABS: (4, 8, 16, 32), PS_TUNE_SETUP_LINKS: (1, 2, 4),
@@ -107,6 +107,8 @@ def lib():
                                             ctypes.POINTER(_TessOut), P, P]
         L.ps_facet_stats.argtypes = [P, P, P, P, I64, P, I64, F, P, P]
         L.ps_get_tuning.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.ps_set_pixel_tolerance.argtypes = [P, ctypes.c_float]
+        L.ps_get_pixel_tolerance.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
         L.ps_tessellate_backward.argtypes = [P, ctypes.POINTER(_Segments), ctypes.POINTER(_Paths),
                                              ctypes.c_float, ctypes.c_int,
                                              ctypes.POINTER(_TessOut), P, P, P, P, P]
@@ -177,6 +179,16 @@ class Context:
     def get_tuning(self, key: int) -> int:
         v = ctypes.c_int(0)
         _check(lib().ps_get_tuning(self.handle, int(key), ctypes.byref(v)), "ps_get_tuning")
+        return v.value
+
+    def set_pixel_tolerance(self, tau: float):
+        """Pixel-scale boost of the angle step for later tessellations (0: off)."""
+        _check(lib().ps_set_pixel_tolerance(self.handle, float(tau)), "ps_set_pixel_tolerance")
+
+    def get_pixel_tolerance(self) -> float:
+        v = ctypes.c_float(0.0)
+        _check(lib().ps_get_pixel_tolerance(self.handle, ctypes.byref(v)),
+               "ps_get_pixel_tolerance")
         return v.value
 
     def status(self) -> int:

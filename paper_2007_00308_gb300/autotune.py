@@ -7,7 +7,10 @@ threads, never what is computed, so any choice gives identical outputs.
 
 ``tune`` runs coordinate descent: for each tunable in turn it times every
 candidate on the caller's own step (median of ``reps`` runs after a warm-up)
-and keeps the fastest, and it repeats the sweep until nothing changes.
+and keeps the fastest, and it repeats the sweep until nothing changes.  A
+candidate is judged by the kernels its tunable changes (the context's
+per-kernel CUDA events): a whole step is dominated by the coverage kernel,
+whose run-to-run spread is larger than the differences being chosen between.
 ``tuned`` caches the choice in a JSON file keyed by device and workload
 signature.  ``reserve_bins`` sizes the (quad, tile) bin reservation from the
 entries a step actually produced.
@@ -23,7 +26,8 @@ import math
 import os
 import statistics
 
-from . import TUNE_CANDIDATES, TUNE_NAMES
+from . import (PS_TUNE_BIN_BLOCKS, PS_TUNE_EMIT_SLABS, PS_TUNE_SETUP_LINKS, TUNE_CANDIDATES,
+               TUNE_NAMES)
 
 _KEY_OF = {v: k for k, v in TUNE_NAMES.items()}
 
@@ -69,7 +73,12 @@ def current(ctx) -> dict:
     return {TUNE_NAMES[k]: ctx.get_tuning(k) for k in TUNE_CANDIDATES}
 
 
-def _cuda_timer(step, flush):
+# the kernels whose launch each tunable shapes (profiling slot names)
+KERNELS_OF = {PS_TUNE_EMIT_SLABS: ("k_emit",), PS_TUNE_SETUP_LINKS: ("k_link_setup",),
+              PS_TUNE_BIN_BLOCKS: ("k_bin_count", "k_bin_scatter")}
+
+
+def _cuda_timer(ctx, step, flush):
     import torch
 
     def run():
@@ -81,40 +90,62 @@ def _cuda_timer(step, flush):
         step()
         e1.record()
         e1.synchronize()
-        return e0.elapsed_time(e1)
+        out = dict(ctx.profile_read())
+        out["step"] = e0.elapsed_time(e1)
+        return out
     return run
+
+
+def _cost(sample, key=None) -> float:
+    """Milliseconds that decide ``key``: its kernels' time when the sample has
+    them, else the whole step."""
+    if not isinstance(sample, dict):
+        return float(sample)
+    names = KERNELS_OF.get(key, ())
+    if names and all(n in sample for n in names):
+        return float(sum(sample[n] for n in names))
+    return float(sample["step"])
 
 
 def tune(ctx, step, *, reps: int = 5, rounds: int = 3, flush=None, timer=None) -> dict:
     """Coordinate descent over the tunables.  ``step()`` runs one step on the
-    current stream; ``timer()`` (default: CUDA events around ``step``) returns
-    the milliseconds of one run.  Returns {"params", "ms", "default_ms", "trials"}."""
-    run = timer if timer is not None else _cuda_timer(step, flush)
+    current stream; ``timer()`` returns one run's milliseconds, either a number
+    or a dict of per-kernel times plus "step" (the default: CUDA events around
+    ``step`` and the context's kernel events, with profiling switched on for
+    the search and off after it).  Returns {"params", "ms", "default_ms",
+    "trials"}, "ms" and "default_ms" being whole-step times."""
+    own = timer is None
+    if own:
+        ctx.profile(True)
+    run = timer if timer is not None else _cuda_timer(ctx, step, flush)
 
-    def measure():
+    def measure(key=None):
         run()  # warm-up with the new setting
-        return statistics.median(run() for _ in range(reps))
+        return statistics.median(_cost(run(), key) for _ in range(reps))
 
-    start = current(ctx)
-    default_ms = measure()
-    best_ms = default_ms
-    trials = []
-    for _ in range(rounds):
-        changed = False
-        for key, cands in TUNE_CANDIDATES.items():
-            was = ctx.get_tuning(key)
-            res = {}
-            for v in cands:
-                ctx.set_tuning(key, v)
-                res[v] = measure()
-                trials.append({TUNE_NAMES[key]: v, "ms": res[v]})
-            v_best = min(res, key=res.get)
-            ctx.set_tuning(key, v_best)
-            best_ms = res[v_best]
-            if v_best != was:
-                changed = True
-        if not changed:
-            break
+    try:
+        start = current(ctx)
+        default_ms = measure()
+        trials = []
+        for _ in range(rounds):
+            changed = False
+            for key, cands in TUNE_CANDIDATES.items():
+                was = ctx.get_tuning(key)
+                res = {}
+                for v in cands:
+                    ctx.set_tuning(key, v)
+                    res[v] = measure(key)
+                    trials.append({TUNE_NAMES[key]: v, "ms": res[v]})
+                v_best = min(res, key=res.get)
+                ctx.set_tuning(key, v_best)
+                if v_best != was:
+                    changed = True
+            if not changed:
+                break
+        best_ms = measure()
+    finally:
+        if own:
+            ctx.profile(False)
     return {"params": current(ctx), "ms": best_ms, "default_ms": default_ms, "start": start,
             "trials": trials}
 

@@ -94,6 +94,7 @@ extern "C" int ps_create(ps_context** out) {
   ctx->tune[PS_TUNE_EMIT_SLABS] = 16;
   ctx->tune[PS_TUNE_SETUP_LINKS] = 2;
   ctx->tune[PS_TUNE_BIN_BLOCKS] = 0;
+  ctx->pixel_tol = 0.f;
   *out = ctx;
   return PS_OK;
 }
@@ -120,6 +121,18 @@ extern "C" int ps_set_tuning(ps_context* ctx, int key, int value) {
 extern "C" int ps_get_tuning(ps_context* ctx, int key, int* value) {
   if (!ctx || !value || key < 0 || key >= PS_TUNE_COUNT) return PS_ERR_INVALID;
   *value = ctx->tune[key];
+  return PS_OK;
+}
+
+extern "C" int ps_set_pixel_tolerance(ps_context* ctx, float tau) {
+  if (!ctx || !(tau >= 0.f) || !(tau < INFINITY)) return PS_ERR_INVALID;
+  ctx->pixel_tol = tau;
+  return PS_OK;
+}
+
+extern "C" int ps_get_pixel_tolerance(ps_context* ctx, float* tau) {
+  if (!ctx || !tau) return PS_ERR_INVALID;
+  *tau = ctx->pixel_tol;
   return PS_OK;
 }
 

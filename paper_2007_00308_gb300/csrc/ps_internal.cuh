@@ -92,6 +92,7 @@ struct ps_context {
   size_t adj_bytes;
   int num_sms;
   int tune[PS_TUNE_COUNT];  // launch parameters (ps_set_tuning)
+  float pixel_tol;          // pixel tolerance of the per-link step boost (0: off)
 };
 
 // ---- status -----------------------------------------------------------------
@@ -171,44 +172,53 @@ __device__ __forceinline__ long long lookback_sum(uint32_t* flag, long long* agg
 // sum of the elements since the last head before the tile (needed by the tile's
 // elements that precede its own first head).  A tile with a head publishes its
 // inclusive value at once, since that value does not depend on the carry.
-__device__ __forceinline__ double lookback_segsum(uint32_t* flag, double* agg, double* incl,
-                                                  double tile_agg, bool tile_head, int64_t t,
-                                                  int32_t* status) {
-  uint32_t hb = tile_head ? TF_HEAD : 0u;
-  if (t == 0) {
-    st_relaxed_f64(&incl[0], tile_agg);
-    st_release_u32(&flag[0], TF_INCL | hb);
-    return 0.0;
+// All 32 lanes of one warp call it: lane k reads the state of tile i - k, so
+// one round of the walk covers 32 predecessors.
+// The walk ends at the nearest tile holding an inclusive value or a head; that
+// tile and every tile nearer than it must have published before the round's
+// values are summed, else the round is read again (bounded by PS_SPIN_LIMIT).
+__device__ __forceinline__ double lookback_segsum_warp(uint32_t* flag, double* agg, double* incl,
+                                                       double tile_agg, bool tile_head, int64_t t,
+                                                       int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    if (t == 0 || tile_head) {
+      st_relaxed_f64(&incl[t], tile_agg);
+      st_release_u32(&flag[t], TF_INCL | (tile_head ? TF_HEAD : 0u));
+    } else {
+      st_relaxed_f64(&agg[t], tile_agg);
+      st_release_u32(&flag[t], TF_AGG);
+    }
   }
-  if (tile_head) {
-    st_relaxed_f64(&incl[t], tile_agg);
-    st_release_u32(&flag[t], TF_INCL | hb);
-  } else {
-    st_relaxed_f64(&agg[t], tile_agg);
-    st_release_u32(&flag[t], TF_AGG);
-  }
+  if (t == 0) return 0.0;
   double carry = 0.0;
   int64_t i = t - 1;
   int spins = 0;
-  while (i >= 0) {
-    uint32_t f = ld_acquire_u32(&flag[i]);
-    if (f & TF_INCL) {
-      carry += ld_relaxed_f64(&incl[i]);
-      break;
-    }
-    if (f & TF_AGG) {
-      carry += ld_relaxed_f64(&agg[i]);
-      if (f & TF_HEAD) break;
-      --i;
+  for (;;) {
+    int64_t j = i - lane;
+    uint32_t f = j >= 0 ? ld_acquire_u32(&flag[j]) : TF_INCL;  // before tile 0: zero
+    bool stop = (f & TF_INCL) || ((f & TF_AGG) && (f & TF_HEAD));
+    unsigned stop_m = __ballot_sync(0xffffffffu, stop);
+    unsigned unready = __ballot_sync(0xffffffffu, (f & (TF_INCL | TF_AGG)) == 0u);
+    int first = stop_m ? __ffs(stop_m) - 1 : 31;
+    unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+    if (unready & need) {
+      if (++spins > PS_SPIN_LIMIT) {
+        if (lane == 0) ps_record_error(status, PS_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(32);
       continue;
     }
-    if (++spins > PS_SPIN_LIMIT) {
-      ps_record_error(status, PS_ERR_TIMEOUT);
-      break;
-    }
-    __nanosleep(64);
+    double v = 0.0;
+    if (lane <= first && j >= 0) v = (f & TF_INCL) ? ld_relaxed_f64(&incl[j]) : ld_relaxed_f64(&agg[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    carry += v;
+    if (stop_m) break;
+    i -= 32;
   }
-  if (!tile_head) {
+  if (lane == 0 && !tile_head) {
     st_relaxed_f64(&incl[t], carry + tile_agg);
     st_release_u32(&flag[t], TF_INCL);
   }

@@ -217,6 +217,78 @@ __device__ __forceinline__ bool near_integer(float x) {
   return fminf(f, 1.f - f) < 4e-5f * fmaxf(1.f, x);
 }
 
+// A link's angle step: q in FP32 for FP32 decisions, qd for the FP64 ones.
+struct Step {
+  float q;
+  double qd;
+};
+
+// Steps for the turning ad (FP32) / ad64 (FP64): decided in FP32, re-decided in
+// FP64 under MIXED when the FP32 ratio sits within rounding of a boundary.
+template <bool MIXED>
+__device__ __forceinline__ int steps_for(float ad, double ad64, Step S) {
+  if (MIXED && near_integer(ad / S.q)) return ceil_steps_d(ad64, S.qd);
+  return ceil_steps(ad, S.q);
+}
+
+// Reading R21 (Sec. 7 suggests boosting q for links near the scale of pixels).
+// With a pixel tolerance tau > 0 a link steps by the largest angle, up to the
+// bounds below, at which each boundary edge stays within tau px of the stroke
+// boundary it replaces; tau = 0 keeps q.  MIXED evaluates the step in FP64.
+//   round join / cap (an arc of radius r): max(q, 2 acos(1 - tau/r)), pi once
+//     tau >= r -- the arc-to-chord gap of a step phi is r (1 - cos(phi/2));
+//   segment: max(q, min(2 atan(tau/L_g), sqrt(pi tau / (2r)), pi/2)), L_g the
+//     control polygon's length -- one step's offset piece is no longer than
+//     L_g + r phi and lies within (length/2) tan(phi/2) of its chord.
+// A conic with w_B <= 0 leaves its control hull and keeps q.
+template <bool MIXED>
+__device__ Step round_step(float q, float tau, float r) {
+  if (!(tau > 0.f)) return Step{q, (double)q};
+  if (MIXED) {
+    double td = tau, rd = r;
+    double qd = td >= rd ? PS_PI_D : 2.0 * acos(1.0 - td / rd);
+    qd = fmax(qd, (double)q);
+    return Step{(float)qd, qd};
+  }
+  // 2 acos(1 - x) = 4 asin(sqrt(x/2)), without the cancellation of 1 - x
+  float qf = tau >= r ? PS_PI_F : 4.f * asinf(sqrtf(0.5f * tau / r));
+  qf = fmaxf(qf, q);
+  return Step{qf, (double)qf};
+}
+
+template <typename R>
+__device__ __forceinline__ R leg(float2 a, float2 b) {
+  R dx = (R)b.x - (R)a.x, dy = (R)b.y - (R)a.y;
+  return sqrt(dx * dx + dy * dy);
+}
+
+template <bool MIXED>
+__device__ Step seg_step(const Seg& g, float q, float tau, float r) {
+  if (!(tau > 0.f) || (g.type == PS_CONIC && !(g.w > 0.f))) return Step{q, (double)q};
+  if (MIXED) {
+    double Lg;
+    switch (g.type) {
+      case PS_LINE: Lg = leg<double>(g.A, g.D); break;
+      case PS_CUBIC: Lg = leg<double>(g.A, g.B) + leg<double>(g.B, g.C) + leg<double>(g.C, g.D); break;
+      default: Lg = leg<double>(g.A, g.B) + leg<double>(g.B, g.D);
+    }
+    double a = Lg > 0.0 ? 2.0 * atan((double)tau / Lg) : PS_PI_D;
+    double b = sqrt(PS_PI_D * (double)tau / (2.0 * (double)r));
+    double qd = fmax(fmin(fmin(a, b), 0.5 * PS_PI_D), (double)q);
+    return Step{(float)qd, qd};
+  }
+  float Lg;
+  switch (g.type) {
+    case PS_LINE: Lg = leg<float>(g.A, g.D); break;
+    case PS_CUBIC: Lg = leg<float>(g.A, g.B) + leg<float>(g.B, g.C) + leg<float>(g.C, g.D); break;
+    default: Lg = leg<float>(g.A, g.B) + leg<float>(g.B, g.D);
+  }
+  float a = Lg > 0.f ? 2.f * atanf(tau / Lg) : PS_PI_F;
+  float b = sqrtf(PS_PI_F * tau / (2.f * r));
+  float qf = fmaxf(fminf(fminf(a, b), 0.5f * PS_PI_F), q);
+  return Step{qf, (double)qf};
+}
+
 // Reversals of a segment with collinear control points: along the common
 // direction v, H(t).v is the Bernstein quadratic lam1 u^2 + 2 lam2 u t + lam3 t^2
 // (linear lam1 u + lam3 t for the quadratic Bezier).  The direction reverses at
@@ -291,7 +363,8 @@ __device__ int collinear_reversals(const Seg& g, float* rts) {
 // Interval table of a segment link (Sec. 3.3.4-3.3.6, Eq. 4-6, 12-13).
 // Returns N (total steps) or -1 if the table does not fit.
 template <bool MIXED>
-__device__ int seg_intervals(const Seg& g, float q, LinkRec& L) {
+__device__ int seg_intervals(const Seg& g, Step S, LinkRec& L) {
+  const float q = S.q;
   float Psi0 = angf(end_grad0(g)), Psin = angf(end_grad1(g));
   CrossPoly<float> Pf;
   CrossPoly<double> Pd;
@@ -335,7 +408,7 @@ __device__ int seg_intervals(const Seg& g, float q, LinkRec& L) {
     for (int k = 0; k < M; ++k) {
       int D;
       if ((pivots >> k) & 1u) {
-        D = ceil_steps(PS_PI_F, q);
+        D = steps_for<MIXED>(PS_PI_F, PS_PI_D, S);
         L.step[k] = PS_PI_F / (float)D;
       } else {
         D = 1;
@@ -434,7 +507,7 @@ __device__ int seg_intervals(const Seg& g, float q, LinkRec& L) {
         // store counts computed from the FP64 turning
         double ad = fabs(dd_);
         if (ad >= PS_PI_D) {
-          int Dh = ceil_steps_d(0.5 * ad, (double)q);
+          int Dh = ceil_steps_d(0.5 * ad, S.qd);
           float psi_s = Psi[k] + 0.5f * delta;
           float ps_ = solve_t<MIXED>(g, psi_s, pa, pb);
           if (M + 2 > 6) return -1;
@@ -443,7 +516,7 @@ __device__ int seg_intervals(const Seg& g, float q, LinkRec& L) {
           L.meta |= META_SPLIT_BIT(M);
           M++;
         } else {
-          int D = ad == 0.0 ? 1 : ceil_steps_d(ad, (double)q);
+          int D = ad == 0.0 ? 1 : ceil_steps_d(ad, S.qd);
           if (M + 1 > 6) return -1;
           L.p[M] = pa; L.psi[M] = Psi[k]; L.step[M] = delta / (float)D; L.dsum[M + 1] = (uint16_t)D; M++;
         }
@@ -493,7 +566,7 @@ __device__ __forceinline__ float ominus_f(float a, float b) {
 // inner radius is zero.
 template <bool MIXED>
 __device__ int pivot_setup(float2 at, float Psi0, float delta, int kind, int style, float r,
-                           float miter, float q, LinkRec& L, float2 g_in = make_float2(0.f, 0.f),
+                           float miter, Step S, LinkRec& L, float2 g_in = make_float2(0.f, 0.f),
                            float2 g_out = make_float2(0.f, 0.f)) {
   int J = 0;
   float ad = fabsf(delta);
@@ -504,14 +577,14 @@ __device__ int pivot_setup(float2 at, float Psi0, float delta, int kind, int sty
       case PS_JOIN_TRIANGLE: J = 2; break;
       case PS_JOIN_MITER:
       case PS_JOIN_MITER_TRUNCATE: J = 3; break;
-      case PS_JOIN_ROUND: J = ceil_steps(ad, q); break;
+      case PS_JOIN_ROUND: J = ceil_steps(ad, S.q); break;
       default: J = 0;
     }
   } else {
     switch (style) {
       case PS_CAP_TRIANGLE: J = 2; break;
       case PS_CAP_SQUARE: J = 4; break;
-      case PS_CAP_ROUND: J = ceil_steps(PS_PI_F, q); break;
+      case PS_CAP_ROUND: J = steps_for<MIXED>(PS_PI_F, PS_PI_D, S); break;
       default: J = 0;
     }
   }
@@ -574,7 +647,7 @@ __device__ int pivot_setup(float2 at, float Psi0, float delta, int kind, int sty
 template <bool MIXED>
 __device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, int32_t s0, int n,
                           int k, float r, int join, int cap, float miter, bool closed, float q,
-                          LinkRec& L) {
+                          float tau, LinkRec& L) {
   L.meta = 0;
   L.w = 1.f;
   L.rN = L.rP = r;
@@ -591,7 +664,7 @@ __device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, i
     L.P[0] = g.A; L.P[1] = g.B; L.P[2] = g.C; L.P[3] = g.D;
     L.w = g.w;
     L.meta = LK_SEG | ((uint32_t)g.type << 2);
-    int N = seg_intervals<MIXED>(g, q, L);
+    int N = seg_intervals<MIXED>(g, seg_step<MIXED>(g, q, tau, r), L);
     if (N < 0) return -1;
     nrib = N > 0 ? N + 1 : 0;
   } else if (k == 0 || k == 2 * n) {
@@ -615,7 +688,8 @@ __device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, i
       Seg c = load_seg(st, sp, sw, s0 + i);
       L.meta = LK_CAP;
       float Psi0 = (k == 0) ? angf(end_grad0(c)) + PS_PI_F : angf(end_grad1(c));
-      int J = pivot_setup<MIXED>(k == 0 ? c.A : c.D, Psi0, PS_PI_F, LK_CAP, cap, r, miter, q, L);
+      Step S = cap == PS_CAP_ROUND ? round_step<MIXED>(q, tau, r) : Step{q, (double)q};
+      int J = pivot_setup<MIXED>(k == 0 ? c.A : c.D, Psi0, PS_PI_F, LK_CAP, cap, r, miter, S, L);
       nrib = J > 0 ? J + 1 : 0;
     } else if (k == 2 * n) {
       if (first < 0 || last < 0) return 0;
@@ -624,7 +698,8 @@ __device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, i
       float Psi0 = angf(end_grad1(a));
       float delta = ominus_f(angf(end_grad0(b)), Psi0);
       if (delta == -PS_PI_F) delta = PS_PI_F;
-      int J = pivot_setup<MIXED>(b.A, Psi0, delta, LK_JOIN, join, r, miter, q, L, end_grad1(a),
+      Step S = join == PS_JOIN_ROUND ? round_step<MIXED>(q, tau, r) : Step{q, (double)q};
+      int J = pivot_setup<MIXED>(b.A, Psi0, delta, LK_JOIN, join, r, miter, S, L, end_grad1(a),
                                  end_grad0(b));
       nrib = J > 0 ? J + 1 : 0;
     }
@@ -643,20 +718,21 @@ __device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, i
     float Psi0 = angf(end_grad1(a));
     float delta = ominus_f(angf(end_grad0(b)), Psi0);
     if (delta == -PS_PI_F) delta = PS_PI_F;
-    if (MIXED && join == PS_JOIN_ROUND && delta != 0.f && near_integer(fabsf(delta) / q)) {
+    Step S = join == PS_JOIN_ROUND ? round_step<MIXED>(q, tau, r) : Step{q, (double)q};
+    if (MIXED && join == PS_JOIN_ROUND && delta != 0.f && near_integer(fabsf(delta) / S.q)) {
       float2 e1 = end_grad1(a), e0 = end_grad0(b);
       double d = atan2((double)e0.y, (double)e0.x) - atan2((double)e1.y, (double)e1.x);
       if (d > PS_PI_D) d -= PS_TWO_PI_D;
       if (d < -PS_PI_D) d += PS_TWO_PI_D;
-      int J = ceil_steps_d(fabs(d), (double)q);
-      int J0 = pivot_setup<MIXED>(b.A, Psi0, delta, LK_JOIN, join, r, miter, q, L, e1, e0);
+      int J = ceil_steps_d(fabs(d), S.qd);
+      int J0 = pivot_setup<MIXED>(b.A, Psi0, delta, LK_JOIN, join, r, miter, S, L, e1, e0);
       if (J0 > 0 && J > 0 && J != J0) {
         L.step[0] = delta / (float)J;
         L.dsum[1] = (uint16_t)J;
       }
       nrib = J0 > 0 ? (J > 0 ? J : J0) + 1 : 0;
     } else {
-      int J = pivot_setup<MIXED>(b.A, Psi0, delta, LK_JOIN, join, r, miter, q, L, end_grad1(a),
+      int J = pivot_setup<MIXED>(b.A, Psi0, delta, LK_JOIN, join, r, miter, S, L, end_grad1(a),
                                  end_grad0(b));
       nrib = J > 0 ? J + 1 : 0;
     }
@@ -716,7 +792,7 @@ __global__ void __launch_bounds__(SETUP_NT) k_link_setup(
     const int32_t* __restrict__ seg_off, const float* __restrict__ width,
     const uint8_t* __restrict__ join, const uint8_t* __restrict__ cap,
     const float* __restrict__ miter, const uint8_t* __restrict__ closed, int n_path,
-    int64_t n_link, float q, LinkRec* __restrict__ recs, int32_t* __restrict__ link_off,
+    int64_t n_link, float q, float tau, LinkRec* __restrict__ recs, int32_t* __restrict__ link_off,
     int32_t* __restrict__ path_off, int64_t* __restrict__ n_rib_out, int64_t capacity,
     uint32_t* tflag, long long* tagg, long long* tincl, int32_t* counters, int32_t* status,
     int64_t n_tiles) {
@@ -742,7 +818,7 @@ __global__ void __launch_bounds__(SETUP_NT) k_link_setup(
       int k = (int)(l - (2 * (int64_t)s0 + p));
       LinkRec L = {};
       int nr = link_setup<MIXED>(st, sp, sw, s0, s1 - s0, k, 0.5f * __ldg(width + p), join[p],
-                                 cap[p], __ldg(miter + p), closed[p] != 0, q, L);
+                                 cap[p], __ldg(miter + p), closed[p] != 0, q, tau, L);
       if (nr < 0) {
         ps_record_error(status, PS_ERR_INVALID);
         nr = 0;
@@ -967,58 +1043,73 @@ __global__ void k_link_path(const int32_t* __restrict__ seg_off, int n_path, int
 // K3: segmented inclusive scan of per-rib chords into cumulative arc length
 // (Eq. 18), restarting at every path's first rib; FP64 accumulation.
 constexpr int SCAN_NT = 256;
-constexpr int SCAN_IPT = 8;
+constexpr int SCAN_IPT = 16;
 constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
 
+// Segmented (by path) inclusive scan of per-rib chords into s (Eq. 18), in
+// place allowed (chord_in == s_out).  Persistent CTAs claim tiles of 4,096 ribs
+// in order; thread k of a tile owns ribs 16k..16k+15 and, with VEC (all three
+// arrays 16-byte aligned), moves them with 128-bit loads and stores.  Within a
+// tile sums are FP32 (relative error ~1e-6 of s); the carry between tiles,
+// which runs over a whole path, is FP64 and comes from a warp-wide look-back.
+template <bool VEC>
 __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
-    const float* __restrict__ chord_in, const uint32_t* __restrict__ tag,
-    const int64_t* __restrict__ n_rib, int64_t capacity, float* __restrict__ s_out,
-    float* __restrict__ path_len, uint32_t* tflag, double* tagg, double* tincl,
-    int32_t* counters, int32_t* status) {
-  // Within a tile (2048 ribs) sums are FP32 (relative error ~1e-6 of s); the
-  // carry between tiles, which runs over a whole path, is FP64.
+    const float* chord_in, const uint32_t* __restrict__ tag, const int64_t* __restrict__ n_rib,
+    int64_t capacity, float* s_out, float* __restrict__ path_len, uint32_t* tflag, double* tagg,
+    double* tincl, int32_t* counters, int32_t* status) {
   __shared__ float sv[SCAN_NT / 32];
   __shared__ int sh[SCAN_NT / 32];
   __shared__ double s_carry;
-  __shared__ int s_tile;
+  __shared__ int64_t s_tile;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int64_t R = *n_rib;
   if (R > capacity) R = capacity;
-  int64_t n_tiles = (R + SCAN_TILE - 1) / SCAN_TILE;
+  const int64_t n_tiles = (R + SCAN_TILE - 1) / SCAN_TILE;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&counters[1], 1);
     __syncthreads();
-    int64_t tile = s_tile;
+    const int64_t tile = s_tile;
     __syncthreads();
     if (tile >= n_tiles) return;
-    int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_IPT;
+    const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_IPT;
+    const bool full = base + SCAN_IPT <= R;
     float c[SCAN_IPT];
     uint32_t pth[SCAN_IPT];
-    bool head[SCAN_IPT];
+    if (VEC && full) {
+      const float4* cp = reinterpret_cast<const float4*>(chord_in + base);
+      const uint4* tp = reinterpret_cast<const uint4*>(tag + base);
+#pragma unroll
+      for (int q = 0; q < SCAN_IPT / 4; ++q) {
+        float4 a = cp[q];
+        uint4 b = __ldg(tp + q);
+        c[4 * q] = a.x; c[4 * q + 1] = a.y; c[4 * q + 2] = a.z; c[4 * q + 3] = a.w;
+        pth[4 * q] = b.x >> 2; pth[4 * q + 1] = b.y >> 2;
+        pth[4 * q + 2] = b.z >> 2; pth[4 * q + 3] = b.w >> 2;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < SCAN_IPT; ++i) {
+        int64_t r = base + i;
+        c[i] = r < R ? chord_in[r] : 0.f;
+        pth[i] = r < R ? (__ldg(tag + r) >> 2) : 0xffffffffu;
+      }
+    }
+    // path of the rib before this thread's first: the previous lane's last
+    uint32_t prevp = __shfl_up_sync(0xffffffffu, pth[SCAN_IPT - 1], 1);
+    if (lane == 0) prevp = (base > 0 && base <= R) ? (__ldg(tag + base - 1) >> 2) : 0xffffffffu;
+    uint32_t hm = 0;  // bit i: rib base + i starts a path
     float acc = 0.f;
-    bool th = false;
-    uint32_t prevp = base > 0 && base <= R ? (tag[base - 1] >> 2) : 0xffffffffu;
 #pragma unroll
     for (int i = 0; i < SCAN_IPT; ++i) {
-      int64_t r = base + i;
-      if (r < R) {
-        c[i] = chord_in[r];
-        pth[i] = tag[r] >> 2;
-        head[i] = (r == 0) || (prevp != pth[i]);
-        prevp = pth[i];
-      } else {
-        c[i] = 0.f;
-        pth[i] = 0xffffffffu;
-        head[i] = false;
-      }
-      if (head[i]) {
+      uint32_t pp = i ? pth[i - 1] : prevp;
+      if (base + i < R && (base + i == 0 || pp != pth[i])) {
+        hm |= 1u << i;
         acc = 0.f;
-        th = true;
       }
       acc += c[i];
     }
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float v = acc;
-    int h = th;
+    int h = hm != 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       float vy = __shfl_up_sync(0xffffffffu, v, o);
@@ -1039,15 +1130,15 @@ __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
       wcarry += sv[w];
       if (sh[w]) { whead = 1; break; }
     }
-    if (threadIdx.x == 0) {
+    if (wid == 0) {
       double tile_v = 0.0;
       int tile_h = 0;
       for (int w = SCAN_NT / 32 - 1; w >= 0; --w) {
         tile_v += (double)sv[w];
         if (sh[w]) { tile_h = 1; break; }
       }
-      for (int w = 0; w < SCAN_NT / 32; ++w) tile_h |= sh[w];
-      s_carry = lookback_segsum(tflag, tagg, tincl, tile_v, tile_h != 0, tile, status);
+      double carry = lookback_segsum_warp(tflag, tagg, tincl, tile_v, tile_h != 0, tile, status);
+      if (lane == 0) s_carry = carry;
     }
     __syncthreads();
     float vprev = __shfl_up_sync(0xffffffffu, v, 1);
@@ -1056,27 +1147,53 @@ __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
       vprev = 0.f;
       hprev = 0;
     }
+    // path of the rib after this thread's last: the next lane's first
+    uint32_t nextp = __shfl_down_sync(0xffffffffu, pth[0], 1);
+    if (lane == 31) nextp = base + SCAN_IPT < R ? (__ldg(tag + base + SCAN_IPT) >> 2) : 0xffffffffu;
     // ribs before this thread's first head continue the running total
-    float carry_f = hprev ? vprev : vprev + wcarry;
-    float tile_carry = (hprev || whead) ? 0.f : (float)s_carry;
-    float run = carry_f;
+    const float tile_carry = (hprev || whead) ? 0.f : (float)s_carry;
+    float run = hprev ? vprev : vprev + wcarry;
     bool after_head = false;
 #pragma unroll
     for (int i = 0; i < SCAN_IPT; ++i) {
-      int64_t r = base + i;
-      if (r >= R) break;
-      if (head[i]) {
+      if ((hm >> i) & 1u) {
         run = 0.f;
         after_head = true;
       }
       run += c[i];
-      float sv_out = after_head ? run : tile_carry + run;
-      s_out[r] = sv_out;
-      bool last = (r == R - 1) || ((tag[r + 1] >> 2) != pth[i]);
-      if (last && path_len) path_len[pth[i]] = sv_out;
+      c[i] = after_head ? run : tile_carry + run;
+      uint32_t np = i + 1 < SCAN_IPT ? pth[i + 1] : nextp;
+      if (path_len && base + i < R && np != pth[i]) path_len[pth[i]] = c[i];
+    }
+    if (VEC && full) {
+      float4* op = reinterpret_cast<float4*>(s_out + base);
+#pragma unroll
+      for (int q = 0; q < SCAN_IPT / 4; ++q)
+        op[q] = make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < SCAN_IPT; ++i)
+        if (base + i < R) s_out[base + i] = c[i];
     }
     __syncthreads();
   }
+}
+
+// Launch of k_arclen_scan with the vector form when every array allows it.
+static void launch_arclen_scan(ps_context* ctx, int grid_override, cudaStream_t st,
+                               const float* chord, const uint32_t* tag, const int64_t* n_rib,
+                               int64_t capacity, float* s_out, float* path_len, uint32_t* flag,
+                               double* agg, double* incl, int32_t* counters, int32_t* status) {
+  const bool vec = ((reinterpret_cast<uintptr_t>(chord) | reinterpret_cast<uintptr_t>(tag) |
+                     reinterpret_cast<uintptr_t>(s_out)) & 15u) == 0;
+  const void* fn = vec ? (const void*)k_arclen_scan<true> : (const void*)k_arclen_scan<false>;
+  int g = grid_override > 0 ? grid_override : ps_persistent_grid(ctx, fn, SCAN_NT, 0);
+  if (vec)
+    k_arclen_scan<true><<<g, SCAN_NT, 0, st>>>(chord, tag, n_rib, capacity, s_out, path_len, flag,
+                                               agg, incl, counters, status);
+  else
+    k_arclen_scan<false><<<g, SCAN_NT, 0, st>>>(chord, tag, n_rib, capacity, s_out, path_len,
+                                                flag, agg, incl, counters, status);
 }
 
 // Chords from rib midpoints (standalone arc length of any rib stream).
@@ -1129,7 +1246,7 @@ static int launch_tessellate(ps_context* ctx, const ps_segments* seg, const ps_p
   ProfScope ps_(ctx, PK_LINK_SETUP, st);
 #define PS_SETUP_ARGS                                                                          \
   seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,         \
-      paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->d_recs,               \
+      paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->pixel_tol, ctx->d_recs, \
       out->d_link_rib_off, out->d_path_rib_off, out->d_n_rib, count_cap, ctx->d_tile_flag,    \
       ctx->d_tile_agg, ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles
   const unsigned g = (unsigned)n_tiles;
@@ -1172,14 +1289,11 @@ static int launch_tessellate(ps_context* ctx, const ps_segments* seg, const ps_p
     int64_t scan_tiles = (out->capacity + SCAN_TILE - 1) / SCAN_TILE;
     cudaMemsetAsync(ctx->d_tile_flag + n_tiles + 1, 0, sizeof(uint32_t) * (scan_tiles + 1), st);
     if (out->d_path_len) cudaMemsetAsync(out->d_path_len, 0, sizeof(float) * P, st);
-    int g2 = ps_persistent_grid(ctx, (const void*)k_arclen_scan, SCAN_NT, 0);
     ProfScope ps_(ctx, PK_ARCLEN, st);
-    k_arclen_scan<<<g2, SCAN_NT, 0, st>>>(out->d_s, out->d_tag, out->d_n_rib, out->capacity,
-                                          out->d_s, out->d_path_len,
-                                          ctx->d_tile_flag + n_tiles + 1,
-                                          ctx->d_tile_aggd + n_tiles + 1,
-                                          ctx->d_tile_incld + n_tiles + 1, ctx->d_counters,
-                                          ctx->d_status);
+    launch_arclen_scan(ctx, 0, st, out->d_s, out->d_tag, out->d_n_rib, out->capacity, out->d_s,
+                       out->d_path_len, ctx->d_tile_flag + n_tiles + 1,
+                       ctx->d_tile_aggd + n_tiles + 1, ctx->d_tile_incld + n_tiles + 1,
+                       ctx->d_counters, ctx->d_status);
     if ((rc = ps_cuda_check(cudaGetLastError())) != PS_OK) return rc;
   }
   return PS_OK;
@@ -1237,11 +1351,9 @@ extern "C" int ps_arclength_scan(ps_context* ctx, const float* d_rib, const uint
   { ProfScope ps_(ctx, PK_MIDCHORD, st);
   k_midpoint_chords<<<g, 256, 0, st>>>(reinterpret_cast<const float4*>(d_rib), d_tag, d_n_rib,
                                        capacity, d_s); }
-  int g2 = ps_persistent_grid(ctx, (const void*)k_arclen_scan, SCAN_NT, 0);
   ProfScope ps_(ctx, PK_ARCLEN, st);
-  k_arclen_scan<<<g2, SCAN_NT, 0, st>>>(d_s, d_tag, d_n_rib, capacity, d_s, d_path_len,
-                                        ctx->d_tile_flag, ctx->d_tile_aggd, ctx->d_tile_incld,
-                                        ctx->d_counters, ctx->d_status);
+  launch_arclen_scan(ctx, 0, st, d_s, d_tag, d_n_rib, capacity, d_s, d_path_len, ctx->d_tile_flag,
+                     ctx->d_tile_aggd, ctx->d_tile_incld, ctx->d_counters, ctx->d_status);
   return ps_cuda_check(cudaGetLastError());
 }
 
@@ -1275,7 +1387,7 @@ constexpr size_t NA_CNT = al256(NA_INCLD + sizeof(double) * NOALLOC_TILES);
 constexpr size_t NA_BYTES = al256(NA_CNT + sizeof(int32_t) * 16);
 }  // namespace
 
-// The workspace: about 2.9 MB held by every device that loads the library until
+// The workspace: about 2.7 MB held by every device that loads the library until
 // the process exits.  Host code must not take this name as a device address; it
 // asks the runtime for the address on each device (below).
 static __device__ __align__(256) unsigned char ps_noalloc_scratch[NA_BYTES];
@@ -1342,13 +1454,13 @@ extern "C" int ps_tessellate_strokes_noalloc(const ps_segments* seg, const ps_pa
   if (precision == PS_PREC_MIXED)
     k_link_setup<true, SETUP_IPT><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
-        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, recs, out->d_link_rib_off,
+        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, 0.f, recs, out->d_link_rib_off,
         out->d_path_rib_off, out->d_n_rib, count_cap, tflag, tagg, tincl, counters, d_status,
         n_tiles);
   else
     k_link_setup<false, SETUP_IPT><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
-        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, recs, out->d_link_rib_off,
+        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, 0.f, recs, out->d_link_rib_off,
         out->d_path_rib_off, out->d_n_rib, count_cap, tflag, tagg, tincl, counters, d_status,
         n_tiles);
   if (cudaGetLastError() != cudaSuccess) return PS_ERR_CUDA;
@@ -1371,12 +1483,13 @@ extern "C" int ps_tessellate_strokes_noalloc(const ps_segments* seg, const ps_pa
     if (out->d_path_len && cudaMemsetAsync(out->d_path_len, 0, sizeof(float) * P, st) != cudaSuccess)
       return PS_ERR_CUDA;
     int per_sm2 = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, (const void*)k_arclen_scan, SCAN_NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, (const void*)k_arclen_scan<true>,
+                                                  SCAN_NT, 0);
     int g2 = g_noalloc_sms[dev] * (per_sm2 > 0 ? per_sm2 : 1);
     int64_t o = NOALLOC_SETUP_TILES + 1;
-    k_arclen_scan<<<g2, SCAN_NT, 0, st>>>(out->d_s, out->d_tag, out->d_n_rib, out->capacity,
-                                          out->d_s, out->d_path_len, tflag + o, taggd + o,
-                                          tincld + o, counters, d_status);
+    launch_arclen_scan(nullptr, g2, st, out->d_s, out->d_tag, out->d_n_rib, out->capacity,
+                       out->d_s, out->d_path_len, tflag + o, taggd + o, tincld + o, counters,
+                       d_status);
     if (cudaGetLastError() != cudaSuccess) return PS_ERR_CUDA;
   }
   return PS_OK;
@@ -1400,13 +1513,15 @@ int ps_run_link_setup(ps_context* ctx, const ps_segments* seg, const ps_paths* p
   if (precision == PS_PREC_MIXED)
     k_link_setup<true, SETUP_IPT><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
-        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->d_recs, d_link_off,
+        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->pixel_tol, ctx->d_recs,
+        d_link_off,
         d_path_off, d_n_rib, INT64_MAX, ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
         ctx->d_counters, ctx->d_status, n_tiles);
   else
     k_link_setup<false, SETUP_IPT><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
-        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->d_recs, d_link_off,
+        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->pixel_tol, ctx->d_recs,
+        d_link_off,
         d_path_off, d_n_rib, INT64_MAX, ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
         ctx->d_counters, ctx->d_status, n_tiles);
   return ps_cuda_check(cudaGetLastError());
@@ -1421,9 +1536,8 @@ int ps_run_segmented_prefix(ps_context* ctx, float* d_vals, const uint32_t* d_ta
   cudaMemsetAsync(ctx->d_tile_flag, 0, sizeof(uint32_t) * (scan_tiles + 1), st);
   cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
   if (d_path_tot && n_path > 0) cudaMemsetAsync(d_path_tot, 0, sizeof(float) * n_path, st);
-  int g2 = ps_persistent_grid(ctx, (const void*)k_arclen_scan, SCAN_NT, 0);
-  k_arclen_scan<<<g2, SCAN_NT, 0, st>>>(d_vals, d_tag, d_n_rib, capacity, d_vals, d_path_tot,
-                                        ctx->d_tile_flag, ctx->d_tile_aggd, ctx->d_tile_incld,
-                                        ctx->d_counters, ctx->d_status);
+  launch_arclen_scan(ctx, 0, st, d_vals, d_tag, d_n_rib, capacity, d_vals, d_path_tot,
+                     ctx->d_tile_flag, ctx->d_tile_aggd, ctx->d_tile_incld, ctx->d_counters,
+                     ctx->d_status);
   return ps_cuda_check(cudaGetLastError());
 }

@@ -7,10 +7,12 @@ import oracle
 F32_EPS = 2.0 ** -24
 
 
-def gpu_tessellate(batch, precision, want_t=True):
+def gpu_tessellate(batch, precision, want_t=True, tau=0.0):
     import torch
     import paper_2007_00308_gb300 as ps
     ctx = ps.Context()
+    if tau:
+        ctx.set_pixel_tolerance(tau)
     db = ps.DeviceBatch(batch)
     out = ps.tessellate(ctx, db, precision, arclength=True, want_t=want_t)
     torch.cuda.synchronize()

@@ -117,3 +117,22 @@ def test_every_tuning_gives_identical_outputs():
         ctx.set_tuning(ps.PS_TUNE_EMIT_SLABS, 5)
     with pytest.raises(ps.PolarStrokeError):
         ctx.set_tuning(99, 1)
+
+
+def test_each_tunable_is_judged_by_its_own_kernels():
+    """With per-kernel samples, a tunable is chosen by its kernels' time even
+    when the whole step's time (here: noise that favours other values) says
+    otherwise."""
+    ctx = FakeCtx()
+    rng = np.random.default_rng(0)
+
+    def timer():
+        e, s, b = (ctx.t[ps.PS_TUNE_EMIT_SLABS], ctx.t[ps.PS_TUNE_SETUP_LINKS],
+                   ctx.t[ps.PS_TUNE_BIN_BLOCKS])
+        k = {"k_emit": 1.0 + 0.1 * abs(np.log2(e) - 5), "k_link_setup": 0.4 + 0.1 * abs(s - 2),
+             "k_bin_count": 1.0 + 0.05 * abs(b - 2), "k_bin_scatter": 1.0 + 0.05 * abs(b - 2)}
+        k["step"] = 20.0 + sum(k.values()) + float(rng.uniform(-1.0, 1.0))
+        return k
+
+    res = AT.tune(ctx, step=lambda: None, timer=timer, reps=3)
+    assert res["params"] == {"emit_slabs": 32, "setup_links": 2, "bin_blocks": 2}
