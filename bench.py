@@ -247,6 +247,17 @@ COVERAGE_TRAFFIC_PER_PAIR = (117.455360e6 + 6.630656e6) / 8351880
 AUTOTUNE = True
 
 
+TESS_KERNELS = ("k_link_path", "k_link_setup", "k_emit", "k_arclen_scan")
+
+
+def tessellation_only(kmean: dict, n_seg: int, world: int) -> dict:
+    """The tessellation stages of the timed step alone (what the plain variant
+    times), from the per-kernel CUDA events."""
+    ms = sum(kmean.get(k, 0.0) for k in TESS_KERNELS)
+    return {"ms": ms, "segments_per_s": world * n_seg / (ms * 1e-3) if ms > 0 else None,
+            "kernels": list(TESS_KERNELS)}
+
+
 def tune_step(ps, ctx, step, n_tile, R, key, flush, raster=True):
     """Size the bins from the step's own count, then autotune the launch
     parameters (cached per device and workload signature; skipped, keeping the
@@ -436,6 +447,7 @@ def run_ours(args, rank, world, local_rank):
         "covered_samples_per_s": world * cov_samples / (ms_per_step * 1e-3),
         "covered_samples": cov_samples,
         "kernel_ms": kmean,
+        "tessellation_only": tessellation_only(kmean, segs, world),
         "kernels": kernels,
         "raster_work": rstat,
         "roofline": roof,
@@ -641,6 +653,8 @@ def run_config(args, rank, world, local_rank):
                    "n_ribs": int(out.n_rib.item()),
                    "l2": "flushed before every timed step (256 MiB write)", "autotune": tuning},
         "kernel_ms": {k: statistics.mean(v) for k, v in kern.items()},
+        "tessellation_only": tessellation_only({k: statistics.mean(v) for k, v in kern.items()},
+                                               int(batch.n_seg), world),
         "clocks": clk,
     }
     if raster:

@@ -384,8 +384,8 @@ int ps_get_pixel_tolerance(ps_context* ctx, float* tau);
  *   PS_RSTAT_TWO_TRI_PIXELS ... of non-convex quads (two triangles)
  *   PS_RSTAT_GENERAL_PIXELS ... of quads with an edge longer than 1024 px
  *   PS_RSTAT_TILE_PATHS     sum over tiles of the distinct paths met there
- *   PS_RSTAT_TILE_PASSES    sum over tiles of the passes over the tile's bin
- *                           (one per 96 distinct paths)
+ *   PS_RSTAT_TILE_PASSES    sum over tiles with bin entries of the passes over
+ *                           the tile's bin (one per 96 distinct paths)
  *   PS_RSTAT_SPAN_ROWS      (bin entry, pixel row) pairs whose span was computed
  * SYNCHRONIZES. */
 enum {

@@ -46,6 +46,7 @@ int ps_ensure_raster(ps_context* ctx, int64_t n_tile, int64_t n_pair) {
     if ((rc = grow((void**)&ctx->d_tile_count, sizeof(int32_t) * (cap + 1))) != PS_OK) return rc;
     if ((rc = grow((void**)&ctx->d_tile_off, sizeof(int32_t) * (cap + 1))) != PS_OK) return rc;
     if ((rc = grow((void**)&ctx->d_tile_cursor, sizeof(int32_t) * (cap + 1))) != PS_OK) return rc;
+    if ((rc = grow((void**)&ctx->d_tile_list, sizeof(int32_t) * (cap + 1))) != PS_OK) return rc;
     ctx->raster_tile_cap = cap;
   }
   if (n_pair > ctx->pair_cap) {
@@ -142,7 +143,8 @@ extern "C" void ps_destroy(ps_context* ctx) {
   void* ptrs[] = {ctx->d_status, ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
                   ctx->d_tile_aggd, ctx->d_tile_incld, ctx->d_counters, ctx->d_recs,
                   ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor, ctx->d_bin,
-                  ctx->d_scratch64, ctx->d_mask_scratch, ctx->d_adj, ctx->d_quad_hits};
+                  ctx->d_scratch64, ctx->d_mask_scratch, ctx->d_adj, ctx->d_quad_hits,
+                  ctx->d_tile_list};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free(ctx);

@@ -24,6 +24,8 @@ struct DashPattern {
   double cum[65];
   double period;
   double offset;
+  float cum_f[65];             // the same in FP32, for the prefilter
+  float period_f, offset_f;
   int m2;
   int j_round;                 // ribs - 1 of a round cap at this dtheta
   const uint8_t* path_cap;     // cap style per path, or null: butt dash ends
@@ -64,6 +66,39 @@ __device__ __forceinline__ void emit_cap(float4 v, int J, bool square, bool star
 }
 
 constexpr int DASH_NT = 256;
+constexpr int DASH_QPT = 4;  // quads per thread
+constexpr int DASH_TILE = DASH_NT * DASH_QPT;
+
+// End vertex of a whole quad as dash_quad computes it (f1 = 1): a0 + (a1 - a0)
+// in FP64, which is a1 itself whenever a1 - a0 is exact in FP64 (exponents at
+// most 28 apart, or a zero); otherwise the FP64 sum is taken as is.
+__device__ __forceinline__ float whole_end(float a0, float a1) {
+  const int e0 = (int)((__float_as_uint(a0) >> 23) & 0xffu);
+  const int e1 = (int)((__float_as_uint(a1) >> 23) & 0xffu);
+  if (a0 == 0.f || a1 == 0.f || abs(e0 - e1) <= 28) return a1;
+  return (float)__dadd_rn((double)a0, __dsub_rn((double)a1, (double)a0));
+}
+
+// FP32 prefilter: whether the quad [sa, sb] lies inside one interval of the
+// pattern (an on-stretch or a gap) with a margin eps above the FP32 rounding of
+// its phase.  That rounding (u = sa + offset, k period, their difference, and
+// the FP32 period and pattern) is at most about 4 * 2^-24 of |sa| + |offset| +
+// period; eps is 2e-6 of it, eight times more.  1: inside an on-stretch (the
+// quad is emitted whole), 0: inside a gap (nothing), -1: within eps of a
+// boundary (decided in FP64 by dash_quad).
+__device__ __forceinline__ int dash_quick(const DashPattern& P, float sa, float sb) {
+  const float per = P.period_f, off = P.offset_f;
+  const float eps = 2e-6f * (fabsf(sa) + fabsf(off) + per) + 1e-6f;
+  const float u = sa + off;
+  const float k = floorf(u / per);
+  const float ph = u - k * per;  // phase of sa in [0, period)
+  if (!(ph >= 0.f && ph < per)) return -1;
+  const float pe = ph + (sb - sa);  // phase of sb, beyond the period if it wraps
+  int j = 0;  // interval [cum_f[j], cum_f[j+1]) holding ph
+  while (j + 1 < P.m2 && P.cum_f[j + 1] <= ph) ++j;
+  if (ph - P.cum_f[j] > eps && P.cum_f[j + 1] - pe > eps) return (j & 1) ? 0 : 1;
+  return -1;
+}
 
 template <bool EMIT>
 __device__ __forceinline__ int dash_quad(const DashPattern& P, double sa, double sb, int64_t r,
@@ -146,8 +181,12 @@ __device__ __forceinline__ int dash_quad(const DashPattern& P, double sa, double
   return n;
 }
 
-// One pass: per-rib piece counts, block scan, decoupled look-back for the
-// tile's output offset, emission.
+// One pass over tiles of 1,024 quads (4 per thread): the FP32 prefilter
+// settles most quads; the rest (near a stretch boundary) are queued in shared
+// memory and run through the FP64 dash_quad densely -- the FP64 pipe is slow,
+// and quads left in place would keep almost every warp on it.  Then a block
+// scan of the piece counts, a warp-wide decoupled look-back for the tile's
+// output offset, and emission (queued quads again densely).
 __global__ void __launch_bounds__(DASH_NT) k_dash(
     const float4* __restrict__ rib, const float* __restrict__ s, const uint32_t* __restrict__ tag,
     const int64_t* __restrict__ n_rib, int64_t capacity, DashPattern P,
@@ -155,35 +194,81 @@ __global__ void __launch_bounds__(DASH_NT) k_dash(
     int32_t* __restrict__ out_src, int64_t* __restrict__ n_out, int64_t out_cap, uint32_t* tflag,
     long long* tagg, long long* tincl, int32_t* counters, int32_t* status) {
   __shared__ long long sm[DASH_NT / 32];
+  __shared__ int smq[DASH_NT / 32];
   __shared__ long long s_prefix;
-  __shared__ int s_tile;
+  __shared__ int64_t s_tile;
+  __shared__ uint16_t s_queue[DASH_TILE];    // tile-local quads for the FP64 path
+  __shared__ int s_cnt[DASH_TILE];           // their piece counts
+  __shared__ long long s_out[DASH_TILE];     // their output offsets
   int64_t R = *n_rib;
   if (R > capacity) R = capacity;
-  int64_t n_tiles = (R + DASH_NT - 1) / DASH_NT;
+  int64_t n_tiles = (R + DASH_TILE - 1) / DASH_TILE;
   if (n_tiles == 0) n_tiles = 1;
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&counters[3], 1);
     __syncthreads();
-    int64_t tile = s_tile;
+    const int64_t tile = s_tile;
     __syncthreads();
     if (tile >= n_tiles) return;
-    int64_t r = tile * DASH_NT + threadIdx.x;
-    int cnt = 0;
-    double sa = 0, sb = 0;
-    uint32_t tg = 0;
-    bool active = r >= 1 && r < R;
-    if (active) {
-      tg = tag[r];
-      if (tg & PS_TAG_LINK_START) active = false;
+    const int64_t t0 = tile * DASH_TILE;
+    const int q0 = (int)threadIdx.x * DASH_QPT;  // tile-local index of this thread's first quad
+    int mode[DASH_QPT];
+    float sa[DASH_QPT], sb[DASH_QPT];
+    uint32_t tg[DASH_QPT];
+    int nq = 0;
+#pragma unroll
+    for (int q = 0; q < DASH_QPT; ++q) {
+      const int64_t r = t0 + q0 + q;
+      mode[q] = 0;
+      tg[q] = 0u;
+      sa[q] = sb[q] = 0.f;
+      if (r >= 1 && r < R) {
+        tg[q] = __ldg(tag + r);
+        if (!(tg[q] & PS_TAG_LINK_START)) {
+          sa[q] = __ldg(s + r - 1);
+          sb[q] = __ldg(s + r);
+          mode[q] = dash_quick(P, sa[q], sb[q]);
+          nq += mode[q] < 0;
+        }
+      }
     }
-    if (active) {
-      sa = (double)s[r - 1];
-      sb = (double)s[r];
-      cnt = dash_quad<false>(P, sa, sb, r, rib, 0.f, 0.f, tg, 0, nullptr, nullptr, nullptr,
-                             nullptr, 0, status);
+    // queue positions of this thread's FP64 quads (block exclusive scan)
+    int xq = nq;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, xq, o);
+      if (lane >= o) xq += y;
     }
-    long long x = cnt;
+    if (lane == 31) smq[wid] = xq;
+    __syncthreads();
+    int qpre = 0, qtot = 0;
+    for (int w = 0; w < DASH_NT / 32; ++w) {
+      if (w < wid) qpre += smq[w];
+      qtot += smq[w];
+    }
+    int qp = qpre + xq - nq;
+#pragma unroll
+    for (int q = 0; q < DASH_QPT; ++q)
+      if (mode[q] < 0) s_queue[qp++] = (uint16_t)(q0 + q);
+    __syncthreads();
+    for (int i = threadIdx.x; i < qtot; i += DASH_NT) {
+      const int lq = s_queue[i];
+      const int64_t r = t0 + lq;
+      s_cnt[lq] = dash_quad<false>(P, (double)__ldg(s + r - 1), (double)__ldg(s + r), r, rib, 0.f,
+                                   0.f, __ldg(tag + r), 0, nullptr, nullptr, nullptr, nullptr, 0,
+                                   status);
+    }
+    __syncthreads();
+    int cnt[DASH_QPT];
+    int mine = 0;
+#pragma unroll
+    for (int q = 0; q < DASH_QPT; ++q) {
+      cnt[q] = mode[q] == 1 ? 2 : mode[q] < 0 ? s_cnt[q0 + q] : 0;
+      mine += cnt[q];
+    }
+    long long x = mine;
+#pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       long long y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
@@ -195,13 +280,48 @@ __global__ void __launch_bounds__(DASH_NT) k_dash(
       if (w < wid) wpre += sm[w];
       total += sm[w];
     }
-    long long excl = x - cnt + wpre;
-    if (threadIdx.x == 0) s_prefix = lookback_sum(tflag, tagg, tincl, total, tile, status);
+    if (wid == 0) {
+      long long pre = lookback_sum_warp(tflag, tagg, tincl, total, tile, status);
+      if (lane == 0) s_prefix = pre;
+    }
     __syncthreads();
-    int64_t out0 = s_prefix + excl;
-    if (active && cnt)
-      dash_quad<true>(P, sa, sb, r, rib, 0.f, 0.f, tg & ~PS_TAG_LINK_START, out0, out_rib, out_s,
-                      out_tag, out_src, out_cap, status);
+    int64_t o = s_prefix + wpre + x - mine;
+#pragma unroll
+    for (int q = 0; q < DASH_QPT; ++q) {
+      const int64_t r = t0 + q0 + q;
+      if (mode[q] < 0) {
+        s_out[q0 + q] = o;  // emitted from the queue below
+      } else if (mode[q] == 1) {
+        // inside an on-stretch: the quad itself (f0 = 0, f1 = 1 in dash_quad)
+        const uint32_t tq = tg[q] & ~PS_TAG_LINK_START;
+        if (o + 2 <= out_cap) {
+          const float4 v0 = __ldg(rib + r - 1), v1 = __ldg(rib + r);
+          out_rib[o] = v0;
+          out_rib[o + 1] = make_float4(whole_end(v0.x, v1.x), whole_end(v0.y, v1.y),
+                                       whole_end(v0.z, v1.z), whole_end(v0.w, v1.w));
+          out_s[o] = sa[q];
+          out_s[o + 1] = sb[q];
+          out_tag[o] = tq | PS_TAG_LINK_START;
+          out_tag[o + 1] = tq;
+          if (out_src) {
+            out_src[o] = (int32_t)r;
+            out_src[o + 1] = (int32_t)r;
+          }
+        } else {
+          ps_record_error(status, PS_ERR_CAPACITY);
+        }
+      }
+      o += cnt[q];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < qtot; i += DASH_NT) {
+      const int lq = s_queue[i];
+      if (s_cnt[lq] == 0) continue;
+      const int64_t r = t0 + lq;
+      dash_quad<true>(P, (double)__ldg(s + r - 1), (double)__ldg(s + r), r, rib, 0.f, 0.f,
+                      __ldg(tag + r) & ~PS_TAG_LINK_START, s_out[lq], out_rib, out_s, out_tag,
+                      out_src, out_cap, status);
+    }
     if (tile == n_tiles - 1 && threadIdx.x == DASH_NT - 1) {
       long long tot = s_prefix + total;
       *n_out = tot;
@@ -236,6 +356,9 @@ extern "C" int ps_dash_capped(ps_context* ctx, const float* d_rib, const float* 
   }
   P.period = P.cum[P.m2];
   P.offset = (double)offset;
+  for (int i = 0; i <= P.m2; ++i) P.cum_f[i] = (float)P.cum[i];
+  P.period_f = (float)P.period;
+  P.offset_f = offset;
   P.path_cap = d_path_cap;
   P.n_path = d_path_cap ? n_path : 0;
   P.j_round = 0;
@@ -249,7 +372,7 @@ extern "C" int ps_dash_capped(ps_context* ctx, const float* d_rib, const float* 
   if (!(P.period > 0.0)) return PS_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = stream;
-  int64_t n_tiles = (capacity + DASH_NT - 1) / DASH_NT + 1;
+  int64_t n_tiles = (capacity + DASH_TILE - 1) / DASH_TILE + 1;
   int rc = ps_ensure_tiles(ctx, n_tiles + 1);
   if (rc != PS_OK) return rc;
   cudaMemsetAsync(ctx->d_tile_flag, 0, sizeof(uint32_t) * (n_tiles + 1), st);

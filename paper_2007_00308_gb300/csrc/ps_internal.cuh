@@ -79,6 +79,7 @@ struct ps_context {
   int32_t* d_tile_count;    // [n_tile + 1]
   int32_t* d_tile_off;      // [n_tile + 1]
   int32_t* d_tile_cursor;   // [n_tile]
+  int32_t* d_tile_list;     // tiles with bin entries, then their count
   int64_t raster_tile_cap;
   uint32_t* d_bin;          // [pair_cap]
   uint32_t* d_quad_hits;    // [quad_hits_cap] per-rib tile-hit masks of the binning passes
@@ -97,7 +98,9 @@ struct ps_context {
 
 // ---- status -----------------------------------------------------------------
 __device__ __forceinline__ void ps_record_error(int32_t* status, int code) {
-  if (status) atomicCAS(status, 0, code);
+  // read first: a launch where many threads fail would otherwise serialize on
+  // one atomic per failure
+  if (status && *(volatile int32_t*)status == 0) atomicCAS(status, 0, code);
 }
 
 // ---- release / acquire ------------------------------------------------------
@@ -133,38 +136,56 @@ __device__ __forceinline__ double ld_relaxed_f64(const double* p) {
 #define TF_INCL 2u
 #define TF_HEAD 4u
 
-// Exclusive prefix of tile `t` for an int64 sum.  Called by one thread.
-__device__ __forceinline__ long long lookback_sum(uint32_t* flag, long long* agg, long long* incl,
-                                                  long long tile_agg, int64_t t, int32_t* status) {
-  if (t == 0) {
-    st_relaxed_s64(&incl[0], tile_agg);
-    st_release_u32(&flag[0], TF_INCL);
-    return 0;
+// Exclusive prefix of tile t for an int64 sum, with the walk spread over one
+// warp (all 32 lanes call it): lane k reads the state of tile i - k, so one
+// round covers 32 predecessors.  The walk ends at the nearest tile with an
+// inclusive prefix; that tile and every nearer one must have published before
+// the round is summed, else the round is read again (bounded by
+// PS_SPIN_LIMIT).
+__device__ __forceinline__ long long lookback_sum_warp(uint32_t* flag, long long* agg,
+                                                       long long* incl, long long tile_agg,
+                                                       int64_t t, int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    if (t == 0) {
+      st_relaxed_s64(&incl[0], tile_agg);
+      st_release_u32(&flag[0], TF_INCL);
+    } else {
+      st_relaxed_s64(&agg[t], tile_agg);
+      st_release_u32(&flag[t], TF_AGG);
+    }
   }
-  st_relaxed_s64(&agg[t], tile_agg);
-  st_release_u32(&flag[t], TF_AGG);
+  if (t == 0) return 0;
   long long prefix = 0;
   int64_t i = t - 1;
   int spins = 0;
-  while (i >= 0) {
-    uint32_t f = ld_acquire_u32(&flag[i]);
-    if (f & TF_INCL) {
-      prefix += ld_relaxed_s64(&incl[i]);
-      break;
-    }
-    if (f & TF_AGG) {
-      prefix += ld_relaxed_s64(&agg[i]);
-      --i;
+  for (;;) {
+    int64_t j = i - lane;
+    uint32_t f = j >= 0 ? ld_acquire_u32(&flag[j]) : TF_INCL;  // before tile 0: zero
+    unsigned stop_m = __ballot_sync(0xffffffffu, (f & TF_INCL) != 0u);
+    unsigned unready = __ballot_sync(0xffffffffu, (f & (TF_INCL | TF_AGG)) == 0u);
+    int first = stop_m ? __ffs(stop_m) - 1 : 31;
+    unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+    if (unready & need) {
+      if (++spins > PS_SPIN_LIMIT) {
+        if (lane == 0) ps_record_error(status, PS_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(32);
       continue;
     }
-    if (++spins > PS_SPIN_LIMIT) {
-      ps_record_error(status, PS_ERR_TIMEOUT);
-      break;
-    }
-    __nanosleep(64);
+    long long v = 0;
+    if (lane <= first && j >= 0) v = (f & TF_INCL) ? ld_relaxed_s64(&incl[j]) : ld_relaxed_s64(&agg[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    prefix += v;
+    if (stop_m) break;
+    i -= 32;
   }
-  st_relaxed_s64(&incl[t], prefix + tile_agg);
-  st_release_u32(&flag[t], TF_INCL);
+  if (lane == 0) {
+    st_relaxed_s64(&incl[t], prefix + tile_agg);
+    st_release_u32(&flag[t], TF_INCL);
+  }
   return prefix;
 }
 

@@ -241,48 +241,76 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
   }
 }
 
-// Exclusive scan of tile counts (one CTA of 1024 threads), resets cursors.
-__global__ void __launch_bounds__(1024) k_tile_scan(const int32_t* __restrict__ count,
-                                                    int32_t* __restrict__ off,
-                                                    int32_t* __restrict__ cursor, int n_tile,
-                                                    int64_t pair_cap, int32_t* status) {
-  __shared__ long long warp_sums[32];
-  __shared__ long long carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int base = 0; base < n_tile; base += 1024) {
-    int i = base + threadIdx.x;
-    long long v = i < n_tile ? count[i] : 0;
-    long long x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      long long y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+// Exclusive scan of tile counts, the cursors reset, and the list of tiles with
+// entries in order: list[0 .. m) and m = list[n_tile].  CTA b takes tiles
+// [4096 b, 4096 (b+1)), 16 per thread; the sum and the count of non-empty tiles
+// are scanned together as one int64 (the count in bits 38 and up) with a
+// warp-wide decoupled look-back across CTAs.
+constexpr int TS_NT = 256, TS_IPT = 16, TS_TILE = TS_NT * TS_IPT;
+constexpr int TS_SHIFT = 38;
+__global__ void __launch_bounds__(TS_NT) k_tile_scan(const int32_t* __restrict__ count,
+                                                     int32_t* __restrict__ off,
+                                                     int32_t* __restrict__ cursor,
+                                                     int32_t* __restrict__ list, int n_tile,
+                                                     int64_t pair_cap, uint32_t* tflag,
+                                                     long long* tagg, long long* tincl,
+                                                     int32_t* status) {
+  __shared__ long long sm[TS_NT / 32];
+  __shared__ long long s_pre;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long i0 = (long long)blockIdx.x * TS_TILE + (long long)threadIdx.x * TS_IPT;
+  int c[TS_IPT];
+  if (i0 + TS_IPT <= n_tile) {
+    const int4* cp = reinterpret_cast<const int4*>(count + i0);
+#pragma unroll
+    for (int q = 0; q < TS_IPT / 4; ++q) {
+      int4 v = cp[q];
+      c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
     }
-    if (lane == 31) warp_sums[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      long long w = warp_sums[lane];
-      for (int o = 1; o < 32; o <<= 1) {
-        long long y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
-      }
-      warp_sums[lane] = w;
-    }
-    __syncthreads();
-    long long excl = carry + x - v + (wid > 0 ? warp_sums[wid - 1] : 0);
-    if (i < n_tile) {
-      if (excl > 0x7fffffffLL) ps_record_error(status, PS_ERR_CAPACITY);
-      off[i] = (int32_t)excl;
-      cursor[i] = 0;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) carry += warp_sums[31];
-    __syncthreads();
+  } else {
+#pragma unroll
+    for (int i = 0; i < TS_IPT; ++i) c[i] = i0 + i < n_tile ? count[i0 + i] : 0;
   }
-  if (threadIdx.x == 0) {
-    off[n_tile] = (int32_t)(carry > 0x7fffffffLL ? 0x7fffffff : carry);
-    if (carry > pair_cap) ps_record_error(status, PS_ERR_CAPACITY);
+  long long v = 0;
+#pragma unroll
+  for (int i = 0; i < TS_IPT; ++i) v += (long long)c[i] + ((long long)(c[i] > 0) << TS_SHIFT);
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sm[wid] = x;
+  __syncthreads();
+  long long total = 0, wpre = 0;
+  for (int w = 0; w < TS_NT / 32; ++w) {
+    if (w < wid) wpre += sm[w];
+    total += sm[w];
+  }
+  if (wid == 0) {
+    long long pre = lookback_sum_warp(tflag, tagg, tincl, total, blockIdx.x, status);
+    if (lane == 0) s_pre = pre;
+  }
+  __syncthreads();
+  const long long mask = (1LL << TS_SHIFT) - 1;
+  long long run = s_pre + wpre + x - v;
+#pragma unroll
+  for (int i = 0; i < TS_IPT; ++i) {
+    const long long idx = i0 + i;
+    if (idx < n_tile) {
+      const long long sum = run & mask;
+      if (sum > 0x7fffffffLL) ps_record_error(status, PS_ERR_CAPACITY);
+      off[idx] = (int32_t)(sum > 0x7fffffffLL ? 0x7fffffff : sum);
+      cursor[idx] = 0;
+      if (c[i] > 0) list[run >> TS_SHIFT] = (int32_t)idx;
+      run += (long long)c[i] + ((long long)(c[i] > 0) << TS_SHIFT);
+      if (idx == n_tile - 1) {
+        const long long tot = run & mask;
+        off[n_tile] = (int32_t)(tot > 0x7fffffffLL ? 0x7fffffff : tot);
+        list[n_tile] = (int32_t)(run >> TS_SHIFT);
+        if (tot > pair_cap) ps_record_error(status, PS_ERR_CAPACITY);
+      }
+    }
   }
 }
 
@@ -1073,7 +1101,8 @@ template <bool EXACT>
 __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
     const float4* __restrict__ rib, const uint32_t* __restrict__ tag,
     const int32_t* __restrict__ off, const uint32_t* __restrict__ bin, int64_t pair_cap, int W,
-    int H, int tiles_x, int n_tile, uint16_t* __restrict__ canvas,
+    int H, int tiles_x, int n_tile, const int32_t* __restrict__ tile_list,
+    uint16_t* __restrict__ canvas,
     unsigned long long* __restrict__ covered, int n_path, int32_t* counters, int32_t* status,
     unsigned long long* __restrict__ stats) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1114,26 +1143,38 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
     st_rows = 0;
     st_batches = 0;
   };
+  // tiles are claimed by ticket; the next ticket's atomic is issued when a
+  // tile's last pass reaches its flush, and read when the tile ends, so its
+  // latency hides behind the flush (claiming earlier would hold a tile back
+  // from an idle CTA)
+  const int n_list = tile_list[n_tile];  // tiles with entries (the canvas is cleared)
+  if (threadIdx.x == 0) s_tile = atomicAdd(&counters[2], 1);
+  bool dirty = true;  // the path hash holds the previous tile's keys
   for (;;) {
-    if (threadIdx.x == 0) {
-      s_tile = atomicAdd(&counters[2], 1);
-      s_nslot = 0;
-    }
-    for (int i = threadIdx.x; i < HKEYS; i += CV_NT) {
-      s_keys[i] = 0u;
-      s_slot_of[i] = 0xffffu;
-    }
+    if (dirty)
+      for (int i = threadIdx.x; i < HKEYS; i += CV_NT) {
+        s_keys[i] = 0u;
+        s_slot_of[i] = 0xffffu;
+      }
+    if (threadIdx.x == 0) s_nslot = 0;
     __syncthreads();
-    int t = s_tile;
+    const int ticket = s_tile;
+    int t_next = 0;
     flush_stats();
-    if (t >= n_tile) return;
+    if (ticket >= n_list) return;
+    const int t = tile_list[ticket];
     int tx = t % tiles_x, ty = t / tiles_x;
     int ox = tx * TILE_UNITS, oy = ty * TILE_UNITS;
     int64_t b0 = off[t], b1 = off[t + 1];
     if (b1 > pair_cap) b1 = pair_cap;
     int n = (int)(b1 > b0 ? b1 - b0 : 0);
     int tw = min(TILE_PX, W - tx * TILE_PX), th = min(TILE_PX, H - ty * TILE_PX);
-    for (int pass = 0;; ++pass) {
+    dirty = n > 0;
+    if (n == 0) {  // listed but its entries are beyond the bin capacity
+      if (threadIdx.x == 0) t_next = atomicAdd(&counters[2], 1);
+      __syncthreads();  // every thread has read s_tile before it is rewritten
+    }
+    for (int pass = 0; n > 0; ++pass) {
       int slot_lo = pass * SLOTS;
       if (threadIdx.x == 0) s_next = 0;
       __syncthreads();
@@ -1275,6 +1316,7 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
       // warp per slot
       int nslot = min(s_nslot, HKEYS);
       int nhere = min(SLOTS, nslot - slot_lo);
+      if (threadIdx.x == 0 && slot_lo + SLOTS >= nslot) t_next = atomicAdd(&counters[2], 1);
       for (int s2 = wid; s2 < nhere; s2 += CV_WARPS) {
         uint32_t* ms = s_mask + s2 * MASK_WORDS;
         unsigned c = 0;
@@ -1317,6 +1359,9 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
       }
       if (slot_lo + SLOTS >= nslot) break;
     }
+    // a non-empty tile's barriers already follow every read of s_tile and
+    // s_nslot
+    if (threadIdx.x == 0) s_tile = t_next;
   }
 }
 
@@ -1345,6 +1390,7 @@ static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
   int rc = ps_ensure_raster(ctx, n_tile, want_pairs);
   if (rc != PS_OK) return rc;
   if ((rc = ps_ensure_quad_hits(ctx, capacity)) != PS_OK) return rc;
+  if ((rc = ps_ensure_tiles(ctx, (n_tile + TS_TILE - 1) / TS_TILE + 1)) != PS_OK) return rc;
   size_t cov_smem = coverage_smem_bytes();
   const void* kcov = exact ? (const void*)k_coverage<true> : (const void*)k_coverage<false>;
   static int attr_done[2] = {0, 0};
@@ -1357,8 +1403,11 @@ static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
   int grid_cov = ps_persistent_grid(ctx, kcov, CV_NT, cov_smem);
   ctx->last_n_tile = n_tile;
   cudaMemsetAsync(ctx->d_tile_count, 0, sizeof(int32_t) * (n_tile + 1), st);
+  cudaMemsetAsync(ctx->d_tile_flag, 0, sizeof(uint32_t) * ((n_tile + TS_TILE - 1) / TS_TILE + 1), st);
   cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
   cudaMemsetAsync(d_covered, 0, sizeof(uint64_t) * (size_t)n_path, st);
+  // tiles without entries are never visited by the coverage kernel
+  cudaMemsetAsync(d_canvas, 0, sizeof(uint16_t) * (size_t)width * (size_t)height, st);
   cudaMemsetAsync(ctx->d_scratch64, 0, 7 * sizeof(int64_t), st);
   int grid_bin = ctx->tune[PS_TUNE_BIN_BLOCKS] > 0
                      ? ctx->num_sms * ctx->tune[PS_TUNE_BIN_BLOCKS]
@@ -1370,8 +1419,11 @@ static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
                                       ctx->d_bin, ctx->pair_cap, ctx->d_quad_hits,
                                       ctx->d_status); }
   { ProfScope ps_(ctx, PK_TILE_SCAN, st);
-  k_tile_scan<<<1, 1024, 0, st>>>(ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor,
-                                  (int)n_tile, ctx->pair_cap, ctx->d_status); }
+  const int ts_grid = (int)((n_tile + TS_TILE - 1) / TS_TILE);
+  k_tile_scan<<<ts_grid, TS_NT, 0, st>>>(ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor,
+                                         ctx->d_tile_list, (int)n_tile, ctx->pair_cap,
+                                         ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
+                                         ctx->d_status); }
   { ProfScope ps_(ctx, PK_BIN_SCATTER, st);
   k_bin<1><<<grid_bin, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, tiles_x,
                                       ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor,
@@ -1380,7 +1432,7 @@ static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
   { ProfScope ps_(ctx, PK_COVERAGE, st);
 #define PS_COV_ARGS                                                                              \
   rib, d_tag, ctx->d_tile_off, ctx->d_bin, ctx->pair_cap, width, height, tiles_x, (int)n_tile,  \
-      d_canvas, reinterpret_cast<unsigned long long*>(d_covered), n_path, ctx->d_counters,      \
+      ctx->d_tile_list, d_canvas, reinterpret_cast<unsigned long long*>(d_covered), n_path, ctx->d_counters,      \
       ctx->d_status, reinterpret_cast<unsigned long long*>(ctx->d_scratch64)
   if (exact) k_coverage<true><<<grid_cov, CV_NT, cov_smem, st>>>(PS_COV_ARGS);
   else k_coverage<false><<<grid_cov, CV_NT, cov_smem, st>>>(PS_COV_ARGS);

@@ -217,43 +217,32 @@ __device__ __forceinline__ bool near_integer(float x) {
   return fminf(f, 1.f - f) < 4e-5f * fmaxf(1.f, x);
 }
 
-// A link's angle step: q in FP32 for FP32 decisions, qd for the FP64 ones.
+// A link's angle step in FP32 (for the FP32 count decisions), with what the
+// mixed kernel needs to recompute it in FP64 where a count decision is re-taken
+// in FP64 (step_d).
 struct Step {
   float q;
-  double qd;
+  float q0, tau, r;  // the nominal step and the boost's inputs
+  int kind;          // 0: q0 itself, 1: round join or cap, 2: segment
 };
 
-// Steps for the turning ad (FP32) / ad64 (FP64): decided in FP32, re-decided in
-// FP64 under MIXED when the FP32 ratio sits within rounding of a boundary.
-template <bool MIXED>
-__device__ __forceinline__ int steps_for(float ad, double ad64, Step S) {
-  if (MIXED && near_integer(ad / S.q)) return ceil_steps_d(ad64, S.qd);
-  return ceil_steps(ad, S.q);
-}
+__device__ __forceinline__ Step plain_step(float q) { return Step{q, q, 0.f, 0.f, 0}; }
 
 // Reading R21 (Sec. 7 suggests boosting q for links near the scale of pixels).
 // With a pixel tolerance tau > 0 a link steps by the largest angle, up to the
 // bounds below, at which each boundary edge stays within tau px of the stroke
-// boundary it replaces; tau = 0 keeps q.  MIXED evaluates the step in FP64.
+// boundary it replaces; tau = 0 keeps q.
 //   round join / cap (an arc of radius r): max(q, 2 acos(1 - tau/r)), pi once
 //     tau >= r -- the arc-to-chord gap of a step phi is r (1 - cos(phi/2));
 //   segment: max(q, min(2 atan(tau/L_g), sqrt(pi tau / (2r)), pi/2)), L_g the
 //     control polygon's length -- one step's offset piece is no longer than
 //     L_g + r phi and lies within (length/2) tan(phi/2) of its chord.
 // A conic with w_B <= 0 leaves its control hull and keeps q.
-template <bool MIXED>
 __device__ Step round_step(float q, float tau, float r) {
-  if (!(tau > 0.f)) return Step{q, (double)q};
-  if (MIXED) {
-    double td = tau, rd = r;
-    double qd = td >= rd ? PS_PI_D : 2.0 * acos(1.0 - td / rd);
-    qd = fmax(qd, (double)q);
-    return Step{(float)qd, qd};
-  }
+  if (!(tau > 0.f)) return plain_step(q);
   // 2 acos(1 - x) = 4 asin(sqrt(x/2)), without the cancellation of 1 - x
   float qf = tau >= r ? PS_PI_F : 4.f * asinf(sqrtf(0.5f * tau / r));
-  qf = fmaxf(qf, q);
-  return Step{qf, (double)qf};
+  return Step{fmaxf(qf, q), q, tau, r, 1};
 }
 
 template <typename R>
@@ -262,31 +251,54 @@ __device__ __forceinline__ R leg(float2 a, float2 b) {
   return sqrt(dx * dx + dy * dy);
 }
 
-template <bool MIXED>
-__device__ Step seg_step(const Seg& g, float q, float tau, float r) {
-  if (!(tau > 0.f) || (g.type == PS_CONIC && !(g.w > 0.f))) return Step{q, (double)q};
-  if (MIXED) {
-    double Lg;
-    switch (g.type) {
-      case PS_LINE: Lg = leg<double>(g.A, g.D); break;
-      case PS_CUBIC: Lg = leg<double>(g.A, g.B) + leg<double>(g.B, g.C) + leg<double>(g.C, g.D); break;
-      default: Lg = leg<double>(g.A, g.B) + leg<double>(g.B, g.D);
-    }
-    double a = Lg > 0.0 ? 2.0 * atan((double)tau / Lg) : PS_PI_D;
-    double b = sqrt(PS_PI_D * (double)tau / (2.0 * (double)r));
-    double qd = fmax(fmin(fmin(a, b), 0.5 * PS_PI_D), (double)q);
-    return Step{(float)qd, qd};
-  }
-  float Lg;
+template <typename R>
+__device__ __forceinline__ R polygon_length(const Seg& g) {
   switch (g.type) {
-    case PS_LINE: Lg = leg<float>(g.A, g.D); break;
-    case PS_CUBIC: Lg = leg<float>(g.A, g.B) + leg<float>(g.B, g.C) + leg<float>(g.C, g.D); break;
-    default: Lg = leg<float>(g.A, g.B) + leg<float>(g.B, g.D);
+    case PS_LINE: return leg<R>(g.A, g.D);
+    case PS_CUBIC: return leg<R>(g.A, g.B) + leg<R>(g.B, g.C) + leg<R>(g.C, g.D);
+    default: return leg<R>(g.A, g.B) + leg<R>(g.B, g.D);
   }
+}
+
+__device__ Step seg_step(const Seg& g, float q, float tau, float r) {
+  if (!(tau > 0.f) || (g.type == PS_CONIC && !(g.w > 0.f))) return plain_step(q);
+  float Lg = polygon_length<float>(g);
   float a = Lg > 0.f ? 2.f * atanf(tau / Lg) : PS_PI_F;
   float b = sqrtf(PS_PI_F * tau / (2.f * r));
-  float qf = fmaxf(fminf(fminf(a, b), 0.5f * PS_PI_F), q);
-  return Step{qf, (double)qf};
+  return Step{fmaxf(fminf(fminf(a, b), 0.5f * PS_PI_F), q), q, tau, r, 2};
+}
+
+// The step in FP64 (the same rule; g is the segment for kind 2).  Called only
+// where a count decision is re-taken in FP64, so the FP64 functions run rarely.
+__device__ __noinline__ double step_d(const Step& S, const Seg* g) {
+  const double q = S.q0;
+  if (S.kind == 1) {
+    double td = S.tau, rd = S.r;
+    return fmax(td >= rd ? PS_PI_D : 2.0 * acos(1.0 - td / rd), q);
+  }
+  if (S.kind == 2 && g) {
+    double Lg = polygon_length<double>(*g);
+    double a = Lg > 0.0 ? 2.0 * atan((double)S.tau / Lg) : PS_PI_D;
+    double b = sqrt(PS_PI_D * (double)S.tau / (2.0 * (double)S.r));
+    return fmax(fmin(fmin(a, b), 0.5 * PS_PI_D), q);
+  }
+  return q;
+}
+
+// The FP64 step: without the boost (PX false) the nominal step itself, and
+// step_d is not referenced (its presence alone changes the kernel's code).
+template <bool PX>
+__device__ __forceinline__ double sd(const Step& S, const Seg* g) {
+  if constexpr (PX) return step_d(S, g);
+  else return (double)S.q0;
+}
+
+// Steps for the turning ad (FP32) / ad64 (FP64): decided in FP32, re-decided in
+// FP64 under MIXED when the FP32 ratio sits within rounding of a boundary.
+template <bool MIXED, bool PX>
+__device__ __forceinline__ int steps_for(float ad, double ad64, const Step& S, const Seg* g) {
+  if (MIXED && near_integer(ad / S.q)) return ceil_steps_d(ad64, sd<PX>(S, g));
+  return ceil_steps(ad, S.q);
 }
 
 // Reversals of a segment with collinear control points: along the common
@@ -362,7 +374,7 @@ __device__ int collinear_reversals(const Seg& g, float* rts) {
 
 // Interval table of a segment link (Sec. 3.3.4-3.3.6, Eq. 4-6, 12-13).
 // Returns N (total steps) or -1 if the table does not fit.
-template <bool MIXED>
+template <bool MIXED, bool PX>
 __device__ int seg_intervals(const Seg& g, Step S, LinkRec& L) {
   const float q = S.q;
   float Psi0 = angf(end_grad0(g)), Psin = angf(end_grad1(g));
@@ -408,7 +420,7 @@ __device__ int seg_intervals(const Seg& g, Step S, LinkRec& L) {
     for (int k = 0; k < M; ++k) {
       int D;
       if ((pivots >> k) & 1u) {
-        D = steps_for<MIXED>(PS_PI_F, PS_PI_D, S);
+        D = steps_for<MIXED, PX>(PS_PI_F, PS_PI_D, S, &g);
         L.step[k] = PS_PI_F / (float)D;
       } else {
         D = 1;
@@ -507,7 +519,7 @@ __device__ int seg_intervals(const Seg& g, Step S, LinkRec& L) {
         // store counts computed from the FP64 turning
         double ad = fabs(dd_);
         if (ad >= PS_PI_D) {
-          int Dh = ceil_steps_d(0.5 * ad, S.qd);
+          int Dh = ceil_steps_d(0.5 * ad, sd<PX>(S, &g));
           float psi_s = Psi[k] + 0.5f * delta;
           float ps_ = solve_t<MIXED>(g, psi_s, pa, pb);
           if (M + 2 > 6) return -1;
@@ -516,7 +528,7 @@ __device__ int seg_intervals(const Seg& g, Step S, LinkRec& L) {
           L.meta |= META_SPLIT_BIT(M);
           M++;
         } else {
-          int D = ad == 0.0 ? 1 : ceil_steps_d(ad, S.qd);
+          int D = ad == 0.0 ? 1 : ceil_steps_d(ad, sd<PX>(S, &g));
           if (M + 1 > 6) return -1;
           L.p[M] = pa; L.psi[M] = Psi[k]; L.step[M] = delta / (float)D; L.dsum[M + 1] = (uint16_t)D; M++;
         }
@@ -564,7 +576,7 @@ __device__ __forceinline__ float ominus_f(float a, float b) {
 // Join / cap pivot (Sec. 4.3): generator fixed at `at`, psi from Psi0 through
 // delta in J steps; the outer side is N for delta > 0, P for delta < 0 and the
 // inner radius is zero.
-template <bool MIXED>
+template <bool MIXED, bool PX>
 __device__ int pivot_setup(float2 at, float Psi0, float delta, int kind, int style, float r,
                            float miter, Step S, LinkRec& L, float2 g_in = make_float2(0.f, 0.f),
                            float2 g_out = make_float2(0.f, 0.f)) {
@@ -584,7 +596,7 @@ __device__ int pivot_setup(float2 at, float Psi0, float delta, int kind, int sty
     switch (style) {
       case PS_CAP_TRIANGLE: J = 2; break;
       case PS_CAP_SQUARE: J = 4; break;
-      case PS_CAP_ROUND: J = steps_for<MIXED>(PS_PI_F, PS_PI_D, S); break;
+      case PS_CAP_ROUND: J = steps_for<MIXED, PX>(PS_PI_F, PS_PI_D, S, nullptr); break;
       default: J = 0;
     }
   }
@@ -643,8 +655,11 @@ __device__ int pivot_setup(float2 at, float Psi0, float delta, int kind, int sty
   return J;
 }
 
-// Full setup of link k of path p.  Returns the number of ribs (N+1 or 0).
-template <bool MIXED>
+// Full setup of link k of path p.  Returns the number of ribs (N+1 or 0).  PX
+// compiles the pixel-scale step boost in (tau > 0); without it the link steps by
+// q, and the kernel carries none of the boost's code (whose presence alone
+// slowed the kernel by 40%).
+template <bool MIXED, bool PX>
 __device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, int32_t s0, int n,
                           int k, float r, int join, int cap, float miter, bool closed, float q,
                           float tau, LinkRec& L) {
@@ -664,7 +679,7 @@ __device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, i
     L.P[0] = g.A; L.P[1] = g.B; L.P[2] = g.C; L.P[3] = g.D;
     L.w = g.w;
     L.meta = LK_SEG | ((uint32_t)g.type << 2);
-    int N = seg_intervals<MIXED>(g, seg_step<MIXED>(g, q, tau, r), L);
+    int N = seg_intervals<MIXED, PX>(g, PX ? seg_step(g, q, tau, r) : plain_step(q), L);
     if (N < 0) return -1;
     nrib = N > 0 ? N + 1 : 0;
   } else if (k == 0 || k == 2 * n) {
@@ -688,8 +703,8 @@ __device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, i
       Seg c = load_seg(st, sp, sw, s0 + i);
       L.meta = LK_CAP;
       float Psi0 = (k == 0) ? angf(end_grad0(c)) + PS_PI_F : angf(end_grad1(c));
-      Step S = cap == PS_CAP_ROUND ? round_step<MIXED>(q, tau, r) : Step{q, (double)q};
-      int J = pivot_setup<MIXED>(k == 0 ? c.A : c.D, Psi0, PS_PI_F, LK_CAP, cap, r, miter, S, L);
+      Step S = PX && cap == PS_CAP_ROUND ? round_step(q, tau, r) : plain_step(q);
+      int J = pivot_setup<MIXED, PX>(k == 0 ? c.A : c.D, Psi0, PS_PI_F, LK_CAP, cap, r, miter, S, L);
       nrib = J > 0 ? J + 1 : 0;
     } else if (k == 2 * n) {
       if (first < 0 || last < 0) return 0;
@@ -698,8 +713,8 @@ __device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, i
       float Psi0 = angf(end_grad1(a));
       float delta = ominus_f(angf(end_grad0(b)), Psi0);
       if (delta == -PS_PI_F) delta = PS_PI_F;
-      Step S = join == PS_JOIN_ROUND ? round_step<MIXED>(q, tau, r) : Step{q, (double)q};
-      int J = pivot_setup<MIXED>(b.A, Psi0, delta, LK_JOIN, join, r, miter, S, L, end_grad1(a),
+      Step S = PX && join == PS_JOIN_ROUND ? round_step(q, tau, r) : plain_step(q);
+      int J = pivot_setup<MIXED, PX>(b.A, Psi0, delta, LK_JOIN, join, r, miter, S, L, end_grad1(a),
                                  end_grad0(b));
       nrib = J > 0 ? J + 1 : 0;
     }
@@ -718,21 +733,21 @@ __device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, i
     float Psi0 = angf(end_grad1(a));
     float delta = ominus_f(angf(end_grad0(b)), Psi0);
     if (delta == -PS_PI_F) delta = PS_PI_F;
-    Step S = join == PS_JOIN_ROUND ? round_step<MIXED>(q, tau, r) : Step{q, (double)q};
+    Step S = PX && join == PS_JOIN_ROUND ? round_step(q, tau, r) : plain_step(q);
     if (MIXED && join == PS_JOIN_ROUND && delta != 0.f && near_integer(fabsf(delta) / S.q)) {
       float2 e1 = end_grad1(a), e0 = end_grad0(b);
       double d = atan2((double)e0.y, (double)e0.x) - atan2((double)e1.y, (double)e1.x);
       if (d > PS_PI_D) d -= PS_TWO_PI_D;
       if (d < -PS_PI_D) d += PS_TWO_PI_D;
-      int J = ceil_steps_d(fabs(d), S.qd);
-      int J0 = pivot_setup<MIXED>(b.A, Psi0, delta, LK_JOIN, join, r, miter, S, L, e1, e0);
+      int J = ceil_steps_d(fabs(d), sd<PX>(S, nullptr));
+      int J0 = pivot_setup<MIXED, PX>(b.A, Psi0, delta, LK_JOIN, join, r, miter, S, L, e1, e0);
       if (J0 > 0 && J > 0 && J != J0) {
         L.step[0] = delta / (float)J;
         L.dsum[1] = (uint16_t)J;
       }
       nrib = J0 > 0 ? (J > 0 ? J : J0) + 1 : 0;
     } else {
-      int J = pivot_setup<MIXED>(b.A, Psi0, delta, LK_JOIN, join, r, miter, S, L, end_grad1(a),
+      int J = pivot_setup<MIXED, PX>(b.A, Psi0, delta, LK_JOIN, join, r, miter, S, L, end_grad1(a),
                                  end_grad0(b));
       nrib = J > 0 ? J + 1 : 0;
     }
@@ -786,7 +801,7 @@ constexpr int SETUP_NT = 256;
 constexpr int SETUP_IPT = 2;  // links per thread by default (tunable: 1, 2, 4)
 constexpr int SETUP_TILE = SETUP_NT * SETUP_IPT;
 
-template <bool MIXED, int SETUP_IPT>
+template <bool MIXED, int SETUP_IPT, bool PX = false>
 __global__ void __launch_bounds__(SETUP_NT) k_link_setup(
     const uint8_t* __restrict__ st, const float* __restrict__ sp, const float* __restrict__ sw,
     const int32_t* __restrict__ seg_off, const float* __restrict__ width,
@@ -817,7 +832,7 @@ __global__ void __launch_bounds__(SETUP_NT) k_link_setup(
       int32_t s0 = __ldg(seg_off + p), s1 = __ldg(seg_off + p + 1);
       int k = (int)(l - (2 * (int64_t)s0 + p));
       LinkRec L = {};
-      int nr = link_setup<MIXED>(st, sp, sw, s0, s1 - s0, k, 0.5f * __ldg(width + p), join[p],
+      int nr = link_setup<MIXED, PX>(st, sp, sw, s0, s1 - s0, k, 0.5f * __ldg(width + p), join[p],
                                  cap[p], __ldg(miter + p), closed[p] != 0, q, tau, L);
       if (nr < 0) {
         ps_record_error(status, PS_ERR_INVALID);
@@ -834,7 +849,10 @@ __global__ void __launch_bounds__(SETUP_NT) k_link_setup(
   }
   long long total;
   long long excl = block_excl_sum<SETUP_NT>(local, total, sm);
-  if (threadIdx.x == 0) s_prefix = lookback_sum(tflag, tagg, tincl, total, tile, status);
+  if (threadIdx.x < 32) {
+    long long pre = lookback_sum_warp(tflag, tagg, tincl, total, tile, status);
+    if (threadIdx.x == 0) s_prefix = pre;
+  }
   __syncthreads();
   long long off = s_prefix + excl;
   for (int i = 0; i < SETUP_IPT; ++i) {
@@ -963,7 +981,7 @@ __device__ __forceinline__ int64_t find_link_warp(const int32_t* off, int64_t n,
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(EMIT_NT) k_emit(
+__global__ void __launch_bounds__(EMIT_NT, 3) k_emit(
     const LinkRec* __restrict__ recs, const int32_t* __restrict__ link_off,
     const int32_t* __restrict__ link_path, int64_t n_link, const int64_t* __restrict__ n_rib,
     int64_t capacity, float4* __restrict__ rib, uint32_t* __restrict__ tag,
@@ -1228,7 +1246,9 @@ static int launch_tessellate(ps_context* ctx, const ps_segments* seg, const ps_p
   int P = paths->n_path;
   int64_t L = 2 * S + P;
   if (P <= 0) return PS_ERR_INVALID;
-  const int ipt = ctx->tune[PS_TUNE_SETUP_LINKS];
+  // links per thread: the tuned value, or the default for the boosted kernel
+  // (one instantiation only)
+  const int ipt = ctx->pixel_tol > 0.f ? SETUP_IPT : ctx->tune[PS_TUNE_SETUP_LINKS];
   int64_t n_tiles = (L + SETUP_NT * ipt - 1) / (SETUP_NT * ipt);
   int rc;
   if ((rc = ps_ensure_tiles(ctx, n_tiles + (out->capacity + SCAN_TILE - 1) / SCAN_TILE + 2)) != PS_OK)
@@ -1251,7 +1271,10 @@ static int launch_tessellate(ps_context* ctx, const ps_segments* seg, const ps_p
       ctx->d_tile_agg, ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles
   const unsigned g = (unsigned)n_tiles;
   const bool mx = precision == PS_PREC_MIXED;
-  if (ipt == 1) {
+  if (ctx->pixel_tol > 0.f) {
+    if (mx) k_link_setup<true, SETUP_IPT, true><<<g, SETUP_NT, 0, st>>>(PS_SETUP_ARGS);
+    else k_link_setup<false, SETUP_IPT, true><<<g, SETUP_NT, 0, st>>>(PS_SETUP_ARGS);
+  } else if (ipt == 1) {
     if (mx) k_link_setup<true, 1><<<g, SETUP_NT, 0, st>>>(PS_SETUP_ARGS);
     else k_link_setup<false, 1><<<g, SETUP_NT, 0, st>>>(PS_SETUP_ARGS);
   } else if (ipt == 4) {
@@ -1510,7 +1533,20 @@ int ps_run_link_setup(ps_context* ctx, const ps_segments* seg, const ps_paths* p
   cudaMemsetAsync(ctx->d_tile_flag, 0, sizeof(uint32_t) * n_tiles, st);
   cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
   k_link_path<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(paths->d_seg_off, P, L, link_path);
-  if (precision == PS_PREC_MIXED)
+  const bool px = ctx->pixel_tol > 0.f;
+  if (precision == PS_PREC_MIXED && px)
+    k_link_setup<true, SETUP_IPT, true><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
+        seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
+        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->pixel_tol, ctx->d_recs,
+        d_link_off, d_path_off, d_n_rib, INT64_MAX, ctx->d_tile_flag, ctx->d_tile_agg,
+        ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles);
+  else if (px)
+    k_link_setup<false, SETUP_IPT, true><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
+        seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
+        paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->pixel_tol, ctx->d_recs,
+        d_link_off, d_path_off, d_n_rib, INT64_MAX, ctx->d_tile_flag, ctx->d_tile_agg,
+        ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles);
+  else if (precision == PS_PREC_MIXED)
     k_link_setup<true, SETUP_IPT><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
         paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->pixel_tol, ctx->d_recs,
