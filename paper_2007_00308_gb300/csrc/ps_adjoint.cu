@@ -199,8 +199,30 @@ __global__ void k_adj_links(const uint8_t* st, const float* sp, const float* sw,
   src[l] = make_int4(R.kind, a, b, R.path);
 }
 
-// Per rib: gradients of g(t_j), psi_j, r; scattered to control points, to the
-// link's boundary-angle adjoints and to the path width.
+// Sum of v over the lanes from this one to the end of its run of equal keys
+// (runs of a key are contiguous); exact at the run's first lane.
+__device__ __forceinline__ float run_sum(float v, long long key) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    float y = __shfl_down_sync(0xffffffffu, v, o);
+    long long ky = __shfl_down_sync(0xffffffffu, key, o);
+    if (lane + o < 32 && ky == key) v += y;
+  }
+  return v;
+}
+
+__device__ __forceinline__ bool run_head(long long key) {
+  long long kp = __shfl_up_sync(0xffffffffu, key, 1);
+  return (threadIdx.x & 31) == 0 || kp != key;
+}
+
+// Per rib: gradients of g(t_j), psi_j, r, for the control points, the link's
+// boundary-angle adjoints and the path width.  A warp takes 32 consecutive
+// ribs (mostly of one link), sums their contributions per target with
+// segmented shuffles, and the first lane of each run adds them atomically:
+// every rib of a segment adds to the same few words, so adding per rib would
+// serialize on them.
 __global__ void __launch_bounds__(256) k_adj_ribs(
     const LinkRec* __restrict__ recs, const int4* __restrict__ src,
     const int32_t* __restrict__ link_off, int64_t n_link, const int64_t* __restrict__ n_rib,
@@ -210,9 +232,23 @@ __global__ void __launch_bounds__(256) k_adj_ribs(
     float* __restrict__ gwidth) {
   int64_t R = *n_rib;
   if (R > capacity) R = capacity;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    int l = find_link_a(link_off, 0, n_link - 1, r);
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < R;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = base + lane;
+    const bool act = r < R;
+    // link of rib r: one search for the warp's first rib, then a short walk
+    int l = 0;
+    if (lane == 0) l = find_link_a(link_off, 0, n_link - 1, base);
+    l = __shfl_sync(0xffffffffu, l, 0);
+    if (act)
+      while (l + 1 < n_link && (int64_t)__ldg(link_off + l + 1) <= r) ++l;
+    // this rib's contributions: point gradients of segment seg_t (slots 0..3),
+    // the path width, and the boundary angles kslot, kslot + 1 of link l
+    float P8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int seg_t = -1, path_t = -1, kslot = 0;
+    float gw = 0.f, psA = 0.f, psB = 0.f;
+    if (act) {
     int j = (int)(r - __ldg(link_off + l));
     int nr = __ldg(link_off + l + 1) - __ldg(link_off + l);
     const LinkRec* L = recs + l;
@@ -264,7 +300,8 @@ __global__ void __launch_bounds__(256) k_adj_ribs(
       // N = g - rN n, P = g + rP n: dN/dpsi = rN T, dP/dpsi = -rP T
       float Gpsi = rN * dot2(T, GN) - rP * dot2(T, GP);
       float Gr = -dot2(n, GN) + dot2(n, GP);  // rN = rP = w/2 on segment links
-      atomicAdd(gwidth + sc.w, 0.5f * Gr);
+      gw = 0.5f * Gr;
+      path_t = sc.w;
       float b[4], beta[4], c;
       float2 H, Hd;
       weights(g, t, b, beta, c, H, Hd);
@@ -309,15 +346,17 @@ __global__ void __launch_bounds__(256) k_adj_ribs(
           }
         }
       }
-      for (int i = 0; i < 4; ++i) add_pt(gpts, sc.y, g.type, i, mk(pt[i][0], pt[i][1]));
-      // psi's adjoint to the interval's boundary angles
-      if (Gpsi != 0.f) {
-        if (boundary) atomicAdd(adj_psi + 8 * (int64_t)l + k, Gpsi);
-        else {
-          atomicAdd(adj_psi + 8 * (int64_t)l + k, (1.f - lam) * Gpsi);
-          atomicAdd(adj_psi + 8 * (int64_t)l + k + 1, lam * Gpsi);
-        }
+      seg_t = sc.y;
+      for (int i = 0; i < 4; ++i) {
+        // quadratic / conic: C's gradient goes to B's slot
+        int slot = (i == 2 && (g.type == PS_QUAD || g.type == PS_CONIC)) ? 1 : i;
+        P8[2 * slot] += pt[i][0];
+        P8[2 * slot + 1] += pt[i][1];
       }
+      // psi's adjoint to the interval's boundary angles
+      kslot = k;
+      psA = boundary ? Gpsi : (1.f - lam) * Gpsi;
+      psB = boundary ? 0.f : lam * Gpsi;
     } else if (kind == LK_JOIN || kind == LK_CAP) {
       int J = (int)__ldg(&L->dsum[1]);
       float psi = (j == J) ? __ldg(&L->psi[1]) : __ldg(&L->psi[0]) + __ldg(&L->step[0]) * (float)j;
@@ -328,9 +367,11 @@ __global__ void __launch_bounds__(256) k_adj_ribs(
       bool ovr = (meta & META_FLAG_OVERRIDE) && (j == 1 || j == 2);
       // the pivot point: the outgoing segment's A (join), the capped end (cap)
       float2 Gat = GN + GP;
-      int sg = kind == LK_JOIN ? sc.z : sc.y;
+      seg_t = kind == LK_JOIN ? sc.z : sc.y;
       int pslot = (kind == LK_CAP && sc.z == 1) ? 3 : 0;
-      add_pt(gpts, sg, __ldg(stype + sg), pslot, Gat);
+      P8[2 * pslot] = Gat.x;
+      P8[2 * pslot + 1] = Gat.y;
+      path_t = sc.w;
       if (!ovr) {  // miter tips: the tip's motion with the angles and width is not followed
         float Gpsi, Gr;
         if (rN > 0.f) {  // N = at - sq r n
@@ -340,14 +381,36 @@ __global__ void __launch_bounds__(256) k_adj_ribs(
           Gpsi = -sq * rP * dot2(T, GP);
           Gr = sq * dot2(n, GP);
         }
-        atomicAdd(gwidth + sc.w, 0.5f * Gr);
+        gw = 0.5f * Gr;
         float fr = (float)j / (float)J;
+        kslot = 0;
         if (kind == LK_JOIN) {
-          atomicAdd(adj_psi + 8 * (int64_t)l + 0, (1.f - fr) * Gpsi);
-          atomicAdd(adj_psi + 8 * (int64_t)l + 1, fr * Gpsi);
+          psA = (1.f - fr) * Gpsi;
+          psB = fr * Gpsi;
         } else {
-          atomicAdd(adj_psi + 8 * (int64_t)l + 0, Gpsi);  // delta = pi is constant
+          psA = Gpsi;  // delta = pi is constant
         }
+      }
+    }
+    }  // act
+    // sums per link (points, width) and per (link, interval) (angles)
+    const long long key1 = act ? (long long)l : -1 - (long long)lane;
+    const long long key2 = act ? 8 * (long long)l + kslot : -1 - (long long)lane;
+    const bool h1 = run_head(key1), h2 = run_head(key2);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float v = run_sum(P8[i], key1);
+      if (h1 && seg_t >= 0 && v != 0.f) atomicAdd(gpts + 8 * (int64_t)seg_t + i, v);
+    }
+    {
+      float v = run_sum(gw, key1);
+      if (h1 && path_t >= 0 && v != 0.f) atomicAdd(gwidth + path_t, v);
+    }
+    {
+      float a = run_sum(psA, key2), b = run_sum(psB, key2);
+      if (h2 && act) {
+        if (a != 0.f) atomicAdd(adj_psi + 8 * (int64_t)l + kslot, a);
+        if (b != 0.f) atomicAdd(adj_psi + 8 * (int64_t)l + kslot + 1, b);
       }
     }
   }
