@@ -25,7 +25,8 @@ struct DashPattern {
   double period;
   double offset;
   float cum_f[65];             // the same in FP32, for the prefilter
-  float period_f, offset_f;
+  float period_f, period_lo;   // period = period_f + period_lo (+ ~2^-48 period)
+  float offset_f;
   int m2;
   int j_round;                 // ribs - 1 of a round cap at this dtheta
   const uint8_t* path_cap;     // cap style per path, or null: butt dash ends
@@ -80,18 +81,25 @@ __device__ __forceinline__ float whole_end(float a0, float a1) {
 }
 
 // FP32 prefilter: whether the quad [sa, sb] lies inside one interval of the
-// pattern (an on-stretch or a gap) with a margin eps above the FP32 rounding of
-// its phase.  That rounding (u = sa + offset, k period, their difference, and
-// the FP32 period and pattern) is at most about 4 * 2^-24 of |sa| + |offset| +
-// period; eps is 2e-6 of it, eight times more.  1: inside an on-stretch (the
-// quad is emitted whole), 0: inside a gap (nothing), -1: within eps of a
-// boundary (decided in FP64 by dash_quad).
+// pattern (an on-stretch or a gap) with a margin eps above the FP32 error of
+// its phase.  The phase of sa is computed with error-free steps: sa + offset as
+// an exact float pair (TwoSum), k period_f exactly with its FMA residual, and
+// the period's low part; what remains is a few roundings of values below two
+// periods plus k * 2^-48 period, under 1e-6 of the period for k < 2^24, while
+// the pattern's own FP32 rounding adds at most 2^-24 of it.  eps is 1e-4 of the
+// period.  1: inside an on-stretch (the quad is emitted whole), 0: inside a gap
+// (nothing), -1: within eps of a boundary (decided in FP64 by dash_quad).
 __device__ __forceinline__ int dash_quick(const DashPattern& P, float sa, float sb) {
-  const float per = P.period_f, off = P.offset_f;
-  const float eps = 2e-6f * (fabsf(sa) + fabsf(off) + per) + 1e-6f;
-  const float u = sa + off;
+  const float per = P.period_f;
+  const float eps = 1e-4f * per;
+  const float u = sa + P.offset_f;  // TwoSum: u + ul == sa + offset exactly
+  const float bv = u - sa;
+  const float ul = (sa - (u - bv)) + (P.offset_f - bv);
   const float k = floorf(u / per);
-  const float ph = u - k * per;  // phase of sa in [0, period)
+  if (!(fabsf(k) < 16777216.f)) return -1;
+  const float kp = k * per;
+  const float ke = fmaf(k, per, -kp);  // k per == kp + ke exactly
+  const float ph = (((u - kp) + ul) - ke) - k * P.period_lo;  // phase of sa
   if (!(ph >= 0.f && ph < per)) return -1;
   const float pe = ph + (sb - sa);  // phase of sb, beyond the period if it wraps
   int j = 0;  // interval [cum_f[j], cum_f[j+1]) holding ph
@@ -358,6 +366,7 @@ extern "C" int ps_dash_capped(ps_context* ctx, const float* d_rib, const float* 
   P.offset = (double)offset;
   for (int i = 0; i <= P.m2; ++i) P.cum_f[i] = (float)P.cum[i];
   P.period_f = (float)P.period;
+  P.period_lo = (float)(P.period - (double)P.period_f);
   P.offset_f = offset;
   P.path_cap = d_path_cap;
   P.n_path = d_path_cap ? n_path : 0;

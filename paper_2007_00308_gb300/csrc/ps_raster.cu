@@ -177,6 +177,29 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
         }
       }
     }
+    // a quad whose bounding box lies in one tile meets that tile: binned in one
+    // direct round, outside the flattened (quad, candidate) loop
+    {
+      const int tdir = Q.n == 1 ? Q.ty0 * tiles_x + Q.tx0 : -1;
+      if (Q.n == 1) {
+        cnt = 0;
+        if (PASS == 0) Q.mask = 1u;
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, tdir);
+      const int leader = __ffs(peers) - 1;
+      if (tdir >= 0) {
+        if (PASS == 0) {
+          if (lane == leader) atomicAdd(count + tdir, __popc(peers));
+        } else {
+          int basepos = 0;
+          if (lane == leader) basepos = atomicAdd(cursor + tdir, __popc(peers));
+          basepos = __shfl_sync(peers, basepos, leader);
+          const int64_t at = (int64_t)off[tdir] + basepos + __popc(peers & ((1u << lane) - 1u));
+          if (at < pair_cap && at < off[tdir + 1]) bin[at] = (uint32_t)r;
+          else ps_record_error(status, PS_ERR_CAPACITY);
+        }
+      }
+    }
     // warp scan of the pair counts
     int x = cnt;
 #pragma unroll
