@@ -225,13 +225,17 @@ def algorithmic(kernel, c):
 # 3 logic ops + 2, 10 lane ops; the general path (edges over 1024 px) ~12.  The
 # SM issues at most 128 lane ops per clock (4 schedulers x 32 lanes).
 OPS_PER_TEST = {"convex_pixels": 7.0, "two_triangle_pixels": 10.0, "general_pixels": 12.0}
+# the crossing-rule mask (--exact): per sample and edge one add and a sign
+# gather (shift, or), 4 edges; its int32 form counts as "convex" pixels
+OPS_PER_TEST_EXACT = {"convex_pixels": 12.0, "two_triangle_pixels": 12.0, "general_pixels": 24.0}
 
 
-def ops_per_test(rstat):
-    n = sum(rstat.get(k, 0) for k in OPS_PER_TEST)
+def ops_per_test(rstat, exact=False):
+    table = OPS_PER_TEST_EXACT if exact else OPS_PER_TEST
+    n = sum(rstat.get(k, 0) for k in table)
     if n <= 0:
-        return 12.0
-    return sum(OPS_PER_TEST[k] * rstat.get(k, 0) for k in OPS_PER_TEST) / n
+        return table["general_pixels"]
+    return sum(table[k] * rstat.get(k, 0) for k in table) / n
 
 
 def alu_peak_tests(sm_mhz, ops):
@@ -241,7 +245,7 @@ def alu_peak_tests(sm_mhz, ops):
 # DRAM traffic of one k_coverage launch per bin entry, from the ncu capture in
 # profiles/k_coverage_c2_1000paths.md (dram__bytes_read.sum + write.sum =
 # 124.1 MB over 8,351,880 bin entries); scaled to the launch by its bin entries.
-COVERAGE_TRAFFIC_PER_PAIR = (117.455360e6 + 6.630656e6) / 8351880
+COVERAGE_TRAFFIC_PER_PAIR = (117.453568e6 + 6.680320e6) / 8351880
 
 
 AUTOTUNE = True
@@ -404,16 +408,18 @@ def run_ours(args, rank, world, local_rank):
                           "achieved_gbs": ach, "frac": ach / hbm_peak}
         else:
             ach = work / (ms * 1e-3) / 1e9
-            opt = ops_per_test(rstat)
+            opt = ops_per_test(rstat, args.exact)
             pk = alu_peak_tests(sm_mhz, opt) / 1e9
             kernels[k] = {"ms": ms, "bound": "alu", "sample_tests": work,
                           "achieved_gtests": ach, "peak_gtests": pk, "frac": ach / pk}
     kd = kernels[dom]
     if kd.get("bound") == "alu":
-        opt = ops_per_test(rstat)
+        opt = ops_per_test(rstat, args.exact)
         roof = {"kernel": dom, "bound": "alu", "achieved": kd["achieved_gtests"],
                 "peak": kd["peak_gtests"], "unit": "Gsample-tests/s", "frac": kd["frac"],
-                "traffic": int(COVERAGE_TRAFFIC_PER_PAIR * pairs) if dom == "k_coverage" else None,
+                # measured on the two-triangle kernel; none for the crossing-rule mode
+                "traffic": (int(COVERAGE_TRAFFIC_PER_PAIR * pairs)
+                            if dom == "k_coverage" and not args.exact else None),
                 "peak_source": (f"derived: 152 SMs x 128 lane ops/clock x {sm_mhz:.0f} MHz / "
                                 f"{opt:.2f} lane ops per sample test (pixel-class mix)"),
                 "algorithmic_work": kd["sample_tests"],

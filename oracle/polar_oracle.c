@@ -18,7 +18,7 @@
  *
  * Every step follows the paper's order and notation.  Where the paper is
  * silent or self-contradictory the reading taken is stated at the step,
- * numbered R1..R19.
+ * numbered R1..R21.
  *
  * Compile with -ffp-contract=off so that no multiply-add is fused behind the
  * source's back: the results are then the same on x86-64 and aarch64.
