@@ -375,6 +375,7 @@ typedef struct {
   double delta[MAXI];     /* signed turning of each interval (Eq. 6, reading R4) */
   int Delta[MAXI];        /* steps per interval (Eq. 12) */
   int pivot[MAXI];        /* interval pivots at a fixed t (collinear reversal) */
+  int split[MAXI + 1];    /* boundary k is a split point (Sec. 3.3.5), t from Eq. 11 */
   int N;                  /* total steps Delta_Sigma(M) (Eq. 13) */
   int fragile64, fragile32;
 } Intervals;
@@ -550,6 +551,7 @@ static void seg_intervals(const Seg* g, double q, Intervals* I) {
       double psi_s = Psi[k] + 0.5 * delta;
       double ps = solve_t(g, psi_s, pa, pb);
       I->p[M] = pa; I->Psi[M] = Psi[k]; I->delta[M] = 0.5 * delta; M++;
+      I->split[M] = 1;
       I->p[M] = ps; I->Psi[M] = psi_s; I->delta[M] = 0.5 * delta; M++;
     } else {
       I->p[M] = pa; I->Psi[M] = Psi[k]; I->delta[M] = delta; M++;
@@ -876,6 +878,13 @@ int orc_tessellate_f64(int64_t n_seg, const uint8_t* seg_type, const double* seg
           if (j == base) {
             t = I.p[kb];
             psi = I.Psi[kb];
+            if (I.split[kb]) {
+              /* a split point is solved from Eq. 11 like an interior rib: its
+               * radius of curvature is reported for the tolerance */
+              V2 H = hodo(&g, t), Hd = hodo_d(&g, t);
+              double cr = fabs(cross(H, Hd)), hl = len(H);
+              rho = cr > 0 ? hodo_scale(&g, t) * hl * hl * hl / cr : 1e300;
+            }
           } else {
             psi = I.Psi[kb] + I.delta[kb] / (double)I.Delta[kb] * (double)(j - base);
             if (I.pivot[kb]) {
