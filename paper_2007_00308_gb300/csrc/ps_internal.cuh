@@ -62,6 +62,7 @@ struct ps_context {
   cudaEvent_t prof_ev[PK_COUNT][2];
   int prof_recorded[PK_COUNT];
   int device;
+  int cov_attr_done[2];  // coverage kernels' shared-memory attribute set on this device
   void* last_stream;
   int32_t* d_status;        // first error recorded by a kernel
   // scan tile states (shared by the passes of one call; calls on one context

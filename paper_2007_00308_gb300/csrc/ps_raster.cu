@@ -1416,12 +1416,13 @@ static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
   if ((rc = ps_ensure_tiles(ctx, (n_tile + TS_TILE - 1) / TS_TILE + 1)) != PS_OK) return rc;
   size_t cov_smem = coverage_smem_bytes();
   const void* kcov = exact ? (const void*)k_coverage<true> : (const void*)k_coverage<false>;
-  static int attr_done[2] = {0, 0};
-  if (!attr_done[exact]) {
+  // the dynamic shared-memory limit is a per-device attribute of the kernel:
+  // set once per context (a context lives on one device)
+  if (!ctx->cov_attr_done[exact]) {
     if ((rc = ps_cuda_check(cudaFuncSetAttribute(kcov, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)cov_smem))) != PS_OK)
       return rc;
-    attr_done[exact] = 1;
+    ctx->cov_attr_done[exact] = 1;
   }
   int grid_cov = ps_persistent_grid(ctx, kcov, CV_NT, cov_smem);
   ctx->last_n_tile = n_tile;
