@@ -84,8 +84,11 @@ __device__ float solve_t(const Seg& g, float psi, float sn, float cs, float pa, 
   solve_coeffs<float>(g, N, a, b, c);
   float disc = b * b - 4.f * a * c, scale = b * b + fabsf(4.f * a * c);
   if (MIXED && c != 0.f && fabsf(disc) < 1e-3f * scale) {
-    double sd, cd;
-    sincos((double)psi, &sd, &cd);
+    // near a double root: coefficients, discriminant and roots in FP64 from the
+    // FP32 normal (its rounding moves the rib along the curve by ~rho 1e-7, far
+    // inside the angle term of the vertex bound; the cancellation is what needs
+    // FP64)
+    const double sd = sn, cd = cs;
     D2 Nd{-sd, cd};
     double ad, bd, cd2;
     solve_coeffs<double>(g, Nd, ad, bd, cd2);
