@@ -11,7 +11,10 @@ module only compiles it with gcc and marshals numpy arrays.
 Parity status per function (see the tests under ``tests/test_oracle_*.py``):
   tessellate       pinned (closed forms: line, circle-arc conic, parabola, cusp
                    structure, per-step turn, total turning, chord error, joins,
-                   caps; coverage against brute force)
+                   caps; coverage against brute force; negative-weight conics
+                   as complementary arcs); tau > 0 pinned (closed-form
+                   sagittas and minimal counts of joins and caps, quarter-circle
+                   counts, densely sampled offset curves of small cubics)
   dash             pinned (straight line against the analytic dash pieces)
   dash_capped      pinned (straight line: caps against the analytic cap shapes;
                    coverage of a capped dashed line against brute force)

@@ -19,19 +19,6 @@ FRAG64 = oracle.FRAGILE64
 EPS_ANG = 4e-6
 
 
-def subset(batch, paths):
-    """The batch restricted to the given paths, in that order (data only)."""
-    off = batch.path_seg_off.astype(np.int64)
-    segs = np.concatenate([np.arange(off[p], off[p + 1]) for p in paths])
-    counts = [int(off[p + 1] - off[p]) for p in paths]
-    b = W.make_batch(batch.name + "_subset", batch.seg_type[segs], batch.seg_pts[segs],
-                     batch.seg_w[segs], counts, batch.path_width[paths], batch.path_join[paths],
-                     batch.path_cap[paths], batch.path_miter[paths], batch.path_closed[paths],
-                     1.0, batch.canvas, batch.dash)
-    b.dtheta = batch.dtheta
-    return b
-
-
 def gpu_run(batch, emit_slabs=None, raster=False):
     import torch
     import paper_2007_00308_gb300 as ps
@@ -89,7 +76,7 @@ def gather(batch, g, paths):
 def check_sampled(batch, g, n_sample, seed):
     rng = np.random.default_rng(seed)
     paths = np.sort(rng.choice(batch.n_path, n_sample, replace=False))
-    sb = subset(batch, paths)
+    sb = batch.subset(paths)
     o = oracle.tessellate(sb)
     gs = gather(batch, g, paths)
     stats, fails = compare_tess(o, gs, sb, FRAG64, EPS_ANG)
