@@ -139,6 +139,22 @@ __device__ __forceinline__ float solve_t(const Seg& g, float psi, float pa, floa
 }
 
 // ---------------------------------------------------------------------------
+// a b - c d.  In FP32 with c d's rounding recovered (Kahan's form): exactly 0
+// when the two products are equal, within about an ulp otherwise.  A plain
+// a * b - c * d is contracted to fma(a, b, -c d), which keeps only c d's
+// rounding, so an exactly flat segment could read as slightly curved.  In FP64
+// the products of FP32 inputs are exact.
+template <typename R>
+__device__ __forceinline__ R diff_prod(R a, R b, R c, R d) {
+  if constexpr (sizeof(R) == 4) {
+    const R w = c * d;
+    const R e = fma(-c, d, w);
+    return fma(a, b, -w) + e;
+  } else {
+    return a * b - c * d;
+  }
+}
+
 // Curvature-sign polynomial C(t) ~ g'(t) x g''(t) in power form c0 + c1 t + c2 t^2.
 template <typename R>
 struct CrossPoly {
@@ -156,7 +172,8 @@ __device__ CrossPoly<R> cross_poly(const Seg& g) {
   switch (g.type) {
     case PS_CUBIC: {
       R d1x = Bx - Ax, d1y = By - Ay, d2x = Cx - Bx, d2y = Cy - By, d3x = Dx - Cx, d3y = Dy - Cy;
-      R X12 = d1x * d2y - d1y * d2x, X13 = d1x * d3y - d1y * d3x, X23 = d2x * d3y - d2y * d3x;
+      R X12 = diff_prod(d1x, d2y, d1y, d2x), X13 = diff_prod(d1x, d3y, d1y, d3x),
+        X23 = diff_prod(d2x, d3y, d2y, d3x);
       P.c0 = X12;
       P.c1 = X13 - R(2) * X12;
       P.c2 = X12 - X13 + X23;
@@ -170,13 +187,13 @@ __device__ CrossPoly<R> cross_poly(const Seg& g) {
       break;
     }
     case PS_QUAD: {
-      R K = (Bx - Ax) * (Dy - By) - (By - Ay) * (Dx - Bx);
+      R K = diff_prod(Bx - Ax, Dy - By, By - Ay, Dx - Bx);
       P.c0 = K;
       P.flat = (K == R(0));
       break;
     }
     case PS_CONIC: {
-      R K = (Bx - Ax) * (Dy - By) - (By - Ay) * (Dx - Bx);
+      R K = diff_prod(Bx - Ax, Dy - By, By - Ay, Dx - Bx);
       R w = g.w, wK = w * K;
       P.c0 = wK;
       P.c1 = wK * (R(2) * w - R(2));
