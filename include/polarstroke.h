@@ -155,6 +155,21 @@ int ps_get_status(ps_context* ctx, int* h_status);
 
 const char* ps_error_string(int code);
 
+/* Failure-detection self-check of the bounded inter-CTA wait (the paper has
+ * no counterpart).  Every single-pass scan of the library waits for its
+ * predecessor tiles (decoupled look-back) for at most 2^22 polls, then records
+ * PS_ERR_TIMEOUT in the status word and carries on, so that a lost tile ends
+ * the launch with an error instead of a hang.  This call launches one warp on
+ * `stream` that waits, through that same wait, on a predecessor tile whose
+ * flag nothing ever sets: which = 0 takes the int64 sum (rib offsets, raster
+ * tile offsets, dash output offsets), which = 1 the segmented FP64 sum (arc
+ * length).  The wait gives up after a second or a few and the kernel returns;
+ * the context stays usable.  Uses a 256-byte scratch allocation of its own.
+ * SYNCHRONIZES.  Returns PS_OK once the kernel has finished, PS_ERR_INVALID
+ * for a null context or another `which`; ps_get_status then reads
+ * PS_ERR_TIMEOUT. */
+int ps_check_wait_timeout(ps_context* ctx, int which, void* stream);
+
 /* ---- the hot path ------------------------------------------------------------ */
 
 /* Tessellate every path (Sec. 4.4's complete algorithm, all links in parallel).

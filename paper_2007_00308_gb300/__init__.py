@@ -26,7 +26,8 @@ EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_statu
            "ps_profile_slot_name", "ps_raster_stats", "ps_tessellate_strokes_noalloc",
            "ps_tessellate_backward", "ps_set_tuning", "ps_get_tuning", "ps_svg_arc_to_conics",
            "ps_uniform_tessellate", "ps_facet_stats", "ps_dash_capped",
-           "ps_rasterize_coverage_exact", "ps_set_pixel_tolerance", "ps_get_pixel_tolerance"]
+           "ps_rasterize_coverage_exact", "ps_set_pixel_tolerance", "ps_get_pixel_tolerance",
+           "ps_check_wait_timeout"]
 PS_PROF_SLOTS = 10
 PS_TUNE_EMIT_SLABS, PS_TUNE_SETUP_LINKS, PS_TUNE_BIN_BLOCKS = 0, 1, 2
 TUNE_CANDIDATES = {PS_TUNE_EMIT_SLABS: (4, 8, 16, 32), PS_TUNE_SETUP_LINKS: (1, 2, 4),
@@ -109,6 +110,7 @@ def lib():
         L.ps_get_tuning.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.ps_set_pixel_tolerance.argtypes = [P, ctypes.c_float]
         L.ps_get_pixel_tolerance.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+        L.ps_check_wait_timeout.argtypes = [P, ctypes.c_int, P]
         L.ps_tessellate_backward.argtypes = [P, ctypes.POINTER(_Segments), ctypes.POINTER(_Paths),
                                              ctypes.c_float, ctypes.c_int,
                                              ctypes.POINTER(_TessOut), P, P, P, P, P]
@@ -350,6 +352,13 @@ def ps_count_ribs_sync(ctx: Context, db: DeviceBatch, out: TessOutput, precision
                                   int(precision), ctypes.byref(o), _stream(stream), ctypes.byref(n))
     _check(rc, "ps_count_ribs_sync")
     return n.value
+
+
+def ps_check_wait_timeout(ctx: Context, which: int, stream=None):
+    """Run the bounded-wait self-check (synchronizes); the status word then
+    holds PS_ERR_TIMEOUT."""
+    _check(lib().ps_check_wait_timeout(ctx.handle, int(which), _stream(stream)),
+           "ps_check_wait_timeout")
 
 
 def ps_arclength_scan(ctx: Context, rib, tag, n_rib, capacity, s, path_len, n_path, stream=None):

@@ -184,6 +184,37 @@ extern "C" int ps_get_status(ps_context* ctx, int* h_status) {
   return ps_cuda_check(cudaStreamSynchronize(st));
 }
 
+// One warp takes the part of tile 1 of a look-back whose tile 0 never
+// publishes: its wait runs to the poll limit, records PS_ERR_TIMEOUT and ends.
+// It touches tiles 0 and 1 only.
+__global__ void k_wait_check(uint32_t* flag, long long* agg, long long* incl, double* aggd,
+                             double* incld, int which, int32_t* status) {
+  if (which == 0)
+    lookback_sum_warp(flag, agg, incl, 1, 1, status);
+  else
+    lookback_segsum_warp(flag, aggd, incld, 1.0, false, 1, status);
+}
+
+extern "C" int ps_check_wait_timeout(ps_context* ctx, int which, void* stream) {
+  if (!ctx || (which != 0 && which != 1)) return PS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  // flags at 0, int64 values at 64 and 96, doubles at 128 and 160 (2 tiles each)
+  char* buf = nullptr;
+  int rc = ps_cuda_check(cudaMalloc((void**)&buf, 256));
+  if (rc != PS_OK) return rc;
+  rc = ps_cuda_check(cudaMemsetAsync(buf, 0, 256, st));
+  if (rc == PS_OK) {
+    k_wait_check<<<1, 32, 0, st>>>((uint32_t*)buf, (long long*)(buf + 64),
+                                   (long long*)(buf + 96), (double*)(buf + 128),
+                                   (double*)(buf + 160), which, ctx->d_status);
+    rc = ps_cuda_check(cudaGetLastError());
+  }
+  if (rc == PS_OK) rc = ps_cuda_check(cudaStreamSynchronize(st));
+  cudaFree(buf);
+  ctx->last_stream = stream;
+  return rc;
+}
+
 void ps_prof_mark(ps_context* ctx, int slot, int end, cudaStream_t st) {
   if (!ctx->prof_on) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

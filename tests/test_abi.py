@@ -62,3 +62,5 @@ def test_host_entry_points(library):
     # null context: argument checks fail without touching a device
     library.ps_set_pixel_tolerance.argtypes = [ctypes.c_void_p, ctypes.c_float]
     assert library.ps_set_pixel_tolerance(None, 0.5) < 0
+    library.ps_check_wait_timeout.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    assert library.ps_check_wait_timeout(None, 0, None) < 0
