@@ -179,7 +179,12 @@ int ps_check_wait_timeout(ps_context* ctx, int which, void* stream);
  * Writes out->d_link_rib_off, d_path_rib_off, *d_n_rib, and (unless COUNT_ONLY)
  * the first min(R, capacity) ribs.  R > capacity records PS_ERR_CAPACITY.
  * Ribs of path p are [path_rib_off[p], path_rib_off[p+1]); ribs of link l are
- * [link_rib_off[l], link_rib_off[l+1]).  Offsets are int32: R < 2^31. */
+ * [link_rib_off[l], link_rib_off[l+1]).  Offsets are int32: R < 2^31.
+ * n_path = 0 with n_seg = 0 is an empty batch: R = 0, link_rib_off[0] =
+ * path_rib_off[0] = 0, no kernel runs and the other pointers may be NULL;
+ * n_path = 0 with segments, or n_path < 0, is PS_ERR_INVALID.  (The same
+ * holds for the allocation-free variant; the adjoint and the uniform
+ * comparison return PS_OK at once on an empty batch.) */
 int ps_tessellate_strokes(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
                           float dtheta, int precision, uint32_t flags, ps_tess_out* out,
                           void* stream);

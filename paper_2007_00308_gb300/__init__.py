@@ -205,7 +205,7 @@ class DeviceBatch:
 
     def __init__(self, batch, device="cuda"):
         import torch
-        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(device)
+        t = lambda a, dt: torch.from_numpy(np.array(a, dtype=dt, order="C")).to(device)
         self.seg_type = t(batch.seg_type, np.uint8)
         self.seg_pts = t(np.asarray(batch.seg_pts, np.float32).reshape(-1), np.float32)
         self.seg_w = t(batch.seg_w, np.float32)

@@ -491,8 +491,10 @@ extern "C" int ps_tessellate_backward(ps_context* ctx, const ps_segments* seg,
                                       const ps_tess_out* fwd, const float* d_grad_rib,
                                       const float* d_grad_s, float* d_grad_pts,
                                       float* d_grad_width, void* stream) {
-  if (!ctx || !seg || !paths || !fwd || !d_grad_rib || !d_grad_pts || !d_grad_width)
-    return PS_ERR_INVALID;
+  if (!ctx || !seg || !paths || !fwd) return PS_ERR_INVALID;
+  // an empty batch has no gradients to write
+  if (paths->n_path == 0 && seg->n_seg == 0) return PS_OK;
+  if (!d_grad_rib || !d_grad_pts || !d_grad_width) return PS_ERR_INVALID;
   if (!fwd->d_rib || !fwd->d_tag || !fwd->d_t || !fwd->d_n_rib || fwd->capacity < 0)
     return PS_ERR_INVALID;
   if (precision != PS_PREC_FP32 && precision != PS_PREC_MIXED) return PS_ERR_INVALID;

@@ -171,9 +171,9 @@ __global__ void __launch_bounds__(FC_NT) k_facet_stats(
 
 extern "C" int ps_uniform_tessellate(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
                                      const ps_tess_out* fwd, float* d_rib_out, void* stream) {
-  if (!ctx || !seg || !paths || !fwd || !d_rib_out || !fwd->d_rib || !fwd->d_link_rib_off ||
-      !fwd->d_n_rib)
-    return PS_ERR_INVALID;
+  if (!ctx || !seg || !paths || !fwd) return PS_ERR_INVALID;
+  if (paths->n_path == 0 && seg->n_seg == 0) return PS_OK;  // empty batch: no ribs
+  if (!d_rib_out || !fwd->d_rib || !fwd->d_link_rib_off || !fwd->d_n_rib) return PS_ERR_INVALID;
   if (paths->n_path <= 0 || seg->n_seg < 0 || fwd->capacity < 0) return PS_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = stream;

@@ -1342,13 +1342,28 @@ static int launch_tessellate(ps_context* ctx, const ps_segments* seg, const ps_p
   return PS_OK;
 }
 
+// An empty batch (no paths, no segments): R = 0 and the single zero entry of
+// each offset array; no kernel runs.
+static int empty_batch(ps_tess_out* out, cudaStream_t st) {
+  if (!out->d_link_rib_off || !out->d_path_rib_off || !out->d_n_rib) return PS_ERR_INVALID;
+  int rc = ps_cuda_check(cudaMemsetAsync(out->d_n_rib, 0, sizeof(int64_t), st));
+  if (rc == PS_OK) rc = ps_cuda_check(cudaMemsetAsync(out->d_link_rib_off, 0, sizeof(int32_t), st));
+  if (rc == PS_OK) rc = ps_cuda_check(cudaMemsetAsync(out->d_path_rib_off, 0, sizeof(int32_t), st));
+  return rc;
+}
+
 extern "C" int ps_tessellate_strokes(ps_context* ctx, const ps_segments* seg,
                                      const ps_paths* paths, float dtheta, int precision,
                                      uint32_t flags, ps_tess_out* out, void* stream) {
   if (!ctx || !seg || !paths || !out) return PS_ERR_INVALID;
   if (!(dtheta >= 1e-4f && dtheta <= 3.14159265f)) return PS_ERR_INVALID;
   if (precision != PS_PREC_FP32 && precision != PS_PREC_MIXED) return PS_ERR_INVALID;
-  if (seg->n_seg < 0 || paths->n_path <= 0 || seg->n_seg > (int64_t)1 << 29) return PS_ERR_INVALID;
+  if (seg->n_seg < 0 || paths->n_path < 0 || seg->n_seg > (int64_t)1 << 29) return PS_ERR_INVALID;
+  if (paths->n_path == 0) {
+    if (seg->n_seg != 0) return PS_ERR_INVALID;
+    ctx->last_stream = stream;
+    return empty_batch(out, (cudaStream_t)stream);
+  }
   if (seg->n_seg > 0 && (!seg->d_type || !seg->d_pts)) return PS_ERR_INVALID;
   if (!paths->d_seg_off || !paths->d_width || !paths->d_join || !paths->d_cap ||
       !paths->d_miter || !paths->d_closed)
@@ -1447,7 +1462,9 @@ extern "C" int ps_tessellate_strokes_noalloc(const ps_segments* seg, const ps_pa
   if (!seg || !paths || !out || !d_status) return PS_ERR_INVALID;
   if (!(dtheta >= 1e-4f && dtheta <= 3.14159265f)) return PS_ERR_INVALID;
   if (precision != PS_PREC_FP32 && precision != PS_PREC_MIXED) return PS_ERR_INVALID;
-  if (seg->n_seg < 0 || paths->n_path <= 0) return PS_ERR_INVALID;
+  if (seg->n_seg < 0 || paths->n_path < 0) return PS_ERR_INVALID;
+  if (paths->n_path == 0)
+    return seg->n_seg != 0 ? PS_ERR_INVALID : empty_batch(out, (cudaStream_t)stream);
   if (seg->n_seg > 0 && (!seg->d_type || !seg->d_pts)) return PS_ERR_INVALID;
   if (!paths->d_seg_off || !paths->d_width || !paths->d_join || !paths->d_cap ||
       !paths->d_miter || !paths->d_closed)
