@@ -367,10 +367,9 @@ struct Edge {
 // advances by 5.
 struct __align__(16) EntrySetup {
   Edge e[6];               // 16 bytes each, read as int4
+  uint16_t rowpre[17];     // prefix of span widths (16-byte aligned; 0xffff past the last row)
   int dm;                  // fast form: 240 * max(|A| + |B|) over the edges
   uint8_t x0[16];          // first pixel of each row's span (rows row0 ..)
-  uint8_t w[16];           // span width of each row
-  uint16_t rowpre[17];     // prefix of span widths
   uint16_t slot;           // mask slot of this pass
   uint8_t valid;           // bit0 tri 0, bit1 tri 1, bit2 int64 path, bit3 convex quad,
                            // bit4 int32 path, bit5 fast convex form, bit6 fast two-triangle
@@ -380,6 +379,7 @@ struct __align__(16) EntrySetup {
 
 static_assert(sizeof(Edge) == 16 && sizeof(EntrySetup) % 16 == 0 && offsetof(EntrySetup, e) == 0,
               "edges are loaded as int4 from shared memory");
+static_assert(offsetof(EntrySetup, rowpre) % 16 == 0, "rowpre is filled with two 16-byte stores");
 
 __device__ __forceinline__ void make_edges(int x0, int y0, int x1, int y1, int x2, int y2, Edge* e,
                                            bool& valid, bool& big) {
@@ -597,12 +597,16 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
   // row spans: group 0 = edges 0..3 (triangle 0 and, for a convex quad, the
   // fourth edge), group 1 = edges 3..5 of the two-triangle form; union of groups
   const bool e3g1 = two;
+  // The loop runs the entry's own rows only (a warp runs the most any of its
+  // lanes has); prefixes past the last row stay 0xffff, above every item index.
   int tot = 0;
+  reinterpret_cast<uint4*>(E.rowpre)[0] = make_uint4(~0u, ~0u, ~0u, ~0u);
+  reinterpret_cast<uint4*>(E.rowpre)[1] = make_uint4(~0u, ~0u, ~0u, ~0u);
   E.rowpre[0] = 0;
   const int nrow = E.nrow;
-  for (int j = 0; j < 16; ++j) {
+  for (int j = 0; j < nrow; ++j) {
     int wj = 0, aj = 0;
-    if (j < nrow) {
+    {
       const float Yb = 256.f * (float)(E.row0 + j);
       float L0 = -INFINITY, M0 = -INFINITY, L1 = -INFINITY, M1 = -INFINITY;
 #pragma unroll
@@ -633,7 +637,6 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
         }
       }
       E.x0[j] = (uint8_t)aj;
-      E.w[j] = (uint8_t)wj;
     }
     tot += wj;
     E.rowpre[j + 1] = (uint16_t)tot;
@@ -654,7 +657,6 @@ __device__ __forceinline__ int finish_spans(EntrySetup& E, int tw) {
       if (E.valid & 32) row_span_fast(E, E.row0 + j, tw, a0, w0);
       else row_span(E, E.row0 + j, tw, a0, w0);
       E.x0[j] = (uint8_t)a0;
-      E.w[j] = (uint8_t)w0;
       tot += w0;
     }
     E.rowpre[j + 1] = (uint16_t)tot;
