@@ -1122,6 +1122,18 @@ __device__ __forceinline__ uint32_t tri_or_quad_mask(const EntrySetup& E, int lx
   return m0 | m1;
 }
 
+// Asynchronous global -> shared copies (cp.async, completion tracked per thread).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <bool EXACT>
 __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
     const float4* __restrict__ rib, const uint32_t* __restrict__ tag,
@@ -1141,6 +1153,10 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
   __shared__ uint8_t s_own[CV_WARPS][32];
   __shared__ uint32_t s_canvas[MASK_WORDS];
   __shared__ uint16_t s_rowmask[EXACT ? 17 * 17 : 1];
+  // each lane's next bin entry (its two ribs and tag), copied in while the
+  // current batch's pixels are processed
+  __shared__ __align__(16) float4 s_pre_rib[CV_WARPS][2][32];
+  __shared__ uint32_t s_pre_tag[CV_WARPS][32];
 
   for (int i = threadIdx.x; i < SLOTS * MASK_WORDS; i += CV_NT) s_mask[i] = 0u;
   for (int i = threadIdx.x; i < MASK_WORDS; i += CV_NT) s_canvas[i] = 0u;
@@ -1210,18 +1226,24 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
       if (lane == 0) base_next = atomicAdd(&s_next, 32);
       base_next = __shfl_sync(0xffffffffu, base_next, 0);
       uint32_t r_next = base_next + lane < n ? bin[b0 + base_next + lane] : 0u;
+      if (base_next + lane < n) {
+        cp_async4(&s_pre_tag[wid][lane], tag + r_next);
+        cp_async16(&s_pre_rib[wid][0][lane], rib + r_next - 1);
+        cp_async16(&s_pre_rib[wid][1][lane], rib + r_next);
+      }
+      cp_async_commit();
       for (;;) {
         const int base = base_next;
-        const uint32_t r = r_next;
         if (base >= n) break;
         const int e = base + lane;
         const bool valid = e < n;
         uint32_t tg = 0u;
         float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
+        cp_async_wait_all();
         if (valid) {
-          tg = __ldg(tag + r);
-          ra = __ldg(rib + r - 1);
-          rb = __ldg(rib + r);
+          tg = s_pre_tag[wid][lane];
+          ra = s_pre_rib[wid][0][lane];
+          rb = s_pre_rib[wid][1][lane];
         }
         if (lane == 0) base_next = atomicAdd(&s_next, 32);
         base_next = __shfl_sync(0xffffffffu, base_next, 0);
@@ -1277,6 +1299,14 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
         }
         const unsigned long long tot3 = __shfl_sync(0xffffffffu, xp, 31);
         const unsigned long long excl3 = xp - packed;
+        // the next batch's ribs and tag (each lane reads only its own copies,
+        // which it has already read for this batch)
+        if (base_next + lane < n) {
+          cp_async4(&s_pre_tag[wid][lane], tag + r_next);
+          cp_async16(&s_pre_rib[wid][0][lane], rib + r_next - 1);
+          cp_async16(&s_pre_rib[wid][1][lane], rib + r_next);
+        }
+        cp_async_commit();
         st_items += tot3;  // three 21-bit fields of at most 8192 per batch
         if (++st_batches == 200) flush_stats();
 #pragma unroll 1
