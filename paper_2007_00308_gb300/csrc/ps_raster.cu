@@ -967,6 +967,9 @@ __device__ __forceinline__ void row_span(const EntrySetup& E, int ly, int tw, in
 // sample value v + A 16 k + B 16 ((5 k) mod 16), and those sums stay within
 // +-(2 dm + 1) < 2^31.  A sample is covered iff no edge is negative there: the
 // sign bit of the OR of the four values.
+// The samples are visited from 15 down to 0 (the same values as stepping up
+// from the clamped sample-0 value, in reverse order), so that each sign bit
+// enters the mask with one funnel shift.
 __device__ __forceinline__ uint32_t fast_mask(const EntrySetup& E, int cx, int cy) {
   const int dm = E.dm;
   int v[4], i1[4], i2[4];
@@ -974,19 +977,20 @@ __device__ __forceinline__ uint32_t fast_mask(const EntrySetup& E, int cx, int c
   for (int i = 0; i < 4; ++i) {
     const int4 ed = *reinterpret_cast<const int4*>(&E.e[i]);
     int t = ed.z + ed.x * cx + ed.y * cy;
-    v[i] = min(max(t, -dm - 1), dm);
+    // sample 15 is 15 columns and 11 sample rows from sample 0
+    v[i] = min(max(t, -dm - 1), dm) + 240 * ed.x + 176 * ed.y;
     i1[i] = ed.w;                 // sample row + 5
     i2[i] = ed.w - ed.y * 256;    // sample row - 11
   }
   uint32_t neg = 0;
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
+  for (int k = 15; k >= 0; --k) {
     uint32_t o = (uint32_t)(v[0] | v[1] | v[2] | v[3]);
-    neg |= (o >> 31) << k;
-    if (k < 15) {
-      const bool up = ((5 * k) & 15) <= 10;  // next sample row is 5 further
+    neg = __funnelshift_l(o, neg, 1);  // neg << 1 | o >> 31
+    if (k > 0) {
+      const bool up = ((5 * (k - 1)) & 15) <= 10;  // sample k's row is 5 above sample k-1's
 #pragma unroll
-      for (int i = 0; i < 4; ++i) v[i] += up ? i1[i] : i2[i];
+      for (int i = 0; i < 4; ++i) v[i] -= up ? i1[i] : i2[i];
     }
   }
   return ~neg & 0xffffu;
@@ -1005,20 +1009,20 @@ __device__ __forceinline__ uint32_t fast_mask2(const EntrySetup& E, int cx, int 
   for (int i = 0; i < 5; ++i) {
     const int4 ed = *reinterpret_cast<const int4*>(&E.e[i]);
     int t = ed.z + ed.x * cx + ed.y * cy;
-    v[i] = min(max(t, -dm - 1), dm);
+    v[i] = min(max(t, -dm - 1), dm) + 240 * ed.x + 176 * ed.y;  // at sample 15
     i1[i] = ed.w;
     i2[i] = ed.w - ed.y * 256;
   }
   uint32_t neg = 0;
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
+  for (int k = 15; k >= 0; --k) {
     uint32_t f0 = (uint32_t)(v[0] | v[1] | v[2]);
     uint32_t f1 = ((uint32_t)v[0] ^ x1) | (uint32_t)(v[3] | v[4]);
-    neg |= ((f0 & f1) >> 31) << k;
-    if (k < 15) {
-      const bool up = ((5 * k) & 15) <= 10;
+    neg = __funnelshift_l(f0 & f1, neg, 1);
+    if (k > 0) {
+      const bool up = ((5 * (k - 1)) & 15) <= 10;
 #pragma unroll
-      for (int i = 0; i < 5; ++i) v[i] += up ? i1[i] : i2[i];
+      for (int i = 0; i < 5; ++i) v[i] -= up ? i1[i] : i2[i];
     }
   }
   return ~neg & 0xffffu;
