@@ -752,19 +752,20 @@ __device__ __forceinline__ uint32_t exact_mask(const EntrySetup& E, int cx, int 
   for (int i = 0; i < 4; ++i) {
     const int4 ed = *reinterpret_cast<const int4*>(&E.e[i]);
     int t = ed.z + ed.x * cx + ed.y * cy;
-    v[i] = min(max(t, -dm - 1), dm);
+    v[i] = min(max(t, -dm - 1), dm) + 240 * ed.x + 176 * ed.y;  // at sample 15
     i1[i] = ed.w;
     i2[i] = ed.w - ed.y * 256;
   }
+  // samples from 15 down to 0, as in fast_mask
   uint32_t sg[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
+  for (int k = 15; k >= 0; --k) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) sg[i] |= ((uint32_t)v[i] >> 31) << k;
-    if (k < 15) {
-      const bool up = ((5 * k) & 15) <= 10;
+    for (int i = 0; i < 4; ++i) sg[i] = __funnelshift_l((uint32_t)v[i], sg[i], 1);
+    if (k > 0) {
+      const bool up = ((5 * (k - 1)) & 15) <= 10;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) v[i] += up ? i1[i] : i2[i];
+      for (int i = 0; i < 4; ++i) v[i] -= up ? i1[i] : i2[i];
     }
   }
   const int4 ya = *reinterpret_cast<const int4*>(&E.e[4]);
