@@ -361,10 +361,11 @@ struct Edge {
 // General form: convex quad in e[0..3], else triangle 0 in e[0..2] and
 // triangle 1 in e[3..5], each edge as {A, B, ex, ey}.  Fast forms: one convex
 // polygon of at most four edges in e[0..3] (bit5), or the union of two
-// triangles e[0..2], e[3..5] (bit6), each edge stored as {A, B, C', i1} with
-// A (x - 8) + B (y - 8) + C' the edge function (C' clamped, see to_fast_edge)
-// and i1 = 16 A + 80 B the step between consecutive samples whose sample row
-// advances by 5.
+// triangles e[0..2], e[3..5] (bit6), each edge stored as {A, B, C15, i1}:
+// A (x - 8) + B (y - 8) + C' is the edge function (C' clamped, see
+// to_fast_edge), C15 = C' + 240 A + 176 B its value at sample 15 (see
+// fast_mask), and i1 = 16 A + 80 B the step between consecutive samples whose
+// sample row advances by 5.
 struct __align__(16) EntrySetup {
   Edge e[6];               // 16 bytes each, read as int4
   uint16_t rowpre[17];     // prefix of span widths (16-byte aligned; 0xffff past the last row)
@@ -441,7 +442,7 @@ __device__ __forceinline__ uint32_t edge_mask32(const Edge& e, int Ec) {
   return em;
 }
 
-// {A, B, ex, ey} -> fast form {A, B, C', i1} (requires |A| + |B| < 2^18).
+// {A, B, ex, ey} -> fast form {A, B, C15, i1} (requires |A| + |B| < 2^18).
 __device__ __forceinline__ void to_fast_edge(Edge& ed) {
   long long A = ed.A, B = ed.B, S = llabs(A) + llabs(B);
   // value at sample 0 of the tile's first pixel: A (8 - ex) + B (8 - ey)
@@ -451,7 +452,9 @@ __device__ __forceinline__ void to_fast_edge(Edge& ed) {
   // fixed, so clamping there changes no sample.
   long long lim = 4080ll * S + 1;
   c = c > lim ? lim : (c < -lim ? -lim : c);
-  ed.ex = (int)c;
+  // stored as the value at sample 15 (15 columns, 11 sample rows further),
+  // where the masks start
+  ed.ex = (int)(c + 240 * A + 176 * B);
   ed.ey = (int)(16 * A + 80 * B);
 }
 
@@ -541,7 +544,7 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
     int lim = 4080 * S + 1;
     int c = (int)(c64 > lim ? lim : (c64 < -lim ? -lim : c64));
     smax = max(smax, S);
-    *reinterpret_cast<int4*>(&E.e[i]) = make_int4(A, B, c, 16 * A + 80 * B);
+    *reinterpret_cast<int4*>(&E.e[i]) = make_int4(A, B, c + 240 * A + 176 * B, 16 * A + 80 * B);
     float fa = (float)A;
     float k = __fdividef((float)-B, fa), u = __fdividef((float)-c, fa);
     float eps = 4.f + 1e-6f * (fabsf(u) + 4096.f * fabsf(k));
@@ -702,7 +705,7 @@ __device__ __forceinline__ void store_exact(const QuadFix& q, EntrySetup& E) {
       c = c > lim ? lim : (c < -lim ? -lim : c);
       E.e[i].A = (int)A[i];
       E.e[i].B = (int)B[i];
-      E.e[i].ex = (int)c;
+      E.e[i].ex = (int)(c + 240 * A[i] + 176 * B[i]);  // at sample 15, as in to_fast_edge
       E.e[i].ey = (int)(16 * A[i] + 80 * B[i]);
     }
     E.dm = (int)(240 * smax);
@@ -751,8 +754,8 @@ __device__ __forceinline__ uint32_t exact_mask(const EntrySetup& E, int cx, int 
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int4 ed = *reinterpret_cast<const int4*>(&E.e[i]);
-    int t = ed.z + ed.x * cx + ed.y * cy;
-    v[i] = min(max(t, -dm - 1), dm) + 240 * ed.x + 176 * ed.y;  // at sample 15
+    int t = ed.z + ed.x * cx + ed.y * cy;  // at sample 15
+    v[i] = min(max(t, -dm - 1), dm);
     i1[i] = ed.w;
     i2[i] = ed.w - ed.y * 256;
   }
@@ -962,24 +965,22 @@ __device__ __forceinline__ void row_span(const EntrySetup& E, int ly, int tw, in
 }
 
 // 16-sample mask of a fast-form entry at pixel corner (cx, cy) (tile-relative,
-// 1/256 px).  Per edge, v = C' + A cx + B cy is the value at sample 0; with
-// S = |A| + |B| < 2^18, |C'| <= 4080 S + 1 and cx, cy <= 3840 it stays below
-// 2^31.  Clamped to [-dm - 1, dm] (dm >= 240 S) it keeps the sign of every
-// sample value v + A 16 k + B 16 ((5 k) mod 16), and those sums stay within
+// 1/256 px).  Per edge, v = C15 + A cx + B cy is the value at sample 15, with
+// C15 = C' + 240 A + 176 B; with S = |A| + |B| < 2^18, |C'| <= 4080 S + 1 and
+// cx, cy <= 3840 it stays within 8160 S + 1 < 2^31.  Every other sample differs
+// from sample 15 by at most 240 S, so v clamped to [-dm - 1, dm] (dm >= 240 S)
+// keeps the sign of every sample value, and the stepped values stay within
 // +-(2 dm + 1) < 2^31.  A sample is covered iff no edge is negative there: the
-// sign bit of the OR of the four values.
-// The samples are visited from 15 down to 0 (the same values as stepping up
-// from the clamped sample-0 value, in reverse order), so that each sign bit
-// enters the mask with one funnel shift.
+// sign bit of the OR of the four values.  The samples are visited from 15 down
+// to 0, so that each sign bit enters the mask with one funnel shift.
 __device__ __forceinline__ uint32_t fast_mask(const EntrySetup& E, int cx, int cy) {
   const int dm = E.dm;
   int v[4], i1[4], i2[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int4 ed = *reinterpret_cast<const int4*>(&E.e[i]);
-    int t = ed.z + ed.x * cx + ed.y * cy;
-    // sample 15 is 15 columns and 11 sample rows from sample 0
-    v[i] = min(max(t, -dm - 1), dm) + 240 * ed.x + 176 * ed.y;
+    int t = ed.z + ed.x * cx + ed.y * cy;  // at sample 15
+    v[i] = min(max(t, -dm - 1), dm);
     i1[i] = ed.w;                 // sample row + 5
     i2[i] = ed.w - ed.y * 256;    // sample row - 11
   }
@@ -1009,8 +1010,8 @@ __device__ __forceinline__ uint32_t fast_mask2(const EntrySetup& E, int cx, int 
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     const int4 ed = *reinterpret_cast<const int4*>(&E.e[i]);
-    int t = ed.z + ed.x * cx + ed.y * cy;
-    v[i] = min(max(t, -dm - 1), dm) + 240 * ed.x + 176 * ed.y;  // at sample 15
+    int t = ed.z + ed.x * cx + ed.y * cy;  // at sample 15
+    v[i] = min(max(t, -dm - 1), dm);
     i1[i] = ed.w;
     i2[i] = ed.w - ed.y * 256;
   }
@@ -1042,7 +1043,8 @@ __device__ __forceinline__ bool band_extent_fast(const Edge* e, float y0, float&
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     const int4 ed = *reinterpret_cast<const int4*>(&e[i]);
-    float A = (float)ed.x, B = (float)ed.y, C = (float)ed.z;
+    // the stored constant is the value at sample 15; C' is the one at sample 0
+    float A = (float)ed.x, B = (float)ed.y, C = (float)(ed.z - 240 * ed.x - 176 * ed.y);
     float n0 = fmaf(B, y0, C), n1 = fmaf(B, y1, C);
     float mag = fabsf(C) + 4096.f * fabsf(B);
     if (ed.x == 0) {
