@@ -369,7 +369,6 @@ struct Edge {
 struct __align__(16) EntrySetup {
   Edge e[6];               // 16 bytes each, read as int4
   uint16_t rowpre[17];     // prefix of span widths (16-byte aligned; 0xffff past the last row)
-  int dm;                  // fast form: 240 * max(|A| + |B|) over the edges
   uint8_t x0[16];          // first pixel of each row's span (rows row0 ..)
   uint16_t slot;           // mask slot of this pass
   uint8_t valid;           // bit0 tri 0, bit1 tri 1, bit2 int64 path, bit3 convex quad,
@@ -529,7 +528,6 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
   // float rounding of k, u and the fma (a few 2^-24 relative to |u| + 4096 |k|).
   float kq[6], uq[6];
   uint32_t lo_side = 0;
-  int smax = 0;
   float k0 = 0.f, u0 = 0.f, eps0 = 0.f;
   bool apos0 = false, anz0 = false;
 #pragma unroll
@@ -543,7 +541,6 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
     long long c64 = (long long)A * (8 - xa) + (long long)B * (8 - ya);
     int lim = 4080 * S + 1;
     int c = (int)(c64 > lim ? lim : (c64 < -lim ? -lim : c64));
-    smax = max(smax, S);
     *reinterpret_cast<int4*>(&E.e[i]) = make_int4(A, B, c + 240 * A + 176 * B, 16 * A + 80 * B);
     float fa = (float)A;
     float k = __fdividef((float)-B, fa), u = __fdividef((float)-c, fa);
@@ -568,7 +565,6 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
       uq[i] = -INFINITY;
     }
   }
-  E.dm = 240 * smax;
   E.valid = cls | (a0 != 0 ? 1 : 0) | (a1 != 0 ? 2 : 0);
   if (two) {
     // With F(p) = cross(P1 - N0, p - N0), triangle 0's diagonal edge is
@@ -708,7 +704,6 @@ __device__ __forceinline__ void store_exact(const QuadFix& q, EntrySetup& E) {
       E.e[i].ex = (int)(c + 240 * A[i] + 176 * B[i]);  // at sample 15, as in to_fast_edge
       E.e[i].ey = (int)(16 * A[i] + 80 * B[i]);
     }
-    E.dm = (int)(240 * smax);
     E.valid = (E.valid & ~(64 | 8)) | 32;
   } else {
 #pragma unroll
@@ -749,13 +744,11 @@ __device__ __forceinline__ uint32_t exact_yrange(int lo, int hi, int base,
 // each limited to its edge's y-range; the parity of the crossings.
 __device__ __forceinline__ uint32_t exact_mask(const EntrySetup& E, int cx, int cy,
                                                const uint16_t* __restrict__ rowmask) {
-  const int dm = E.dm;
   int v[4], i1[4], i2[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int4 ed = *reinterpret_cast<const int4*>(&E.e[i]);
-    int t = ed.z + ed.x * cx + ed.y * cy;  // at sample 15
-    v[i] = min(max(t, -dm - 1), dm);
+    v[i] = ed.z + ed.x * cx + ed.y * cy;  // at sample 15
     i1[i] = ed.w;
     i2[i] = ed.w - ed.y * 256;
   }
@@ -892,7 +885,6 @@ __device__ __forceinline__ int setup_edges(const float4 ra, const float4 rb, int
         f[3].ey = 0;
       }
       for (int i = 0; i < 4; ++i) E.e[i] = f[i];
-      E.dm = (int)(240 * smax);
       E.valid |= 32;
     }
   }
@@ -966,21 +958,19 @@ __device__ __forceinline__ void row_span(const EntrySetup& E, int ly, int tw, in
 
 // 16-sample mask of a fast-form entry at pixel corner (cx, cy) (tile-relative,
 // 1/256 px).  Per edge, v = C15 + A cx + B cy is the value at sample 15, with
-// C15 = C' + 240 A + 176 B; with S = |A| + |B| < 2^18, |C'| <= 4080 S + 1 and
-// cx, cy <= 3840 it stays within 8160 S + 1 < 2^31.  Every other sample differs
-// from sample 15 by at most 240 S, so v clamped to [-dm - 1, dm] (dm >= 240 S)
-// keeps the sign of every sample value, and the stepped values stay within
-// +-(2 dm + 1) < 2^31.  A sample is covered iff no edge is negative there: the
+// C15 = C' + 240 A + 176 B, and stepping visits the values at the other
+// samples.  Each is C' + A (x - 8) + B (y - 8) at a sample (x, y) of the tile,
+// 0 <= x - 8, y - 8 <= 4080; with S = |A| + |B| < 2^18 and |C'| <= 4080 S + 1
+// it stays within 8160 S + 1 < 2^31, and the clamp of C' (see to_fast_edge)
+// changed no sign.  A sample is covered iff no edge is negative there: the
 // sign bit of the OR of the four values.  The samples are visited from 15 down
 // to 0, so that each sign bit enters the mask with one funnel shift.
 __device__ __forceinline__ uint32_t fast_mask(const EntrySetup& E, int cx, int cy) {
-  const int dm = E.dm;
   int v[4], i1[4], i2[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int4 ed = *reinterpret_cast<const int4*>(&E.e[i]);
-    int t = ed.z + ed.x * cx + ed.y * cy;  // at sample 15
-    v[i] = min(max(t, -dm - 1), dm);
+    v[i] = ed.z + ed.x * cx + ed.y * cy;  // at sample 15
     i1[i] = ed.w;                 // sample row + 5
     i2[i] = ed.w - ed.y * 256;    // sample row - 11
   }
@@ -1004,14 +994,12 @@ __device__ __forceinline__ uint32_t fast_mask(const EntrySetup& E, int cx, int c
 // is covered iff one triangle has no failing edge there (same bounds as
 // fast_mask).
 __device__ __forceinline__ uint32_t fast_mask2(const EntrySetup& E, int cx, int cy) {
-  const int dm = E.dm;
   const uint32_t x1 = (uint32_t)E.e[5].A;
   int v[5], i1[5], i2[5];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     const int4 ed = *reinterpret_cast<const int4*>(&E.e[i]);
-    int t = ed.z + ed.x * cx + ed.y * cy;  // at sample 15
-    v[i] = min(max(t, -dm - 1), dm);
+    v[i] = ed.z + ed.x * cx + ed.y * cy;  // at sample 15
     i1[i] = ed.w;
     i2[i] = ed.w - ed.y * 256;
   }
