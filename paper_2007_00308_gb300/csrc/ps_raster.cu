@@ -526,8 +526,9 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
   // wh(Y0) = fma(-k, Y0, uh), so both kinds reduce with max.  Edges with A = 0
   // (horizontal, or the always-true edge) bound nothing here.  eps covers the
   // float rounding of k, u and the fma (a few 2^-24 relative to |u| + 4096 |k|).
-  float kq[6], uq[6];
-  uint32_t lo_side = 0;
+  // Each edge keeps ul and uh, the side it does not bound set to -inf, so that
+  // a row reduces both sides with one fma and one max each.
+  float kq[6], ul[6], uh[6];
   float k0 = 0.f, u0 = 0.f, eps0 = 0.f;
   bool apos0 = false, anz0 = false;
 #pragma unroll
@@ -555,14 +556,16 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
     }
     if (A > 0) {
       kq[i] = k;
-      uq[i] = u + fminf(0.f, k240) - eps;
-      lo_side |= 1u << i;
+      ul[i] = u + fminf(0.f, k240) - eps;
+      uh[i] = -INFINITY;
     } else if (A < 0) {
       kq[i] = -k;
-      uq[i] = -(u + fmaxf(0.f, k240) + eps);
+      ul[i] = -INFINITY;
+      uh[i] = -(u + fmaxf(0.f, k240) + eps);
     } else {
       kq[i] = 0.f;
-      uq[i] = -INFINITY;
+      ul[i] = -INFINITY;
+      uh[i] = -INFINITY;
     }
   }
   E.valid = cls | (a0 != 0 ? 1 : 0) | (a1 != 0 ? 2 : 0);
@@ -585,12 +588,12 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
     float k240 = 240.f * k0;
     if (lo5) {
       kq[5] = k0;
-      uq[5] = u0 + fminf(0.f, k240) - eps0;
-      lo_side |= 1u << 5;
+      ul[5] = u0 + fminf(0.f, k240) - eps0;
+      uh[5] = -INFINITY;
     } else {
       kq[5] = -k0;
-      uq[5] = -(u0 + fmaxf(0.f, k240) + eps0);
-      lo_side &= ~(1u << 5);
+      ul[5] = -INFINITY;
+      uh[5] = -(u0 + fmaxf(0.f, k240) + eps0);
     }
   }
   // row spans: group 0 = edges 0..3 (triangle 0 and, for a convex quad, the
@@ -610,15 +613,18 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
       float L0 = -INFINITY, M0 = -INFINITY, L1 = -INFINITY, M1 = -INFINITY;
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        float w = fmaf(kq[i], Yb, uq[i]);
-        bool lo = (lo_side >> i) & 1u;
-        bool g1 = i >= 4 || (i == 3 && e3g1);
-        if (g1) {
-          L1 = lo ? fmaxf(L1, w) : L1;
-          M1 = lo ? M1 : fmaxf(M1, w);
+        const float wl = fmaf(kq[i], Yb, ul[i]), wh = fmaf(kq[i], Yb, uh[i]);
+        if (i >= 4) {
+          L1 = fmaxf(L1, wl);
+          M1 = fmaxf(M1, wh);
+        } else if (i == 3) {
+          L1 = e3g1 ? fmaxf(L1, wl) : L1;
+          M1 = e3g1 ? fmaxf(M1, wh) : M1;
+          L0 = e3g1 ? L0 : fmaxf(L0, wl);
+          M0 = e3g1 ? M0 : fmaxf(M0, wh);
         } else {
-          L0 = lo ? fmaxf(L0, w) : L0;
-          M0 = lo ? M0 : fmaxf(M0, w);
+          L0 = fmaxf(L0, wl);
+          M0 = fmaxf(M0, wh);
         }
       }
       float lo0 = L0, hi0 = -M0, lo1 = L1, hi1 = -M1;
