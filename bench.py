@@ -219,15 +219,17 @@ def algorithmic(kernel, c):
 
 # ALU peak for the coverage kernel.  One sample test is one sample against one
 # quad.  The branch-free masks step every edge value from sample to sample with
-# one add and combine sign bits with three-input logic ops: a convex quad (or
-# single triangle) takes 4 adds + 2 logic ops + 1 op to gather the sign bit,
-# 7 lane ops; a non-convex quad (two triangles sharing the diagonal) 5 adds +
-# 3 logic ops + 2, 10 lane ops; the general path (edges over 1024 px) ~12.  The
-# SM issues at most 128 lane ops per clock (4 schedulers x 32 lanes).
-OPS_PER_TEST = {"convex_pixels": 7.0, "two_triangle_pixels": 10.0, "general_pixels": 12.0}
-# the crossing-rule mask (--exact): per sample and edge one add and a sign
-# gather (shift, or), 4 edges; its int32 form counts as "convex" pixels
-OPS_PER_TEST_EXACT = {"convex_pixels": 12.0, "two_triangle_pixels": 12.0, "general_pixels": 24.0}
+# one add, combine sign bits with three-input logic ops and shift the result's
+# sign bit into the mask with one funnel shift: a convex quad (or single
+# triangle) takes 4 adds + 2 logic ops + 1 shift, 7 lane ops; a non-convex quad
+# (two triangles sharing the diagonal) 5 adds + 3 logic ops + 1 shift, 9 lane
+# ops; the general path (edges over 1024 px) ~12.  The SM issues at most 128
+# lane ops per clock (4 schedulers x 32 lanes).
+OPS_PER_TEST = {"convex_pixels": 7.0, "two_triangle_pixels": 9.0, "general_pixels": 12.0}
+# the crossing-rule mask (--exact): per sample and edge one add and one funnel
+# shift of its sign bit, 4 edges (the y-range terms are per pixel); its int32
+# form counts as "convex" pixels
+OPS_PER_TEST_EXACT = {"convex_pixels": 8.0, "two_triangle_pixels": 8.0, "general_pixels": 24.0}
 
 
 def ops_per_test(rstat, exact=False):
@@ -244,8 +246,8 @@ def alu_peak_tests(sm_mhz, ops):
 
 # DRAM traffic of one k_coverage launch per bin entry, from the ncu capture in
 # profiles/k_coverage_c2_1000paths.md (dram__bytes_read.sum + write.sum =
-# 124.1 MB over 8,351,880 bin entries); scaled to the launch by its bin entries.
-COVERAGE_TRAFFIC_PER_PAIR = (117.453568e6 + 6.680320e6) / 8351880
+# 124.0 MB over 8,351,880 bin entries); scaled to the launch by its bin entries.
+COVERAGE_TRAFFIC_PER_PAIR = (117.496576e6 + 6.497792e6) / 8351880
 
 
 AUTOTUNE = True
