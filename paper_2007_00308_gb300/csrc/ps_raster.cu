@@ -110,7 +110,12 @@ __device__ __forceinline__ bool quad_meets_tile(const QuadFix& q, bool small, in
 // per lane, and flattens their (quad, candidate) pairs with a warp scan so that
 // each lane tests one pair at a time; lanes of the warp that hit the same tile
 // are grouped: one atomic per group.
+// Per-quad word from the count pass for the scatter pass: 0 = no tile; bit 31
+// with the tile index below it = the quad's bounding box lies in that one tile
+// (the scatter pass then skips the quad's ribs); HITS_RETEST = more than 31
+// candidate tiles (retested); otherwise the hit mask over the candidates.
 constexpr uint32_t HITS_RETEST = 0xffffffffu;
+constexpr uint32_t HITS_DIRECT = 0x80000000u;
 constexpr int BIN_NT = 256;
 
 struct BinQuad {
@@ -139,7 +144,10 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
   int64_t stride = (int64_t)gridDim.x * BIN_NT;
   for (int64_t base = (int64_t)blockIdx.x * BIN_NT; base < R; base += stride) {
     const int64_t r = base + threadIdx.x;
-    const bool act = r >= 1 && r < R && !(__ldg(tag + r) & PS_TAG_LINK_START);
+    const bool in = r >= 1 && r < R;
+    const uint32_t h = PASS == 1 && in ? __ldg(hits + r) : 0u;
+    const bool direct1 = PASS == 1 && (h & HITS_DIRECT) && h != HITS_RETEST;
+    const bool act = PASS == 0 ? in && !(__ldg(tag + r) & PS_TAG_LINK_START) : h != 0u && !direct1;
     BinQuad& Q = wq[lane];
     int cnt = 0;
     Q.n = 0;
@@ -168,9 +176,8 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
           Q.n = Q.ntx * (ty1 - ty0 + 1);
           Q.small = mxx - mnx < (1 << 14) && mxy - mny < (1 << 14);
           if (PASS == 1) {
-            uint32_t m = __ldg(hits + r);
-            Q.mask = m;
-            cnt = Q.n <= 31 ? __popc(m) : Q.n;
+            Q.mask = h;
+            cnt = Q.n <= 31 ? __popc(h) : Q.n;
           } else {
             cnt = Q.n;
           }
@@ -179,8 +186,9 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
     }
     // a quad whose bounding box lies in one tile meets that tile: binned in one
     // direct round, outside the flattened (quad, candidate) loop
+    int tdir = Q.n == 1 ? Q.ty0 * tiles_x + Q.tx0 : -1;
+    if (direct1) tdir = (int)(h & ~HITS_DIRECT);
     {
-      const int tdir = Q.n == 1 ? Q.ty0 * tiles_x + Q.tx0 : -1;
       if (Q.n == 1) {
         cnt = 0;
         if (PASS == 0) Q.mask = 1u;
@@ -259,7 +267,10 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
       }
     }
     __syncwarp();
-    if (PASS == 0 && act) hits[r] = Q.n <= 31 ? Q.mask : HITS_RETEST;
+    if (PASS == 0 && in)
+      hits[r] = !act ? 0u
+                : Q.n == 1 ? HITS_DIRECT | (uint32_t)tdir
+                : Q.n <= 31 ? Q.mask : HITS_RETEST;
     __syncwarp();
   }
 }
