@@ -624,7 +624,10 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
       float L0 = -INFINITY, M0 = -INFINITY, L1 = -INFINITY, M1 = -INFINITY;
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
-        const float wl = fmaf(kq[i], Yb, ul[i]), wh = fmaf(kq[i], Yb, uh[i]);
+        // both bounds in one packed fma (each lane of it rounds as fmaf does)
+        const float2 w2 = __ffma2_rn(make_float2(kq[i], kq[i]), make_float2(Yb, Yb),
+                                     make_float2(ul[i], uh[i]));
+        const float wl = w2.x, wh = w2.y;
         if (i >= 4) {
           L1 = fmaxf(L1, wl);
           M1 = fmaxf(M1, wh);
