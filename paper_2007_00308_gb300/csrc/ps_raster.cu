@@ -641,19 +641,18 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
           M0 = fmaxf(M0, wh);
         }
       }
-      float lo0 = L0, hi0 = -M0, lo1 = L1, hi1 = -M1;
-      bool ok0 = lo0 <= hi0, ok1 = two && lo1 <= hi1;
-      float lo = ok0 ? (ok1 ? fminf(lo0, lo1) : lo0) : lo1;
-      float hi = ok0 ? (ok1 ? fmaxf(hi0, hi1) : hi0) : hi1;
-      if (ok0 || ok1) {
-        lo = fmaxf(lo, -1e9f);
-        hi = fminf(hi, 1e9f);
-        int pa = max(0, (int)ceilf((lo - 240.f) * (1.f / 256.f)));
-        int pb = min(tw - 1, (int)floorf(hi * (1.f / 256.f)));
-        if (pb >= pa) {
-          aj = pa;
-          wj = pb - pa + 1;
-        }
+      const float hi0 = -M0, hi1 = -M1;
+      const bool ok0 = L0 <= hi0, ok1 = two && L1 <= hi1;
+      // union of the groups' extents (an empty group adds nothing); the
+      // float-to-int conversions saturate, so an unbounded side (+-inf) gives
+      // pixel 0 or tw - 1 and an empty row gives pb < pa
+      const float lo = fminf(ok0 ? L0 : INFINITY, ok1 ? L1 : INFINITY);
+      const float hi = fmaxf(ok0 ? hi0 : -INFINITY, ok1 ? hi1 : -INFINITY);
+      const int pa = max(0, __float2int_ru((lo - 240.f) * (1.f / 256.f)));
+      const int pb = min(tw - 1, __float2int_rd(hi * (1.f / 256.f)));
+      if (pb >= pa) {
+        aj = pa;
+        wj = pb - pa + 1;
       }
       E.x0[j] = (uint8_t)aj;
     }
