@@ -27,15 +27,16 @@ struct QuadFix {
 __device__ __forceinline__ bool snap_quad(const float4 a, const float4 b, QuadFix& q) {
   float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
   int s[8];
+  bool ok = true;  // one test at the end (NaN fails it too)
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     float f = v[i] * 256.f;  // exact scaling by a power of two
-    if (!(fabsf(f) < (float)COORD_LIMIT)) return false;
+    ok &= fabsf(f) < (float)COORD_LIMIT;
     s[i] = __float2int_rn(f);  // round half to even
   }
   q.x[0] = s[0]; q.y[0] = s[1]; q.x[1] = s[2]; q.y[1] = s[3];
   q.x[2] = s[4]; q.y[2] = s[5]; q.x[3] = s[6]; q.y[3] = s[7];
-  return true;
+  return ok;
 }
 
 // Pixel range whose sample window [256p + 8, 256p + 248] meets [lo, hi].
@@ -565,19 +566,11 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
       apos0 = A > 0;
       anz0 = A != 0;
     }
-    if (A > 0) {
-      kq[i] = k;
-      ul[i] = u + fminf(0.f, k240) - eps;
-      uh[i] = -INFINITY;
-    } else if (A < 0) {
-      kq[i] = -k;
-      ul[i] = -INFINITY;
-      uh[i] = -(u + fmaxf(0.f, k240) + eps);
-    } else {
-      kq[i] = 0.f;
-      ul[i] = -INFINITY;
-      uh[i] = -INFINITY;
-    }
+    // branch-free: k and u are not finite when A = 0, and are not used then
+    const float lo_b = u + fminf(0.f, k240) - eps, hi_b = -(u + fmaxf(0.f, k240) + eps);
+    kq[i] = A > 0 ? k : (A < 0 ? -k : 0.f);
+    ul[i] = A > 0 ? lo_b : -INFINITY;
+    uh[i] = A < 0 ? hi_b : -INFINITY;
   }
   E.valid = cls | (a0 != 0 ? 1 : 0) | (a1 != 0 ? 2 : 0);
   if (two) {
@@ -591,21 +584,16 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
     E.e[5].A = (a0 > 0) == (a1 > 0) ? -1 : 0;
   }
   if (entry_rows(ymin, ymax, th, E) == 0) return 0;
-  if (two && anz0) {
+  {
     // slot 5 for spans: triangle 1's diagonal bound (e[0] reversed when the
     // triangles lie on opposite sides, else e[0] itself); a horizontal diagonal
-    // bounds no x and leaves slot 5 as the always-true edge
-    bool lo5 = ((a0 > 0) == (a1 > 0)) ? !apos0 : apos0;
-    float k240 = 240.f * k0;
-    if (lo5) {
-      kq[5] = k0;
-      ul[5] = u0 + fminf(0.f, k240) - eps0;
-      uh[5] = -INFINITY;
-    } else {
-      kq[5] = -k0;
-      ul[5] = -INFINITY;
-      uh[5] = -(u0 + fmaxf(0.f, k240) + eps0);
-    }
+    // bounds no x and leaves slot 5 as the always-true edge (branch-free)
+    const bool use5 = two && anz0;
+    const bool lo5 = ((a0 > 0) == (a1 > 0)) ? !apos0 : apos0;
+    const float k240 = 240.f * k0;
+    kq[5] = use5 ? (lo5 ? k0 : -k0) : kq[5];
+    ul[5] = use5 ? (lo5 ? u0 + fminf(0.f, k240) - eps0 : -INFINITY) : ul[5];
+    uh[5] = use5 ? (lo5 ? -INFINITY : -(u0 + fmaxf(0.f, k240) + eps0)) : uh[5];
   }
   // row spans: group 0 = edges 0..3 (triangle 0 and, for a convex quad, the
   // fourth edge), group 1 = edges 3..5 of the two-triangle form; union of groups
