@@ -490,23 +490,26 @@ constexpr uint32_t EL_TRI0_NEG = 0x8u | 0x6u << 4 | 0x1u << 8;   // 0->2 2->1 1-
 constexpr uint32_t EL_TRI1_POS = 0x8u | 0xEu << 4 | 0x3u << 8;   // 0->2 2->3 3->0
 constexpr uint32_t EL_TRI1_NEG = 0xCu | 0xBu << 4 | 0x2u << 8;   // 0->3 3->2 2->0
 
-// Setup of a quad whose extent is below 2^15 (128 px) on both axes: every
-// cross product of vertex differences is below 2^30 in magnitude and their
-// differences fit in int32; the fast-form constant A (8 - x) + B (8 - y) is
-// formed in int64 (|8 - x| < 2^15 + 4104, as the quad meets the tile) and
-// clamped into int32.  One code path serves all classes.
+// Setup of a quad whose extent is below 2^16 (256 px) on both axes: the cross
+// products of vertex differences are formed in int64, every edge has
+// |A| + |B| < 2^17 (inside the fast form's 2^18), and the fast-form constant
+// A (8 - x) + B (8 - y) is formed in int64 (|8 - x| < 2^16 + 4104, as the quad
+// meets the tile) and clamped into int32.  One code path serves all classes.
 __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax, int tw, int th,
                                            EntrySetup& E) {
   const int X0 = q.x[0], Y0 = q.y[0], X1 = q.x[1], Y1 = q.y[1];  // N0 P0
   const int X2 = q.x[3], Y2 = q.y[3], X3 = q.x[2], Y3 = q.y[2];  // P1 N1
-  int a0 = (X1 - X0) * (Y2 - Y0) - (Y1 - Y0) * (X2 - X0);          // N0 P0 P1
-  int a1 = (X2 - X0) * (Y3 - Y0) - (Y2 - Y0) * (X3 - X0);          // N0 P1 N1
+  auto cross = [](int ax, int ay, int bx, int by) {
+    return (long long)ax * by - (long long)ay * bx;
+  };
+  const long long a0 = cross(X1 - X0, Y1 - Y0, X2 - X0, Y2 - Y0);  // N0 P0 P1
+  const long long a1 = cross(X2 - X0, Y2 - Y0, X3 - X0, Y3 - Y0);  // N0 P1 N1
   if (a0 == 0 && a1 == 0) return 0;
   // turns at the four corners of N0 P0 P1 N1
-  int c0 = (X1 - X0) * (Y2 - Y1) - (Y1 - Y0) * (X2 - X1);
-  int c1 = (X2 - X1) * (Y3 - Y2) - (Y2 - Y1) * (X3 - X2);
-  int c2 = (X3 - X2) * (Y0 - Y3) - (Y3 - Y2) * (X0 - X3);
-  int c3 = (X0 - X3) * (Y1 - Y0) - (Y0 - Y3) * (X1 - X0);
+  const long long c0 = cross(X1 - X0, Y1 - Y0, X2 - X1, Y2 - Y1);
+  const long long c1 = cross(X2 - X1, Y2 - Y1, X3 - X2, Y3 - Y2);
+  const long long c2 = cross(X3 - X2, Y3 - Y2, X0 - X3, Y0 - Y3);
+  const long long c3 = cross(X0 - X3, Y0 - Y3, X1 - X0, Y1 - Y0);
   bool pos = c0 >= 0 && c1 >= 0 && c2 >= 0 && c3 >= 0;
   bool neg = c0 <= 0 && c1 <= 0 && c2 <= 0 && c3 <= 0;
   uint32_t el0 = a0 > 0 ? EL_TRI0_POS : EL_TRI0_NEG;
@@ -820,7 +823,7 @@ __device__ __forceinline__ int setup_edges(const float4 ra, const float4 rb, int
     int mxx = max(max(q.x[0], q.x[1]), max(q.x[2], q.x[3]));
     int mny = min(min(q.y[0], q.y[1]), min(q.y[2], q.y[3]));
     int mxy = max(max(q.y[0], q.y[1]), max(q.y[2], q.y[3]));
-    if (mxx - mnx < (1 << 15) && mxy - mny < (1 << 15)) {
+    if (mxx - mnx < (1 << 16) && mxy - mny < (1 << 16)) {
       int tot = setup_small(q, mny, mxy, tw, th, E);
       if (EXACT && tot > 0) store_exact(q, E);
       return tot;
