@@ -51,8 +51,28 @@ __device__ __forceinline__ void pix_range(int lo, int hi, int n, int& p0, int& p
 // Can triangle (x0,y0)-(x1,y1)-(x2,y2) cover a sample of the tile whose samples
 // lie in [rx0, rx1] x [ry0, ry1]?  Separating-axis test on the triangle's edges
 // (the rectangle's own axes are settled by the bounding-box range).
+// (Branch-free: a zero-area triangle meets nothing, and the vertices of a
+// clockwise one are swapped by selects.)
 __device__ __forceinline__ bool tri_meets_rect(int x0, int y0, int x1, int y1, int x2, int y2,
                                                int rx0, int ry0, int rx1, int ry1) {
+  const long long area = (long long)(x1 - x0) * (y2 - y0) - (long long)(y1 - y0) * (x2 - x0);
+  const bool cw = area < 0;
+  const int vx[3] = {x0, cw ? x2 : x1, cw ? x1 : x2}, vy[3] = {y0, cw ? y2 : y1, cw ? y1 : y2};
+  bool ok = area != 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    long long A = (long long)vy[i] - vy[(i + 1) % 3], B = (long long)vx[(i + 1) % 3] - vx[i];
+    // the rectangle corner maximizing A x + B y
+    long long cx = A >= 0 ? rx1 : rx0, cy = B >= 0 ? ry1 : ry0;
+    ok &= A * (cx - vx[i]) + B * (cy - vy[i]) >= 0;
+  }
+  return ok;
+}
+
+// Early-exit forms of the two tests (fewer registers: the scatter pass, which
+// re-tests only quads with more than 31 candidate tiles, keeps its occupancy).
+__device__ __forceinline__ bool tri_meets_rect_ee(int x0, int y0, int x1, int y1, int x2, int y2,
+                                                  int rx0, int ry0, int rx1, int ry1) {
   long long area = (long long)(x1 - x0) * (y2 - y0) - (long long)(y1 - y0) * (x2 - x0);
   if (area == 0) return false;
   if (area < 0) {
@@ -63,17 +83,13 @@ __device__ __forceinline__ bool tri_meets_rect(int x0, int y0, int x1, int y1, i
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     long long A = (long long)vy[i] - vy[(i + 1) % 3], B = (long long)vx[(i + 1) % 3] - vx[i];
-    // the rectangle corner maximizing A x + B y
     long long cx = A >= 0 ? rx1 : rx0, cy = B >= 0 ? ry1 : ry0;
     if (A * (cx - vx[i]) + B * (cy - vy[i]) < 0) return false;
   }
   return true;
 }
-
-// Same test in int32, for triangles whose extent is below 2^14 on both axes
-// and rectangles within 2^14 + 4096 of them: every product stays below 2^29.
-__device__ __forceinline__ bool tri_meets_rect32(int x0, int y0, int x1, int y1, int x2, int y2,
-                                                 int rx0, int ry0, int rx1, int ry1) {
+__device__ __forceinline__ bool tri_meets_rect32_ee(int x0, int y0, int x1, int y1, int x2, int y2,
+                                                    int rx0, int ry0, int rx1, int ry1) {
   int area = (x1 - x0) * (y2 - y0) - (y1 - y0) * (x2 - x0);
   if (area == 0) return false;
   if (area < 0) {
@@ -90,17 +106,42 @@ __device__ __forceinline__ bool tri_meets_rect32(int x0, int y0, int x1, int y1,
   return true;
 }
 
+// Same test in int32, for triangles whose extent is below 2^14 on both axes
+// and rectangles within 2^14 + 4096 of them: every product stays below 2^29.
+__device__ __forceinline__ bool tri_meets_rect32(int x0, int y0, int x1, int y1, int x2, int y2,
+                                                 int rx0, int ry0, int rx1, int ry1) {
+  const int area = (x1 - x0) * (y2 - y0) - (y1 - y0) * (x2 - x0);
+  const bool cw = area < 0;
+  const int vx[3] = {x0, cw ? x2 : x1, cw ? x1 : x2}, vy[3] = {y0, cw ? y2 : y1, cw ? y1 : y2};
+  bool ok = area != 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    int A = vy[i] - vy[(i + 1) % 3], B = vx[(i + 1) % 3] - vx[i];
+    int cx = A >= 0 ? rx1 : rx0, cy = B >= 0 ? ry1 : ry0;
+    ok &= A * (cx - vx[i]) + B * (cy - vy[i]) >= 0;
+  }
+  return ok;
+}
+
 // Does quad q (triangles N0 P0 P1 and N0 P1 N1) meet tile (tx, ty)'s sample
-// rectangle, clipped to the canvas?
+// rectangle, clipped to the canvas?  BF: the branch-free tests.
+template <bool BF>
 __device__ __forceinline__ bool quad_meets_tile(const QuadFix& q, bool small, int tx, int ty,
                                                 int W, int H) {
   int rx0 = tx * TILE_UNITS + 8, ry0 = ty * TILE_UNITS + 8;
   int rx1 = min(tx * TILE_UNITS + TILE_UNITS, W * 256) - 8;
   int ry1 = min(ty * TILE_UNITS + TILE_UNITS, H * 256) - 8;
+  if (!BF) {
+    if (small)
+      return tri_meets_rect32_ee(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], rx0, ry0, rx1, ry1) ||
+             tri_meets_rect32_ee(q.x[0], q.y[0], q.x[3], q.y[3], q.x[2], q.y[2], rx0, ry0, rx1, ry1);
+    return tri_meets_rect_ee(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], rx0, ry0, rx1, ry1) ||
+           tri_meets_rect_ee(q.x[0], q.y[0], q.x[3], q.y[3], q.x[2], q.y[2], rx0, ry0, rx1, ry1);
+  }
   if (small)
-    return tri_meets_rect32(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], rx0, ry0, rx1, ry1) ||
+    return tri_meets_rect32(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], rx0, ry0, rx1, ry1) |
            tri_meets_rect32(q.x[0], q.y[0], q.x[3], q.y[3], q.x[2], q.y[2], rx0, ry0, rx1, ry1);
-  return tri_meets_rect(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], rx0, ry0, rx1, ry1) ||
+  return tri_meets_rect(q.x[0], q.y[0], q.x[1], q.y[1], q.x[3], q.y[3], rx0, ry0, rx1, ry1) |
          tri_meets_rect(q.x[0], q.y[0], q.x[3], q.y[3], q.x[2], q.y[2], rx0, ry0, rx1, ry1);
 }
 
@@ -243,7 +284,7 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
             q.x[v] = B.x[v];
             q.y[v] = B.y[v];
           }
-          hit = B.n == 1 || quad_meets_tile(q, B.small != 0, tx, ty, W, H);
+          hit = B.n == 1 || quad_meets_tile<PASS == 0>(q, B.small != 0, tx, ty, W, H);
         }
         if (hit) {
           t = (B.ty0 + i / B.ntx) * tiles_x + (B.tx0 + i % B.ntx);
@@ -1470,9 +1511,14 @@ static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
   // tiles without entries are never visited by the coverage kernel
   cudaMemsetAsync(d_canvas, 0, sizeof(uint16_t) * (size_t)width * (size_t)height, st);
   cudaMemsetAsync(ctx->d_scratch64, 0, 7 * sizeof(int64_t), st);
+  // persistent grids, each pass at its own occupancy (the count pass holds more
+  // registers)
   int grid_bin = ctx->tune[PS_TUNE_BIN_BLOCKS] > 0
                      ? ctx->num_sms * ctx->tune[PS_TUNE_BIN_BLOCKS]
                      : ps_persistent_grid(ctx, (const void*)k_bin<0>, BIN_NT, 0);
+  int grid_bin1 = ctx->tune[PS_TUNE_BIN_BLOCKS] > 0
+                      ? grid_bin
+                      : ps_persistent_grid(ctx, (const void*)k_bin<1>, BIN_NT, 0);
   const float4* rib = reinterpret_cast<const float4*>(d_rib);
   { ProfScope ps_(ctx, PK_BIN_COUNT, st);
   k_bin<0><<<grid_bin, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, tiles_x,
@@ -1486,7 +1532,7 @@ static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
                                          ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
                                          ctx->d_status); }
   { ProfScope ps_(ctx, PK_BIN_SCATTER, st);
-  k_bin<1><<<grid_bin, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, tiles_x,
+  k_bin<1><<<grid_bin1, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, tiles_x,
                                       ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor,
                                       ctx->d_bin, ctx->pair_cap, ctx->d_quad_hits,
                                       ctx->d_status); }
