@@ -1378,16 +1378,13 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
             __syncwarp();
             const int it = it0 + lane;
             if (it < total) {
+              // branch-free: the owner table is read at p = 0 when no start
+              // lies at or before this lane (and not used then)
               const uint32_t sm = starts & ((2u << lane) - 1u);
-              int e, first;
-              if (sm) {
-                const int p = 31 - __clz(sm);
-                e = s_own[wid][p];
-                first = it0 + p;
-              } else {
-                e = ebase;
-                first = pebase;
-              }
+              const int p = sm ? 31 - __clz(sm) : 0;
+              const int eo = s_own[wid][p];
+              const int e = sm ? eo : ebase;
+              const int first = sm ? it0 + p : pebase;
               const EntrySetup& E = my[e];
               const int li = it - first;
               int k = 0;
