@@ -1387,11 +1387,22 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
               const int first = sm ? it0 + p : pebase;
               const EntrySetup& E = my[e];
               const int li = it - first;
-              int k = 0;
-#pragma unroll
-              for (int st = 8; st > 0; st >>= 1)
-                if ((int)E.rowpre[k + st] <= li) k += st;
-              const int ly = E.row0 + k, lx = E.x0[k] + (li - (int)E.rowpre[k]);
+              // the item's row: the last k with rowpre[k] <= li, as a binary
+              // search in two rounds of three independent loads
+              const int r4 = E.rowpre[4], r8 = E.rowpre[8], r12 = E.rowpre[12];
+              int k = r8 <= li ? 8 : 0;
+              const int rk0 = k ? r8 : 0;
+              const int rk4 = k ? r12 : r4;
+              const bool s4 = rk4 <= li;
+              k += s4 ? 4 : 0;
+              const int rb = s4 ? rk4 : rk0;  // rowpre[k]
+              const int q1 = E.rowpre[k + 1], q2 = E.rowpre[k + 2], q3 = E.rowpre[k + 3];
+              const bool s2 = q2 <= li;
+              const int rodd = s2 ? q3 : q1;  // rowpre[k + 2 s2 + 1]
+              const bool s1 = rodd <= li;
+              const int pre = s1 ? rodd : (s2 ? q2 : rb);
+              k += (s2 ? 2 : 0) + (s1 ? 1 : 0);
+              const int ly = E.row0 + k, lx = E.x0[k] + (li - pre);
               uint32_t m;
               if (EXACT)
                 m = cls == 0 ? exact_mask(E, lx * 256, ly * 256, s_rowmask)
