@@ -511,10 +511,12 @@ __device__ __forceinline__ void to_fast_edge(Edge& ed) {
 }
 
 // Pixel rows whose sample band [256 ly + 8, 256 ly + 248] meets [ymin, ymax].
+// (ymin, ymax are tile-relative: snapped coordinates and tile origins are both
+// below 2^29 in magnitude, so int32 holds every step.)
 __device__ __forceinline__ int entry_rows(int ymin, int ymax, int th, EntrySetup& E) {
-  int64_t c0 = ceil256((int64_t)ymin - 248), c1 = floor256((int64_t)ymax - 8);
-  int ly0 = (int)(c0 < 0 ? 0 : c0);
-  int ly1 = (int)(c1 > th - 1 ? th - 1 : c1);
+  const int c0 = -((248 - ymin) >> 8), c1 = (ymax - 8) >> 8;  // ceil, floor of / 256
+  int ly0 = c0 < 0 ? 0 : c0;
+  int ly1 = c1 > th - 1 ? th - 1 : c1;
   if (ly1 < ly0) return 0;
   E.row0 = (uint8_t)ly0;
   E.nrow = (uint8_t)(ly1 - ly0 + 1);
@@ -555,25 +557,19 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
   bool neg = c0 <= 0 && c1 <= 0 && c2 <= 0 && c3 <= 0;
   uint32_t el0 = a0 > 0 ? EL_TRI0_POS : EL_TRI0_NEG;
   uint32_t el1 = a1 > 0 ? EL_TRI1_POS : EL_TRI1_NEG;
-  uint32_t el;
-  uint8_t cls;
-  if (a0 != 0 && a1 != 0 && (pos || neg)) {
-    el = pos ? EL_CONVEX_POS : EL_CONVEX_NEG;
-    cls = 8 | 32;
-  } else if (a0 != 0 && a1 != 0) {
-    // diagonal first (as triangle 0 orients it), then the other two edges of
-    // each triangle; slot 5 unused
-    uint32_t d0 = a0 > 0 ? 0x2u : 0x8u;            // 2->0 or 0->2
-    uint32_t t0 = a0 > 0 ? (0x4u | 0x9u << 4)      // 0->1 1->2
-                         : (0x6u | 0x1u << 4);     // 2->1 1->0
-    uint32_t t1 = a1 > 0 ? (0xEu | 0x3u << 4)      // 2->3 3->0
-                         : (0xCu | 0xBu << 4);     // 0->3 3->2
-    el = d0 | t0 << 4 | t1 << 12;
-    cls = 64;
-  } else {
-    el = a0 != 0 ? el0 : el1;
-    cls = 32;
-  }
+  // class and edge list by selects: a convex quad, two triangles (diagonal
+  // first, as triangle 0 orients it, then the other two edges of each
+  // triangle; slot 5 unused), or the one real triangle
+  const bool both = a0 != 0 && a1 != 0, convex = both && (pos || neg);
+  const uint32_t d0 = a0 > 0 ? 0x2u : 0x8u;            // 2->0 or 0->2
+  const uint32_t t0 = a0 > 0 ? (0x4u | 0x9u << 4)      // 0->1 1->2
+                             : (0x6u | 0x1u << 4);     // 2->1 1->0
+  const uint32_t t1 = a1 > 0 ? (0xEu | 0x3u << 4)      // 2->3 3->0
+                             : (0xCu | 0xBu << 4);     // 0->3 3->2
+  const uint32_t el = convex ? (pos ? EL_CONVEX_POS : EL_CONVEX_NEG)
+                      : both ? (d0 | t0 << 4 | t1 << 12)
+                             : (a0 != 0 ? el0 : el1);
+  const uint8_t cls = convex ? (8 | 32) : both ? 64 : 32;
   const bool two = cls == 64;
   // Per edge, the line A X + B Y + C' = 0 (X = x - 8, Y = y - 8) as X = k Y + u.
   // An edge with A > 0 bounds X from below: over a row's sample band
@@ -1431,12 +1427,10 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
         unsigned c = 0;
 #pragma unroll
         for (int w = lane; w < MASK_WORDS; w += 32) {
-          uint32_t v = ms[w];
-          if (v) {
-            ms[w] = 0u;
-            c += __popc(v);
-            atomicOr(&s_canvas[w], v);
-          }
+          const uint32_t v = ms[w];
+          ms[w] = 0u;
+          c += __popc(v);
+          if (v) atomicOr(&s_canvas[w], v);
         }
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if (lane == 0 && c) {
