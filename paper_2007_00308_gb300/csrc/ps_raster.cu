@@ -583,13 +583,16 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
   float kq[6], ul[6], uh[6];
   float k0 = 0.f, u0 = 0.f, eps0 = 0.f;
   bool apos0 = false, anz0 = false;
+  // The polygon's vertices, parked in the entry's (not yet written) row
+  // prefixes so that each edge reads its end points by index instead of
+  // through chains of selects.
+  int* const vxs = reinterpret_cast<int*>(E.rowpre);      // 4 x, then 4 y (32 bytes)
+  reinterpret_cast<int4*>(E.rowpre)[0] = make_int4(X0, X1, X2, X3);
+  reinterpret_cast<int4*>(E.rowpre)[1] = make_int4(Y0, Y1, Y2, Y3);
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     int ia = (el >> (4 * i)) & 3, ib = (el >> (4 * i + 2)) & 3;
-    int xa = ia == 0 ? X0 : ia == 1 ? X1 : ia == 2 ? X2 : X3;
-    int ya = ia == 0 ? Y0 : ia == 1 ? Y1 : ia == 2 ? Y2 : Y3;
-    int xb = ib == 0 ? X0 : ib == 1 ? X1 : ib == 2 ? X2 : X3;
-    int yb = ib == 0 ? Y0 : ib == 1 ? Y1 : ib == 2 ? Y2 : Y3;
+    int xa = vxs[ia], ya = vxs[4 + ia], xb = vxs[ib], yb = vxs[4 + ib];
     int A = ya - yb, B = xb - xa, S = abs(A) + abs(B);
     long long c64 = (long long)A * (8 - xa) + (long long)B * (8 - ya);
     int lim = 4080 * S + 1;
