@@ -790,8 +790,9 @@ __device__ __forceinline__ uint32_t exact_yrange(int lo, int hi, int base,
 }
 
 // Fast exact mask: the four sign-normalised edge values stepped from sample to
-// sample as in fast_mask (same clamp and int32 bounds), one sign mask per edge,
-// each limited to its edge's y-range; the parity of the crossings.
+// sample as in fast_mask (the same clamped C', C15 and int32 bounds), one sign
+// mask per edge, each limited to its edge's y-range; the parity of the
+// crossings.
 __device__ __forceinline__ uint32_t exact_mask(const EntrySetup& E, int cx, int cy,
                                                const uint16_t* __restrict__ rowmask) {
   int v[4], i1[4], i2[4];
