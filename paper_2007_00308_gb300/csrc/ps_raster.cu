@@ -1322,6 +1322,10 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
             if (prev == 0u) break;
             h = (h + 1) & (HKEYS - 1);
           }
+          // a full table (more than HKEYS paths on the tile) leaves the path
+          // without a slot; a slot never published ends the bounded wait above
+          if (slot < 0) ps_record_error(status, PS_ERR_CAPACITY);
+          else if (slot >= HKEYS) ps_record_error(status, PS_ERR_TIMEOUT);
         }
         slot = __shfl_sync(0xffffffffu, slot, leader);
         unsigned long long packed = 0;

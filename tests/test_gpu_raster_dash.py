@@ -154,3 +154,36 @@ def test_capped_dash_matches_oracle_on_gpu_ribs(cap):
     ocan, ocov = oracle.raster(grib, gtag, 512, 512, 1)
     assert np.array_equal(can.cpu().numpy().view(np.uint16), ocan)
     assert int(cov.item()) == int(ocov[0])
+
+
+@pytest.mark.parametrize("n_paths", [1000, 1100])
+def test_tile_path_limit(n_paths):
+    """One 16x16 tile met by n_paths distinct paths: up to 1,024 the coverage
+    kernel takes them in passes of 96 (every per-path count bit-exact against the
+    oracle's raster of the GPU's vertices); beyond that it records
+    PS_ERR_CAPACITY instead of dropping paths silently."""
+    import torch
+    import paper_2007_00308_gb300 as ps
+    rng = np.random.default_rng(n_paths)
+    a = rng.uniform(1.0, 6.0, (n_paths, 2))
+    d = rng.uniform(10.0, 15.0, (n_paths, 2))
+    pts = np.zeros((n_paths, 4, 2))
+    pts[:, 0], pts[:, 1], pts[:, 2], pts[:, 3] = a, a, d, d
+    pts = np.round(pts * 64) / 64
+    b = W.make_batch("tile_limit", [W.LINE] * n_paths, pts, [1.0] * n_paths, [1] * n_paths,
+                     rng.uniform(0.5, 2.0, n_paths), W.JOIN_ROUND, W.CAP_BUTT, canvas=(16, 16))
+    g = gpu_tessellate(b, 1)
+    ctx, out = g["ctx"], g["out"]
+    canvas = torch.zeros((16, 16), dtype=torch.int16, device="cuda")
+    covered = torch.zeros(n_paths, dtype=torch.int64, device="cuda")
+    ps.ps_rasterize_coverage(ctx, out.rib, out.tag, out.n_rib, out.capacity, n_paths, 16, 16,
+                             canvas, covered)
+    torch.cuda.synchronize()
+    st = ctx.status()
+    if n_paths <= 1024:
+        assert st == ps.PS_OK
+        ocan, ocov = oracle.raster(g["rib"], g["tag"], 16, 16, n_paths)
+        assert np.array_equal(canvas.cpu().numpy().view(np.uint16), ocan)
+        assert np.array_equal(covered.cpu().numpy().view(np.uint64), ocov)
+    else:
+        assert st == ps.PS_ERR_CAPACITY
