@@ -246,8 +246,8 @@ def alu_peak_tests(sm_mhz, ops):
 
 # DRAM traffic of one k_coverage launch per bin entry, from the ncu capture in
 # profiles/k_coverage_c2_1000paths.md (dram__bytes_read.sum + write.sum =
-# 124.2 MB over 8,351,880 bin entries); scaled to the launch by its bin entries.
-COVERAGE_TRAFFIC_PER_PAIR = (117.595136e6 + 6.567168e6) / 8351880
+# 124.4 MB over 8,351,880 bin entries); scaled to the launch by its bin entries.
+COVERAGE_TRAFFIC_PER_PAIR = (117.652480e6 + 6.708736e6) / 8351880
 
 
 AUTOTUNE = True
