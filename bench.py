@@ -76,6 +76,9 @@ def max_over_ranks(value: float, device) -> float:
     return float(t.item())
 
 
+PG_TIMEOUT_S = 300
+
+
 def job_throughput(units_per_rank: int, world: int, max_ms: float) -> float:
     """Whole-job units/s: every rank processes its own batch (weak scaling)."""
     return world * units_per_rank / (max_ms * 1e-3)
@@ -704,10 +707,13 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if world > 1:
+        import datetime
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
-        dist.init_process_group("nccl")
+        # a rank that dies ends the others' next collective with an error within
+        # this time instead of holding the job (the timed work is about a minute)
+        dist.init_process_group("nccl", timeout=datetime.timedelta(seconds=PG_TIMEOUT_S))
     try:
         if args.workload != "c2":
             return run_config(args, rank, world, local_rank)

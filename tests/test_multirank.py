@@ -51,3 +51,44 @@ def test_single_process_passthrough():
     import bench
     assert bench.max_over_ranks(3.5, "cpu") == 3.5
     assert bench.job_throughput(100, 1, 10.0) == pytest.approx(1e4)
+
+
+def _dying_worker(rank, world, port, q):
+    import datetime
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+    import bench
+    dist.barrier()
+
+    def report(what):
+        q.put((rank, what))
+        q.close()
+        q.join_thread()  # flushed before the hard exit below
+
+    if rank == 1:
+        report("left")
+        os._exit(0)  # leaves between steps, before the timing collective
+    try:
+        bench.max_over_ranks(10.0, "cpu")
+        report("no error")
+    except Exception:
+        report("error")
+    os._exit(0)
+
+
+def test_a_rank_that_leaves_ends_the_timing_collective_with_an_error():
+    """Failure detection on the host: when one rank exits between steps, the
+    other's max-over-ranks collective raises within the process group's timeout
+    instead of waiting forever."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dying_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+    assert res == {0: "error", 1: "left"}
