@@ -64,3 +64,26 @@ def test_host_entry_points(library):
     assert library.ps_set_pixel_tolerance(None, 0.5) < 0
     library.ps_check_wait_timeout.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     assert library.ps_check_wait_timeout(None, 0, None) < 0
+
+
+def test_static_rib_bound_holds_on_the_workloads(library):
+    """ps_max_ribs (host only) bounds the oracle's rib count on samples of every
+    workload and on degenerate and pivot-heavy inputs: callers size their rib
+    buffers with it."""
+    import numpy as np
+    import oracle
+    from paper_2007_00308_gb300 import workloads as W
+    library.ps_max_ribs.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_float,
+                                    ctypes.POINTER(ctypes.c_int64)]
+    cusp = [[[0, 0], [1, 1], [0, 1], [1, 0]]]
+    batches = [W.c1_plain_small(), W.c2_batching(n_paths=200), W.c3_large_path(n_seg=300),
+               W.c4_precision(n=500), W.c5_differentiation(n_paths=8),
+               W.single([W.CUBIC], cusp, width=4.0, dtheta_deg=0.5),
+               W.single([W.CONIC], [[[0, 0], [50, 80], [50, 80], [100, 0]]], w=-0.9,
+                        width=6.0, dtheta_deg=1.0)]
+    for b in batches:
+        bound = ctypes.c_int64(0)
+        assert library.ps_max_ribs(len(b.seg_type), len(b.path_width), float(b.dtheta),
+                                   ctypes.byref(bound)) == 0
+        r = len(oracle.tessellate(b)["s"])
+        assert r <= bound.value, (b.name, r, bound.value)
