@@ -1,0 +1,31 @@
+"""The benchmark's roofline arithmetic on the CPU: the coverage kernel's lane
+ops per sample test for a pixel-class mix, the derived ALU peak, and the
+whole-job throughput of weak scaling."""
+import pytest
+
+import bench
+
+
+def test_ops_per_test_follow_the_pixel_mix():
+    mix = {"convex_pixels": 402330351, "two_triangle_pixels": 564822565, "general_pixels": 0}
+    ops = bench.ops_per_test(mix)
+    assert ops == pytest.approx((7 * 402330351 + 9 * 564822565) / 967152916)
+    assert 7.0 < ops < 9.0
+    assert bench.ops_per_test(mix, exact=True) == pytest.approx(8.0)
+    assert bench.ops_per_test({}) == bench.OPS_PER_TEST["general_pixels"]
+
+
+def test_derived_alu_peak():
+    # 152 SMs x 128 lane ops per clock at 2070 MHz, 8 ops per test
+    assert bench.alu_peak_tests(2070.0, 8.0) == pytest.approx(152 * 128 * 2070e6 / 8.0)
+    assert bench.alu_peak_tests(2070.0, 8.168) == pytest.approx(4.93e12, rel=2e-3)
+
+
+def test_coverage_traffic_per_entry_is_a_plausible_gather():
+    # DRAM bytes per bin entry from the capture: below the 40-byte gather of two
+    # ribs, a tag and a bin id (neighbouring entries share ribs in L2)
+    assert 4.0 < bench.COVERAGE_TRAFFIC_PER_PAIR < 40.0
+
+
+def test_weak_scaling_throughput():
+    assert bench.job_throughput(295431, 4, 17.29) == pytest.approx(4 * 295431 / 17.29e-3)
