@@ -191,11 +191,12 @@ int ps_tessellate_strokes(ps_context* ctx, const ps_segments* seg, const ps_path
 
 /* Allocation-free variant of ps_tessellate_strokes (the paper has no
  * counterpart; this is an interface for callers that cannot allocate device
- * memory when they stroke -- for example code running during a global-mode
- * stream capture, or under an allocator that owns the device's memory).
+ * memory when they stroke -- for example code running under an allocator that
+ * owns the device's memory budget, or code that must not block on, or fail
+ * in, an allocation partway through its work).
  * Same arguments, outputs and semantics as ps_tessellate_strokes, except:
  *   - no context: the workspace is a fixed array inside the library image
- *     (about 2.7 MB on every device that loads the library, kept until exit);
+ *     (about 4.0 MB on every device that loads the library, kept until exit);
  *     the call makes no cudaMalloc, cudaFree or other allocating call;
  *   - d_status: caller-owned device int32 that kernels set to the first
  *     PS_ERR_* they meet (the caller zeroes it and reads it back);

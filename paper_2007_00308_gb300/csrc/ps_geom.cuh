@@ -2,9 +2,13 @@
 // polynomial, interval construction, the t(psi) solve and rib evaluation.
 #pragma once
 
+#include "ps_df.cuh"
 #include "ps_internal.cuh"
 
 namespace ps {
+
+// sin, cos of k pi/256 as float pairs (df_sincos); one copy per translation unit
+static __device__ const float4 ps_sc_tab[512] = {PS_SINCOS_TABLE_VALUES};
 
 struct Seg {
   int type;
@@ -150,32 +154,9 @@ __device__ __forceinline__ float2 g_rel(const Seg& g, float t) {
 }
 
 // Compensated g(t) - A (PS_PREC_MIXED): the Bernstein sum of (P_i - A) in
-// double-float arithmetic -- every product and sum carried as an unevaluated
-// pair through error-free transformations (Dekker 1971; Knuth's TwoSum), the
-// pair rounded once at the end.  About ten times the flops of g_rel.
-struct DF {
-  float hi, lo;
-};
-__device__ __forceinline__ DF fast_two_sum(float a, float b) {
-  float s = a + b;
-  return DF{s, b - (s - a)};
-}
-__device__ __forceinline__ DF two_sum(float a, float b) {
-  float s = a + b;
-  float bb = s - a;
-  return DF{s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-  float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-  return fast_two_sum(p, e);
-}
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  DF s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
-}
-__device__ __forceinline__ float2 g_rel_comp(const Seg& g, float t) {
+// double-float arithmetic (ps_df.cuh) -- every product and sum carried as an
+// unevaluated pair through error-free transformations, at the float t.
+__device__ __forceinline__ DF2 g_rel_comp_df(const Seg& g, float t) {
   DF T{t, 0.f};
   DF U = two_sum(1.f, -t);
   DF x{0.f, 0.f}, y{0.f, 0.f};
@@ -207,18 +188,115 @@ __device__ __forceinline__ float2 g_rel_comp(const Seg& g, float t) {
       DF den = df_add(df_add(df_mul(U, U), wb), wd);
       x = df_add(df_mul(bx, wb), df_mul(dx, wd));
       y = df_add(df_mul(by, wb), df_mul(dy, wd));
+      // the quotient in double-float: q_hi, then the residual's quotient
       float inv = 1.f / den.hi;
-      // one Newton step of the quotient in double-float
-      DF qx{x.hi * inv, 0.f}, qy{y.hi * inv, 0.f};
-      DF rx = df_add(x, df_mul(DF{-qx.hi, 0.f}, den));
-      DF ry = df_add(y, df_mul(DF{-qy.hi, 0.f}, den));
-      return mk(qx.hi + rx.hi * inv, qy.hi + ry.hi * inv);
+      float qx = x.hi * inv, qy = y.hi * inv;
+      DF rx = df_sub(x, df_mul_f(den, qx));
+      DF ry = df_sub(y, df_mul_f(den, qy));
+      return DF2{fast_two_sum(qx, rx.hi * inv), fast_two_sum(qy, ry.hi * inv)};
     }
     default:
       x = df_mul(dx, T);
       y = df_mul(dy, T);
   }
-  return mk(x.hi + x.lo, y.hi + y.lo);
+  return DF2{x, y};
+}
+__device__ __forceinline__ float2 g_rel_comp(const Seg& g, float t) {
+  DF2 v = g_rel_comp_df(g, t);
+  return mk(df_f(v.x), df_f(v.y));
+}
+
+// g'(t) in FP32: c(t) H(t) with c = 3 (cubic), 2 (quadratic), 2/den^2 (conic).
+__device__ __forceinline__ float2 deriv_f(const Seg& g, float t) {
+  float2 H = hodo(g, t);
+  switch (g.type) {
+    case PS_CUBIC: return H * 3.f;
+    case PS_QUAD: return H * 2.f;
+    case PS_CONIC: {
+      float u = 1.f - t, s = 1.f - 2.f * t;
+      float den = s * s + 2.f * (1.f + g.w) * u * t;
+      return H * (2.f / (den * den));
+    }
+    default: return H;
+  }
+}
+
+// g(t) - A at a double-float t: the compensated sum at t.hi plus g'(t.hi) t.lo
+// (|t.lo| <= 2^-25 t.hi, so the second-order term is below 1e-15 of g'').
+__device__ __forceinline__ DF2 g_rel_df(const Seg& g, DF t) {
+  DF2 v = g_rel_comp_df(g, t.hi);
+  if (t.lo != 0.f) {
+    float2 d = deriv_f(g, t.hi);
+    v.x = df_add_f(v.x, d.x * t.lo);
+    v.y = df_add_f(v.y, d.y * t.lo);
+  }
+  return v;
+}
+
+// The control-point differences of Table 1's end gradients, exactly, as pairs.
+__device__ __forceinline__ DF2 df_vec(float2 b, float2 a) {
+  return DF2{two_sum(b.x, -a.x), two_sum(b.y, -a.y)};
+}
+__device__ __forceinline__ DF2 df_scale_sign(DF2 v, float s) {
+  return s < 0.f ? DF2{df_neg(v.x), df_neg(v.y)} : v;
+}
+__device__ __forceinline__ DF2 end_grad0_df(const Seg& g) {
+  switch (g.type) {
+    case PS_CUBIC:
+      if (!is0(g.B - g.A)) return df_vec(g.B, g.A);
+      if (!is0(g.C - g.A)) return df_vec(g.C, g.A);
+      return df_vec(g.D, g.A);
+    case PS_QUAD:
+      return !is0(g.B - g.A) ? df_vec(g.B, g.A) : df_vec(g.D, g.A);
+    case PS_CONIC:
+      if (!is0(g.B - g.A) && g.w != 0.f) return df_scale_sign(df_vec(g.B, g.A), g.w);
+      return df_vec(g.D, g.A);
+    default:
+      return df_vec(g.D, g.A);
+  }
+}
+__device__ __forceinline__ DF2 end_grad1_df(const Seg& g) {
+  switch (g.type) {
+    case PS_CUBIC:
+      if (!is0(g.D - g.C)) return df_vec(g.D, g.C);
+      if (!is0(g.D - g.B)) return df_vec(g.D, g.B);
+      return df_vec(g.D, g.A);
+    case PS_QUAD:
+      return !is0(g.D - g.B) ? df_vec(g.D, g.B) : df_vec(g.D, g.A);
+    case PS_CONIC:
+      if (!is0(g.D - g.B) && g.w != 0.f) return df_scale_sign(df_vec(g.D, g.B), g.w);
+      return df_vec(g.D, g.A);
+    default:
+      return df_vec(g.D, g.A);
+  }
+}
+
+// Hodograph direction H(t) in double-float at a float t (differences exact).
+__device__ __forceinline__ DF2 hodo_df(const Seg& g, float t) {
+  DF T{t, 0.f};
+  DF U = two_sum(1.f, -t);
+  DF2 d0, d1, d2;
+  DF b0, b1, b2;
+  switch (g.type) {
+    case PS_CUBIC:
+      d0 = df_vec(g.B, g.A); d1 = df_vec(g.C, g.B); d2 = df_vec(g.D, g.C);
+      b0 = df_mul(U, U); b1 = df_mul_f(df_mul(U, T), 2.f); b2 = two_prod(t, t);
+      break;
+    case PS_QUAD:
+      d0 = df_vec(g.B, g.A); d1 = df_vec(g.D, g.B); d2 = DF2{{0.f, 0.f}, {0.f, 0.f}};
+      b0 = U; b1 = T; b2 = DF{0.f, 0.f};
+      break;
+    case PS_CONIC:
+      d0 = df_vec(g.B, g.A); d1 = df_vec(g.D, g.A); d2 = df_vec(g.D, g.B);
+      b0 = df_mul_f(df_mul(U, U), g.w); b1 = df_mul(U, T); b2 = df_mul_f(two_prod(t, t), g.w);
+      break;
+    default:
+      return df_vec(g.D, g.A);
+  }
+  DF2 r;
+  r.x = df_add(df_add(df_mul(d0.x, b0), df_mul(d1.x, b1)), df_mul(d2.x, b2));
+  r.y = df_add(df_add(df_mul(d0.y, b0), df_mul(d1.y, b1)), df_mul(d2.y, b2));
+  return r;
 }
 
 }  // namespace ps

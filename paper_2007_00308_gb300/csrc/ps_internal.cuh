@@ -22,8 +22,10 @@
 enum { LK_EMPTY = 0, LK_SEG = 1, LK_JOIN = 2, LK_CAP = 3 };
 
 // Per-link interval record written by the setup pass and read by the rib pass.
-// 160 bytes; at most 6 intervals (3 curvature-monotone intervals of a cubic,
-// each split once at pi -- Sec. 3.3.5), boundaries k = 0..M.
+// 240 bytes; at most 6 intervals (3 curvature-monotone intervals of a cubic,
+// each split once at pi -- Sec. 3.3.5), boundaries k = 0..M.  The *_lo fields
+// complete psi, p and step to double-float pairs (hi + lo) in PS_PREC_MIXED;
+// they are zero in PS_PREC_FP32.
 struct __align__(16) LinkRec {
   float2 P[4];        // control points (segment) / P[0] = pivot point (join, cap)
   float w;            // conic weight
@@ -35,8 +37,11 @@ struct __align__(16) LinkRec {
   uint16_t dsum[7];   // Delta_Sigma(k) (Eq. 13)
   uint16_t pad;
   float2 v1, v2;      // miter override vertices for ribs 1 and 2
+  float psi_lo[7];
+  float p_lo[7];
+  float step_lo[6];
 };
-static_assert(sizeof(LinkRec) == 160, "LinkRec layout");
+static_assert(sizeof(LinkRec) == 240, "LinkRec layout");
 
 #define META_KIND(m) ((m) & 3u)
 #define META_TYPE(m) (((m) >> 2) & 3u)

@@ -73,44 +73,15 @@ __device__ __forceinline__ void solve_coeffs(const Seg& g, V N, R& a, R& b, R& c
   }
 }
 
-// t(psi) in [pa, pb] (Sec. 3.4): roots of H(t).N(psi) = 0 inside the range (with a
-// small slack), the one whose tangent points along psi (largest H.T(psi)), else
-// the endpoint with the smaller |H.N|.  MIXED redoes near-double roots in FP64.
-template <bool MIXED>
-__device__ float solve_t(const Seg& g, float psi, float sn, float cs, float pa, float pb) {
-  if (g.type == PS_LINE) return pa;
+// t(psi) in [pa, pb] (Sec. 3.4) in FP32: roots of H(t).N(psi) = 0 inside the
+// range (with a small slack), the one whose tangent points along psi (largest
+// H.T(psi)), else the endpoint with the smaller |H.N|.  Returns whether a root
+// was taken, and the power-form coefficients for the caller's refinement.
+__device__ __forceinline__ bool solve_t32(const Seg& g, float sn, float cs, float pa, float pb,
+                                          float& t_out, float& a, float& b, float& c) {
   float2 N = mk(-sn, cs), T = mk(cs, sn);
-  float a, b, c;
   solve_coeffs<float>(g, N, a, b, c);
   float disc = b * b - 4.f * a * c, scale = b * b + fabsf(4.f * a * c);
-  if (MIXED && c != 0.f && fabsf(disc) < 1e-3f * scale) {
-    // near a double root: coefficients, discriminant and roots in FP64 from the
-    // FP32 normal (its rounding moves the rib along the curve by ~rho 1e-7, far
-    // inside the angle term of the vertex bound; the cancellation is what needs
-    // FP64)
-    const double sd = sn, cd = cs;
-    D2 Nd{-sd, cd};
-    double ad, bd, cd2;
-    solve_coeffs<double>(g, Nd, ad, bd, cd2);
-    double discd = bd * bd - 4.0 * ad * cd2, scaled = bd * bd + fabs(4.0 * ad * cd2);
-    double r[2];
-    int n = quad_roots<double>(ad, bd, cd2, discd, scaled, 1e-12, r);
-    double best = 0.0, bestv = -1e300;
-    bool found = false;
-    for (int i = 0; i < n; ++i) {
-      double t = r[i];
-      if (!(t >= (double)pa - 1e-9 && t <= (double)pb + 1e-9)) continue;
-      t = fmin(fmax(t, (double)pa), (double)pb);
-      D2 H = hodo_d64(g, t);
-      double v = H.x * cd + H.y * sd;
-      if (!found || v > bestv) {
-        bestv = v;
-        best = t;
-        found = true;
-      }
-    }
-    if (found) return (float)best;
-  }
   float r[2];
   int n = quad_roots<float>(a, b, c, disc, scale, 1e-5f, r);
   float best = 0.f, bestv = -3.0e38f;
@@ -126,16 +97,129 @@ __device__ float solve_t(const Seg& g, float psi, float sn, float cs, float pa, 
       found = true;
     }
   }
-  if (found) return best;
+  if (found) {
+    t_out = best;
+    return true;
+  }
   float fa = fabsf(dot2(hodo(g, pa), N)), fb = fabsf(dot2(hodo(g, pb), N));
-  return fa < fb ? pa : pb;
+  t_out = fa < fb ? pa : pb;
+  return false;
 }
 
-template <bool MIXED>
+__device__ __forceinline__ float solve_t(const Seg& g, float sn, float cs, float pa, float pb) {
+  if (g.type == PS_LINE) return pa;
+  float t, a, b, c;
+  solve_t32(g, sn, cs, pa, pb, t, a, b, c);
+  return t;
+}
+
 __device__ __forceinline__ float solve_t(const Seg& g, float psi, float pa, float pb) {
   float sn, cs;
   sincosf(psi, &sn, &cs);
-  return solve_t<MIXED>(g, psi, sn, cs, pa, pb);
+  return solve_t(g, sn, cs, pa, pb);
+}
+
+// The roots of H(t).N = 0 in FP64 from a double normal (the near-double-root
+// island of PS_PREC_MIXED: there the discriminant cancels).  Returns false when
+// no root lies in [pa, pb] (slack 1e-9).
+__device__ __noinline__ bool solve_t64(const Seg& g, double sn, double cs, double pa, double pb,
+                                       double& t_out) {
+  D2 Nd{-sn, cs};
+  double a, b, c;
+  solve_coeffs<double>(g, Nd, a, b, c);
+  double disc = b * b - 4.0 * a * c, scale = b * b + fabs(4.0 * a * c);
+  double r[2];
+  int n = quad_roots<double>(a, b, c, disc, scale, 1e-12, r);
+  double best = 0.0, bestv = -1e300;
+  bool found = false;
+  for (int i = 0; i < n; ++i) {
+    double t = r[i];
+    if (!(t >= pa - 1e-9 && t <= pb + 1e-9)) continue;
+    t = fmin(fmax(t, pa), pb);
+    D2 H = hodo_d64(g, t);
+    double v = H.x * cs + H.y * sn;
+    if (!found || v > bestv) {
+      bestv = v;
+      best = t;
+      found = true;
+    }
+  }
+  t_out = best;
+  return found;
+}
+
+// e_i = d_i . N for H(t) = sum_i d_i b_i(t) (the differences of Table 1's
+// hodograph, exact as pairs; N a double-float normal).
+__device__ __forceinline__ void hn_coeffs(const Seg& g, DF2 N, DF e[3]) {
+  DF2 d0, d1, d2;
+  switch (g.type) {
+    case PS_CUBIC: d0 = df_vec(g.B, g.A); d1 = df_vec(g.C, g.B); d2 = df_vec(g.D, g.C); break;
+    case PS_QUAD: d0 = df_vec(g.B, g.A); d1 = df_vec(g.D, g.B); d2 = d1; break;
+    default: d0 = df_vec(g.B, g.A); d1 = df_vec(g.D, g.A); d2 = df_vec(g.D, g.B); break;
+  }
+  e[0] = df_dot(d0, N);
+  e[1] = df_dot(d1, N);
+  e[2] = df_dot(d2, N);
+}
+
+// f(t) = H(t).N at a float t in double-float: cubic e0 u^2 + 2 e1 u t + e2 t^2,
+// quadratic e0 u + e1 t, conic w e0 u^2 + e1 u t + w e2 t^2 (u = 1 - t exact).
+__device__ __forceinline__ DF hn_eval(const Seg& g, const DF e[3], float t) {
+  const DF T{t, 0.f}, U = two_sum(1.f, -t);
+  switch (g.type) {
+    case PS_CUBIC: {
+      DF ut = df_mul(U, T);
+      return df_add(df_add(df_mul(e[0], df_mul(U, U)), df_mul_f(df_mul(e[1], ut), 2.f)),
+                    df_mul(e[2], two_prod(t, t)));
+    }
+    case PS_QUAD:
+      return df_add(df_mul(e[0], U), df_mul_f(e[1], t));
+    default:
+      return df_add(df_add(df_mul_f(df_mul(e[0], df_mul(U, U)), g.w), df_mul(e[1], df_mul(U, T))),
+                    df_mul_f(df_mul(e[2], two_prod(t, t)), g.w));
+  }
+}
+
+// t(psi) in PS_PREC_MIXED (Eq. 11), as a double-float pair.  The root is chosen
+// in FP32 as above (alias rejection, endpoint rule), then refined by Newton
+// steps on H(t).N(psi) = 0 with the residual in double-float from the
+// double-float normal (sn, cs): one step from the FP32 root, a second one when
+// the first moved t by more than a few ulps.  A near double root (|disc| below
+// 1e-3 of its scale), or a step that moved t by more than 1e-4, is solved in
+// FP64 instead (the cancellation there needs it).
+__device__ DF solve_t_mx(const Seg& g, DF sn, DF cs, DF pa, DF pb) {
+  if (g.type == PS_LINE) return pa;
+  float t0, a, b, c;
+  const bool root = solve_t32(g, sn.hi, cs.hi, pa.hi, pb.hi, t0, a, b, c);
+  const float disc = b * b - 4.f * a * c, scale = b * b + fabsf(4.f * a * c);
+  bool f64 = c != 0.f && fabsf(disc) < 1e-3f * scale;
+  DF t;
+  if (!f64) {
+    if (!root) return t0 == pa.hi ? pa : pb;  // endpoint rule
+    DF e[3];
+    hn_coeffs(g, DF2{df_neg(sn), cs}, e);
+    float fp = fmaf(2.f * c, t0, b);
+    float dt = fp != 0.f ? -df_f(hn_eval(g, e, t0)) / fp : 0.f;
+    if (fabsf(dt) > 2.4e-7f * fmaxf(fabsf(t0), 1e-3f)) {
+      t0 += dt;
+      fp = fmaf(2.f * c, t0, b);
+      dt = fp != 0.f ? -df_f(hn_eval(g, e, t0)) / fp : 0.f;
+    }
+    f64 = !(fabsf(dt) <= 1e-4f);
+    t = two_sum(t0, dt);
+  }
+  if (f64) {
+    double td;
+    if (solve_t64(g, df_d(sn), df_d(cs), df_d(pa), df_d(pb), td)) {
+      t = df_from_d(td);
+    } else {
+      if (!root) return t0 == pa.hi ? pa : pb;
+      t = df_of(t0);
+    }
+  }
+  if (df_lt(t, pa)) t = pa;
+  if (df_lt(pb, t)) t = pb;
+  return t;
 }
 
 // ---------------------------------------------------------------------------
@@ -305,20 +389,24 @@ __device__ __noinline__ double step_d(const Step& S, const Seg* g) {
   return q;
 }
 
-// The FP64 step: without the boost (PX false) the nominal step itself, and
-// step_d is not referenced (its presence alone changes the kernel's code).
-template <bool PX>
-__device__ __forceinline__ double sd(const Step& S, const Seg* g) {
-  if constexpr (PX) return step_d(S, g);
-  else return (double)S.q0;
-}
+// Steps for the turning ad in FP32 (Eq. 12 with the nominal-step snap).
+__device__ __forceinline__ int steps32(float ad, const Step& S) { return ceil_steps(ad, S.q); }
 
-// Steps for the turning ad (FP32) / ad64 (FP64): decided in FP32, re-decided in
-// FP64 under MIXED when the FP32 ratio sits within rounding of a boundary.
-template <bool MIXED, bool PX>
-__device__ __forceinline__ int steps_for(float ad, double ad64, const Step& S, const Seg* g) {
-  if (MIXED && near_integer(ad / S.q)) return ceil_steps_d(ad64, sd<PX>(S, g));
-  return ceil_steps(ad, S.q);
+// Steps for a double-float turning ad > 0 (PS_PREC_MIXED): decided in FP32,
+// re-decided in double-float when the FP32 ratio sits within rounding of a
+// boundary, ceil(ad/q - snap) with the pair's exact ceiling.  With the pixel
+// boost a re-decided link step comes from the FP64 form of its rule (step_d).
+template <bool PX>
+__device__ __forceinline__ int steps_mx(DF ad, const Step& S, const Seg* g) {
+  if (!near_integer(ad.hi / S.q)) return ceil_steps(ad.hi, S.q);
+  if constexpr (PX) {
+    if (S.kind != 0) return ceil_steps_d(df_d(ad), step_d(S, g));
+  }
+  const DF x = df_sub(df_div_f(ad, S.q0), DF{PS_DF_SNAP_HI, PS_DF_SNAP_LO});
+  float c = ceilf(x.hi);
+  if (c == x.hi && x.lo > 0.f) c += 1.f;
+  const int D = (int)c;
+  return D < 1 ? 1 : D;
 }
 
 // Reversals of a segment with collinear control points: along the common
@@ -326,9 +414,10 @@ __device__ __forceinline__ int steps_for(float ad, double ad64, const Step& S, c
 // (linear lam1 u + lam3 t for the quadratic Bezier).  The direction reverses at
 // its simple roots inside (0,1): two when lam2^2 - lam1 lam3 > 0 (sign taken with
 // error-free products), none otherwise (a double root is a kink); roots at the
-// ends (lam1 = 0, lam3 = 0) are factored out exactly.
-template <typename R>
-__device__ int collinear_reversals(const Seg& g, float* rts) {
+// ends (lam1 = 0, lam3 = 0) are factored out exactly.  R: the arithmetic, T: the
+// type of the roots.
+template <typename R, typename T>
+__device__ int collinear_reversals(const Seg& g, T* rts) {
   float2 vf = end_grad0(g);
   R vx = vf.x, vy = vf.y;
   R Ax = g.A.x, Ay = g.A.y, Bx = g.B.x, By = g.B.y, Cx = g.C.x, Cy = g.C.y, Dx = g.D.x, Dy = g.D.y;
@@ -342,7 +431,7 @@ __device__ int collinear_reversals(const Seg& g, float* rts) {
     case PS_QUAD: {
       R a1 = (Bx - Ax) * vx + (By - Ay) * vy, a3 = (Dx - Bx) * vx + (Dy - By) * vy;
       if ((a1 > R(0) && a3 < R(0)) || (a1 < R(0) && a3 > R(0))) {
-        rts[0] = (float)(a1 / (a1 - a3));
+        rts[0] = (T)(a1 / (a1 - a3));
         return 1;
       }
       return 0;
@@ -364,7 +453,7 @@ __device__ int collinear_reversals(const Seg& g, float* rts) {
     R den = R(2) * l2 - l3;
     if (den != R(0)) {
       R r = R(2) * l2 / den;
-      if (r > R(0) && r < R(1)) rts[n++] = (float)r;
+      if (r > R(0) && r < R(1)) rts[n++] = (T)r;
     }
     return n;
   }
@@ -372,7 +461,7 @@ __device__ int collinear_reversals(const Seg& g, float* rts) {
     R den = l1 - R(2) * l2;
     if (den != R(0)) {
       R r = l1 / den;
-      if (r > R(0) && r < R(1)) rts[n++] = (float)r;
+      if (r > R(0) && r < R(1)) rts[n++] = (T)r;
     }
     return n;
   }
@@ -383,38 +472,34 @@ __device__ int collinear_reversals(const Seg& g, float* rts) {
   R a = l1, b = R(2) * (l2 - l1), c = l1 - R(2) * l2 + l3, r[2];
   int m = quad_roots<R>(a, b, c, R(4) * disc, R(1), R(0), r);
   for (int i = 0; i < m; ++i)
-    if (r[i] > R(0) && r[i] < R(1)) rts[n++] = (float)r[i];
+    if (r[i] > R(0) && r[i] < R(1)) rts[n++] = (T)r[i];
   if (n == 2 && rts[0] > rts[1]) {
-    float t = rts[0];
+    T t = rts[0];
     rts[0] = rts[1];
     rts[1] = t;
   }
   return n;
 }
 
-// Interval table of a segment link (Sec. 3.3.4-3.3.6, Eq. 4-6, 12-13).
+// Record fields as pairs (the lo parts stay zero in FP32).
+__device__ __forceinline__ void put_psi(LinkRec& L, int k, DF v) { L.psi[k] = v.hi; L.psi_lo[k] = v.lo; }
+__device__ __forceinline__ void put_p(LinkRec& L, int k, DF v) { L.p[k] = v.hi; L.p_lo[k] = v.lo; }
+__device__ __forceinline__ void put_step(LinkRec& L, int k, DF v) { L.step[k] = v.hi; L.step_lo[k] = v.lo; }
+
+// Interval table of a segment link in FP32 (Sec. 3.3.4-3.3.6, Eq. 4-6, 12-13).
 // Returns N (total steps) or -1 if the table does not fit.
-template <bool MIXED, bool PX>
-__device__ int seg_intervals(const Seg& g, Step S, LinkRec& L) {
+template <bool PX>
+__device__ int seg_intervals32(const Seg& g, Step S, LinkRec& L) {
   const float q = S.q;
   float Psi0 = angf(end_grad0(g)), Psin = angf(end_grad1(g));
-  CrossPoly<float> Pf;
-  CrossPoly<double> Pd;
-  bool flat;
-  if (MIXED) {
-    Pd = cross_poly<double>(g);
-    flat = Pd.flat;
-  } else {
-    Pf = cross_poly<float>(g);
-    flat = Pf.flat;
-  }
+  CrossPoly<float> Pf = cross_poly<float>(g);
   int M = 0;
   uint32_t pivots = 0;
-  if (flat) {
+  if (Pf.flat) {
     // zero curvature: flat pieces with +pi pivots where H reverses (collinear
     // control points with back-tracking); one quad per flat piece
     float rts[2];
-    int nr = MIXED ? collinear_reversals<double>(g, rts) : collinear_reversals<float>(g, rts);
+    int nr = collinear_reversals<float, float>(g, rts);
     float psi = Psi0, pp = 0.f;
     for (int i = 0; i <= nr; ++i) {
       float pe = (i < nr) ? rts[i] : 1.f;
@@ -427,7 +512,6 @@ __device__ int seg_intervals(const Seg& g, Step S, LinkRec& L) {
         L.p[M] = pe;
         L.psi[M] = psi;
         pivots |= 1u << M;
-        L.step[M] = PS_PI_F;  // overwritten below with pi / Delta
         M++;
         psi = psi + PS_PI_F;
       }
@@ -438,13 +522,11 @@ __device__ int seg_intervals(const Seg& g, Step S, LinkRec& L) {
     int N = 0;
     L.dsum[0] = 0;
     for (int k = 0; k < M; ++k) {
-      int D;
+      int D = 1;
+      L.step[k] = 0.f;
       if ((pivots >> k) & 1u) {
-        D = steps_for<MIXED, PX>(PS_PI_F, PS_PI_D, S, &g);
+        D = steps32(PS_PI_F, S);
         L.step[k] = PS_PI_F / (float)D;
-      } else {
-        D = 1;
-        L.step[k] = 0.f;
       }
       N += D;
       L.dsum[k + 1] = (uint16_t)N;
@@ -456,24 +538,12 @@ __device__ int seg_intervals(const Seg& g, Step S, LinkRec& L) {
   // Eq. 4: curvature-sign changes strictly inside (0,1)
   float roots[2];
   int nroot = 0;
-  if (MIXED) {
-    if (Pd.c1 != 0.0 || Pd.c2 != 0.0) {
-      double r[2];
-      int n = quad_roots<double>(Pd.c0, Pd.c1, Pd.c2, Pd.disc, Pd.scale, 0.0, r);
-      if (n == 2 && Pd.disc <= 0.0) n = 0;
-      for (int i = 0; i < n; ++i)
-        if (r[i] > 0.0 && r[i] < 1.0 && (nroot == 0 || (float)r[i] > roots[nroot - 1]))
-          roots[nroot++] = (float)r[i];
-    }
-  } else {
-    if (Pf.c1 != 0.f || Pf.c2 != 0.f) {
-      float r[2];
-      int n = quad_roots<float>(Pf.c0, Pf.c1, Pf.c2, Pf.disc, Pf.scale, 0.f, r);
-      if (n == 2 && Pf.disc <= 0.f) n = 0;
-      for (int i = 0; i < n; ++i)
-        if (r[i] > 0.f && r[i] < 1.f && (nroot == 0 || r[i] > roots[nroot - 1]))
-          roots[nroot++] = r[i];
-    }
+  if (Pf.c1 != 0.f || Pf.c2 != 0.f) {
+    float r[2];
+    int n = quad_roots<float>(Pf.c0, Pf.c1, Pf.c2, Pf.disc, Pf.scale, 0.f, r);
+    if (n == 2 && Pf.disc <= 0.f) n = 0;
+    for (int i = 0; i < n; ++i)
+      if (r[i] > 0.f && r[i] < 1.f && (nroot == 0 || r[i] > roots[nroot - 1])) roots[nroot++] = r[i];
   }
   // Eq. 5
   float p[4], Psi[4];
@@ -483,14 +553,7 @@ __device__ int seg_intervals(const Seg& g, Step S, LinkRec& L) {
   n++;
   for (int i = 0; i < nroot; ++i) {
     p[n] = roots[i];
-    if (MIXED) {
-      // H near an inflection of a near-cusp cubic is a small difference of
-      // large terms: evaluate it in FP64, round the direction to FP32
-      D2 H = hodo_d64(g, (double)roots[i]);
-      Psi[n] = atan2f((float)H.y, (float)H.x);
-    } else {
-      Psi[n] = angf(hodo(g, roots[i]));
-    }
+    Psi[n] = angf(hodo(g, roots[i]));
     n++;
   }
   p[n] = 1.f;
@@ -502,73 +565,27 @@ __device__ int seg_intervals(const Seg& g, Step S, LinkRec& L) {
     float sgn = 0.f;
     float probes[3] = {0.5f * (pa + pb), 0.75f * pa + 0.25f * pb, 0.25f * pa + 0.75f * pb};
     for (int i = 0; i < 3 && sgn == 0.f; ++i) {
-      float v = MIXED ? (float)Pd.eval((double)probes[i]) : Pf.eval(probes[i]);
+      float v = Pf.eval(probes[i]);
       sgn = v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f);
     }
     float delta = 0.f;
     if (sgn != 0.f) {
       delta = sgn * wrap2pi(sgn * (Psi[k + 1] - Psi[k]));
-      bool redo = false;
-      if (MIXED) {
-        float ad = fabsf(delta);
-        redo = near_integer(ad / q) || near_integer(0.5f * ad / q) ||
-               fabsf(ad - PS_PI_F) < 1e-4f || ad > PS_TWO_PI_F - 1e-4f || ad < 1e-4f;
-      }
-      if (redo) {
-        // FP64 island: end angles from FP64 gradients (exact differences of the
-        // FP32 inputs), turning and its direction in FP64
-        D2 a0, a1;
-        if (k == 0) {
-          float2 e0 = end_grad0(g);
-          a0 = D2{(double)e0.x, (double)e0.y};
-        } else {
-          a0 = hodo_d64(g, (double)p[k]);
-        }
-        if (k == n - 1) {
-          float2 e1 = end_grad1(g);
-          a1 = D2{(double)e1.x, (double)e1.y};
-        } else {
-          a1 = hodo_d64(g, (double)p[k + 1]);
-        }
-        double d = (double)sgn * (atan2(a1.y, a1.x) - atan2(a0.y, a0.x));
-        d = fmod(d, PS_TWO_PI_D);
-        if (d < 0) d += PS_TWO_PI_D;
-        if (d > PS_TWO_PI_D - 1e-9) d = 0.0;
-        double dd_ = (double)sgn * d;
-        delta = (float)dd_;
-        // store counts computed from the FP64 turning
-        double ad = fabs(dd_);
-        if (ad >= PS_PI_D) {
-          int Dh = ceil_steps_d(0.5 * ad, sd<PX>(S, &g));
-          float psi_s = Psi[k] + 0.5f * delta;
-          float ps_ = solve_t<MIXED>(g, psi_s, pa, pb);
-          if (M + 2 > 6) return -1;
-          L.p[M] = pa; L.psi[M] = Psi[k]; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh; M++;
-          L.p[M] = ps_; L.psi[M] = psi_s; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh;
-          L.meta |= META_SPLIT_BIT(M);
-          M++;
-        } else {
-          int D = ad == 0.0 ? 1 : ceil_steps_d(ad, sd<PX>(S, &g));
-          if (M + 1 > 6) return -1;
-          L.p[M] = pa; L.psi[M] = Psi[k]; L.step[M] = delta / (float)D; L.dsum[M + 1] = (uint16_t)D; M++;
-        }
-        continue;
-      }
       if (fabsf(delta) > PS_TWO_PI_F - 1e-5f) delta = 0.f;
     }
     float ad = fabsf(delta);
     if (ad >= PS_PI_F) {
       // Sec. 3.3.5: split at half the turning, p by Eq. 11
       float psi_s = Psi[k] + 0.5f * delta;
-      float ps_ = solve_t<MIXED>(g, psi_s, pa, pb);
-      int Dh = ceil_steps(0.5f * ad, q);
+      float ps_ = solve_t(g, psi_s, pa, pb);
+      int Dh = steps32(0.5f * ad, S);
       if (M + 2 > 6) return -1;
       L.p[M] = pa; L.psi[M] = Psi[k]; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh; M++;
       L.p[M] = ps_; L.psi[M] = psi_s; L.step[M] = 0.5f * delta / (float)Dh; L.dsum[M + 1] = (uint16_t)Dh;
       L.meta |= META_SPLIT_BIT(M);
       M++;
     } else {
-      int D = ad == 0.f ? (pb > pa ? 1 : 0) : ceil_steps(ad, q);
+      int D = ad == 0.f ? (pb > pa ? 1 : 0) : steps32(ad, S);
       if (M + 1 > 6) return -1;
       L.p[M] = pa; L.psi[M] = Psi[k]; L.step[M] = D ? delta / (float)D : 0.f; L.dsum[M + 1] = (uint16_t)D; M++;
     }
@@ -586,6 +603,142 @@ __device__ int seg_intervals(const Seg& g, Step S, LinkRec& L) {
   return N;
 }
 
+// The same table in PS_PREC_MIXED.  Angles, parameters and steps are
+// double-float pairs: end angles by the double-float atan2 of the exact
+// control-point differences, inflections from the curvature polynomial's
+// roots in FP64 (the discriminant island; an exact cusp gives a zero
+// discriminant), their angles from the double-float hodograph, turnings and
+// counts in double-float, split points by the double-float t solve.
+template <bool PX>
+__device__ int seg_intervals_mx(const Seg& g, Step S, LinkRec& L) {
+  const DF2 ge0 = end_grad0_df(g), ge1 = end_grad1_df(g);
+  const DF Psi0 = df_atan2(ge0.y, ge0.x, ps_sc_tab), Psin = df_atan2(ge1.y, ge1.x, ps_sc_tab);
+  const CrossPoly<double> Pd = cross_poly<double>(g);
+  const DF zero = df_of(0.f), one = df_of(1.f);
+  int M = 0;
+  uint32_t pivots = 0;
+  if (Pd.flat) {
+    double rts[2];
+    int nr = collinear_reversals<double, double>(g, rts);
+    DF psi = Psi0, pp = zero;
+    for (int i = 0; i <= nr; ++i) {
+      DF pe = (i < nr) ? df_from_d(rts[i]) : one;
+      put_p(L, M, pp);
+      put_psi(L, M, psi);
+      put_step(L, M, zero);
+      L.dsum[M + 1] = 0;
+      M++;
+      if (i < nr) {
+        put_p(L, M, pe);
+        put_psi(L, M, psi);
+        pivots |= 1u << M;
+        M++;
+        psi = df_add(psi, df_pi());
+      }
+      pp = pe;
+    }
+    put_p(L, M, one);
+    put_psi(L, M, psi);
+    int N = 0;
+    L.dsum[0] = 0;
+    for (int k = 0; k < M; ++k) {
+      int D = 1;
+      put_step(L, k, zero);
+      if ((pivots >> k) & 1u) {
+        D = steps_mx<PX>(df_pi(), S, &g);
+        put_step(L, k, df_div_f(df_pi(), (float)D));
+      }
+      N += D;
+      L.dsum[k + 1] = (uint16_t)N;
+    }
+    L.meta |= ((uint32_t)M << 4) | (pivots << 8);
+    return N;
+  }
+
+  // Eq. 4 (FP64 island: the curvature polynomial's discriminant and roots)
+  double roots[2];
+  int nroot = 0;
+  if (Pd.c1 != 0.0 || Pd.c2 != 0.0) {
+    double r[2];
+    int n = quad_roots<double>(Pd.c0, Pd.c1, Pd.c2, Pd.disc, Pd.scale, 0.0, r);
+    if (n == 2 && Pd.disc <= 0.0) n = 0;
+    for (int i = 0; i < n; ++i)
+      if (r[i] > 0.0 && r[i] < 1.0 && (nroot == 0 || r[i] > roots[nroot - 1])) roots[nroot++] = r[i];
+  }
+  // Eq. 5: an inflection's angle is insensitive to its parameter to first
+  // order (the tangent turns at rate 0 there), so H is taken at the float root
+  DF p[4], Psi[4];
+  double pd[4];
+  int n = 0;
+  p[n] = zero;
+  pd[n] = 0.0;
+  Psi[n] = Psi0;
+  n++;
+  for (int i = 0; i < nroot; ++i) {
+    p[n] = df_from_d(roots[i]);
+    pd[n] = roots[i];
+    DF2 H = hodo_df(g, p[n].hi);
+    Psi[n] = df_atan2(H.y, H.x, ps_sc_tab);
+    n++;
+  }
+  p[n] = one;
+  pd[n] = 1.0;
+  Psi[n] = Psin;
+
+  // Eq. 6: turning in the direction of the curvature sign, modulo 2 pi
+  const DF full = DF{PS_DF_FULL_TURN_SLACK_HI, PS_DF_FULL_TURN_SLACK_LO};
+  for (int k = 0; k < n; ++k) {
+    const double pa = pd[k], pb = pd[k + 1];
+    double sgn = 0.0;
+    const double probes[3] = {0.5 * (pa + pb), 0.75 * pa + 0.25 * pb, 0.25 * pa + 0.75 * pb};
+    for (int i = 0; i < 3 && sgn == 0.0; ++i) {
+      double v = Pd.eval(probes[i]);
+      sgn = v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0);
+    }
+    DF delta = zero;
+    if (sgn != 0.0) {
+      DF d = df_sub(Psi[k + 1], Psi[k]);
+      if (sgn < 0.0) d = df_neg(d);
+      d = df_mod2pi(d);
+      if (df_lt(full, d)) d = zero;  // a full turn within rounding: numerically flat
+      delta = sgn < 0.0 ? df_neg(d) : d;
+    }
+    const DF ad = df_abs(delta);
+    if (df_le(df_pi(), ad)) {
+      // Sec. 3.3.5: split at half the turning, p by Eq. 11
+      const DF half{0.5f * delta.hi, 0.5f * delta.lo};
+      const DF psi_s = df_add(Psi[k], half);
+      DF sn, cs;
+      df_sincos(psi_s, ps_sc_tab, sn, cs);
+      const DF ps_ = solve_t_mx(g, sn, cs, p[k], p[k + 1]);
+      const int Dh = steps_mx<PX>(df_abs(half), S, &g);
+      const DF st = df_div_f(half, (float)Dh);
+      if (M + 2 > 6) return -1;
+      put_p(L, M, p[k]); put_psi(L, M, Psi[k]); put_step(L, M, st); L.dsum[M + 1] = (uint16_t)Dh; M++;
+      put_p(L, M, ps_); put_psi(L, M, psi_s); put_step(L, M, st); L.dsum[M + 1] = (uint16_t)Dh;
+      L.meta |= META_SPLIT_BIT(M);
+      M++;
+    } else {
+      const int D = df_is0(ad) ? (pb > pa ? 1 : 0) : steps_mx<PX>(ad, S, &g);
+      if (M + 1 > 6) return -1;
+      put_p(L, M, p[k]); put_psi(L, M, Psi[k]);
+      put_step(L, M, D ? df_div_f(delta, (float)D) : zero);
+      L.dsum[M + 1] = (uint16_t)D;
+      M++;
+    }
+  }
+  put_p(L, M, one);
+  put_psi(L, M, Psin);
+  int N = 0;
+  L.dsum[0] = 0;
+  for (int k = 0; k < M; ++k) {
+    N += L.dsum[k + 1];
+    L.dsum[k + 1] = (uint16_t)N;
+  }
+  L.meta |= ((uint32_t)M << 4);
+  return N;
+}
+
 __device__ __forceinline__ float ominus_f(float a, float b) {
   float d = a - b;
   if (d > PS_PI_F) return d - PS_TWO_PI_F;
@@ -593,33 +746,38 @@ __device__ __forceinline__ float ominus_f(float a, float b) {
   return d;
 }
 
-// Join / cap pivot (Sec. 4.3): generator fixed at `at`, psi from Psi0 through
-// delta in J steps; the outer side is N for delta > 0, P for delta < 0 and the
-// inner radius is zero.
-template <bool MIXED, bool PX>
-__device__ int pivot_setup(float2 at, float Psi0, float delta, int kind, int style, float r,
-                           float miter, Step S, LinkRec& L, float2 g_in = make_float2(0.f, 0.f),
-                           float2 g_out = make_float2(0.f, 0.f)) {
-  int J = 0;
-  float ad = fabsf(delta);
+// J of a join or cap (Sec. 4.3.2-4.3.5; reading R8: bevel 1, triangle 2,
+// miters 3, round ceil(|delta|/q); caps: triangle 2, square 4, round
+// ceil(pi/q)).  round: the round style's step count.
+__device__ __forceinline__ int pivot_count(int kind, int style, bool zero_turn, int round) {
   if (kind == LK_JOIN) {
-    if (delta == 0.f) return 0;
+    if (zero_turn) return 0;
     switch (style) {
-      case PS_JOIN_BEVEL: J = 1; break;
-      case PS_JOIN_TRIANGLE: J = 2; break;
+      case PS_JOIN_BEVEL: return 1;
+      case PS_JOIN_TRIANGLE: return 2;
       case PS_JOIN_MITER:
-      case PS_JOIN_MITER_TRUNCATE: J = 3; break;
-      case PS_JOIN_ROUND: J = ceil_steps(ad, S.q); break;
-      default: J = 0;
-    }
-  } else {
-    switch (style) {
-      case PS_CAP_TRIANGLE: J = 2; break;
-      case PS_CAP_SQUARE: J = 4; break;
-      case PS_CAP_ROUND: J = steps_for<MIXED, PX>(PS_PI_F, PS_PI_D, S, nullptr); break;
-      default: J = 0;
+      case PS_JOIN_MITER_TRUNCATE: return 3;
+      case PS_JOIN_ROUND: return round;
+      default: return 0;
     }
   }
+  switch (style) {
+    case PS_CAP_TRIANGLE: return 2;
+    case PS_CAP_SQUARE: return 4;
+    case PS_CAP_ROUND: return round;
+    default: return 0;
+  }
+}
+
+// Join / cap pivot in FP32 (Sec. 4.3): generator fixed at `at`, psi from Psi0
+// through delta in J steps; the outer side is N for delta > 0, P for delta < 0
+// and the inner radius is zero.
+template <bool PX>
+__device__ int pivot_setup32(float2 at, float Psi0, float delta, int kind, int style, float r,
+                             float miter, Step S, LinkRec& L) {
+  const bool rnd = (kind == LK_JOIN && style == PS_JOIN_ROUND) || (kind == LK_CAP && style == PS_CAP_ROUND);
+  const float ad = fabsf(delta);
+  int J = pivot_count(kind, style, delta == 0.f, rnd ? steps32(ad, S) : 0);
   if (J == 0) return 0;
   L.P[0] = at;
   L.rN = delta > 0.f ? r : 0.f;
@@ -644,18 +802,8 @@ __device__ int pivot_setup(float2 at, float Psi0, float delta, int kind, int sty
     // miter ratio 1/sin(phi/2), phi = pi - |delta|; infinite at a reversal
     float cm = cosf(0.5f * ad);
     float ratio = cm > 0.f ? 1.f / cm : INFINITY;
-    bool accept = ratio <= miter;
-    if (MIXED && fabsf(ratio - miter) < 1e-4f * miter) {
-      // FP64 island: the miter decision sits on the limit; decide it from the
-      // turning computed in FP64 from the end gradients
-      double d = atan2((double)g_out.y, (double)g_out.x) - atan2((double)g_in.y, (double)g_in.x);
-      if (d > PS_PI_D) d -= PS_TWO_PI_D;
-      if (d < -PS_PI_D) d += PS_TWO_PI_D;
-      double cd = cos(0.5 * fabs(d));
-      accept = cd > 0.0 && 1.0 / cd <= (double)miter;
-    }
     float2 v1, v2;
-    if (accept) {
+    if (ratio <= miter) {
       float2 tip = at + mk(-sh, ch) * (sd * r * ratio);
       v1 = tip;
       v2 = tip;
@@ -667,6 +815,67 @@ __device__ int pivot_setup(float2 at, float Psi0, float delta, int kind, int sty
       lam = fmaxf(lam, 0.f);
       v1 = O0 + mk(c0, s0) * lam;
       v2 = O3 - mk(c1, s1) * lam;
+    }
+    L.v1 = v1;
+    L.v2 = v2;
+    L.meta |= META_FLAG_OVERRIDE;
+  }
+  return J;
+}
+
+// a + b (a float, b a pair) rounded once
+__device__ __forceinline__ float add_round(float a, DF b) { return df_f(df_add_f(b, a)); }
+
+// The same pivot in PS_PREC_MIXED: Psi0 and delta are double-float pairs, the
+// counts are re-decided in double-float at their boundaries, and the miter
+// decision and override vertices are taken in double-float.
+template <bool PX>
+__device__ int pivot_setup_mx(float2 at, DF Psi0, DF delta, int kind, int style, float r,
+                              float miter, Step S, LinkRec& L) {
+  const bool rnd = (kind == LK_JOIN && style == PS_JOIN_ROUND) || (kind == LK_CAP && style == PS_CAP_ROUND);
+  const DF ad = df_abs(delta);
+  int J = pivot_count(kind, style, df_is0(delta), rnd && !df_is0(delta) ? steps_mx<PX>(ad, S, nullptr) : 0);
+  if (J == 0) return 0;
+  const bool pos = df_lt(df_of(0.f), delta);
+  L.P[0] = at;
+  L.rN = pos ? r : 0.f;
+  L.rP = pos ? 0.f : r;
+  put_psi(L, 0, Psi0);
+  put_psi(L, 1, df_add(Psi0, delta));
+  put_step(L, 0, df_div_f(delta, (float)J));
+  L.dsum[0] = 0;
+  L.dsum[1] = (uint16_t)J;
+  L.p[0] = 0.f;
+  L.p[1] = 1.f;
+  L.meta |= (1u << 4) | ((uint32_t)style << 16);
+  if (kind == LK_CAP && style == PS_CAP_SQUARE) L.meta |= META_FLAG_SQUARE;
+  if (kind == LK_JOIN && (style == PS_JOIN_MITER || style == PS_JOIN_MITER_TRUNCATE)) {
+    const float sdr = pos ? -r : r;  // outer offset = at + sdr * n, n = (-sin, cos)
+    const DF half{0.5f * delta.hi, 0.5f * delta.lo}, ahalf = df_abs(half);
+    DF s0, c0, s1, c1, sh, ch, sa, ca;
+    df_sincos(Psi0, ps_sc_tab, s0, c0);
+    df_sincos(df_add(Psi0, delta), ps_sc_tab, s1, c1);
+    df_sincos(df_add(Psi0, half), ps_sc_tab, sh, ch);
+    df_sincos(ahalf, ps_sc_tab, sa, ca);
+    // miter ratio 1/cos(|delta|/2) <= limit  <=>  limit cos(|delta|/2) >= 1
+    const bool accept = ca.hi > 0.f && df_le(df_of(1.f), df_mul_f(ca, miter));
+    DF2 O0{df_mul_f(df_neg(s0), sdr), df_mul_f(c0, sdr)};  // relative to at
+    DF2 O3{df_mul_f(df_neg(s1), sdr), df_mul_f(c1, sdr)};
+    float2 v1, v2;
+    if (accept) {
+      const DF len = df_div(df_of(sdr), ca);
+      const float tx = add_round(at.x, df_mul(df_neg(sh), len)), ty = add_round(at.y, df_mul(ch, len));
+      v1 = mk(tx, ty);
+      v2 = v1;
+    } else if (style == PS_JOIN_MITER) {
+      v1 = mk(add_round(at.x, O0.x), add_round(at.y, O0.y));
+      v2 = mk(add_round(at.x, O3.x), add_round(at.y, O3.y));
+    } else {
+      // truncate: clip at limit * r along the bisector
+      DF lam = df_div(df_sub(two_prod(miter, r), df_mul_f(ca, r)), sa);
+      if (lam.hi < 0.f) lam = df_of(0.f);
+      v1 = mk(add_round(at.x, df_add(O0.x, df_mul(c0, lam))), add_round(at.y, df_add(O0.y, df_mul(s0, lam))));
+      v2 = mk(add_round(at.x, df_sub(O3.x, df_mul(c1, lam))), add_round(at.y, df_sub(O3.y, df_mul(s1, lam))));
     }
     L.v1 = v1;
     L.v2 = v2;
@@ -699,78 +908,87 @@ __device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, i
     L.P[0] = g.A; L.P[1] = g.B; L.P[2] = g.C; L.P[3] = g.D;
     L.w = g.w;
     L.meta = LK_SEG | ((uint32_t)g.type << 2);
-    int N = seg_intervals<MIXED, PX>(g, PX ? seg_step(g, q, tau, r) : plain_step(q), L);
+    const Step S = PX ? seg_step(g, q, tau, r) : plain_step(q);
+    int N = MIXED ? seg_intervals_mx<PX>(g, S, L) : seg_intervals32<PX>(g, S, L);
     if (N < 0) return -1;
     nrib = N > 0 ? N + 1 : 0;
-  } else if (k == 0 || k == 2 * n) {
-    // first / last non-degenerate segment
-    int first = -1, last = -1;
-    if (k == 0 || closed) {
-      for (int i = 0; i < n; ++i) {
-        Seg g = load_seg(st, sp, sw, s0 + i);
-        if (!zero_length(g)) { first = i; break; }
-      }
-    }
-    if (k == 2 * n) {
-      for (int i = n - 1; i >= 0; --i) {
-        Seg g = load_seg(st, sp, sw, s0 + i);
-        if (!zero_length(g)) { last = i; break; }
-      }
-    }
-    if (!closed) {
-      int i = (k == 0) ? first : last;
-      if (i < 0) return 0;
-      Seg c = load_seg(st, sp, sw, s0 + i);
-      L.meta = LK_CAP;
-      float Psi0 = (k == 0) ? angf(end_grad0(c)) + PS_PI_F : angf(end_grad1(c));
-      Step S = PX && cap == PS_CAP_ROUND ? round_step(q, tau, r) : plain_step(q);
-      int J = pivot_setup<MIXED, PX>(k == 0 ? c.A : c.D, Psi0, PS_PI_F, LK_CAP, cap, r, miter, S, L);
-      nrib = J > 0 ? J + 1 : 0;
-    } else if (k == 2 * n) {
-      if (first < 0 || last < 0) return 0;
-      Seg a = load_seg(st, sp, sw, s0 + last), b = load_seg(st, sp, sw, s0 + first);
-      L.meta = LK_JOIN;
-      float Psi0 = angf(end_grad1(a));
-      float delta = ominus_f(angf(end_grad0(b)), Psi0);
-      if (delta == -PS_PI_F) delta = PS_PI_F;
-      Step S = PX && join == PS_JOIN_ROUND ? round_step(q, tau, r) : plain_step(q);
-      int J = pivot_setup<MIXED, PX>(b.A, Psi0, delta, LK_JOIN, join, r, miter, S, L, end_grad1(a),
-                                 end_grad0(b));
-      nrib = J > 0 ? J + 1 : 0;
-    }
   } else {
-    int i = k / 2 - 1;
-    Seg b = load_seg(st, sp, sw, s0 + i + 1);
-    if (zero_length(b)) return 0;
-    int inc = -1;
-    for (int m = i; m >= 0; --m) {
-      Seg a = load_seg(st, sp, sw, s0 + m);
-      if (!zero_length(a)) { inc = m; break; }
-    }
-    if (inc < 0) return 0;
-    Seg a = load_seg(st, sp, sw, s0 + inc);
-    L.meta = LK_JOIN;
-    float Psi0 = angf(end_grad1(a));
-    float delta = ominus_f(angf(end_grad0(b)), Psi0);
-    if (delta == -PS_PI_F) delta = PS_PI_F;
-    Step S = PX && join == PS_JOIN_ROUND ? round_step(q, tau, r) : plain_step(q);
-    if (MIXED && join == PS_JOIN_ROUND && delta != 0.f && near_integer(fabsf(delta) / S.q)) {
-      float2 e1 = end_grad1(a), e0 = end_grad0(b);
-      double d = atan2((double)e0.y, (double)e0.x) - atan2((double)e1.y, (double)e1.x);
-      if (d > PS_PI_D) d -= PS_TWO_PI_D;
-      if (d < -PS_PI_D) d += PS_TWO_PI_D;
-      int J = ceil_steps_d(fabs(d), sd<PX>(S, nullptr));
-      int J0 = pivot_setup<MIXED, PX>(b.A, Psi0, delta, LK_JOIN, join, r, miter, S, L, e1, e0);
-      if (J0 > 0 && J > 0 && J != J0) {
-        L.step[0] = delta / (float)J;
-        L.dsum[1] = (uint16_t)J;
+    // a cap (k = 0 or 2n of an open path), a join between the nearest
+    // non-degenerate segments, or the closing join of a closed path
+    int ia = -1, ib = -1;  // incoming / outgoing segment (cap: ia = ib = the end segment)
+    int kind;
+    if (k == 0 || k == 2 * n) {
+      int first = -1, last = -1;
+      if (k == 0 || closed) {
+        for (int i = 0; i < n; ++i) {
+          Seg g = load_seg(st, sp, sw, s0 + i);
+          if (!zero_length(g)) { first = i; break; }
+        }
       }
-      nrib = J0 > 0 ? (J > 0 ? J : J0) + 1 : 0;
+      if (k == 2 * n) {
+        for (int i = n - 1; i >= 0; --i) {
+          Seg g = load_seg(st, sp, sw, s0 + i);
+          if (!zero_length(g)) { last = i; break; }
+        }
+      }
+      if (!closed) {
+        kind = LK_CAP;
+        ia = ib = (k == 0) ? first : last;
+        if (ia < 0) return 0;
+      } else {
+        if (k != 2 * n || first < 0 || last < 0) return 0;
+        kind = LK_JOIN;
+        ia = last;
+        ib = first;
+      }
     } else {
-      int J = pivot_setup<MIXED, PX>(b.A, Psi0, delta, LK_JOIN, join, r, miter, S, L, end_grad1(a),
-                                 end_grad0(b));
-      nrib = J > 0 ? J + 1 : 0;
+      int i = k / 2 - 1;
+      Seg b = load_seg(st, sp, sw, s0 + i + 1);
+      if (zero_length(b)) return 0;
+      for (int m = i; m >= 0; --m) {
+        Seg a = load_seg(st, sp, sw, s0 + m);
+        if (!zero_length(a)) { ia = m; break; }
+      }
+      if (ia < 0) return 0;
+      ib = i + 1;
+      kind = LK_JOIN;
     }
+    const Seg a = load_seg(st, sp, sw, s0 + ia), b = load_seg(st, sp, sw, s0 + ib);
+    const int style = kind == LK_CAP ? cap : join;
+    const bool rnd = (kind == LK_CAP && cap == PS_CAP_ROUND) || (kind == LK_JOIN && join == PS_JOIN_ROUND);
+    const Step S = PX && rnd ? round_step(q, tau, r) : plain_step(q);
+    const float2 at = kind == LK_CAP ? (k == 0 ? a.A : a.D) : b.A;
+    L.meta = kind;
+    int J;
+    if constexpr (MIXED) {
+      DF Psi0, delta;
+      if (kind == LK_CAP) {
+        // start cap: a pivot from Psi_s + pi through pi; stop cap: from Psi_e (R7)
+        const DF2 e = k == 0 ? end_grad0_df(a) : end_grad1_df(a);
+        Psi0 = df_atan2(e.y, e.x, ps_sc_tab);
+        if (k == 0) Psi0 = df_add(Psi0, df_pi());
+        delta = df_pi();
+      } else {
+        // Sec. 4.3.1: delta = Psi_1 (-) Psi_0, taken as the angle from the
+        // incoming to the outgoing gradient; an exact reversal is +pi (R10)
+        const DF2 e1 = end_grad1_df(a), e0 = end_grad0_df(b);
+        Psi0 = df_atan2(e1.y, e1.x, ps_sc_tab);
+        delta = df_atan2(df_cross(e1, e0), df_dot(e1, e0), ps_sc_tab);
+      }
+      J = pivot_setup_mx<PX>(at, Psi0, delta, kind, style, r, miter, S, L);
+    } else {
+      float Psi0, delta;
+      if (kind == LK_CAP) {
+        Psi0 = k == 0 ? angf(end_grad0(a)) + PS_PI_F : angf(end_grad1(a));
+        delta = PS_PI_F;
+      } else {
+        Psi0 = angf(end_grad1(a));
+        delta = ominus_f(angf(end_grad0(b)), Psi0);
+        if (delta == -PS_PI_F) delta = PS_PI_F;
+      }
+      J = pivot_setup32<PX>(at, Psi0, delta, kind, style, r, miter, S, L);
+    }
+    nrib = J > 0 ? J + 1 : 0;
   }
   if (nrib == 0) L.meta = 0;
   return nrib;
@@ -906,12 +1124,12 @@ constexpr int EMIT_K = 16;  // slabs of 32 ribs per chunk by default (tunable: 4
 struct RibEval {
   float4 v;      // N.x N.y P.x P.y
   float2 grel;   // g(t) - A (segments) for the chord
-  float t;
+  float t, tlo;  // t as a pair (tlo = 0 in FP32)
   bool seg;
 };
 
-template <bool MIXED>
-__device__ __forceinline__ RibEval eval_rib(const LinkRec* __restrict__ L, int j) {
+// One rib, FP32 (PS_PREC_FP32).
+__device__ __forceinline__ RibEval eval_rib32(const LinkRec* __restrict__ L, int j) {
   // fields are read where needed (L1-cached) instead of copying the record
   RibEval R;
   uint32_t meta = __ldg(&L->meta);
@@ -919,6 +1137,7 @@ __device__ __forceinline__ RibEval eval_rib(const LinkRec* __restrict__ L, int j
   int M = META_M(meta);
   float4 p01 = __ldg(reinterpret_cast<const float4*>(L->P));
   float rN = __ldg(&L->rN), rP = __ldg(&L->rP);
+  R.tlo = 0.f;
   if (kind == LK_SEG) {
     Seg g;
     float4 p23 = __ldg(reinterpret_cast<const float4*>(L->P) + 1);
@@ -936,9 +1155,9 @@ __device__ __forceinline__ RibEval eval_rib(const LinkRec* __restrict__ L, int j
     sincosf(psi, &sn, &cs);
     float pa = __ldg(&L->p[k]);
     if (bnd || META_PIVOT(meta, k)) t = pa;
-    else t = solve_t<MIXED>(g, psi, sn, cs, pa, __ldg(&L->p[k + 1]));
+    else t = solve_t(g, sn, cs, pa, __ldg(&L->p[k + 1]));
     float2 n = mk(-sn, cs);
-    float2 gr = MIXED ? g_rel_comp(g, t) : g_rel(g, t);
+    float2 gr = g_rel(g, t);
     float2 Nv = gr - n * rN, Pv = gr + n * rP;
     R.v = make_float4(g.A.x + Nv.x, g.A.y + Nv.y, g.A.x + Pv.x, g.A.y + Pv.y);
     R.grel = gr;
@@ -968,6 +1187,80 @@ __device__ __forceinline__ RibEval eval_rib(const LinkRec* __restrict__ L, int j
     R.seg = false;
   }
   return R;
+}
+
+__device__ __forceinline__ DF ld_pair(const float* hi, const float* lo) { return DF{__ldg(hi), __ldg(lo)}; }
+
+// One rib, PS_PREC_MIXED: psi(j) = Psi_k + step_k (j - Delta_Sigma(k)) as a
+// pair, its normal by the double-float sincos, t by the double-float solve,
+// g(t) compensated, and each vertex coordinate summed as a pair and rounded
+// once (Eq. 14-17).
+__device__ __forceinline__ RibEval eval_rib_mx(const LinkRec* __restrict__ L, int j) {
+  RibEval R;
+  uint32_t meta = __ldg(&L->meta);
+  int kind = META_KIND(meta);
+  int M = META_M(meta);
+  float4 p01 = __ldg(reinterpret_cast<const float4*>(L->P));
+  float rN = __ldg(&L->rN), rP = __ldg(&L->rP);
+  if (kind == LK_SEG) {
+    Seg g;
+    float4 p23 = __ldg(reinterpret_cast<const float4*>(L->P) + 1);
+    g.type = META_TYPE(meta);
+    g.A = mk(p01.x, p01.y); g.B = mk(p01.z, p01.w); g.C = mk(p23.x, p23.y); g.D = mk(p23.z, p23.w);
+    g.w = __ldg(&L->w);
+    int k = 0;
+    while (k < M && j >= (int)__ldg(&L->dsum[k + 1])) ++k;
+    const int dk = (int)__ldg(&L->dsum[k]);
+    const bool bnd = j == dk;
+    DF psi = ld_pair(&L->psi[k], &L->psi_lo[k]);
+    if (!bnd) psi = df_add(psi, df_mul_f(ld_pair(&L->step[k], &L->step_lo[k]), (float)(j - dk)));
+    DF sn, cs;
+    df_sincos(psi, ps_sc_tab, sn, cs);
+    const DF pa = ld_pair(&L->p[k], &L->p_lo[k]);
+    DF t = pa;
+    if (!bnd && !META_PIVOT(meta, k)) t = solve_t_mx(g, sn, cs, pa, ld_pair(&L->p[k + 1], &L->p_lo[k + 1]));
+    const DF2 gr = g_rel_df(g, t);
+    // N = A + g - rN n, P = A + g + rP n with n = (-sin psi, cos psi)
+    const DF gx = df_add_f(gr.x, g.A.x), gy = df_add_f(gr.y, g.A.y);
+    R.v = make_float4(df_f(df_add(gx, df_mul_f(sn, rN))), df_f(df_sub(gy, df_mul_f(cs, rN))),
+                      df_f(df_sub(gx, df_mul_f(sn, rP))), df_f(df_add(gy, df_mul_f(cs, rP))));
+    R.grel = mk(df_f(gr.x), df_f(gr.y));
+    R.t = t.hi;
+    R.tlo = t.lo;
+    R.seg = true;
+  } else {
+    const int J = (int)__ldg(&L->dsum[1]);
+    DF psi;
+    if (j == J) psi = ld_pair(&L->psi[1], &L->psi_lo[1]);
+    else psi = df_add(ld_pair(&L->psi[0], &L->psi_lo[0]), df_mul_f(ld_pair(&L->step[0], &L->step_lo[0]), (float)j));
+    DF sn, cs;
+    df_sincos(psi, ps_sc_tab, sn, cs);
+    DF rn = df_of(rN), rp = df_of(rP);
+    if ((meta & META_FLAG_SQUARE) && (j == 1 || j == 3)) {
+      rn = df_mul_f(df_sqrt2(), rN);
+      rp = df_mul_f(df_sqrt2(), rP);
+    }
+    const float2 at = mk(p01.x, p01.y);
+    float2 Nv = mk(add_round(at.x, df_mul(sn, rn)), add_round(at.y, df_neg(df_mul(cs, rn))));
+    float2 Pv = mk(add_round(at.x, df_neg(df_mul(sn, rp))), add_round(at.y, df_mul(cs, rp)));
+    if ((meta & META_FLAG_OVERRIDE) && (j == 1 || j == 2)) {
+      float4 vv = __ldg(reinterpret_cast<const float4*>(&L->v1));
+      float2 v = j == 1 ? mk(vv.x, vv.y) : mk(vv.z, vv.w);
+      if (rN > 0.f) Nv = v; else Pv = v;
+    }
+    R.v = make_float4(Nv.x, Nv.y, Pv.x, Pv.y);
+    R.grel = mk(0.f, 0.f);
+    R.t = 0.f;
+    R.tlo = 0.f;
+    R.seg = false;
+  }
+  return R;
+}
+
+template <bool MIXED>
+__device__ __forceinline__ RibEval eval_rib(const LinkRec* __restrict__ L, int j) {
+  if constexpr (MIXED) return eval_rib_mx(L, j);
+  else return eval_rib32(L, j);
 }
 
 __device__ __forceinline__ int64_t find_link(const int32_t* off, int64_t lo, int64_t hi, int64_t r) {
@@ -1001,7 +1294,7 @@ __device__ __forceinline__ int64_t find_link_warp(const int32_t* off, int64_t n,
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(EMIT_NT, 3) k_emit(
+__global__ void __launch_bounds__(EMIT_NT, MIXED ? 2 : 3) k_emit(
     const LinkRec* __restrict__ recs, const int32_t* __restrict__ link_off,
     const int32_t* __restrict__ link_path, int64_t n_link, const int64_t* __restrict__ n_rib,
     int64_t capacity, float4* __restrict__ rib, uint32_t* __restrict__ tag,
@@ -1017,7 +1310,7 @@ __global__ void __launch_bounds__(EMIT_NT, 3) k_emit(
     const int64_t r0 = c * chunk;
     int64_t l = find_link_warp(link_off, n_link, r0, lane);
     float2 carry_g = mk(0.f, 0.f);
-    float carry_t = 0.f;
+    float carry_t = 0.f, carry_tl = 0.f;
 #pragma unroll 1
     for (int s = 0; s < emit_k; ++s) {
       const int64_t r = r0 + (int64_t)s * 32 + lane;
@@ -1025,6 +1318,7 @@ __global__ void __launch_bounds__(EMIT_NT, 3) k_emit(
       RibEval E;
       E.grel = mk(0.f, 0.f);
       E.t = 0.f;
+      E.tlo = 0.f;
       E.seg = false;
       int j = 0;
       if (active) {
@@ -1034,7 +1328,7 @@ __global__ void __launch_bounds__(EMIT_NT, 3) k_emit(
         rib[r] = E.v;
         uint32_t p = (uint32_t)__ldg(link_path + l);
         tag[r] = (p << 2) | (E.seg ? PS_TAG_SEGMENT : 0u) | (j == 0 ? PS_TAG_LINK_START : 0u);
-        if (tout) tout[r] = E.t;
+        if (tout) tout[r] = E.t + E.tlo;
       }
       if (chord) {
         // rib r - 1 is in the same link iff j > 0
@@ -1042,13 +1336,16 @@ __global__ void __launch_bounds__(EMIT_NT, 3) k_emit(
         pg.x = __shfl_up_sync(0xffffffffu, E.grel.x, 1);
         pg.y = __shfl_up_sync(0xffffffffu, E.grel.y, 1);
         float pt = __shfl_up_sync(0xffffffffu, E.t, 1);
+        float ptl = MIXED ? __shfl_up_sync(0xffffffffu, E.tlo, 1) : 0.f;
         if (lane == 0) {
           pg = carry_g;
           pt = carry_t;
+          ptl = carry_tl;
         }
         carry_g.x = __shfl_sync(0xffffffffu, E.grel.x, 31);
         carry_g.y = __shfl_sync(0xffffffffu, E.grel.y, 31);
         carry_t = __shfl_sync(0xffffffffu, E.t, 31);
+        if (MIXED) carry_tl = __shfl_sync(0xffffffffu, E.tlo, 31);
         if (active) {
           float cl = 0.f;
           if (E.seg && j > 0) {
@@ -1056,8 +1353,10 @@ __global__ void __launch_bounds__(EMIT_NT, 3) k_emit(
               RibEval Ep = eval_rib<MIXED>(recs + l, j - 1);
               pg = Ep.grel;
               pt = Ep.t;
+              ptl = Ep.tlo;
             }
-            if (E.t >= pt) {
+            // Sec. 7: a step whose t decreases adds no length
+            if (E.t > pt || (E.t == pt && E.tlo >= ptl)) {
               float dx = E.grel.x - pg.x, dy = E.grel.y - pg.y;
               cl = sqrtf(dx * dx + dy * dy);
             }
@@ -1420,10 +1719,9 @@ extern "C" int ps_arclength_scan(ps_context* ctx, const float* d_rib, const uint
 //
 // ps_tessellate_strokes keeps its workspace (per-link records, scan tile states)
 // in a context that grows it with cudaMalloc.  Some callers cannot allocate
-// device memory at the point where they stroke: code that runs while a stream is
-// being captured into a CUDA graph in global capture mode, code that runs where
-// another allocator owns the device's memory budget, or code that must not risk
-// a failed or blocking allocation in the middle of its work.  For them this
+// device memory at the point where they stroke: code that runs where another
+// allocator owns the device's memory budget, or code that must not risk a
+// failed or blocking allocation in the middle of its work.  For them this
 // variant takes its workspace from a fixed array that is part of the loaded
 // library image, so it makes no allocation of any kind.
 namespace {
@@ -1445,7 +1743,7 @@ constexpr size_t NA_CNT = al256(NA_INCLD + sizeof(double) * NOALLOC_TILES);
 constexpr size_t NA_BYTES = al256(NA_CNT + sizeof(int32_t) * 16);
 }  // namespace
 
-// The workspace: about 2.7 MB held by every device that loads the library until
+// The workspace: about 4.0 MB held by every device that loads the library until
 // the process exits.  Host code must not take this name as a device address; it
 // asks the runtime for the address on each device (below).
 static __device__ __align__(256) unsigned char ps_noalloc_scratch[NA_BYTES];

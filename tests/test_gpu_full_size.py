@@ -16,7 +16,6 @@ from tests._parity import compare_tess
 pytestmark = pytest.mark.gpu
 
 FRAG64 = oracle.FRAGILE64
-EPS_ANG = 4e-6
 
 
 def gpu_run(batch, emit_slabs=None, raster=False):
@@ -79,7 +78,7 @@ def check_sampled(batch, g, n_sample, seed):
     sb = batch.subset(paths)
     o = oracle.tessellate(sb)
     gs = gather(batch, g, paths)
-    stats, fails = compare_tess(o, gs, sb, FRAG64, EPS_ANG)
+    stats, fails = compare_tess(o, gs, sb, FRAG64)
     print(batch.name, "full size, sampled", n_sample, stats)
     assert not fails, fails
     assert stats["count_mismatch_fragile"] <= max(2, 2e-3 * stats["links"])

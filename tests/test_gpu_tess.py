@@ -16,8 +16,9 @@ from tests._parity import compare_tess, gpu_tessellate
 pytestmark = pytest.mark.gpu
 
 PLAIN, MIXED = 0, 1
-# angle error of the FP32 angle pipeline (atan2f, psi accumulation, sincosf), rad
-EPS_ANG = {PLAIN: 4e-6, MIXED: 4e-6}
+# angle error of the FP32 kernel's angle pipeline (atan2f, psi accumulation,
+# sincosf), rad, for its diagnostic bound; None: the contract bar (mixed)
+EPS_ANG = {PLAIN: 4e-6, MIXED: None}
 FRAG = {PLAIN: oracle.FRAGILE32, MIXED: oracle.FRAGILE64}
 
 

@@ -1,9 +1,9 @@
 """The allocation-free tessellation entry point.
 
 ps_tessellate_strokes_noalloc serves callers that cannot allocate device memory
-when they stroke (for example while a stream is being captured in global mode,
-or where another allocator owns the device's memory): it takes its workspace
-from a fixed array inside the library instead of a context.  This test calls it
+when they stroke (for example where another allocator owns the device's memory
+budget, or where an allocation must not block or fail partway through): it
+takes its workspace from a fixed array inside the library instead of a context.  This test calls it
 through the C ABI twice in a row and checks each result against the regular
 entry point's, with the tolerances the other parity tests use; it also checks
 that a problem larger than the fixed workspace is refused before any launch.
@@ -63,8 +63,9 @@ def test_noalloc_matches_regular_entry_point_twice(name, prec):
         assert np.array_equal(g["tag"], ref["tag"])
         # floating outputs within the parity tolerances, judged against the oracle
         frag = oracle.FRAGILE32 if prec == 0 else oracle.FRAGILE64
-        st_ref, f_ref = compare_tess(o, ref, b, frag, 4e-6)
-        st_new, f_new = compare_tess(o, g, b, frag, 4e-6)
+        eps = None if prec == 1 else 4e-6  # the contract bar in mixed precision
+        st_ref, f_ref = compare_tess(o, ref, b, frag, eps)
+        st_new, f_new = compare_tess(o, g, b, frag, eps)
         assert f_new == f_ref == []
         assert np.abs(g["rib"] - ref["rib"]).max() <= 1e-4
         assert np.abs(g["s"] - ref["s"]).max() <= 1e-5 * max(1.0, float(np.abs(ref["s"]).max()))
