@@ -106,6 +106,38 @@ PS_HD DF df_diff(float b, float a) { return two_sum(b, -a); }
 PS_HD DF df_cross(DF2 a, DF2 b) { return df_sub(df_mul(a.x, b.y), df_mul(a.y, b.x)); }
 PS_HD DF df_dot(DF2 a, DF2 b) { return df_add(df_mul(a.x, b.x), df_mul(a.y, b.y)); }
 
+// A lazily normalized sum: value s + e, where e gathers the rounding errors of
+// the terms added to s (|e| need not be below ulp(s)/2).  Sums of a few exact
+// products of pairs reach the same ~2^-48 accuracy as normalized pair
+// arithmetic with fewer operations.
+struct Acc {
+  float s, e;
+};
+// A += x y (x, y pairs)
+PS_HD void acc_prod(Acc& A, DF x, DF y) {
+  const float p = x.hi * y.hi;
+  const float pe = fmaf(x.hi, y.hi, -p);
+  const float s = A.s + p;
+  const float bb = s - A.s;
+  A.e += ((A.s - (s - bb)) + (p - bb)) + (pe + fmaf(x.hi, y.lo, x.lo * y.hi));
+  A.s = s;
+}
+PS_HD Acc acc_first(DF x, DF y) {
+  const float p = x.hi * y.hi;
+  return Acc{p, fmaf(x.hi, y.hi, -p) + fmaf(x.hi, y.lo, x.lo * y.hi)};
+}
+PS_HD DF acc_df(Acc A) { return DF{A.s, A.e}; }  // unnormalized pair
+PS_HD float acc_round(Acc A) { return A.s + A.e; }
+
+// a + g + x y rounded once (a a float; g, x, y pairs)
+PS_HD float sum_prod_round(DF s1, float gl, DF x, DF y) {
+  // s1 = two_sum(a, g.hi), gl = g.lo
+  const float p = x.hi * y.hi;
+  const float pe = fmaf(x.hi, y.hi, -p);
+  const DF s2 = two_sum(s1.hi, p);
+  return s2.hi + (s2.lo + ((s1.lo + gl) + (pe + fmaf(x.hi, y.lo, x.lo * y.hi))));
+}
+
 PS_HD DF df_pi() { return DF{PS_DF_PI_HI, PS_DF_PI_LO}; }
 PS_HD DF df_two_pi() { return DF{PS_DF_TWO_PI_HI, PS_DF_TWO_PI_LO}; }
 PS_HD DF df_sqrt2() { return DF{PS_DF_SQRT2_HI, PS_DF_SQRT2_LO}; }
@@ -145,8 +177,27 @@ PS_HD void df_sincos(DF x, const float4* tab, DF& s, DF& c) {
   const DF cr = fast_two_sum(0.5f * h2.hi, fmaf(0.5f, h2.lo, fmaf(rh, rl, -r2 * r2 * (1.f / 24.f))));
   const float4 e = sc_tab_load(tab, k & 511);
   const DF Sa{e.x, e.y}, Ca{e.z, e.w};
-  s = df_sub(df_add(Sa, df_mul(Ca, sr)), df_mul(Sa, cr));
-  c = df_sub(df_sub(Ca, df_mul(Sa, sr)), df_mul(Ca, cr));
+  // S_a + C_a sin r - S_a c and C_a - S_a sin r - C_a c, the products exact in
+  // their high parts, the remaining terms gathered in FP32 (all below 2^-24 of
+  // the result's ulp)
+  {
+    const float p1 = Ca.hi * sr.hi, e1 = fmaf(Ca.hi, sr.hi, -p1);
+    const float p2 = Sa.hi * cr.hi, e2 = fmaf(Sa.hi, cr.hi, -p2);
+    const DF a = two_sum(Sa.hi, p1);
+    const DF b = two_sum(a.hi, -p2);
+    const float lo = (a.lo + b.lo) + (Sa.lo + (e1 - e2)) +
+                     (fmaf(Ca.hi, sr.lo, Ca.lo * sr.hi) - fmaf(Sa.hi, cr.lo, Sa.lo * cr.hi));
+    s = fast_two_sum(b.hi, lo);
+  }
+  {
+    const float p1 = Sa.hi * sr.hi, e1 = fmaf(Sa.hi, sr.hi, -p1);
+    const float p2 = Ca.hi * cr.hi, e2 = fmaf(Ca.hi, cr.hi, -p2);
+    const DF a = two_sum(Ca.hi, -p1);
+    const DF b = two_sum(a.hi, -p2);
+    const float lo = (a.lo + b.lo) + (Ca.lo - (e1 + e2)) -
+                     (fmaf(Sa.hi, sr.lo, Sa.lo * sr.hi) + fmaf(Ca.hi, cr.lo, Ca.lo * cr.hi));
+    c = fast_two_sum(b.hi, lo);
+  }
 }
 
 // atan2(y, x) in (-pi, pi] to ~1e-14 (y = +0, x < 0 gives +pi).  a0 = atan2f (a few ulp); with

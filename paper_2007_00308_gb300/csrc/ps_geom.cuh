@@ -153,53 +153,48 @@ __device__ __forceinline__ float2 g_rel(const Seg& g, float t) {
   }
 }
 
-// Compensated g(t) - A (PS_PREC_MIXED): the Bernstein sum of (P_i - A) in
-// double-float arithmetic (ps_df.cuh) -- every product and sum carried as an
-// unevaluated pair through error-free transformations, at the float t.
+// Compensated g(t) - A (PS_PREC_MIXED): the Bernstein sum of (P_i - A) at the
+// float t in double-float arithmetic (ps_df.cuh) -- the differences exact as
+// pairs, the weights as pairs, the products exact in their high parts and the
+// rounding errors gathered lazily; the conic's quotient by one residual step.
 __device__ __forceinline__ DF2 g_rel_comp_df(const Seg& g, float t) {
-  DF T{t, 0.f};
-  DF U = two_sum(1.f, -t);
-  DF x{0.f, 0.f}, y{0.f, 0.f};
-  DF bx = two_sum(g.B.x, -g.A.x), by = two_sum(g.B.y, -g.A.y);
-  DF dx = two_sum(g.D.x, -g.A.x), dy = two_sum(g.D.y, -g.A.y);
+  const DF U = two_sum(1.f, -t);
+  const DF bx = two_sum(g.B.x, -g.A.x), by = two_sum(g.B.y, -g.A.y);
+  const DF dx = two_sum(g.D.x, -g.A.x), dy = two_sum(g.D.y, -g.A.y);
   switch (g.type) {
     case PS_CUBIC: {
-      DF cx = two_sum(g.C.x, -g.A.x), cy = two_sum(g.C.y, -g.A.y);
-      DF ut = df_mul(U, T);
-      DF wb = df_mul(df_mul(ut, U), DF{3.f, 0.f});
-      DF wc = df_mul(df_mul(ut, T), DF{3.f, 0.f});
-      DF wd = df_mul(df_mul(T, T), T);
-      x = df_add(df_add(df_mul(bx, wb), df_mul(cx, wc)), df_mul(dx, wd));
-      y = df_add(df_add(df_mul(by, wb), df_mul(cy, wc)), df_mul(dy, wd));
-      break;
+      const DF cx = two_sum(g.C.x, -g.A.x), cy = two_sum(g.C.y, -g.A.y);
+      const DF ut3 = df_mul_f(df_mul_f(U, t), 3.f);
+      const DF wb = df_mul(ut3, U), wc = df_mul_f(ut3, t), wd = df_mul_f(two_prod(t, t), t);
+      Acc x = acc_first(bx, wb), y = acc_first(by, wb);
+      acc_prod(x, cx, wc); acc_prod(y, cy, wc);
+      acc_prod(x, dx, wd); acc_prod(y, dy, wd);
+      return DF2{acc_df(x), acc_df(y)};
     }
     case PS_QUAD: {
-      DF wb = df_mul(df_mul(U, T), DF{2.f, 0.f});
-      DF wd = df_mul(T, T);
-      x = df_add(df_mul(bx, wb), df_mul(dx, wd));
-      y = df_add(df_mul(by, wb), df_mul(dy, wd));
-      break;
+      const DF wb = df_mul_f(df_mul_f(U, t), 2.f), wd = two_prod(t, t);
+      Acc x = acc_first(bx, wb), y = acc_first(by, wb);
+      acc_prod(x, dx, wd); acc_prod(y, dy, wd);
+      return DF2{acc_df(x), acc_df(y)};
     }
     case PS_CONIC: {
-      DF W{g.w, 0.f};
-      DF ut = df_mul(U, T);
-      DF wb = df_mul(df_mul(ut, W), DF{2.f, 0.f});
-      DF wd = df_mul(T, T);
-      DF den = df_add(df_add(df_mul(U, U), wb), wd);
-      x = df_add(df_mul(bx, wb), df_mul(dx, wd));
-      y = df_add(df_mul(by, wb), df_mul(dy, wd));
+      const DF ut = df_mul_f(U, t);
+      const DF wb = df_mul_f(ut, 2.f * g.w);  // 2w exact
+      const DF wd = two_prod(t, t);
+      const DF den = df_add(df_add(df_mul(U, U), wb), wd);
+      Acc ax = acc_first(bx, wb), ay = acc_first(by, wb);
+      acc_prod(ax, dx, wd); acc_prod(ay, dy, wd);
+      const DF x = fast_two_sum(ax.s, ax.e), y = fast_two_sum(ay.s, ay.e);
       // the quotient in double-float: q_hi, then the residual's quotient
-      float inv = 1.f / den.hi;
-      float qx = x.hi * inv, qy = y.hi * inv;
-      DF rx = df_sub(x, df_mul_f(den, qx));
-      DF ry = df_sub(y, df_mul_f(den, qy));
+      const float inv = 1.f / den.hi;
+      const float qx = x.hi * inv, qy = y.hi * inv;
+      const DF rx = df_sub(x, df_mul_f(den, qx));
+      const DF ry = df_sub(y, df_mul_f(den, qy));
       return DF2{fast_two_sum(qx, rx.hi * inv), fast_two_sum(qy, ry.hi * inv)};
     }
     default:
-      x = df_mul(dx, T);
-      y = df_mul(dy, T);
+      return DF2{df_mul_f(dx, t), df_mul_f(dy, t)};
   }
-  return DF2{x, y};
 }
 __device__ __forceinline__ float2 g_rel_comp(const Seg& g, float t) {
   DF2 v = g_rel_comp_df(g, t);

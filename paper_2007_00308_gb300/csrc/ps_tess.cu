@@ -73,17 +73,49 @@ __device__ __forceinline__ void solve_coeffs(const Seg& g, V N, R& a, R& b, R& c
   }
 }
 
+// The same roots with approximate division and square root (relative error
+// ~2^-22): the starting guesses of the mixed path, which Newton steps refine.
+__device__ __forceinline__ int quad_roots_fast(float a, float b, float c, float disc, float scale,
+                                               float tol, float* r) {
+  if (c == 0.f) {
+    if (b == 0.f) return 0;
+    r[0] = __fdividef(-a, b);
+    return 1;
+  }
+  if (disc < 0.f) {
+    if (-disc > tol * scale) return 0;
+    disc = 0.f;
+  }
+  const float sq = disc > 0.f ? disc * rsqrtf(disc) : 0.f;
+  const float q = -0.5f * (b + (b >= 0.f ? sq : -sq));
+  if (q != 0.f) {
+    r[0] = __fdividef(q, c);
+    r[1] = __fdividef(a, q);
+  } else {
+    r[0] = 0.f;
+    r[1] = 0.f;
+  }
+  if (r[0] > r[1]) {
+    float s = r[0];
+    r[0] = r[1];
+    r[1] = s;
+  }
+  return 2;
+}
+
 // t(psi) in [pa, pb] (Sec. 3.4) in FP32: roots of H(t).N(psi) = 0 inside the
 // range (with a small slack), the one whose tangent points along psi (largest
 // H.T(psi)), else the endpoint with the smaller |H.N|.  Returns whether a root
 // was taken, and the power-form coefficients for the caller's refinement.
+template <bool FAST = false>
 __device__ __forceinline__ bool solve_t32(const Seg& g, float sn, float cs, float pa, float pb,
                                           float& t_out, float& a, float& b, float& c) {
   float2 N = mk(-sn, cs), T = mk(cs, sn);
   solve_coeffs<float>(g, N, a, b, c);
   float disc = b * b - 4.f * a * c, scale = b * b + fabsf(4.f * a * c);
   float r[2];
-  int n = quad_roots<float>(a, b, c, disc, scale, 1e-5f, r);
+  int n = FAST ? quad_roots_fast(a, b, c, disc, scale, 1e-5f, r)
+               : quad_roots<float>(a, b, c, disc, scale, 1e-5f, r);
   float best = 0.f, bestv = -3.0e38f;
   bool found = false;
   for (int i = 0; i < n; ++i) {
@@ -148,36 +180,35 @@ __device__ __noinline__ bool solve_t64(const Seg& g, double sn, double cs, doubl
   return found;
 }
 
-// e_i = d_i . N for H(t) = sum_i d_i b_i(t) (the differences of Table 1's
-// hodograph, exact as pairs; N a double-float normal).
-__device__ __forceinline__ void hn_coeffs(const Seg& g, DF2 N, DF e[3]) {
+// f(t) = H(t).N at a float t in double-float (ps_df.cuh): H = sum_i w_i d_i with
+// the differences d_i exact as pairs and the weights as pairs -- cubic
+// (B-A) u^2 + 2(C-B) u t + (D-C) t^2, quadratic (B-A) u + (D-B) t, conic
+// w(B-A) u^2 + (D-A) u t + w(D-B) t^2 (u = 1 - t exact) -- and N a pair.
+// The power-form coefficients of solve_coeffs describe the same function.
+__device__ __forceinline__ float hn_resid(const Seg& g, float t, DF nx, DF ny) {
+  const DF U = two_sum(1.f, -t);
   DF2 d0, d1, d2;
+  DF w0, w1, w2;
   switch (g.type) {
-    case PS_CUBIC: d0 = df_vec(g.B, g.A); d1 = df_vec(g.C, g.B); d2 = df_vec(g.D, g.C); break;
-    case PS_QUAD: d0 = df_vec(g.B, g.A); d1 = df_vec(g.D, g.B); d2 = d1; break;
-    default: d0 = df_vec(g.B, g.A); d1 = df_vec(g.D, g.A); d2 = df_vec(g.D, g.B); break;
-  }
-  e[0] = df_dot(d0, N);
-  e[1] = df_dot(d1, N);
-  e[2] = df_dot(d2, N);
-}
-
-// f(t) = H(t).N at a float t in double-float: cubic e0 u^2 + 2 e1 u t + e2 t^2,
-// quadratic e0 u + e1 t, conic w e0 u^2 + e1 u t + w e2 t^2 (u = 1 - t exact).
-__device__ __forceinline__ DF hn_eval(const Seg& g, const DF e[3], float t) {
-  const DF T{t, 0.f}, U = two_sum(1.f, -t);
-  switch (g.type) {
-    case PS_CUBIC: {
-      DF ut = df_mul(U, T);
-      return df_add(df_add(df_mul(e[0], df_mul(U, U)), df_mul_f(df_mul(e[1], ut), 2.f)),
-                    df_mul(e[2], two_prod(t, t)));
-    }
+    case PS_CUBIC:
+      d0 = df_vec(g.B, g.A); d1 = df_vec(g.C, g.B); d2 = df_vec(g.D, g.C);
+      w0 = df_mul(U, U); w1 = df_mul_f(U, 2.f * t); w2 = two_prod(t, t);
+      break;
     case PS_QUAD:
-      return df_add(df_mul(e[0], U), df_mul_f(e[1], t));
+      d0 = df_vec(g.B, g.A); d1 = df_vec(g.D, g.B); d2 = d1;
+      w0 = U; w1 = DF{t, 0.f}; w2 = DF{0.f, 0.f};
+      break;
     default:
-      return df_add(df_add(df_mul_f(df_mul(e[0], df_mul(U, U)), g.w), df_mul(e[1], df_mul(U, T))),
-                    df_mul_f(df_mul(e[2], two_prod(t, t)), g.w));
+      d0 = df_vec(g.B, g.A); d1 = df_vec(g.D, g.A); d2 = df_vec(g.D, g.B);
+      w0 = df_mul_f(df_mul(U, U), g.w); w1 = df_mul_f(U, t); w2 = df_mul_f(two_prod(t, t), g.w);
+      break;
   }
+  Acc hx = acc_first(d0.x, w0), hy = acc_first(d0.y, w0);
+  acc_prod(hx, d1.x, w1); acc_prod(hy, d1.y, w1);
+  acc_prod(hx, d2.x, w2); acc_prod(hy, d2.y, w2);
+  Acc f = acc_first(acc_df(hx), nx);
+  acc_prod(f, acc_df(hy), ny);
+  return acc_round(f);
 }
 
 // t(psi) in PS_PREC_MIXED (Eq. 11), as a double-float pair.  The root is chosen
@@ -190,20 +221,19 @@ __device__ __forceinline__ DF hn_eval(const Seg& g, const DF e[3], float t) {
 __device__ DF solve_t_mx(const Seg& g, DF sn, DF cs, DF pa, DF pb) {
   if (g.type == PS_LINE) return pa;
   float t0, a, b, c;
-  const bool root = solve_t32(g, sn.hi, cs.hi, pa.hi, pb.hi, t0, a, b, c);
+  const bool root = solve_t32<true>(g, sn.hi, cs.hi, pa.hi, pb.hi, t0, a, b, c);
   const float disc = b * b - 4.f * a * c, scale = b * b + fabsf(4.f * a * c);
   bool f64 = c != 0.f && fabsf(disc) < 1e-3f * scale;
   DF t;
   if (!f64) {
     if (!root) return t0 == pa.hi ? pa : pb;  // endpoint rule
-    DF e[3];
-    hn_coeffs(g, DF2{df_neg(sn), cs}, e);
+    const DF nx = df_neg(sn);
     float fp = fmaf(2.f * c, t0, b);
-    float dt = fp != 0.f ? -df_f(hn_eval(g, e, t0)) / fp : 0.f;
+    float dt = fp != 0.f ? -__fdividef(hn_resid(g, t0, nx, cs), fp) : 0.f;
     if (fabsf(dt) > 2.4e-7f * fmaxf(fabsf(t0), 1e-3f)) {
       t0 += dt;
       fp = fmaf(2.f * c, t0, b);
-      dt = fp != 0.f ? -df_f(hn_eval(g, e, t0)) / fp : 0.f;
+      dt = fp != 0.f ? -__fdividef(hn_resid(g, t0, nx, cs), fp) : 0.f;
     }
     f64 = !(fabsf(dt) <= 1e-4f);
     t = two_sum(t0, dt);
@@ -490,7 +520,6 @@ __device__ __forceinline__ void put_step(LinkRec& L, int k, DF v) { L.step[k] = 
 // Returns N (total steps) or -1 if the table does not fit.
 template <bool PX>
 __device__ int seg_intervals32(const Seg& g, Step S, LinkRec& L) {
-  const float q = S.q;
   float Psi0 = angf(end_grad0(g)), Psin = angf(end_grad1(g));
   CrossPoly<float> Pf = cross_poly<float>(g);
   int M = 0;
@@ -1192,68 +1221,69 @@ __device__ __forceinline__ RibEval eval_rib32(const LinkRec* __restrict__ L, int
 __device__ __forceinline__ DF ld_pair(const float* hi, const float* lo) { return DF{__ldg(hi), __ldg(lo)}; }
 
 // One rib, PS_PREC_MIXED: psi(j) = Psi_k + step_k (j - Delta_Sigma(k)) as a
-// pair, its normal by the double-float sincos, t by the double-float solve,
-// g(t) compensated, and each vertex coordinate summed as a pair and rounded
-// once (Eq. 14-17).
+// pair, its normal by the double-float sincos (one call for every kind of
+// link), t by the double-float solve, g(t) compensated, and each vertex
+// coordinate summed in double-float and rounded once (Eq. 14-17).
 __device__ __forceinline__ RibEval eval_rib_mx(const LinkRec* __restrict__ L, int j) {
   RibEval R;
-  uint32_t meta = __ldg(&L->meta);
-  int kind = META_KIND(meta);
-  int M = META_M(meta);
-  float4 p01 = __ldg(reinterpret_cast<const float4*>(L->P));
-  float rN = __ldg(&L->rN), rP = __ldg(&L->rP);
-  if (kind == LK_SEG) {
+  const uint32_t meta = __ldg(&L->meta);
+  const int kind = META_KIND(meta);
+  const float4 p01 = __ldg(reinterpret_cast<const float4*>(L->P));
+  const float rN = __ldg(&L->rN), rP = __ldg(&L->rP);
+  const bool seg = kind == LK_SEG;
+  // the rib's angle
+  int k = 0, dk = 0;
+  DF psi;
+  if (seg) {
+    const int M = META_M(meta);
+    while (k < M && j >= (int)__ldg(&L->dsum[k + 1])) ++k;
+    dk = (int)__ldg(&L->dsum[k]);
+  } else {
+    dk = j == (int)__ldg(&L->dsum[1]) ? j : 0;  // the last pivot rib is Psi_1 itself
+    k = dk ? 1 : 0;
+  }
+  psi = ld_pair(&L->psi[k], &L->psi_lo[k]);
+  if (j != dk) psi = df_add(psi, df_mul_f(ld_pair(&L->step[k], &L->step_lo[k]), (float)(j - dk)));
+  DF sn, cs;
+  df_sincos(psi, ps_sc_tab, sn, cs);
+  // the generator point, relative parts as a pair
+  float ax = p01.x, ay = p01.y;
+  DF gx{0.f, 0.f}, gy{0.f, 0.f};
+  DF rn = df_of(rN), rp = df_of(rP);
+  R.grel = mk(0.f, 0.f);
+  R.t = 0.f;
+  R.tlo = 0.f;
+  if (seg) {
     Seg g;
-    float4 p23 = __ldg(reinterpret_cast<const float4*>(L->P) + 1);
+    const float4 p23 = __ldg(reinterpret_cast<const float4*>(L->P) + 1);
     g.type = META_TYPE(meta);
     g.A = mk(p01.x, p01.y); g.B = mk(p01.z, p01.w); g.C = mk(p23.x, p23.y); g.D = mk(p23.z, p23.w);
     g.w = __ldg(&L->w);
-    int k = 0;
-    while (k < M && j >= (int)__ldg(&L->dsum[k + 1])) ++k;
-    const int dk = (int)__ldg(&L->dsum[k]);
-    const bool bnd = j == dk;
-    DF psi = ld_pair(&L->psi[k], &L->psi_lo[k]);
-    if (!bnd) psi = df_add(psi, df_mul_f(ld_pair(&L->step[k], &L->step_lo[k]), (float)(j - dk)));
-    DF sn, cs;
-    df_sincos(psi, ps_sc_tab, sn, cs);
     const DF pa = ld_pair(&L->p[k], &L->p_lo[k]);
     DF t = pa;
-    if (!bnd && !META_PIVOT(meta, k)) t = solve_t_mx(g, sn, cs, pa, ld_pair(&L->p[k + 1], &L->p_lo[k + 1]));
+    if (j != dk && !META_PIVOT(meta, k))
+      t = solve_t_mx(g, sn, cs, pa, ld_pair(&L->p[k + 1], &L->p_lo[k + 1]));
     const DF2 gr = g_rel_df(g, t);
-    // N = A + g - rN n, P = A + g + rP n with n = (-sin psi, cos psi)
-    const DF gx = df_add_f(gr.x, g.A.x), gy = df_add_f(gr.y, g.A.y);
-    R.v = make_float4(df_f(df_add(gx, df_mul_f(sn, rN))), df_f(df_sub(gy, df_mul_f(cs, rN))),
-                      df_f(df_sub(gx, df_mul_f(sn, rP))), df_f(df_add(gy, df_mul_f(cs, rP))));
+    gx = gr.x;
+    gy = gr.y;
     R.grel = mk(df_f(gr.x), df_f(gr.y));
     R.t = t.hi;
     R.tlo = t.lo;
-    R.seg = true;
-  } else {
-    const int J = (int)__ldg(&L->dsum[1]);
-    DF psi;
-    if (j == J) psi = ld_pair(&L->psi[1], &L->psi_lo[1]);
-    else psi = df_add(ld_pair(&L->psi[0], &L->psi_lo[0]), df_mul_f(ld_pair(&L->step[0], &L->step_lo[0]), (float)j));
-    DF sn, cs;
-    df_sincos(psi, ps_sc_tab, sn, cs);
-    DF rn = df_of(rN), rp = df_of(rP);
-    if ((meta & META_FLAG_SQUARE) && (j == 1 || j == 3)) {
-      rn = df_mul_f(df_sqrt2(), rN);
-      rp = df_mul_f(df_sqrt2(), rP);
-    }
-    const float2 at = mk(p01.x, p01.y);
-    float2 Nv = mk(add_round(at.x, df_mul(sn, rn)), add_round(at.y, df_neg(df_mul(cs, rn))));
-    float2 Pv = mk(add_round(at.x, df_neg(df_mul(sn, rp))), add_round(at.y, df_mul(cs, rp)));
-    if ((meta & META_FLAG_OVERRIDE) && (j == 1 || j == 2)) {
-      float4 vv = __ldg(reinterpret_cast<const float4*>(&L->v1));
-      float2 v = j == 1 ? mk(vv.x, vv.y) : mk(vv.z, vv.w);
-      if (rN > 0.f) Nv = v; else Pv = v;
-    }
-    R.v = make_float4(Nv.x, Nv.y, Pv.x, Pv.y);
-    R.grel = mk(0.f, 0.f);
-    R.t = 0.f;
-    R.tlo = 0.f;
-    R.seg = false;
+  } else if ((meta & META_FLAG_SQUARE) && (j == 1 || j == 3)) {
+    rn = df_mul_f(df_sqrt2(), rN);
+    rp = df_mul_f(df_sqrt2(), rP);
   }
+  // N = A + g - rn n, P = A + g + rp n, n = (-sin psi, cos psi)
+  const DF sx = two_sum(ax, gx.hi), sy = two_sum(ay, gy.hi);
+  float4 v = make_float4(sum_prod_round(sx, gx.lo, sn, rn), sum_prod_round(sy, gy.lo, df_neg(cs), rn),
+                         sum_prod_round(sx, gx.lo, df_neg(sn), rp), sum_prod_round(sy, gy.lo, cs, rp));
+  if ((meta & META_FLAG_OVERRIDE) && (j == 1 || j == 2)) {
+    const float4 vv = __ldg(reinterpret_cast<const float4*>(&L->v1));
+    const float2 o = j == 1 ? mk(vv.x, vv.y) : mk(vv.z, vv.w);
+    if (rN > 0.f) { v.x = o.x; v.y = o.y; } else { v.z = o.x; v.w = o.y; }
+  }
+  R.v = v;
+  R.seg = seg;
   return R;
 }
 
