@@ -248,24 +248,47 @@ __global__ void __launch_bounds__(256) k_adj_ribs(
     float P8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int seg_t = -1, path_t = -1, kslot = 0;
     float gw = 0.f, psA = 0.f, psB = 0.f;
-    if (act) {
-    int j = (int)(r - __ldg(link_off + l));
-    int nr = __ldg(link_off + l + 1) - __ldg(link_off + l);
     const LinkRec* L = recs + l;
-    uint32_t meta = __ldg(&L->meta);
-    int kind = META_KIND(meta);
+    const uint32_t meta = act ? __ldg(&L->meta) : 0u;
+    const int kind = META_KIND(meta);
+    const int j = act ? (int)(r - __ldg(link_off + l)) : 0;
+    const int nr = act ? __ldg(link_off + l + 1) - __ldg(link_off + l) : 0;
+    // The chords of Eq. 18 beside this rib: their directions from the
+    // centreline points g(t) - A in double-float, differenced before rounding
+    // (a short chord between points far from A keeps its direction); the
+    // neighbours' points come from the neighbouring lanes of the same link.
+    Seg g;
+    float t = 0.f;
+    DF2 gc{{0.f, 0.f}, {0.f, 0.f}};
+    if (kind == LK_SEG) {
+      const float4 p01 = __ldg(reinterpret_cast<const float4*>(L->P));
+      const float4 p23 = __ldg(reinterpret_cast<const float4*>(L->P) + 1);
+      g.type = META_TYPE(meta);
+      g.A = mk(p01.x, p01.y); g.B = mk(p01.z, p01.w); g.C = mk(p23.x, p23.y); g.D = mk(p23.z, p23.w);
+      g.w = __ldg(&L->w);
+      t = __ldg(tf + r);
+      gc = g_rel_comp_df(g, t);
+    }
+    DF2 gprev, gnext;
+    gprev.x.hi = __shfl_up_sync(0xffffffffu, gc.x.hi, 1);
+    gprev.x.lo = __shfl_up_sync(0xffffffffu, gc.x.lo, 1);
+    gprev.y.hi = __shfl_up_sync(0xffffffffu, gc.y.hi, 1);
+    gprev.y.lo = __shfl_up_sync(0xffffffffu, gc.y.lo, 1);
+    gnext.x.hi = __shfl_down_sync(0xffffffffu, gc.x.hi, 1);
+    gnext.x.lo = __shfl_down_sync(0xffffffffu, gc.x.lo, 1);
+    gnext.y.hi = __shfl_down_sync(0xffffffffu, gc.y.hi, 1);
+    gnext.y.lo = __shfl_down_sync(0xffffffffu, gc.y.lo, 1);
+    if (kind == LK_SEG) {
+      if (lane == 0 && j > 0) gprev = g_rel_comp_df(g, __ldg(tf + r - 1));
+      if (lane == 31 && j + 1 < nr) gnext = g_rel_comp_df(g, __ldg(tf + r + 1));
+    }
+    if (act) {
     int4 sc = __ldg(src + l);
     float4 G = __ldg(grib + r);
     float2 GN = mk(G.x, G.y), GP = mk(G.z, G.w);
     float rN = __ldg(&L->rN), rP = __ldg(&L->rP);
     if (kind == LK_SEG) {
       int M = META_M(meta);
-      Seg g;
-      float4 p01 = __ldg(reinterpret_cast<const float4*>(L->P));
-      float4 p23 = __ldg(reinterpret_cast<const float4*>(L->P) + 1);
-      g.type = META_TYPE(meta);
-      g.A = mk(p01.x, p01.y); g.B = mk(p01.z, p01.w); g.C = mk(p23.x, p23.y); g.D = mk(p23.z, p23.w);
-      g.w = __ldg(&L->w);
       int k = 0;
       while (k < M && j >= (int)__ldg(&L->dsum[k + 1])) ++k;
       int dk = (int)__ldg(&L->dsum[k]);
@@ -277,23 +300,19 @@ __global__ void __launch_bounds__(256) k_adj_ribs(
         psi = __ldg(&L->psi[k]) + __ldg(&L->step[k]) * (float)(j - dk);
         lam = (float)(j - dk) / (float)Dk;
       }
-      float t = __ldg(tf + r);
       float sn, cs;
       sincosf(psi, &sn, &cs);
       float2 n = mk(-sn, cs), T = mk(cs, sn);
       // upstream on the centreline point: both vertices, and the chords to the
       // neighbouring ribs of this link (Eq. 18; a step with decreasing t adds 0)
       float2 Gg = GN + GP;
-      float2 m = mk(0.5f * (__ldg(&rib[r].x) + __ldg(&rib[r].z)), 0.5f * (__ldg(&rib[r].y) + __ldg(&rib[r].w)));
       if (j > 0 && t >= __ldg(tf + r - 1)) {
-        float4 q = __ldg(rib + r - 1);
-        float2 d = m - mk(0.5f * (q.x + q.z), 0.5f * (q.y + q.w));
+        float2 d = mk(df_f(df_sub(gc.x, gprev.x)), df_f(df_sub(gc.y, gprev.y)));
         float len = sqrtf(dot2(d, d));
         if (len > 0.f) Gg = Gg + d * (__ldg(suffix + r) / len);
       }
       if (j + 1 < nr && __ldg(tf + r + 1) >= t) {
-        float4 q = __ldg(rib + r + 1);
-        float2 d = mk(0.5f * (q.x + q.z), 0.5f * (q.y + q.w)) - m;
+        float2 d = mk(df_f(df_sub(gnext.x, gc.x)), df_f(df_sub(gnext.y, gc.y)));
         float len = sqrtf(dot2(d, d));
         if (len > 0.f) Gg = Gg - d * (__ldg(suffix + r + 1) / len);
       }

@@ -96,6 +96,12 @@ PS_HD DF df_div(DF a, DF b) {
   DF r = df_sub(a, df_mul_f(b, q));
   return fast_two_sum(q, r.hi / b.hi);
 }
+PS_HD DF df_sqrt(DF a) {
+  if (!(a.hi > 0.f)) return DF{0.f, 0.f};
+  const float s = sqrtf(a.hi);
+  const DF e = df_sub(a, two_prod(s, s));
+  return fast_two_sum(s, e.hi / (2.f * s));
+}
 PS_HD bool df_lt(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 PS_HD bool df_le(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
 PS_HD DF df_abs(DF a) { return (a.hi < 0.f || (a.hi == 0.f && a.lo < 0.f)) ? df_neg(a) : a; }

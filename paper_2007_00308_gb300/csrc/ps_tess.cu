@@ -211,45 +211,124 @@ __device__ __forceinline__ float hn_resid(const Seg& g, float t, DF nx, DF ny) {
   return acc_round(f);
 }
 
+// H(t).N as a power-form quadratic a + b t + c t^2 with double-float
+// coefficients (the differences exact as pairs, N a pair).
+__device__ __forceinline__ void hn_coeffs_df(const Seg& g, DF nx, DF ny, DF& a, DF& b, DF& c) {
+  DF2 d0, d1, d2;
+  switch (g.type) {
+    case PS_CUBIC: d0 = df_vec(g.B, g.A); d1 = df_vec(g.C, g.B); d2 = df_vec(g.D, g.C); break;
+    case PS_QUAD: d0 = df_vec(g.B, g.A); d1 = df_vec(g.D, g.B); d2 = d1; break;
+    default: d0 = df_vec(g.B, g.A); d1 = df_vec(g.D, g.A); d2 = df_vec(g.D, g.B); break;
+  }
+  auto dotn = [&](DF2 d) {
+    Acc A = acc_first(d.x, nx);
+    acc_prod(A, d.y, ny);
+    return fast_two_sum(A.s, A.e);
+  };
+  const DF e0 = dotn(d0), e1 = dotn(d1), e2 = dotn(d2);
+  switch (g.type) {
+    case PS_CUBIC:  // e0 u^2 + 2 e1 u t + e2 t^2
+      a = e0;
+      b = df_mul_f(df_sub(e1, e0), 2.f);
+      c = df_add(df_sub(e0, df_mul_f(e1, 2.f)), e2);
+      break;
+    case PS_QUAD:  // e0 u + e1 t
+      a = e0;
+      b = df_sub(e1, e0);
+      c = DF{0.f, 0.f};
+      break;
+    default: {  // w e0 u^2 + e1 u t + w e2 t^2
+      const DF we0 = df_mul_f(e0, g.w), we2 = df_mul_f(e2, g.w);
+      a = we0;
+      b = df_sub(e1, df_mul_f(we0, 2.f));
+      c = df_add(df_sub(we0, e1), we2);
+    }
+  }
+}
+
+// t(psi) by the oracle's steps (stable quadratic formula, range test with a
+// 1e-12 slack, alias rejection by the largest H.T, endpoint rule) with
+// double-float coefficients and roots: the near-double-root case, where the
+// FP32 discriminant cancels.  A discriminant within 1e-10 of its scale (a
+// double root to double-float precision) is solved in FP64.
+__device__ DF solve_t_quad_df(const Seg& g, DF sn, DF cs, DF pa, DF pb) {
+  const DF nx = df_neg(sn);
+  DF a, b, c;
+  hn_coeffs_df(g, nx, cs, a, b, c);
+  DF r[2];
+  int n = 0;
+  if (df_is0(c)) {
+    if (!df_is0(b)) r[n++] = df_neg(df_div(a, b));
+  } else {
+    DF disc = df_sub(df_mul(b, b), df_mul_f(df_mul(a, c), 4.f));
+    const float scale = b.hi * b.hi + fabsf(4.f * a.hi * c.hi);
+    if (fabsf(disc.hi) < 1e-10f * scale) {
+      double td;
+      if (solve_t64(g, df_d(sn), df_d(cs), df_d(pa), df_d(pb), td)) return df_from_d(td);
+    }
+    if (disc.hi < 0.f && -disc.hi <= 1e-12f * scale) disc = DF{0.f, 0.f};
+    if (!(disc.hi < 0.f)) {
+      const DF sq = df_sqrt(disc);
+      const DF q = df_mul_f(df_add(b, b.hi >= 0.f ? sq : df_neg(sq)), -0.5f);
+      if (!df_is0(q)) {
+        r[n++] = df_div(q, c);
+        r[n++] = df_div(a, q);
+      }
+    }
+  }
+  const DF lo = df_add_f(pa, -1e-12f), hi = df_add_f(pb, 1e-12f);
+  const float2 T = mk(cs.hi, sn.hi);
+  DF best = pa;
+  float bestv = -3.0e38f;
+  bool found = false;
+  for (int i = 0; i < n; ++i) {
+    DF t = r[i];
+    if (df_lt(t, lo) || df_lt(hi, t)) continue;
+    if (df_lt(t, pa)) t = pa;
+    if (df_lt(pb, t)) t = pb;
+    const float v = dot2(hodo(g, t.hi), T);
+    if (!found || v > bestv) {
+      bestv = v;
+      best = t;
+      found = true;
+    }
+  }
+  if (found) return best;
+  const float2 N = mk(nx.hi, cs.hi);
+  const float fa = fabsf(dot2(hodo(g, pa.hi), N)), fb = fabsf(dot2(hodo(g, pb.hi), N));
+  return fa < fb ? pa : pb;
+}
+
 // t(psi) in PS_PREC_MIXED (Eq. 11), as a double-float pair.  The root is chosen
-// in FP32 as above (alias rejection, endpoint rule), then refined by Newton
-// steps on H(t).N(psi) = 0 with the residual in double-float from the
-// double-float normal (sn, cs): one step from the FP32 root, a second one when
-// the first moved t by more than a few ulps.  A near double root (|disc| below
-// 1e-3 of its scale), or a step that moved t by more than 1e-4, is solved in
-// FP64 instead (the cancellation there needs it).
+// in FP32 as above (alias rejection, endpoint rule), then refined by a Newton
+// step on H(t).N(psi) = 0 with the residual in double-float from the
+// double-float normal (sn, cs), and a second step where the first one's
+// quadratic term, c dt^2 / f', could exceed 1e-12.  A near double root (the
+// FP32 discriminant below 1e-3 of its scale), or a step that moved t by more
+// than 1e-4, takes the double-float quadratic solve instead.
 __device__ DF solve_t_mx(const Seg& g, DF sn, DF cs, DF pa, DF pb) {
   if (g.type == PS_LINE) return pa;
   float t0, a, b, c;
   const bool root = solve_t32<true>(g, sn.hi, cs.hi, pa.hi, pb.hi, t0, a, b, c);
   const float disc = b * b - 4.f * a * c, scale = b * b + fabsf(4.f * a * c);
-  bool f64 = c != 0.f && fabsf(disc) < 1e-3f * scale;
-  DF t;
-  if (!f64) {
+  if (!(c != 0.f && fabsf(disc) < 1e-3f * scale)) {
     if (!root) return t0 == pa.hi ? pa : pb;  // endpoint rule
     const DF nx = df_neg(sn);
     float fp = fmaf(2.f * c, t0, b);
     float dt = fp != 0.f ? -__fdividef(hn_resid(g, t0, nx, cs), fp) : 0.f;
-    if (fabsf(dt) > 2.4e-7f * fmaxf(fabsf(t0), 1e-3f)) {
+    if (fabsf(c * dt * dt) > 1e-12f * fabsf(fp)) {
       t0 += dt;
       fp = fmaf(2.f * c, t0, b);
       dt = fp != 0.f ? -__fdividef(hn_resid(g, t0, nx, cs), fp) : 0.f;
     }
-    f64 = !(fabsf(dt) <= 1e-4f);
-    t = two_sum(t0, dt);
-  }
-  if (f64) {
-    double td;
-    if (solve_t64(g, df_d(sn), df_d(cs), df_d(pa), df_d(pb), td)) {
-      t = df_from_d(td);
-    } else {
-      if (!root) return t0 == pa.hi ? pa : pb;
-      t = df_of(t0);
+    if (fabsf(dt) <= 1e-4f) {
+      DF t = two_sum(t0, dt);
+      if (df_lt(t, pa)) t = pa;
+      if (df_lt(pb, t)) t = pb;
+      return t;
     }
   }
-  if (df_lt(t, pa)) t = pa;
-  if (df_lt(pb, t)) t = pb;
-  return t;
+  return solve_t_quad_df(g, sn, cs, pa, pb);
 }
 
 // ---------------------------------------------------------------------------
@@ -1153,6 +1232,7 @@ constexpr int EMIT_K = 16;  // slabs of 32 ribs per chunk by default (tunable: 4
 struct RibEval {
   float4 v;      // N.x N.y P.x P.y
   float2 grel;   // g(t) - A (segments) for the chord
+  float2 glo;    // its low parts as pairs (0 in FP32)
   float t, tlo;  // t as a pair (tlo = 0 in FP32)
   bool seg;
 };
@@ -1167,6 +1247,7 @@ __device__ __forceinline__ RibEval eval_rib32(const LinkRec* __restrict__ L, int
   float4 p01 = __ldg(reinterpret_cast<const float4*>(L->P));
   float rN = __ldg(&L->rN), rP = __ldg(&L->rP);
   R.tlo = 0.f;
+  R.glo = mk(0.f, 0.f);
   if (kind == LK_SEG) {
     Seg g;
     float4 p23 = __ldg(reinterpret_cast<const float4*>(L->P) + 1);
@@ -1251,6 +1332,7 @@ __device__ __forceinline__ RibEval eval_rib_mx(const LinkRec* __restrict__ L, in
   DF gx{0.f, 0.f}, gy{0.f, 0.f};
   DF rn = df_of(rN), rp = df_of(rP);
   R.grel = mk(0.f, 0.f);
+  R.glo = mk(0.f, 0.f);
   R.t = 0.f;
   R.tlo = 0.f;
   if (seg) {
@@ -1266,7 +1348,8 @@ __device__ __forceinline__ RibEval eval_rib_mx(const LinkRec* __restrict__ L, in
     const DF2 gr = g_rel_df(g, t);
     gx = gr.x;
     gy = gr.y;
-    R.grel = mk(df_f(gr.x), df_f(gr.y));
+    R.grel = mk(gr.x.hi, gr.y.hi);
+    R.glo = mk(gr.x.lo, gr.y.lo);
     R.t = t.hi;
     R.tlo = t.lo;
   } else if ((meta & META_FLAG_SQUARE) && (j == 1 || j == 3)) {
@@ -1339,7 +1422,7 @@ __global__ void __launch_bounds__(EMIT_NT, MIXED ? 2 : 3) k_emit(
   for (int64_t c = warp0; c < n_chunks; c += n_warps) {
     const int64_t r0 = c * chunk;
     int64_t l = find_link_warp(link_off, n_link, r0, lane);
-    float2 carry_g = mk(0.f, 0.f);
+    float2 carry_g = mk(0.f, 0.f), carry_gl = mk(0.f, 0.f);
     float carry_t = 0.f, carry_tl = 0.f;
 #pragma unroll 1
     for (int s = 0; s < emit_k; ++s) {
@@ -1347,6 +1430,7 @@ __global__ void __launch_bounds__(EMIT_NT, MIXED ? 2 : 3) k_emit(
       const bool active = r < R;
       RibEval E;
       E.grel = mk(0.f, 0.f);
+      E.glo = mk(0.f, 0.f);
       E.t = 0.f;
       E.tlo = 0.f;
       E.seg = false;
@@ -1362,18 +1446,27 @@ __global__ void __launch_bounds__(EMIT_NT, MIXED ? 2 : 3) k_emit(
       }
       if (chord) {
         // rib r - 1 is in the same link iff j > 0
-        float2 pg;
+        float2 pg, pgl = mk(0.f, 0.f);
         pg.x = __shfl_up_sync(0xffffffffu, E.grel.x, 1);
         pg.y = __shfl_up_sync(0xffffffffu, E.grel.y, 1);
+        if (MIXED) {
+          pgl.x = __shfl_up_sync(0xffffffffu, E.glo.x, 1);
+          pgl.y = __shfl_up_sync(0xffffffffu, E.glo.y, 1);
+        }
         float pt = __shfl_up_sync(0xffffffffu, E.t, 1);
         float ptl = MIXED ? __shfl_up_sync(0xffffffffu, E.tlo, 1) : 0.f;
         if (lane == 0) {
           pg = carry_g;
+          pgl = carry_gl;
           pt = carry_t;
           ptl = carry_tl;
         }
         carry_g.x = __shfl_sync(0xffffffffu, E.grel.x, 31);
         carry_g.y = __shfl_sync(0xffffffffu, E.grel.y, 31);
+        if (MIXED) {
+          carry_gl.x = __shfl_sync(0xffffffffu, E.glo.x, 31);
+          carry_gl.y = __shfl_sync(0xffffffffu, E.glo.y, 31);
+        }
         carry_t = __shfl_sync(0xffffffffu, E.t, 31);
         if (MIXED) carry_tl = __shfl_sync(0xffffffffu, E.tlo, 31);
         if (active) {
@@ -1382,12 +1475,15 @@ __global__ void __launch_bounds__(EMIT_NT, MIXED ? 2 : 3) k_emit(
             if (lane == 0 && s == 0) {
               RibEval Ep = eval_rib<MIXED>(recs + l, j - 1);
               pg = Ep.grel;
+              pgl = Ep.glo;
               pt = Ep.t;
               ptl = Ep.tlo;
             }
-            // Sec. 7: a step whose t decreases adds no length
+            // Sec. 7: a step whose t decreases adds no length.  The chord is
+            // differenced as pairs before rounding (MIXED).
             if (E.t > pt || (E.t == pt && E.tlo >= ptl)) {
-              float dx = E.grel.x - pg.x, dy = E.grel.y - pg.y;
+              float dx = (E.grel.x - pg.x) + (E.glo.x - pgl.x);
+              float dy = (E.grel.y - pg.y) + (E.glo.y - pgl.y);
               cl = sqrtf(dx * dx + dy * dy);
             }
           }
