@@ -271,25 +271,60 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
-# Algorithmic work per launch of each kernel: bytes the method must move for
-# the HBM-class kernels; sample tests for the coverage kernel (ALU-bound).
-# Per unit: link setup reads 40 B/segment + 24 B/path and writes a 160 B record
-# + 4 B offset per link; the emitter writes 16 B rib + 4 B tag + 4 B chord per
-# rib and reads its link's record (168 B/link); the arc-length scan reads
-# chord + tag and writes s (12 B/rib); binning reads a quad (two ribs, shared
-# with the next quad: 16 B/rib + 4 B tag) per pass and the scatter writes 4 B
-# per bin entry; coverage tests 16 samples per span pixel.
+# Algorithmic work per launch of each kernel: the bytes the method itself must
+# move for the HBM-class kernels, sample tests for the coverage kernel.  The
+# tessellation stage reads 40 B per segment and 24 B per path and writes 16 B
+# per rib (N, P), 4 B per rib (s) and 4 B per link (offset): 40S + 24P + 20R +
+# 4L, split as link set-up 40S + 24P + 4L, emitter 16R, arc length 4R.  Binning
+# reads 16 B per rib once, writes 4 B per (quad, tile) entry and 4 B per tile
+# offset: 16R + 4 pairs + 4 tiles, split as count 16R, tile scan 4 tiles,
+# scatter 4 pairs.  The library's own workspace (per-link records, per-rib tags
+# and chords, the binning passes' per-rib hit words) is not the method's work:
+# it is listed per kernel as workspace_bytes (design figures; DRAM traffic
+# measured by ncu is in profiles/).
 def algorithmic(kernel, c):
-    R, L, S, P, pairs, px = c["R"], c["L"], c["S"], c["P"], c["pairs"], c["px"]
+    R, L, S, P, pairs, tiles = c["R"], c["L"], c["S"], c["P"], c["pairs"], c["tiles"]
     table = {
-        "k_link_setup": ("hbm", 40 * S + 24 * P + (160 + 4) * L),
-        "k_emit": ("hbm", 24 * R + 168 * L),
-        "k_arclen_scan": ("hbm", 12 * R),
-        "k_bin_count": ("hbm", 20 * R),
-        "k_bin_scatter": ("hbm", 20 * R + 4 * pairs),
+        "k_link_setup": ("hbm", 40 * S + 24 * P + 4 * L),
+        "k_emit": ("hbm", 16 * R),
+        "k_arclen_scan": ("hbm", 4 * R),
+        "k_bin_count": ("hbm", 16 * R),
+        "k_tile_scan": ("hbm", 4 * tiles),
+        "k_bin_scatter": ("hbm", 4 * pairs),
         "k_coverage": ("alu", 16 * c["span_px"]),
     }
     return table.get(kernel)
+
+
+def workspace_bytes(kernel, c):
+    """Bytes of the library's own workspace a kernel writes and reads (design
+    figures): 240 B link records, 4 B tags and 4 B chords per rib, 4 B hit words
+    per rib between the binning passes, 4 B bin entries read by the scatter's
+    cursor pass."""
+    R, L = c["R"], c["L"]
+    return {"k_link_setup": 240 * L, "k_emit": 240 * L + 8 * R, "k_arclen_scan": 8 * R,
+            "k_bin_count": 8 * R, "k_bin_scatter": 16 * R + 8 * R}.get(kernel, 0)
+
+
+STAGES = {
+    "tessellation": (("k_link_setup", "k_emit", "k_arclen_scan"),
+                     lambda c: 40 * c["S"] + 24 * c["P"] + 20 * c["R"] + 4 * c["L"]),
+    "binning": (("k_bin_count", "k_tile_scan", "k_bin_scatter"),
+                lambda c: 16 * c["R"] + 4 * c["pairs"] + 4 * c["tiles"]),
+}
+
+
+def stage_report(kmean, c, hbm_peak):
+    out = {}
+    for name, (ks, fn) in STAGES.items():
+        ms = sum(kmean.get(k, 0.0) for k in ks)
+        if ms <= 0:
+            continue
+        b = fn(c)
+        out[name] = {"kernels": list(ks), "ms": ms, "algorithmic_bytes": b,
+                     "achieved_gbs": b / (ms * 1e-3) / 1e9,
+                     "frac": b / (ms * 1e-3) / 1e9 / hbm_peak}
+    return out
 
 
 # ALU peak for the coverage kernel.  One sample test is one sample against one
@@ -319,8 +354,8 @@ def alu_peak_tests(sm_mhz, ops):
     return 152 * 128 * sm_mhz * 1e6 / ops
 
 
-# DRAM traffic of one k_coverage launch per bin entry, from the ncu capture in
-# profiles/k_coverage_c2_1000paths.md (dram__bytes_read.sum + write.sum =
+# DRAM traffic of one k_coverage launch per bin entry, from an ncu capture of
+# the first 1,000 paths of the workload (dram__bytes_read.sum + write.sum =
 # 124.4 MB over 8,351,880 bin entries); scaled to the launch by its bin entries.
 COVERAGE_TRAFFIC_PER_PAIR = (117.652480e6 + 6.708736e6) / 8351880
 
@@ -470,7 +505,8 @@ def run_ours(args, rank, world, local_rank):
     rstat = ps.ps_raster_stats(ctx)
     pairs, span_px = rstat["pairs"], rstat["span_pixels"]
     counts = {"R": R_now, "L": db.n_link, "S": segs, "P": db.n_path, "px": Wd * Ht,
-              "pairs": pairs, "span_px": span_px}
+              "pairs": pairs, "span_px": span_px,
+              "tiles": ((Wd + 15) // 16) * ((Ht + 15) // 16)}
     sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     kernels = {}
     for k, ms in kmean.items():
@@ -482,7 +518,8 @@ def run_ours(args, rank, world, local_rank):
         if bound == "hbm":
             ach = work / (ms * 1e-3) / 1e9
             kernels[k] = {"ms": ms, "bound": "hbm", "algorithmic_bytes": work,
-                          "achieved_gbs": ach, "frac": ach / hbm_peak}
+                          "achieved_gbs": ach, "frac": ach / hbm_peak,
+                          "workspace_bytes": workspace_bytes(k, counts)}
         else:
             ach = work / (ms * 1e-3) / 1e9
             opt = ops_per_test(rstat, args.exact)
@@ -532,10 +569,12 @@ def run_ours(args, rank, world, local_rank):
         "kernel_ms": kmean,
         "tessellation_only": tessellation_only(kmean, segs, world),
         "kernels": kernels,
+        "stages": stage_report(kmean, counts, hbm_peak),
         "raster_work": rstat,
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": 8 * args.steps,
+        # our kernels per step, from the profile slots that recorded a launch
+        "gpu_launches": len(kmean) * args.steps,
         "clocks": clk,
         "plain": plain,
     }

@@ -251,7 +251,7 @@ __device__ __forceinline__ void hn_coeffs_df(const Seg& g, DF nx, DF ny, DF& a, 
 // double-float coefficients and roots: the near-double-root case, where the
 // FP32 discriminant cancels.  A discriminant within 1e-10 of its scale (a
 // double root to double-float precision) is solved in FP64.
-__device__ DF solve_t_quad_df(const Seg& g, DF sn, DF cs, DF pa, DF pb) {
+__device__ __noinline__ DF solve_t_quad_df(const Seg& g, DF sn, DF cs, DF pa, DF pb) {
   const DF nx = df_neg(sn);
   DF a, b, c;
   hn_coeffs_df(g, nx, cs, a, b, c);

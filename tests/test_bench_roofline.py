@@ -29,3 +29,18 @@ def test_coverage_traffic_per_entry_is_a_plausible_gather():
 
 def test_weak_scaling_throughput():
     assert bench.job_throughput(295431, 4, 17.29) == pytest.approx(4 * 295431 / 17.29e-3)
+
+
+def test_algorithmic_bytes_follow_the_method():
+    # tessellation 40S + 24P + 20R + 4L, binning 16R + 4 pairs + 4 tiles, split
+    # over the stage's kernels; coverage counts 16 sample tests per span pixel
+    c = {"R": 1000, "L": 70, "S": 30, "P": 10, "pairs": 5000, "tiles": 64, "span_px": 777}
+    tess = sum(bench.algorithmic(k, c)[1] for k in ("k_link_setup", "k_emit", "k_arclen_scan"))
+    assert tess == 40 * 30 + 24 * 10 + 20 * 1000 + 4 * 70
+    binb = sum(bench.algorithmic(k, c)[1] for k in ("k_bin_count", "k_tile_scan", "k_bin_scatter"))
+    assert binb == 16 * 1000 + 4 * 5000 + 4 * 64
+    assert bench.algorithmic("k_coverage", c) == ("alu", 16 * 777)
+    st = bench.stage_report({"k_link_setup": 1.0, "k_emit": 2.0, "k_arclen_scan": 1.0}, c, 1000.0)
+    assert st["tessellation"]["algorithmic_bytes"] == tess
+    assert st["tessellation"]["achieved_gbs"] == pytest.approx(tess / 4e-3 / 1e9)
+    assert "binning" not in st
