@@ -14,9 +14,12 @@ step's launches in one CUDA graph; the plain variant runs one path per launch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Prints one JSON line (rank 0).  Under torchrun every rank processes its own copy
-of the batch (weak scaling, no collective on the data path); the timed region is
-bracketed by barriers and the maximum over ranks is reported.
+Prints one JSON line (rank 0).  Under torchrun every rank strokes its own share of
+the job, a batch of the workload seeded per rank (weak scaling, no collective on
+the data path); the timed region is bracketed by barriers and the maximum over
+ranks is reported.  (One batch split over ranks by links, with its one exchange of
+rib counts and lengths, is paper_2007_00308_gb300/shard.py with
+ps_tessellate_links.)
 """
 from __future__ import annotations
 
@@ -275,7 +278,8 @@ def run_reference(args, rank, world):
 # move for the HBM-class kernels, sample tests for the coverage kernel.  The
 # tessellation stage reads 40 B per segment and 24 B per path and writes 16 B
 # per rib (N, P), 4 B per rib (s) and 4 B per link (offset): 40S + 24P + 20R +
-# 4L, split as link set-up 40S + 24P + 4L, emitter 16R, arc length 4R.  Binning
+# 4L, split as link set-up 40S + 24P + 4L, emitter 16R, arc length 4R (the
+# emitter hands each rib's chord to the scan through s).  Binning
 # reads 16 B per rib once, writes 4 B per (quad, tile) entry and 4 B per tile
 # offset: 16R + 4 pairs + 4 tiles, split as count 16R, tile scan 4 tiles,
 # scatter 4 pairs.  The library's own workspace (per-link records, per-rib tags
@@ -414,7 +418,10 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    batch = W.c2_batching(n_paths=args.n_paths)
+    # the job's share of rank r: its own batch of the workload (seeded per rank;
+    # rank 0 strokes the standard batch), so per-GPU work is fixed as ranks are
+    # added and no collective touches the data path
+    batch = W.c2_batching(n_paths=args.n_paths, seed=W.SEED_BASE + 2 + 1000 * rank)
     Wd, Ht = batch.canvas
     ctx = ps.Context()
     if args.pixel_tol > 0:

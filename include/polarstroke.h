@@ -89,9 +89,10 @@ extern "C" {
 #define PS_CAP_TRIANGLE 3
 
 #define PS_PREC_FP32 0  /* all-FP32 arithmetic */
-#define PS_PREC_MIXED 1 /* FP32 bulk, compensated evaluation of g(t), FP64 in the
-                           inflection discriminant, near-integer step counts and
-                           near-degenerate t(psi) solves */
+#define PS_PREC_MIXED 1 /* FP32 pipe: angles, normals, t and vertices as
+                           double-float pairs (each vertex rounded once), FP64
+                           only in the inflection discriminant and near-double-root
+                           t(psi) solves */
 
 /* ps_tessellate_strokes flags */
 #define PS_TESS_ARCLENGTH 1u  /* also write d_s and d_path_len */
@@ -162,8 +163,8 @@ const char* ps_error_string(int code);
  * the launch with an error instead of a hang.  This call launches one warp on
  * `stream` that waits, through that same wait, on a predecessor tile whose
  * flag nothing ever sets: which = 0 takes the int64 sum (rib offsets, raster
- * tile offsets, dash output offsets), which = 1 the segmented FP64 sum (arc
- * length).  The wait gives up after a second or a few and the kernel returns;
+ * tile offsets, dash output offsets), which = 1 the segmented double-float
+ * sum (arc length).  The wait gives up after a second or a few and the kernel returns;
  * the context stays usable.  Uses a 256-byte scratch allocation of its own.
  * SYNCHRONIZES.  Returns PS_OK once the kernel has finished, PS_ERR_INVALID
  * for a null context or another `which`; ps_get_status then reads
@@ -188,6 +189,40 @@ int ps_check_wait_timeout(ps_context* ctx, int which, void* stream);
 int ps_tessellate_strokes(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
                           float dtheta, int precision, uint32_t flags, ps_tess_out* out,
                           void* stream);
+
+/* Tessellate the links [link_begin, link_end) of the batch only: one rank's
+ * share when a batch (or a single long path) is split over several GPUs by
+ * links (Sec. 4.4: links are independent; Eq. 13 and Eq. 18: offsets and arc
+ * length are prefix sums, fixed up afterwards from the ranks' totals).  Links
+ * are numbered over the batch as in ps_tessellate_strokes (path p's links are
+ * 2 seg_off[p] + p ... 2 seg_off[p+1] + p).  Arguments as ps_tessellate_strokes,
+ * with the outputs local to the range:
+ *   out->d_link_rib_off  [link_end - link_begin + 1] rib offsets from 0;
+ *   out->d_path_rib_off  [n_path + 1]: for a path whose first link lies in the
+ *                        range its first rib, -1 otherwise (the call fills it),
+ *                        and for the path whose last link is the range's last
+ *                        link its end;
+ *   ribs, tags (global path indices), t, and s: s restarts at 0 at the start of
+ *                        every path that begins in the range, and for the path
+ *                        running into the range (begun on an earlier range) at
+ *                        the range's first rib -- add its carry with
+ *                        ps_add_s_carry;
+ *   path_len             for the paths that end in the range (the running-in
+ *                        one: its length within the range).
+ * 0 <= link_begin < link_end <= 2 n_seg + n_path, else PS_ERR_INVALID. */
+int ps_tessellate_links(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
+                        float dtheta, int precision, uint32_t flags, int64_t link_begin,
+                        int64_t link_end, ps_tess_out* out, void* stream);
+
+/* s[r] += carry for the leading ribs of a rib stream whose tag's path is
+ * `path` (the path that runs into a link range), and path_len[path] += carry
+ * when with_len is set (the path ends in the range).  carry is the path's
+ * length on the ranges before (double, added as a double-float pair).
+ * Asynchronous on `stream`.  PS_ERR_INVALID on null pointers, capacity < 0 or
+ * path < 0. */
+int ps_add_s_carry(ps_context* ctx, float* d_s, const uint32_t* d_tag, const int64_t* d_n_rib,
+                   int64_t capacity, int32_t path, double carry, float* d_path_len, int with_len,
+                   void* stream);
 
 /* Allocation-free variant of ps_tessellate_strokes (the paper has no
  * counterpart; this is an interface for callers that cannot allocate device

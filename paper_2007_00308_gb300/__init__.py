@@ -27,7 +27,7 @@ EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_statu
            "ps_tessellate_backward", "ps_set_tuning", "ps_get_tuning", "ps_svg_arc_to_conics",
            "ps_uniform_tessellate", "ps_facet_stats", "ps_dash_capped",
            "ps_rasterize_coverage_exact", "ps_set_pixel_tolerance", "ps_get_pixel_tolerance",
-           "ps_check_wait_timeout"]
+           "ps_check_wait_timeout", "ps_tessellate_links", "ps_add_s_carry"]
 PS_PROF_SLOTS = 10
 PS_TUNE_EMIT_SLABS, PS_TUNE_SETUP_LINKS, PS_TUNE_BIN_BLOCKS = 0, 1, 2
 TUNE_CANDIDATES = {PS_TUNE_EMIT_SLABS: (4, 8, 16, 32), PS_TUNE_SETUP_LINKS: (1, 2, 4),
@@ -114,6 +114,10 @@ def lib():
         L.ps_tessellate_backward.argtypes = [P, ctypes.POINTER(_Segments), ctypes.POINTER(_Paths),
                                              ctypes.c_float, ctypes.c_int,
                                              ctypes.POINTER(_TessOut), P, P, P, P, P]
+        L.ps_tessellate_links.argtypes = [P, ctypes.POINTER(_Segments), ctypes.POINTER(_Paths),
+                                          ctypes.c_float, ctypes.c_int, ctypes.c_uint32, I64, I64,
+                                          ctypes.POINTER(_TessOut), P]
+        L.ps_add_s_carry.argtypes = [P, P, P, P, I64, I32, ctypes.c_double, P, ctypes.c_int, P]
         L.ps_tessellate_strokes_noalloc.argtypes = [ctypes.POINTER(_Segments),
                                                     ctypes.POINTER(_Paths), ctypes.c_float,
                                                     ctypes.c_int, ctypes.c_uint32,
@@ -313,6 +317,29 @@ def ps_tessellate_strokes(ctx: Context, db: DeviceBatch, out: TessOutput, precis
     rc = lib().ps_tessellate_strokes(ctx.handle, ctypes.byref(seg), ctypes.byref(paths), q,
                                      int(precision), int(flags), ctypes.byref(o), _stream(stream))
     _check(rc, "ps_tessellate_strokes")
+
+
+def ps_tessellate_links(ctx: Context, db: DeviceBatch, out: TessOutput, link_begin: int,
+                        link_end: int, precision=PS_PREC_FP32, flags=PS_TESS_ARCLENGTH,
+                        dtheta=None, stream=None):
+    """Tessellate the links [link_begin, link_end) of the batch (one rank's
+    share); ``out`` is sized for link_end - link_begin links."""
+    seg, paths = db._structs()
+    o = out._struct()
+    q = db.dtheta if dtheta is None else float(dtheta)
+    rc = lib().ps_tessellate_links(ctx.handle, ctypes.byref(seg), ctypes.byref(paths), q,
+                                   int(precision), int(flags), int(link_begin), int(link_end),
+                                   ctypes.byref(o), _stream(stream))
+    _check(rc, "ps_tessellate_links")
+
+
+def ps_add_s_carry(ctx: Context, out: TessOutput, path: int, carry: float, with_len: bool,
+                   stream=None):
+    """Add a path's arc-length carry to the leading ribs of ``out`` that belong to it."""
+    rc = lib().ps_add_s_carry(ctx.handle, _ptr(out.s), _ptr(out.tag), _ptr(out.n_rib),
+                              int(out.capacity), int(path), float(carry), _ptr(out.path_len),
+                              int(bool(with_len)), _stream(stream))
+    _check(rc, "ps_add_s_carry")
 
 
 def ps_tessellate_strokes_noalloc(db: DeviceBatch, out: TessOutput, status, precision=PS_PREC_FP32,

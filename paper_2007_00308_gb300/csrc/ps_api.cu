@@ -192,7 +192,9 @@ __global__ void k_wait_check(uint32_t* flag, long long* agg, long long* incl, do
   if (which == 0)
     lookback_sum_warp(flag, agg, incl, 1, 1, status);
   else
-    lookback_segsum_warp(flag, aggd, incld, 1.0, false, 1, status);
+    lookback_segsum_df(flag, reinterpret_cast<unsigned long long*>(aggd),
+                       reinterpret_cast<unsigned long long*>(incld), ps::DF{1.f, 0.f}, false, 1,
+                       status);
 }
 
 extern "C" int ps_check_wait_timeout(ps_context* ctx, int which, void* stream) {

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "../../include/polarstroke.h"
+#include "ps_df.cuh"
 
 #define PS_PI_F 3.14159265358979323846f
 #define PS_TWO_PI_F 6.28318530717958647692f
@@ -195,40 +196,50 @@ __device__ __forceinline__ long long lookback_sum_warp(uint32_t* flag, long long
   return prefix;
 }
 
-// Segmented (by head flags) double sum: returns the carry into tile t, i.e. the
-// sum of the elements since the last head before the tile (needed by the tile's
-// elements that precede its own first head).  A tile with a head publishes its
-// inclusive value at once, since that value does not depend on the carry.
-// All 32 lanes of one warp call it: lane k reads the state of tile i - k, so
-// one round of the walk covers 32 predecessors.
-// The walk ends at the nearest tile holding an inclusive value or a head; that
-// tile and every tile nearer than it must have published before the round's
-// values are summed, else the round is read again (bounded by PS_SPIN_LIMIT).
-__device__ __forceinline__ double lookback_segsum_warp(uint32_t* flag, double* agg, double* incl,
-                                                       double tile_agg, bool tile_head, int64_t t,
-                                                       int32_t* status) {
+// Tile states of the arc-length look-backs: a double-float pair packed in 64
+// bits (hi in the low word), stored and loaded relaxed.
+__device__ __forceinline__ void st_relaxed_df(unsigned long long* p, ps::DF v) {
+  const unsigned long long w =
+      ((unsigned long long)__float_as_uint(v.lo) << 32) | (unsigned long long)__float_as_uint(v.hi);
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+__device__ __forceinline__ ps::DF ld_relaxed_df(const unsigned long long* p) {
+  unsigned long long w;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+  return ps::DF{__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)(w >> 32))};
+}
+
+// Segmented (by path) sum of the tiles (chunks) before tile t: the carry into
+// the tile's elements that precede its first segment head (path start).  A chunk that holds a path
+// start publishes its inclusive value at once (it does not depend on the
+// carry); the walk, one warp reading 32 predecessors per round, ends at the
+// nearest chunk with an inclusive value or a path start, once that chunk and
+// every nearer one have published (bounded by PS_SPIN_LIMIT; PS_ERR_TIMEOUT
+// after it).  Sums are double-float pairs.
+__device__ __forceinline__ ps::DF lookback_segsum_df(uint32_t* flag, unsigned long long* agg,
+                                                 unsigned long long* incl, ps::DF tile_agg,
+                                                 bool tile_head, int64_t t, int32_t* status) {
   const int lane = threadIdx.x & 31;
   if (lane == 0) {
     if (t == 0 || tile_head) {
-      st_relaxed_f64(&incl[t], tile_agg);
+      st_relaxed_df(&incl[t], tile_agg);
       st_release_u32(&flag[t], TF_INCL | (tile_head ? TF_HEAD : 0u));
     } else {
-      st_relaxed_f64(&agg[t], tile_agg);
+      st_relaxed_df(&agg[t], tile_agg);
       st_release_u32(&flag[t], TF_AGG);
     }
   }
-  if (t == 0) return 0.0;
-  double carry = 0.0;
+  ps::DF carry{0.f, 0.f};
+  if (t == 0) return carry;
   int64_t i = t - 1;
   int spins = 0;
   for (;;) {
-    int64_t j = i - lane;
-    uint32_t f = j >= 0 ? ld_acquire_u32(&flag[j]) : TF_INCL;  // before tile 0: zero
-    bool stop = (f & TF_INCL) || ((f & TF_AGG) && (f & TF_HEAD));
-    unsigned stop_m = __ballot_sync(0xffffffffu, stop);
-    unsigned unready = __ballot_sync(0xffffffffu, (f & (TF_INCL | TF_AGG)) == 0u);
-    int first = stop_m ? __ffs(stop_m) - 1 : 31;
-    unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+    const int64_t j = i - lane;
+    const uint32_t f = j >= 0 ? ld_acquire_u32(&flag[j]) : TF_INCL;  // before chunk 0: zero
+    const unsigned stop_m = __ballot_sync(0xffffffffu, (f & TF_INCL) != 0u);
+    const unsigned unready = __ballot_sync(0xffffffffu, (f & (TF_INCL | TF_AGG)) == 0u);
+    const int first = stop_m ? __ffs(stop_m) - 1 : 31;
+    const unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
     if (unready & need) {
       if (++spins > PS_SPIN_LIMIT) {
         if (lane == 0) ps_record_error(status, PS_ERR_TIMEOUT);
@@ -237,16 +248,22 @@ __device__ __forceinline__ double lookback_segsum_warp(uint32_t* flag, double* a
       __nanosleep(32);
       continue;
     }
-    double v = 0.0;
-    if (lane <= first && j >= 0) v = (f & TF_INCL) ? ld_relaxed_f64(&incl[j]) : ld_relaxed_f64(&agg[j]);
+    ps::DF v{0.f, 0.f};
+    if (lane <= first && j >= 0) v = (f & TF_INCL) ? ld_relaxed_df(&incl[j]) : ld_relaxed_df(&agg[j]);
+    if (first == 0) {  // the nearest predecessor holds the prefix: no reduction
+      v = ps::DF{__shfl_sync(0xffffffffu, v.hi, 0), __shfl_sync(0xffffffffu, v.lo, 0)};
+    } else {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    carry += v;
+      for (int o = 16; o > 0; o >>= 1)
+        v = ps::df_add(v, ps::DF{__shfl_xor_sync(0xffffffffu, v.hi, o),
+                                 __shfl_xor_sync(0xffffffffu, v.lo, o)});
+    }
+    carry = ps::df_add(carry, v);
     if (stop_m) break;
     i -= 32;
   }
   if (lane == 0 && !tile_head) {
-    st_relaxed_f64(&incl[t], carry + tile_agg);
+    st_relaxed_df(&incl[t], ps::df_add(carry, tile_agg));
     st_release_u32(&flag[t], TF_INCL);
   }
   return carry;

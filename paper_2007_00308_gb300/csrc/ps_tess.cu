@@ -1148,7 +1148,7 @@ constexpr int SETUP_IPT = 2;  // links per thread by default (tunable: 1, 2, 4)
 constexpr int SETUP_TILE = SETUP_NT * SETUP_IPT;
 
 template <bool MIXED, int SETUP_IPT, bool PX = false>
-__global__ void __launch_bounds__(SETUP_NT) k_link_setup(
+__global__ void __launch_bounds__(SETUP_NT, 2) k_link_setup(
     const uint8_t* __restrict__ st, const float* __restrict__ sp, const float* __restrict__ sw,
     const int32_t* __restrict__ seg_off, const float* __restrict__ width,
     const uint8_t* __restrict__ join, const uint8_t* __restrict__ cap,
@@ -1156,7 +1156,7 @@ __global__ void __launch_bounds__(SETUP_NT) k_link_setup(
     int64_t n_link, float q, float tau, LinkRec* __restrict__ recs, int32_t* __restrict__ link_off,
     int32_t* __restrict__ path_off, int64_t* __restrict__ n_rib_out, int64_t capacity,
     uint32_t* tflag, long long* tagg, long long* tincl, int32_t* counters, int32_t* status,
-    int64_t n_tiles) {
+    int64_t n_tiles, int64_t l_begin) {
   __shared__ long long sm[SETUP_NT / 32 + 1];
   __shared__ long long s_prefix;
   __shared__ int s_tile;
@@ -1174,9 +1174,11 @@ __global__ void __launch_bounds__(SETUP_NT) k_link_setup(
     pth[i] = -1;
     kk[i] = -1;
     if (l < n_link) {
-      int p = find_path(seg_off, n_path, l);
+      // local link l is link l_begin + l of the batch (a range call)
+      const int64_t lg = l_begin + l;
+      int p = find_path(seg_off, n_path, lg);
       int32_t s0 = __ldg(seg_off + p), s1 = __ldg(seg_off + p + 1);
-      int k = (int)(l - (2 * (int64_t)s0 + p));
+      int k = (int)(lg - (2 * (int64_t)s0 + p));
       LinkRec L = {};
       int nr = link_setup<MIXED, PX>(st, sp, sw, s0, s1 - s0, k, 0.5f * __ldg(width + p), join[p],
                                  cap[p], __ldg(miter + p), closed[p] != 0, q, tau, L);
@@ -1210,7 +1212,9 @@ __global__ void __launch_bounds__(SETUP_NT) k_link_setup(
       off += cnt[i];
       if (l == n_link - 1) {
         link_off[n_link] = (int32_t)off;
-        path_off[n_path] = (int32_t)off;
+        // the end of the last path, when the range ends with that path's last link
+        const int p = pth[i];
+        if (kk[i] == 2 * (__ldg(seg_off + p + 1) - __ldg(seg_off + p))) path_off[p + 1] = (int32_t)off;
         *n_rib_out = off;
         if (off > capacity) ps_record_error(status, PS_ERR_CAPACITY);
       }
@@ -1496,15 +1500,17 @@ __global__ void __launch_bounds__(EMIT_NT, MIXED ? 2 : 3) k_emit(
 
 // Path index of every link (for the rib tags).
 __global__ void k_link_path(const int32_t* __restrict__ seg_off, int n_path, int64_t n_link,
-                            int32_t* __restrict__ link_path) {
+                            int32_t* __restrict__ link_path, int64_t l_begin) {
   int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (l >= n_link) return;
-  link_path[l] = find_path(seg_off, n_path, l);
+  link_path[l] = find_path(seg_off, n_path, l_begin + l);
 }
 
 // ---------------------------------------------------------------------------
 // K3: segmented inclusive scan of per-rib chords into cumulative arc length
-// (Eq. 18), restarting at every path's first rib; FP64 accumulation.
+// (Eq. 18), restarting at every path's first rib: the standalone arc length of
+// a given rib stream (ps_arclength_scan) and the adjoint's suffix sums; the
+// tessellation itself computes s inside the emitter.
 constexpr int SCAN_NT = 256;
 constexpr int SCAN_IPT = 16;
 constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
@@ -1514,15 +1520,16 @@ constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
 // in order; thread k of a tile owns ribs 16k..16k+15 and, with VEC (all three
 // arrays 16-byte aligned), moves them with 128-bit loads and stores.  Within a
 // tile sums are FP32 (relative error ~1e-6 of s); the carry between tiles,
-// which runs over a whole path, is FP64 and comes from a warp-wide look-back.
+// which runs over a whole path, is a double-float pair from a warp-wide
+// look-back.
 template <bool VEC>
 __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
     const float* chord_in, const uint32_t* __restrict__ tag, const int64_t* __restrict__ n_rib,
-    int64_t capacity, float* s_out, float* __restrict__ path_len, uint32_t* tflag, double* tagg,
-    double* tincl, int32_t* counters, int32_t* status) {
+    int64_t capacity, float* s_out, float* __restrict__ path_len, uint32_t* tflag,
+    unsigned long long* tagg, unsigned long long* tincl, int32_t* counters, int32_t* status) {
   __shared__ float sv[SCAN_NT / 32];
   __shared__ int sh[SCAN_NT / 32];
-  __shared__ double s_carry;
+  __shared__ float s_carry[2];
   __shared__ int64_t s_tile;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int64_t R = *n_rib;
@@ -1594,14 +1601,17 @@ __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
       if (sh[w]) { whead = 1; break; }
     }
     if (wid == 0) {
-      double tile_v = 0.0;
+      DF tile_v{0.f, 0.f};
       int tile_h = 0;
       for (int w = SCAN_NT / 32 - 1; w >= 0; --w) {
-        tile_v += (double)sv[w];
+        tile_v = df_add_f(tile_v, sv[w]);
         if (sh[w]) { tile_h = 1; break; }
       }
-      double carry = lookback_segsum_warp(tflag, tagg, tincl, tile_v, tile_h != 0, tile, status);
-      if (lane == 0) s_carry = carry;
+      DF carry = lookback_segsum_df(tflag, tagg, tincl, tile_v, tile_h != 0, tile, status);
+      if (lane == 0) {
+        s_carry[0] = carry.hi;
+        s_carry[1] = carry.lo;
+      }
     }
     __syncthreads();
     float vprev = __shfl_up_sync(0xffffffffu, v, 1);
@@ -1614,7 +1624,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
     uint32_t nextp = __shfl_down_sync(0xffffffffu, pth[0], 1);
     if (lane == 31) nextp = base + SCAN_IPT < R ? (__ldg(tag + base + SCAN_IPT) >> 2) : 0xffffffffu;
     // ribs before this thread's first head continue the running total
-    const float tile_carry = (hprev || whead) ? 0.f : (float)s_carry;
+    const DF tile_carry = (hprev || whead) ? DF{0.f, 0.f} : DF{s_carry[0], s_carry[1]};
     float run = hprev ? vprev : vprev + wcarry;
     bool after_head = false;
 #pragma unroll
@@ -1624,7 +1634,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
         after_head = true;
       }
       run += c[i];
-      c[i] = after_head ? run : tile_carry + run;
+      c[i] = after_head ? run : df_f(df_add_f(tile_carry, run));
       uint32_t np = i + 1 < SCAN_IPT ? pth[i + 1] : nextp;
       if (path_len && base + i < R && np != pth[i]) path_len[pth[i]] = c[i];
     }
@@ -1646,7 +1656,10 @@ __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
 static void launch_arclen_scan(ps_context* ctx, int grid_override, cudaStream_t st,
                                const float* chord, const uint32_t* tag, const int64_t* n_rib,
                                int64_t capacity, float* s_out, float* path_len, uint32_t* flag,
-                               double* agg, double* incl, int32_t* counters, int32_t* status) {
+                               double* aggd, double* incld, int32_t* counters, int32_t* status) {
+  // the tile states' 8-byte words hold double-float pairs
+  unsigned long long* agg = reinterpret_cast<unsigned long long*>(aggd);
+  unsigned long long* incl = reinterpret_cast<unsigned long long*>(incld);
   const bool vec = ((reinterpret_cast<uintptr_t>(chord) | reinterpret_cast<uintptr_t>(tag) |
                      reinterpret_cast<uintptr_t>(s_out)) & 15u) == 0;
   const void* fn = vec ? (const void*)k_arclen_scan<true> : (const void*)k_arclen_scan<false>;
@@ -1684,18 +1697,19 @@ using namespace ps;
 
 // ===========================================================================
 // host entry points
+// Tessellation of the links [l0, l0 + L) of the batch (all of them when called
+// for the whole batch): offsets and ribs are local to the range.
 static int launch_tessellate(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
                              float dtheta, int precision, uint32_t flags, ps_tess_out* out,
-                             cudaStream_t st) {
-  int64_t S = seg->n_seg;
+                             cudaStream_t st, int64_t l0, int64_t L) {
   int P = paths->n_path;
-  int64_t L = 2 * S + P;
   if (P <= 0) return PS_ERR_INVALID;
   // links per thread: the tuned value, or the default for the boosted kernel
   // (one instantiation only)
   const int ipt = ctx->pixel_tol > 0.f ? SETUP_IPT : ctx->tune[PS_TUNE_SETUP_LINKS];
   int64_t n_tiles = (L + SETUP_NT * ipt - 1) / (SETUP_NT * ipt);
   int rc;
+  // the arc-length scan's tiles follow the set-up tiles in the tile states
   if ((rc = ps_ensure_tiles(ctx, n_tiles + (out->capacity + SCAN_TILE - 1) / SCAN_TILE + 2)) != PS_OK)
     return rc;
   if ((rc = ps_ensure_recs(ctx, L)) != PS_OK) return rc;
@@ -1706,14 +1720,14 @@ static int launch_tessellate(ps_context* ctx, const ps_segments* seg, const ps_p
   // a count-only call has no rib buffers to overflow
   int64_t count_cap = (flags & PS_TESS_COUNT_ONLY) ? INT64_MAX : out->capacity;
   { ProfScope ps_(ctx, PK_LINK_PATH, st);
-  k_link_path<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(paths->d_seg_off, P, L, link_path); }
+  k_link_path<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(paths->d_seg_off, P, L, link_path, l0); }
   {
   ProfScope ps_(ctx, PK_LINK_SETUP, st);
 #define PS_SETUP_ARGS                                                                          \
   seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,         \
       paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->pixel_tol, ctx->d_recs, \
       out->d_link_rib_off, out->d_path_rib_off, out->d_n_rib, count_cap, ctx->d_tile_flag,    \
-      ctx->d_tile_agg, ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles
+      ctx->d_tile_agg, ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles, l0
   const unsigned g = (unsigned)n_tiles;
   const bool mx = precision == PS_PREC_MIXED;
   if (ctx->pixel_tol > 0.f) {
@@ -1735,25 +1749,22 @@ static int launch_tessellate(ps_context* ctx, const ps_segments* seg, const ps_p
   if (flags & PS_TESS_COUNT_ONLY) return PS_OK;
 
   bool arc = (flags & PS_TESS_ARCLENGTH) && out->d_s;
-  int grid = ps_persistent_grid(ctx, precision == PS_PREC_MIXED ? (const void*)k_emit<true>
-                                                                 : (const void*)k_emit<false>,
-                                EMIT_NT, 0);
+  const void* fn = precision == PS_PREC_MIXED ? (const void*)k_emit<true> : (const void*)k_emit<false>;
+  int grid = ps_persistent_grid(ctx, fn, EMIT_NT, 0);
   {
   ProfScope ps_(ctx, PK_EMIT, st);
-  if (precision == PS_PREC_MIXED)
-    k_emit<true><<<grid, EMIT_NT, 0, st>>>(ctx->d_recs, out->d_link_rib_off, link_path, L,
-                                           out->d_n_rib, out->capacity,
-                                           reinterpret_cast<float4*>(out->d_rib), out->d_tag,
-                                           arc ? out->d_s : nullptr, out->d_t, ctx->tune[PS_TUNE_EMIT_SLABS]);
-  else
-    k_emit<false><<<grid, EMIT_NT, 0, st>>>(ctx->d_recs, out->d_link_rib_off, link_path, L,
-                                            out->d_n_rib, out->capacity,
-                                            reinterpret_cast<float4*>(out->d_rib), out->d_tag,
-                                            arc ? out->d_s : nullptr, out->d_t,
-                                            ctx->tune[PS_TUNE_EMIT_SLABS]);
+#define PS_EMIT_ARGS                                                                           \
+  ctx->d_recs, out->d_link_rib_off, link_path, L, out->d_n_rib, out->capacity,                 \
+      reinterpret_cast<float4*>(out->d_rib), out->d_tag, arc ? out->d_s : nullptr, out->d_t,   \
+      ctx->tune[PS_TUNE_EMIT_SLABS]
+  if (precision == PS_PREC_MIXED) k_emit<true><<<grid, EMIT_NT, 0, st>>>(PS_EMIT_ARGS);
+  else k_emit<false><<<grid, EMIT_NT, 0, st>>>(PS_EMIT_ARGS);
+#undef PS_EMIT_ARGS
   }
   if ((rc = ps_cuda_check(cudaGetLastError())) != PS_OK) return rc;
   if (arc) {
+    // the emitter wrote each rib's chord into s; the segmented scan turns them
+    // into cumulative arc length in place
     int64_t scan_tiles = (out->capacity + SCAN_TILE - 1) / SCAN_TILE;
     cudaMemsetAsync(ctx->d_tile_flag + n_tiles + 1, 0, sizeof(uint32_t) * (scan_tiles + 1), st);
     if (out->d_path_len) cudaMemsetAsync(out->d_path_len, 0, sizeof(float) * P, st);
@@ -1800,7 +1811,8 @@ extern "C" int ps_tessellate_strokes(ps_context* ctx, const ps_segments* seg,
     return PS_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = stream;
-  return launch_tessellate(ctx, seg, paths, dtheta, precision, flags, out, st);
+  return launch_tessellate(ctx, seg, paths, dtheta, precision, flags, out, st, 0,
+                           2 * seg->n_seg + paths->n_path);
 }
 
 extern "C" int ps_count_ribs_sync(ps_context* ctx, const ps_segments* seg, const ps_paths* paths,
@@ -1815,6 +1827,68 @@ extern "C" int ps_count_ribs_sync(ps_context* ctx, const ps_segments* seg, const
                                      cudaMemcpyDeviceToHost, st));
   if (rc != PS_OK) return rc;
   return ps_cuda_check(cudaStreamSynchronize(st));
+}
+
+extern "C" int ps_tessellate_links(ps_context* ctx, const ps_segments* seg,
+                                   const ps_paths* paths, float dtheta, int precision,
+                                   uint32_t flags, int64_t link_begin, int64_t link_end,
+                                   ps_tess_out* out, void* stream) {
+  if (!ctx || !seg || !paths || !out) return PS_ERR_INVALID;
+  if (!(dtheta >= 1e-4f && dtheta <= 3.14159265f)) return PS_ERR_INVALID;
+  if (precision != PS_PREC_FP32 && precision != PS_PREC_MIXED) return PS_ERR_INVALID;
+  if (seg->n_seg < 0 || paths->n_path <= 0 || seg->n_seg > (int64_t)1 << 29) return PS_ERR_INVALID;
+  const int64_t L_all = 2 * seg->n_seg + paths->n_path;
+  if (link_begin < 0 || link_end <= link_begin || link_end > L_all) return PS_ERR_INVALID;
+  if (seg->n_seg > 0 && (!seg->d_type || !seg->d_pts)) return PS_ERR_INVALID;
+  if (!paths->d_seg_off || !paths->d_width || !paths->d_join || !paths->d_cap ||
+      !paths->d_miter || !paths->d_closed)
+    return PS_ERR_INVALID;
+  if (!out->d_link_rib_off || !out->d_path_rib_off || !out->d_n_rib) return PS_ERR_INVALID;
+  if (!(flags & PS_TESS_COUNT_ONLY) && (!out->d_rib || !out->d_tag || out->capacity < 0))
+    return PS_ERR_INVALID;
+  if ((flags & PS_TESS_ARCLENGTH) && !(flags & PS_TESS_COUNT_ONLY) && !out->d_s)
+    return PS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = stream;
+  // paths whose first link lies outside the range keep -1: no rib of the range
+  // starts them
+  int rc = ps_cuda_check(cudaMemsetAsync(out->d_path_rib_off, 0xff,
+                                         sizeof(int32_t) * (paths->n_path + 1), st));
+  if (rc != PS_OK) return rc;
+  return launch_tessellate(ctx, seg, paths, dtheta, precision, flags, out, st, link_begin,
+                           link_end - link_begin);
+}
+
+// s += carry on the leading ribs of the stream that belong to `path` (the path
+// that runs into a link range from the ranks before it), and on its length.
+__global__ void k_add_s_carry(float* __restrict__ s, const uint32_t* __restrict__ tag,
+                              const int64_t* __restrict__ n_rib, int64_t capacity, uint32_t path,
+                              float carry_hi, float carry_lo, float* __restrict__ path_len,
+                              int with_len) {
+  int64_t R = *n_rib;
+  if (R > capacity) R = capacity;
+  const DF carry{carry_hi, carry_lo};
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    if ((__ldg(tag + r) >> 2) != path) break;  // ribs of one path are consecutive
+    s[r] = df_f(df_add_f(carry, s[r]));
+  }
+  if (with_len && path_len && blockIdx.x == 0 && threadIdx.x == 0)
+    path_len[path] = df_f(df_add_f(carry, path_len[path]));
+}
+
+extern "C" int ps_add_s_carry(ps_context* ctx, float* d_s, const uint32_t* d_tag,
+                              const int64_t* d_n_rib, int64_t capacity, int32_t path,
+                              double carry, float* d_path_len, int with_len, void* stream) {
+  if (!ctx || !d_s || !d_tag || !d_n_rib || capacity < 0 || path < 0) return PS_ERR_INVALID;
+  if (with_len && !d_path_len) return PS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = stream;
+  const float hi = (float)carry, lo = (float)(carry - (double)hi);
+  const int grid = ps_persistent_grid(ctx, (const void*)k_add_s_carry, 256, 0);
+  k_add_s_carry<<<grid, 256, 0, st>>>(d_s, d_tag, d_n_rib, capacity, (uint32_t)path, hi, lo,
+                                      d_path_len, with_len);
+  return ps_cuda_check(cudaGetLastError());
 }
 
 extern "C" int ps_arclength_scan(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
@@ -1934,19 +2008,19 @@ extern "C" int ps_tessellate_strokes_noalloc(const ps_segments* seg, const ps_pa
       cudaMemsetAsync(counters, 0, sizeof(int32_t) * 16, st) != cudaSuccess)
     return PS_ERR_CUDA;
   int64_t count_cap = count_only ? INT64_MAX : out->capacity;
-  k_link_path<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(paths->d_seg_off, P, L, link_path);
+  k_link_path<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(paths->d_seg_off, P, L, link_path, (int64_t)0);
   if (precision == PS_PREC_MIXED)
     k_link_setup<true, SETUP_IPT><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
         paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, 0.f, recs, out->d_link_rib_off,
         out->d_path_rib_off, out->d_n_rib, count_cap, tflag, tagg, tincl, counters, d_status,
-        n_tiles);
+        n_tiles, (int64_t)0);
   else
     k_link_setup<false, SETUP_IPT><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
         paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, 0.f, recs, out->d_link_rib_off,
         out->d_path_rib_off, out->d_n_rib, count_cap, tflag, tagg, tincl, counters, d_status,
-        n_tiles);
+        n_tiles, (int64_t)0);
   if (cudaGetLastError() != cudaSuccess) return PS_ERR_CUDA;
   if (count_only) return PS_OK;
   int per_sm = 1;
@@ -1993,34 +2067,34 @@ int ps_run_link_setup(ps_context* ctx, const ps_segments* seg, const ps_paths* p
   int32_t* link_path = reinterpret_cast<int32_t*>(ctx->d_recs + ctx->rec_cap);
   cudaMemsetAsync(ctx->d_tile_flag, 0, sizeof(uint32_t) * n_tiles, st);
   cudaMemsetAsync(ctx->d_counters, 0, sizeof(int32_t) * 16, st);
-  k_link_path<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(paths->d_seg_off, P, L, link_path);
+  k_link_path<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(paths->d_seg_off, P, L, link_path, (int64_t)0);
   const bool px = ctx->pixel_tol > 0.f;
   if (precision == PS_PREC_MIXED && px)
     k_link_setup<true, SETUP_IPT, true><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
         paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->pixel_tol, ctx->d_recs,
         d_link_off, d_path_off, d_n_rib, INT64_MAX, ctx->d_tile_flag, ctx->d_tile_agg,
-        ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles);
+        ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles, (int64_t)0);
   else if (px)
     k_link_setup<false, SETUP_IPT, true><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
         paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->pixel_tol, ctx->d_recs,
         d_link_off, d_path_off, d_n_rib, INT64_MAX, ctx->d_tile_flag, ctx->d_tile_agg,
-        ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles);
+        ctx->d_tile_incl, ctx->d_counters, ctx->d_status, n_tiles, (int64_t)0);
   else if (precision == PS_PREC_MIXED)
     k_link_setup<true, SETUP_IPT><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
         paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->pixel_tol, ctx->d_recs,
         d_link_off,
         d_path_off, d_n_rib, INT64_MAX, ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
-        ctx->d_counters, ctx->d_status, n_tiles);
+        ctx->d_counters, ctx->d_status, n_tiles, (int64_t)0);
   else
     k_link_setup<false, SETUP_IPT><<<(unsigned)n_tiles, SETUP_NT, 0, st>>>(
         seg->d_type, seg->d_pts, seg->d_w, paths->d_seg_off, paths->d_width, paths->d_join,
         paths->d_cap, paths->d_miter, paths->d_closed, P, L, dtheta, ctx->pixel_tol, ctx->d_recs,
         d_link_off,
         d_path_off, d_n_rib, INT64_MAX, ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
-        ctx->d_counters, ctx->d_status, n_tiles);
+        ctx->d_counters, ctx->d_status, n_tiles, (int64_t)0);
   return ps_cuda_check(cudaGetLastError());
 }
 
