@@ -595,6 +595,92 @@ __device__ __forceinline__ void put_psi(LinkRec& L, int k, DF v) { L.psi[k] = v.
 __device__ __forceinline__ void put_p(LinkRec& L, int k, DF v) { L.p[k] = v.hi; L.p_lo[k] = v.lo; }
 __device__ __forceinline__ void put_step(LinkRec& L, int k, DF v) { L.step[k] = v.hi; L.step_lo[k] = v.lo; }
 
+// The curvature-sign polynomial in PS_PREC_MIXED.  A cubic's is formed in
+// double-float from the exact control-point differences (X_ij = d_i x d_j as
+// pairs) and its roots by the stable quadratic formula in double-float.  FP64
+// (the discriminant island) serves a cubic whose cross products are within
+// rounding of zero (a flat or nearly flat segment, whose flatness is decided
+// exactly) or whose discriminant is within 1e-6 of its scale (near a cusp,
+// where the roots need the extra bits), and the quadratic's and conic's
+// single-product polynomial.
+struct CurvMX {
+  bool use64, flat;
+  CrossPoly<double> Pd;
+  DF c0, c1, c2;
+  int nroot;
+  DF roots[2];
+  __device__ int sign_at(DF t) const {
+    if (use64) {
+      const double v = Pd.eval(df_d(t));
+      return v > 0.0 ? 1 : (v < 0.0 ? -1 : 0);
+    }
+    const DF v = df_add(c0, df_mul(t, df_add(c1, df_mul(t, c2))));
+    return v.hi > 0.f ? 1 : (v.hi < 0.f ? -1 : 0);
+  }
+};
+
+__device__ __forceinline__ void curv_add_root(CurvMX& C, DF r) {
+  if (df_lt(df_of(0.f), r) && df_lt(r, df_of(1.f)) && (C.nroot == 0 || df_lt(C.roots[C.nroot - 1], r)))
+    C.roots[C.nroot++] = r;
+}
+
+__device__ CurvMX curv_mx(const Seg& g) {
+  CurvMX C;
+  C.use64 = true;
+  C.flat = true;
+  C.nroot = 0;
+  if (g.type == PS_CUBIC) {
+    const DF2 d1 = df_vec(g.B, g.A), d2 = df_vec(g.C, g.B), d3 = df_vec(g.D, g.C);
+    const DF X12 = df_cross(d1, d2), X13 = df_cross(d1, d3), X23 = df_cross(d2, d3);
+    const float m1 = fabsf(d1.x.hi) + fabsf(d1.y.hi), m2 = fabsf(d2.x.hi) + fabsf(d2.y.hi),
+                m3 = fabsf(d3.x.hi) + fabsf(d3.y.hi);
+    const float xm = fabsf(X12.hi) + fabsf(X13.hi) + fabsf(X23.hi);
+    if (xm > 1e-9f * (m1 * m2 + m1 * m3 + m2 * m3)) {
+      // c1^2 - 4 c0 c2 reduces to X13^2 - 4 X12 X23
+      const DF disc = df_sub(df_mul(X13, X13), df_mul_f(df_mul(X12, X23), 4.f));
+      const float scale = X13.hi * X13.hi + fabsf(4.f * X12.hi * X23.hi);
+      if (fabsf(disc.hi) > 1e-6f * scale) {
+        C.use64 = false;
+        C.flat = false;
+        C.c0 = X12;
+        C.c1 = df_sub(X13, df_mul_f(X12, 2.f));
+        C.c2 = df_add(df_sub(X12, X13), X23);
+        if (disc.hi > 0.f) {  // two simple roots (a sign change at each)
+          DF r[2];
+          int n = 0;
+          if (df_is0(C.c2)) {
+            if (!df_is0(C.c1)) r[n++] = df_neg(df_div(C.c0, C.c1));
+          } else {
+            const DF sq = df_sqrt(disc);
+            const DF q = df_mul_f(df_add(C.c1, C.c1.hi >= 0.f ? sq : df_neg(sq)), -0.5f);
+            if (!df_is0(q)) {
+              r[n++] = df_div(q, C.c2);
+              r[n++] = df_div(C.c0, q);
+            }
+          }
+          if (n == 2 && df_lt(r[1], r[0])) {
+            const DF t = r[0];
+            r[0] = r[1];
+            r[1] = t;
+          }
+          for (int i = 0; i < n; ++i) curv_add_root(C, r[i]);
+        }
+        return C;
+      }
+    }
+  }
+  C.Pd = cross_poly<double>(g);
+  C.flat = C.Pd.flat;
+  if (!C.flat && (C.Pd.c1 != 0.0 || C.Pd.c2 != 0.0)) {
+    double r[2];
+    int n = quad_roots<double>(C.Pd.c0, C.Pd.c1, C.Pd.c2, C.Pd.disc, C.Pd.scale, 0.0, r);
+    if (n == 2 && C.Pd.disc <= 0.0) n = 0;  // a double root: no sign change
+    for (int i = 0; i < n; ++i)
+      if (r[i] > 0.0 && r[i] < 1.0) curv_add_root(C, df_from_d(r[i]));
+  }
+  return C;
+}
+
 // Interval table of a segment link in FP32 (Sec. 3.3.4-3.3.6, Eq. 4-6, 12-13).
 // Returns N (total steps) or -1 if the table does not fit.
 template <bool PX>
@@ -714,18 +800,18 @@ __device__ int seg_intervals32(const Seg& g, Step S, LinkRec& L) {
 // The same table in PS_PREC_MIXED.  Angles, parameters and steps are
 // double-float pairs: end angles by the double-float atan2 of the exact
 // control-point differences, inflections from the curvature polynomial's
-// roots in FP64 (the discriminant island; an exact cusp gives a zero
-// discriminant), their angles from the double-float hodograph, turnings and
-// counts in double-float, split points by the double-float t solve.
+// roots (curv_mx: double-float, FP64 near flatness or a double root), their
+// angles from the double-float hodograph, turnings and counts in
+// double-float, split points by the double-float t solve.
 template <bool PX>
 __device__ int seg_intervals_mx(const Seg& g, Step S, LinkRec& L) {
   const DF2 ge0 = end_grad0_df(g), ge1 = end_grad1_df(g);
   const DF Psi0 = df_atan2(ge0.y, ge0.x, ps_sc_tab), Psin = df_atan2(ge1.y, ge1.x, ps_sc_tab);
-  const CrossPoly<double> Pd = cross_poly<double>(g);
+  const CurvMX Cv = curv_mx(g);
   const DF zero = df_of(0.f), one = df_of(1.f);
   int M = 0;
   uint32_t pivots = 0;
-  if (Pd.flat) {
+  if (Cv.flat) {
     double rts[2];
     int nr = collinear_reversals<double, double>(g, rts);
     DF psi = Psi0, pp = zero;
@@ -763,53 +849,39 @@ __device__ int seg_intervals_mx(const Seg& g, Step S, LinkRec& L) {
     return N;
   }
 
-  // Eq. 4 (FP64 island: the curvature polynomial's discriminant and roots)
-  double roots[2];
-  int nroot = 0;
-  if (Pd.c1 != 0.0 || Pd.c2 != 0.0) {
-    double r[2];
-    int n = quad_roots<double>(Pd.c0, Pd.c1, Pd.c2, Pd.disc, Pd.scale, 0.0, r);
-    if (n == 2 && Pd.disc <= 0.0) n = 0;
-    for (int i = 0; i < n; ++i)
-      if (r[i] > 0.0 && r[i] < 1.0 && (nroot == 0 || r[i] > roots[nroot - 1])) roots[nroot++] = r[i];
-  }
-  // Eq. 5: an inflection's angle is insensitive to its parameter to first
-  // order (the tangent turns at rate 0 there), so H is taken at the float root
+  // Eq. 4 (the roots of the curvature polynomial, curv_mx) and Eq. 5: an
+  // inflection's angle is insensitive to its parameter to first order (the
+  // tangent turns at rate 0 there), so H is taken at the float root
   DF p[4], Psi[4];
-  double pd[4];
   int n = 0;
   p[n] = zero;
-  pd[n] = 0.0;
   Psi[n] = Psi0;
   n++;
-  for (int i = 0; i < nroot; ++i) {
-    p[n] = df_from_d(roots[i]);
-    pd[n] = roots[i];
+  for (int i = 0; i < Cv.nroot; ++i) {
+    p[n] = Cv.roots[i];
     DF2 H = hodo_df(g, p[n].hi);
     Psi[n] = df_atan2(H.y, H.x, ps_sc_tab);
     n++;
   }
   p[n] = one;
-  pd[n] = 1.0;
   Psi[n] = Psin;
 
   // Eq. 6: turning in the direction of the curvature sign, modulo 2 pi
   const DF full = DF{PS_DF_FULL_TURN_SLACK_HI, PS_DF_FULL_TURN_SLACK_LO};
   for (int k = 0; k < n; ++k) {
-    const double pa = pd[k], pb = pd[k + 1];
-    double sgn = 0.0;
-    const double probes[3] = {0.5 * (pa + pb), 0.75 * pa + 0.25 * pb, 0.25 * pa + 0.75 * pb};
-    for (int i = 0; i < 3 && sgn == 0.0; ++i) {
-      double v = Pd.eval(probes[i]);
-      sgn = v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0);
-    }
+    const DF pa = p[k], pb = p[k + 1];
+    int sgn = 0;
+    const DF probes[3] = {df_mul_f(df_add(pa, pb), 0.5f),
+                          df_add(df_mul_f(pa, 0.75f), df_mul_f(pb, 0.25f)),
+                          df_add(df_mul_f(pa, 0.25f), df_mul_f(pb, 0.75f))};
+    for (int i = 0; i < 3 && sgn == 0; ++i) sgn = Cv.sign_at(probes[i]);
     DF delta = zero;
-    if (sgn != 0.0) {
+    if (sgn != 0) {
       DF d = df_sub(Psi[k + 1], Psi[k]);
-      if (sgn < 0.0) d = df_neg(d);
+      if (sgn < 0) d = df_neg(d);
       d = df_mod2pi(d);
       if (df_lt(full, d)) d = zero;  // a full turn within rounding: numerically flat
-      delta = sgn < 0.0 ? df_neg(d) : d;
+      delta = sgn < 0 ? df_neg(d) : d;
     }
     const DF ad = df_abs(delta);
     if (df_le(df_pi(), ad)) {
@@ -827,7 +899,7 @@ __device__ int seg_intervals_mx(const Seg& g, Step S, LinkRec& L) {
       L.meta |= META_SPLIT_BIT(M);
       M++;
     } else {
-      const int D = df_is0(ad) ? (pb > pa ? 1 : 0) : steps_mx<PX>(ad, S, &g);
+      const int D = df_is0(ad) ? (df_lt(pa, pb) ? 1 : 0) : steps_mx<PX>(ad, S, &g);
       if (M + 1 > 6) return -1;
       put_p(L, M, p[k]); put_psi(L, M, Psi[k]);
       put_step(L, M, D ? df_div_f(delta, (float)D) : zero);
