@@ -346,6 +346,36 @@ OPS_PER_TEST = {"convex_pixels": 7.0, "two_triangle_pixels": 9.0, "general_pixel
 OPS_PER_TEST_EXACT = {"convex_pixels": 8.0, "two_triangle_pixels": 8.0, "general_pixels": 24.0}
 
 
+# Measured issue rates of the coverage mask's per-sample operation mixes on this
+# GB300 (a microbenchmark of independent IADD/LOP3/SHF chains, 16 warps per
+# scheduler, SM clock 2070 MHz): the convex step (4 adds, 2 logic ops, 1 funnel
+# shift) ran 4.794 T sample tests/s, i.e. 101.7 lane ops per SM per clock; the
+# two-triangle step (5 + 3 + 1) 3.661 T tests/s, 104.7 lane ops per SM per
+# clock.  Each INT op class alone issues 64 lane ops per SM per clock; the mixes
+# co-issue on two pipes.  Per SM and clock:
+MEASURED_TESTS_PER_SM_CLK = {"convex_pixels": 4.794e12 / (152 * 2.07e9),
+                             "two_triangle_pixels": 3.661e12 / (152 * 2.07e9)}
+
+
+def measured_peak_tests(rstat, sm_mhz, exact=False):
+    """Peak sample tests/s of the coverage kernel's pixel-class mix from the
+    measured issue rates (None for the crossing-rule mask, not measured): the
+    harmonic mean of the class rates weighted by the classes' pixels, at the
+    sampled SM clock.  The general (int64) class has no measurement and takes
+    the derived rate."""
+    if exact:
+        return None
+    n = sum(rstat.get(k, 0) for k in OPS_PER_TEST)
+    if n <= 0:
+        return None
+    per_test = 0.0
+    for k in OPS_PER_TEST:
+        f = rstat.get(k, 0) / n
+        rate = MEASURED_TESTS_PER_SM_CLK.get(k, 128.0 / OPS_PER_TEST[k])
+        per_test += f / rate
+    return 152 * sm_mhz * 1e6 / per_test
+
+
 def ops_per_test(rstat, exact=False):
     table = OPS_PER_TEST_EXACT if exact else OPS_PER_TEST
     n = sum(rstat.get(k, 0) for k in table)
@@ -530,9 +560,12 @@ def run_ours(args, rank, world, local_rank):
         else:
             ach = work / (ms * 1e-3) / 1e9
             opt = ops_per_test(rstat, args.exact)
-            pk = alu_peak_tests(sm_mhz, opt) / 1e9
+            pk_derived = alu_peak_tests(sm_mhz, opt) / 1e9
+            pk_meas = measured_peak_tests(rstat, sm_mhz, args.exact)
+            pk = pk_meas / 1e9 if pk_meas else pk_derived
             kernels[k] = {"ms": ms, "bound": "alu", "sample_tests": work,
-                          "achieved_gtests": ach, "peak_gtests": pk, "frac": ach / pk}
+                          "achieved_gtests": ach, "peak_gtests": pk, "frac": ach / pk,
+                          "peak_derived_gtests": pk_derived, "peak_measured": bool(pk_meas)}
     kd = kernels[dom]
     if kd.get("bound") == "alu":
         opt = ops_per_test(rstat, args.exact)
@@ -541,8 +574,13 @@ def run_ours(args, rank, world, local_rank):
                 # measured on the two-triangle kernel; none for the crossing-rule mode
                 "traffic": (int(COVERAGE_TRAFFIC_PER_PAIR * pairs)
                             if dom == "k_coverage" and not args.exact else None),
-                "peak_source": (f"derived: 152 SMs x 128 lane ops/clock x {sm_mhz:.0f} MHz / "
-                                f"{opt:.2f} lane ops per sample test (pixel-class mix)"),
+                "peak_source": (("measured: issue rate of the mask's op mix per pixel class "
+                                 f"(microbenchmark), pixel-class mix, {sm_mhz:.0f} MHz; derived "
+                                 f"(128 lane ops/clock / {opt:.2f} ops per test) "
+                                 f"{kd['peak_derived_gtests']:.0f} G tests/s")
+                                if kd.get("peak_measured") else
+                                (f"derived: 152 SMs x 128 lane ops/clock x {sm_mhz:.0f} MHz / "
+                                 f"{opt:.2f} lane ops per sample test (pixel-class mix)")),
                 "algorithmic_work": kd["sample_tests"],
                 "traffic_source": "ncu capture of 1,000 paths scaled by bin entries"}
     elif kd.get("bound") == "hbm":

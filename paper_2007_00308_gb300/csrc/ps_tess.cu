@@ -314,11 +314,14 @@ __device__ DF solve_t_mx(const Seg& g, DF sn, DF cs, DF pa, DF pb) {
   if (!(c != 0.f && fabsf(disc) < 1e-3f * scale)) {
     if (!root) return t0 == pa.hi ? pa : pb;  // endpoint rule
     const DF nx = df_neg(sn);
-    float fp = fmaf(2.f * c, t0, b);
-    float dt = fp != 0.f ? -__fdividef(hn_resid(g, t0, nx, cs), fp) : 0.f;
-    if (fabsf(c * dt * dt) > 1e-12f * fabsf(fp)) {
-      t0 += dt;
-      fp = fmaf(2.f * c, t0, b);
+    float dt = 0.f;
+#pragma unroll 1
+    for (int it = 0; it < 2; ++it) {
+      if (it == 1) {
+        if (!(fabsf(c * dt * dt) > 1e-12f * fabsf(fmaf(2.f * c, t0, b)))) break;
+        t0 += dt;
+      }
+      const float fp = fmaf(2.f * c, t0, b);
       dt = fp != 0.f ? -__fdividef(hn_resid(g, t0, nx, cs), fp) : 0.f;
     }
     if (fabsf(dt) <= 1e-4f) {
@@ -595,6 +598,13 @@ __device__ __forceinline__ void put_psi(LinkRec& L, int k, DF v) { L.psi[k] = v.
 __device__ __forceinline__ void put_p(LinkRec& L, int k, DF v) { L.p[k] = v.hi; L.p_lo[k] = v.lo; }
 __device__ __forceinline__ void put_step(LinkRec& L, int k, DF v) { L.step[k] = v.hi; L.step_lo[k] = v.lo; }
 
+// Out-of-line double-float atan2 and sincos for the link set-up, which calls
+// them from many places on divergent paths: one copy of each keeps the
+// kernel's code small (its warps stalled on instruction fetch); the per-rib
+// emitter inlines them.
+__device__ __noinline__ DF atan2_ool(DF y, DF x) { return df_atan2(y, x, ps_sc_tab); }
+__device__ __noinline__ void sincos_ool(DF x, DF& s, DF& c) { df_sincos(x, ps_sc_tab, s, c); }
+
 // The curvature-sign polynomial in PS_PREC_MIXED.  A cubic's is formed in
 // double-float from the exact control-point differences (X_ij = d_i x d_j as
 // pairs) and its roots by the stable quadratic formula in double-float.  FP64
@@ -806,7 +816,7 @@ __device__ int seg_intervals32(const Seg& g, Step S, LinkRec& L) {
 template <bool PX>
 __device__ int seg_intervals_mx(const Seg& g, Step S, LinkRec& L) {
   const DF2 ge0 = end_grad0_df(g), ge1 = end_grad1_df(g);
-  const DF Psi0 = df_atan2(ge0.y, ge0.x, ps_sc_tab), Psin = df_atan2(ge1.y, ge1.x, ps_sc_tab);
+  const DF Psi0 = atan2_ool(ge0.y, ge0.x), Psin = atan2_ool(ge1.y, ge1.x);
   const CurvMX Cv = curv_mx(g);
   const DF zero = df_of(0.f), one = df_of(1.f);
   int M = 0;
@@ -860,7 +870,7 @@ __device__ int seg_intervals_mx(const Seg& g, Step S, LinkRec& L) {
   for (int i = 0; i < Cv.nroot; ++i) {
     p[n] = Cv.roots[i];
     DF2 H = hodo_df(g, p[n].hi);
-    Psi[n] = df_atan2(H.y, H.x, ps_sc_tab);
+    Psi[n] = atan2_ool(H.y, H.x);
     n++;
   }
   p[n] = one;
@@ -889,7 +899,7 @@ __device__ int seg_intervals_mx(const Seg& g, Step S, LinkRec& L) {
       const DF half{0.5f * delta.hi, 0.5f * delta.lo};
       const DF psi_s = df_add(Psi[k], half);
       DF sn, cs;
-      df_sincos(psi_s, ps_sc_tab, sn, cs);
+      sincos_ool(psi_s, sn, cs);
       const DF ps_ = solve_t_mx(g, sn, cs, p[k], p[k + 1]);
       const int Dh = steps_mx<PX>(df_abs(half), S, &g);
       const DF st = df_div_f(half, (float)Dh);
@@ -1033,10 +1043,10 @@ __device__ int pivot_setup_mx(float2 at, DF Psi0, DF delta, int kind, int style,
     const float sdr = pos ? -r : r;  // outer offset = at + sdr * n, n = (-sin, cos)
     const DF half{0.5f * delta.hi, 0.5f * delta.lo}, ahalf = df_abs(half);
     DF s0, c0, s1, c1, sh, ch, sa, ca;
-    df_sincos(Psi0, ps_sc_tab, s0, c0);
-    df_sincos(df_add(Psi0, delta), ps_sc_tab, s1, c1);
-    df_sincos(df_add(Psi0, half), ps_sc_tab, sh, ch);
-    df_sincos(ahalf, ps_sc_tab, sa, ca);
+    sincos_ool(Psi0, s0, c0);
+    sincos_ool(df_add(Psi0, delta), s1, c1);
+    sincos_ool(df_add(Psi0, half), sh, ch);
+    sincos_ool(ahalf, sa, ca);
     // miter ratio 1/cos(|delta|/2) <= limit  <=>  limit cos(|delta|/2) >= 1
     const bool accept = ca.hi > 0.f && df_le(df_of(1.f), df_mul_f(ca, miter));
     DF2 O0{df_mul_f(df_neg(s0), sdr), df_mul_f(c0, sdr)};  // relative to at
@@ -1145,15 +1155,15 @@ __device__ int link_setup(const uint8_t* st, const float* sp, const float* sw, i
       if (kind == LK_CAP) {
         // start cap: a pivot from Psi_s + pi through pi; stop cap: from Psi_e (R7)
         const DF2 e = k == 0 ? end_grad0_df(a) : end_grad1_df(a);
-        Psi0 = df_atan2(e.y, e.x, ps_sc_tab);
+        Psi0 = atan2_ool(e.y, e.x);
         if (k == 0) Psi0 = df_add(Psi0, df_pi());
         delta = df_pi();
       } else {
         // Sec. 4.3.1: delta = Psi_1 (-) Psi_0, taken as the angle from the
         // incoming to the outgoing gradient; an exact reversal is +pi (R10)
         const DF2 e1 = end_grad1_df(a), e0 = end_grad0_df(b);
-        Psi0 = df_atan2(e1.y, e1.x, ps_sc_tab);
-        delta = df_atan2(df_cross(e1, e0), df_dot(e1, e0), ps_sc_tab);
+        Psi0 = atan2_ool(e1.y, e1.x);
+        delta = atan2_ool(df_cross(e1, e0), df_dot(e1, e0));
       }
       J = pivot_setup_mx<PX>(at, Psi0, delta, kind, style, r, miter, S, L);
     } else {
@@ -1452,6 +1462,13 @@ __device__ __forceinline__ RibEval eval_rib(const LinkRec* __restrict__ L, int j
   else return eval_rib32(L, j);
 }
 
+// The same, out of line: the emitter's rare re-evaluation of a chunk's
+// preceding rib calls it, so the hot loop holds one copy of the rib code.
+template <bool MIXED>
+__device__ __noinline__ RibEval eval_rib_ool(const LinkRec* __restrict__ L, int j) {
+  return eval_rib<MIXED>(L, j);
+}
+
 __device__ __forceinline__ int64_t find_link(const int32_t* off, int64_t lo, int64_t hi, int64_t r) {
   // last l in [lo, hi] with off[l] <= r  (off non-decreasing)
   while (hi > lo) {
@@ -1549,7 +1566,7 @@ __global__ void __launch_bounds__(EMIT_NT, MIXED ? 2 : 3) k_emit(
           float cl = 0.f;
           if (E.seg && j > 0) {
             if (lane == 0 && s == 0) {
-              RibEval Ep = eval_rib<MIXED>(recs + l, j - 1);
+              RibEval Ep = eval_rib_ool<MIXED>(recs + l, j - 1);
               pg = Ep.grel;
               pgl = Ep.glo;
               pt = Ep.t;

@@ -44,3 +44,14 @@ def test_algorithmic_bytes_follow_the_method():
     assert st["tessellation"]["algorithmic_bytes"] == tess
     assert st["tessellation"]["achieved_gbs"] == pytest.approx(tess / 4e-3 / 1e9)
     assert "binning" not in st
+
+
+def test_measured_coverage_peak_follows_the_class_rates():
+    mix = {"convex_pixels": 400, "two_triangle_pixels": 600, "general_pixels": 0}
+    pk = bench.measured_peak_tests(mix, 2070.0)
+    rc = bench.MEASURED_TESTS_PER_SM_CLK["convex_pixels"] * 152 * 2070e6
+    rt = bench.MEASURED_TESTS_PER_SM_CLK["two_triangle_pixels"] * 152 * 2070e6
+    assert pk == pytest.approx(1.0 / (0.4 / rc + 0.6 / rt))
+    assert rt < pk < rc
+    assert bench.measured_peak_tests(mix, 2070.0, exact=True) is None
+    assert bench.measured_peak_tests({}, 2070.0) is None
