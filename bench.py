@@ -348,13 +348,14 @@ OPS_PER_TEST_EXACT = {"convex_pixels": 8.0, "two_triangle_pixels": 8.0, "general
 
 # Measured issue rates of the coverage mask's per-sample operation mixes on this
 # GB300 (a microbenchmark of independent IADD/LOP3/SHF chains, 16 warps per
-# scheduler, SM clock 2070 MHz): the convex step (4 adds, 2 logic ops, 1 funnel
-# shift) ran 4.794 T sample tests/s, i.e. 101.7 lane ops per SM per clock; the
-# two-triangle step (5 + 3 + 1) 3.661 T tests/s, 104.7 lane ops per SM per
-# clock.  Each INT op class alone issues 64 lane ops per SM per clock; the mixes
-# co-issue on two pipes.  Per SM and clock:
-MEASURED_TESTS_PER_SM_CLK = {"convex_pixels": 4.794e12 / (152 * 2.07e9),
-                             "two_triangle_pixels": 3.661e12 / (152 * 2.07e9)}
+# scheduler, best of 2,000 launches, every sampled SM clock 2070 MHz): the
+# convex step (4 adds, 2 logic ops, 1 funnel shift) ran 4.802 T sample tests/s,
+# i.e. 106.8 lane ops per SM per clock; the two-triangle step (5 + 3 + 1)
+# 3.668 T tests/s, 104.9 lane ops per SM per clock.  Each INT op class alone
+# issues 63 lane ops per SM per clock; the mixes co-issue on two pipes.  Per
+# SM and clock:
+MEASURED_TESTS_PER_SM_CLK = {"convex_pixels": 4.802e12 / (152 * 2.07e9),
+                             "two_triangle_pixels": 3.668e12 / (152 * 2.07e9)}
 
 
 def measured_peak_tests(rstat, sm_mhz, exact=False):
