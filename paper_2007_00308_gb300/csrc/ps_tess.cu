@@ -420,12 +420,7 @@ __device__ __forceinline__ int ceil_steps(float ad, float q) {
   int D = (int)ceilf(ad / q - STEP_SNAP);
   return D < 1 ? 1 : D;
 }
-__device__ __forceinline__ int ceil_steps_d(double ad, double q) {
-  if (ad == 0.0) return 0;
-  int D = (int)ceil(ad / q - 1e-4);
-  return D < 1 ? 1 : D;
-}
-// MIXED: re-evaluate a step count in FP64 when its FP32 argument is within
+// MIXED: re-evaluate a step count in double-float when its FP32 argument is within
 // rounding of the boundary
 __device__ __forceinline__ bool near_integer(float x) {
   x -= STEP_SNAP;
@@ -434,8 +429,8 @@ __device__ __forceinline__ bool near_integer(float x) {
 }
 
 // A link's angle step in FP32 (for the FP32 count decisions), with what the
-// mixed kernel needs to recompute it in FP64 where a count decision is re-taken
-// in FP64 (step_d).
+// mixed kernel needs to recompute it in double-float where a count decision is
+// re-taken (step_df).
 struct Step {
   float q;
   float q0, tau, r;  // the nominal step and the boost's inputs
@@ -484,19 +479,42 @@ __device__ Step seg_step(const Seg& g, float q, float tau, float r) {
   return Step{fmaxf(fminf(fminf(a, b), 0.5f * PS_PI_F), q), q, tau, r, 2};
 }
 
-// The step in FP64 (the same rule; g is the segment for kind 2).  Called only
-// where a count decision is re-taken in FP64, so the FP64 functions run rarely.
-__device__ __noinline__ double step_d(const Step& S, const Seg* g) {
-  const double q = S.q0;
+// Out-of-line double-float atan2 and sincos for the link set-up, which calls
+// them from many places on divergent paths: one copy of each keeps the
+// kernel's code small (its warps stalled on instruction fetch); the per-rib
+// emitter inlines them.
+__device__ __noinline__ DF atan2_ool(DF y, DF x) { return df_atan2(y, x, ps_sc_tab); }
+__device__ __noinline__ void sincos_ool(DF x, DF& s, DF& c) { df_sincos(x, ps_sc_tab, s, c); }
+
+__device__ __forceinline__ DF df_max(DF a, DF b) { return df_lt(a, b) ? b : a; }
+__device__ __forceinline__ DF df_min(DF a, DF b) { return df_lt(a, b) ? a : b; }
+
+// The link step of the same rule in double-float (g is the segment for kind
+// 2), where a count decision is re-taken: 2 acos(1 - x) = 4 asin(sqrt(x/2)) =
+// 4 atan2(sqrt(x/2), sqrt(1 - x/2)), atan(tau/L_g) = atan2(tau, L_g).
+__device__ __noinline__ DF step_df(const Step& S, const Seg* g) {
+  const DF q = df_of(S.q0), tau = df_of(S.tau);
   if (S.kind == 1) {
-    double td = S.tau, rd = S.r;
-    return fmax(td >= rd ? PS_PI_D : 2.0 * acos(1.0 - td / rd), q);
+    if (S.tau >= S.r) return df_max(df_pi(), q);
+    const DF h = df_div_f(tau, 2.f * S.r);  // tau / (2 r), 2r exact
+    const DF a = atan2_ool(df_sqrt(h), df_sqrt(df_sub(df_of(1.f), h)));
+    return df_max(df_mul_f(a, 4.f), q);
   }
   if (S.kind == 2 && g) {
-    double Lg = polygon_length<double>(*g);
-    double a = Lg > 0.0 ? 2.0 * atan((double)S.tau / Lg) : PS_PI_D;
-    double b = sqrt(PS_PI_D * (double)S.tau / (2.0 * (double)S.r));
-    return fmax(fmin(fmin(a, b), 0.5 * PS_PI_D), q);
+    auto leg = [](float2 a, float2 b) {
+      const DF dx = two_sum(b.x, -a.x), dy = two_sum(b.y, -a.y);
+      return df_sqrt(df_add(df_mul(dx, dx), df_mul(dy, dy)));
+    };
+    DF Lg;
+    switch (g->type) {
+      case PS_LINE: Lg = leg(g->A, g->D); break;
+      case PS_CUBIC: Lg = df_add(df_add(leg(g->A, g->B), leg(g->B, g->C)), leg(g->C, g->D)); break;
+      default: Lg = df_add(leg(g->A, g->B), leg(g->B, g->D));
+    }
+    const DF a = df_is0(Lg) ? df_pi() : df_mul_f(atan2_ool(tau, Lg), 2.f);
+    const DF b = df_sqrt(df_div_f(df_mul(df_pi(), tau), 2.f * S.r));
+    const DF half_pi{PS_DF_HALF_PI_HI, PS_DF_HALF_PI_LO};
+    return df_max(df_min(df_min(a, b), half_pi), q);
   }
   return q;
 }
@@ -507,14 +525,13 @@ __device__ __forceinline__ int steps32(float ad, const Step& S) { return ceil_st
 // Steps for a double-float turning ad > 0 (PS_PREC_MIXED): decided in FP32,
 // re-decided in double-float when the FP32 ratio sits within rounding of a
 // boundary, ceil(ad/q - snap) with the pair's exact ceiling.  With the pixel
-// boost a re-decided link step comes from the FP64 form of its rule (step_d).
+// boost a re-decided link step comes from its rule in double-float (step_df).
 template <bool PX>
 __device__ __forceinline__ int steps_mx(DF ad, const Step& S, const Seg* g) {
   if (!near_integer(ad.hi / S.q)) return ceil_steps(ad.hi, S.q);
-  if constexpr (PX) {
-    if (S.kind != 0) return ceil_steps_d(df_d(ad), step_d(S, g));
-  }
-  const DF x = df_sub(df_div_f(ad, S.q0), DF{PS_DF_SNAP_HI, PS_DF_SNAP_LO});
+  DF x;
+  if (PX && S.kind != 0) x = df_sub(df_div(ad, step_df(S, g)), DF{PS_DF_SNAP_HI, PS_DF_SNAP_LO});
+  else x = df_sub(df_div_f(ad, S.q0), DF{PS_DF_SNAP_HI, PS_DF_SNAP_LO});
   float c = ceilf(x.hi);
   if (c == x.hi && x.lo > 0.f) c += 1.f;
   const int D = (int)c;
@@ -597,13 +614,6 @@ __device__ int collinear_reversals(const Seg& g, T* rts) {
 __device__ __forceinline__ void put_psi(LinkRec& L, int k, DF v) { L.psi[k] = v.hi; L.psi_lo[k] = v.lo; }
 __device__ __forceinline__ void put_p(LinkRec& L, int k, DF v) { L.p[k] = v.hi; L.p_lo[k] = v.lo; }
 __device__ __forceinline__ void put_step(LinkRec& L, int k, DF v) { L.step[k] = v.hi; L.step_lo[k] = v.lo; }
-
-// Out-of-line double-float atan2 and sincos for the link set-up, which calls
-// them from many places on divergent paths: one copy of each keeps the
-// kernel's code small (its warps stalled on instruction fetch); the per-rib
-// emitter inlines them.
-__device__ __noinline__ DF atan2_ool(DF y, DF x) { return df_atan2(y, x, ps_sc_tab); }
-__device__ __noinline__ void sincos_ool(DF x, DF& s, DF& c) { df_sincos(x, ps_sc_tab, s, c); }
 
 // The curvature-sign polynomial in PS_PREC_MIXED.  A cubic's is formed in
 // double-float from the exact control-point differences (X_ij = d_i x d_j as
