@@ -238,6 +238,8 @@ int ps_add_s_carry(ps_context* ctx, float* d_s, const uint32_t* d_tag, const int
  *   - limits: at most 16384 links (2 n_seg + n_path) and, with
  *     PS_TESS_ARCLENGTH, a rib capacity of at most 4194304; larger problems
  *     return PS_ERR_CAPACITY before any launch;
+ *   - PS_TESS_ARCLENGTH with d_s == NULL returns PS_ERR_INVALID (the
+ *     regular call then skips arc length and writes no d_s);
  *   - the first call on a device looks up the array's device address (with
  *     that device current); make that first call outside any stream capture;
  *   - every call uses the same array, which keeps the previous call's

@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(TS_NT) k_tile_scan(const int32_t* __restrict__
 // warp runs its own queue: it takes the next 32 bin entries, each lane sets one
 // up (the path's mask slot from a shared hash, the edge functions relative to
 // the tile, the pixel span of every pixel row the quad can reach), a warp scan
-// flattens the entries' pixels so that every lane gets one pixel at a time, and
+// flattens the entries' pixels so that every lane gets two pixels at a time, and
 // each pixel's 16-sample mask is ORed into the path's mask in shared memory.
 // Block-wide barriers only open and close a tile: per-path popcounts and the
 // canvas OR are taken there.  Paths beyond SLOTS per tile take further passes.
@@ -1197,6 +1197,7 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
   uint32_t* s_slot_path = reinterpret_cast<uint32_t*>(s_slot_of + HKEYS);        // HKEYS
   __shared__ int s_tile, s_nslot, s_next;
   __shared__ uint8_t s_own[CV_WARPS][32];
+  __shared__ uint8_t s_own2[CV_WARPS][32];
   __shared__ uint32_t s_canvas[MASK_WORDS];
   __shared__ uint16_t s_rowmask[EXACT ? 17 * 17 : 1];
   // each lane's next bin entry (its two ribs and tag), copied in while the
@@ -1366,29 +1367,38 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
           // this lane's entry: first item and item count in the class
           const int pe = (int)((excl3 >> sh) & 0x1fffffu);
           const int ce = (int)((packed >> sh) & 0x1fffffu);
-          for (int it0 = 0; it0 < total; it0 += 32) {
-            // Items it0 .. it0 + 31 go one per lane.  Entries whose first item
-            // falls inside the round (after its first position) mark their
-            // start bit; the item's entry is the last start at or before the
-            // lane, else the entry holding item it0.
+          for (int it0 = 0; it0 < total; it0 += 64) {
+            // Items it0 .. it0 + 63 go two per lane (it0 + lane and it0 + 32 +
+            // lane), so that each lane has two independent decode and mask
+            // chains in flight.  Per 32-item window, entries whose first item
+            // falls inside it (after its first position) mark their start bit;
+            // an item's entry is the last start at or before it, else the
+            // entry holding the window's first item.
             __syncwarp();
-            const int sp = pe - it0;
-            const bool starts_here = ce > 0 && sp > 0 && sp < 32;
-            const uint32_t starts = __reduce_or_sync(0xffffffffu, starts_here ? 1u << sp : 0u);
-            if (starts_here) s_own[wid][sp] = (uint8_t)lane;
-            const uint32_t held = __ballot_sync(0xffffffffu, ce > 0 && pe <= it0);
-            const int ebase = 31 - __clz(held);
-            const int pebase = __shfl_sync(0xffffffffu, pe, ebase);
+            const int spa = pe - it0, spb = spa - 32;
+            const bool sta = ce > 0 && spa > 0 && spa < 32;
+            const bool stb = ce > 0 && spb > 0 && spb < 32;
+            const uint32_t startsA = __reduce_or_sync(0xffffffffu, sta ? 1u << spa : 0u);
+            const uint32_t startsB = __reduce_or_sync(0xffffffffu, stb ? 1u << spb : 0u);
+            if (sta) s_own[wid][spa] = (uint8_t)lane;
+            if (stb) s_own2[wid][spb] = (uint8_t)lane;
+            const uint32_t heldA = __ballot_sync(0xffffffffu, ce > 0 && pe <= it0);
+            const uint32_t heldB = __ballot_sync(0xffffffffu, ce > 0 && pe <= it0 + 32);
+            const int ebaseA = 31 - __clz(heldA);
+            const int ebaseB = heldB ? 31 - __clz(heldB) : 0;
+            const int pebaseA = __shfl_sync(0xffffffffu, pe, ebaseA);
+            const int pebaseB = __shfl_sync(0xffffffffu, pe, ebaseB);
             __syncwarp();
-            const int it = it0 + lane;
-            if (it < total) {
-              // branch-free: the owner table is read at p = 0 when no start
-              // lies at or before this lane (and not used then)
+            const int itA = it0 + lane, itB = it0 + 32 + lane;
+            // decode (every index stays in range for items past the end, whose
+            // masks are dropped)
+            auto decode = [&](int it, int w0, uint32_t starts, const uint8_t* own, int ebase,
+                              int pebase, int& e, int& lx, int& ly) {
               const uint32_t sm = starts & ((2u << lane) - 1u);
               const int p = sm ? 31 - __clz(sm) : 0;
-              const int eo = s_own[wid][p];
-              const int e = sm ? eo : ebase;
-              const int first = sm ? it0 + p : pebase;
+              const int eo = own[p];
+              e = sm ? eo : ebase;
+              const int first = sm ? w0 + p : pebase;
               const EntrySetup& E = my[e];
               const int li = it - first;
               // the item's row: the last k with rowpre[k] <= li, as a binary
@@ -1406,19 +1416,35 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
               const bool s1 = rodd <= li;
               const int pre = s1 ? rodd : (s2 ? q2 : rb);
               k += (s2 ? 2 : 0) + (s1 ? 1 : 0);
-              const int ly = E.row0 + k, lx = E.x0[k] + (li - pre);
-              uint32_t m;
+              ly = E.row0 + k;
+              lx = E.x0[k] + (li - pre);
+            };
+            auto mask_of = [&](int e, int lx, int ly, bool ok) -> uint32_t {
+              const EntrySetup& E = my[e];
               if (EXACT)
-                m = cls == 0 ? exact_mask(E, lx * 256, ly * 256, s_rowmask)
-                             : exact_mask_general(E, lx, ly);
-              else
-                m = cls == 0 ? fast_mask(E, lx * 256, ly * 256)
-                    : cls == 1 ? fast_mask2(E, lx * 256, ly * 256)
-                               : tri_or_quad_mask(E, lx, ly);
-              if (m) {
-                int lp = ly * TILE_PX + lx;
-                atomicOr(&s_mask[E.slot * MASK_WORDS + (lp >> 1)], m << (16 * (lp & 1)));
-              }
+                return cls == 0 ? exact_mask(E, lx * 256, ly * 256, s_rowmask)
+                                : (ok ? exact_mask_general(E, lx, ly) : 0u);
+              return cls == 0 ? fast_mask(E, lx * 256, ly * 256)
+                     : cls == 1 ? fast_mask2(E, lx * 256, ly * 256)
+                                : (ok ? tri_or_quad_mask(E, lx, ly) : 0u);
+            };
+            auto put = [&](int e, int lx, int ly, uint32_t m) {
+              const int lp = ly * TILE_PX + lx;
+              atomicOr(&s_mask[my[e].slot * MASK_WORDS + (lp >> 1)], m << (16 * (lp & 1)));
+            };
+            if (it0 + 32 < total) {  // warp-uniform: both halves hold items
+              int eA, lxA, lyA, eB, lxB, lyB;
+              decode(itA, it0, startsA, s_own[wid], ebaseA, pebaseA, eA, lxA, lyA);
+              decode(itB, it0 + 32, startsB, s_own2[wid], ebaseB, pebaseB, eB, lxB, lyB);
+              const uint32_t mA = mask_of(eA, lxA, lyA, true);
+              const uint32_t mB = mask_of(eB, lxB, lyB, itB < total);
+              if (mA) put(eA, lxA, lyA, mA);
+              if (itB < total && mB) put(eB, lxB, lyB, mB);
+            } else {
+              int eA, lxA, lyA;
+              decode(itA, it0, startsA, s_own[wid], ebaseA, pebaseA, eA, lxA, lyA);
+              const uint32_t mA = mask_of(eA, lxA, lyA, itA < total);
+              if (itA < total && mA) put(eA, lxA, lyA, mA);
             }
           }
         }
