@@ -1252,25 +1252,63 @@ __global__ void __launch_bounds__(SETUP_NT, 2) k_link_setup(
   __shared__ long long sm[SETUP_NT / 32 + 1];
   __shared__ long long s_prefix;
   __shared__ int s_tile;
+  // The tile's links are counting-sorted by class (the segment's type; a
+  // join; a cap) so that each warp sets up links of one class: the classes
+  // take different branches, and links alternate between segments and joins.
+  constexpr int NCLS = 6;
+  constexpr int TILE_L = SETUP_NT * SETUP_IPT;
+  __shared__ int s_ncls[NCLS];
+  __shared__ uint16_t s_perm[TILE_L];
+  __shared__ int s_cnt[TILE_L];  // rib count of each local link
+  __shared__ int s_pth[TILE_L];  // its path
+  __shared__ int s_kk[TILE_L];   // its index within the path
   if (threadIdx.x == 0) s_tile = atomicAdd(&counters[0], 1);
+  if (threadIdx.x < NCLS) s_ncls[threadIdx.x] = 0;
   __syncthreads();
   int64_t tile = s_tile;
   if (tile >= n_tiles) return;
-  int cnt[SETUP_IPT];
-  int pth[SETUP_IPT];
-  int kk[SETUP_IPT];
-  long long local = 0;
+  const int64_t l_tile = tile * (int64_t)TILE_L;
+  int cls_rank[SETUP_IPT];
   for (int i = 0; i < SETUP_IPT; ++i) {
-    int64_t l = tile * (SETUP_NT * SETUP_IPT) + (int64_t)threadIdx.x * SETUP_IPT + i;
-    cnt[i] = 0;
-    pth[i] = -1;
-    kk[i] = -1;
+    const int li = threadIdx.x * SETUP_IPT + i;
+    const int64_t l = l_tile + li;
+    cls_rank[i] = -1;
+    s_cnt[li] = 0;
     if (l < n_link) {
       // local link l is link l_begin + l of the batch (a range call)
       const int64_t lg = l_begin + l;
-      int p = find_path(seg_off, n_path, lg);
-      int32_t s0 = __ldg(seg_off + p), s1 = __ldg(seg_off + p + 1);
-      int k = (int)(lg - (2 * (int64_t)s0 + p));
+      const int p = find_path(seg_off, n_path, lg);
+      const int32_t s0 = __ldg(seg_off + p), n = __ldg(seg_off + p + 1) - s0;
+      const int k = (int)(lg - (2 * (int64_t)s0 + p));
+      s_pth[li] = p;
+      s_kk[li] = k;
+      const int c = (k & 1) ? min((int)__ldg(st + s0 + ((k - 1) >> 1)), 3)
+                            : ((k == 0 || k == 2 * n) && !closed[p]) ? 5 : 4;
+      cls_rank[i] = c << 16 | atomicAdd(&s_ncls[c], 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int c = 0; c < NCLS; ++c) {
+      const int v = s_ncls[c];
+      s_ncls[c] = acc;
+      acc += v;
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < SETUP_IPT; ++i)
+    if (cls_rank[i] >= 0)
+      s_perm[s_ncls[cls_rank[i] >> 16] + (cls_rank[i] & 0xffff)] =
+          (uint16_t)(threadIdx.x * SETUP_IPT + i);
+  __syncthreads();
+  const int n_here = (int)min((int64_t)TILE_L, n_link > l_tile ? n_link - l_tile : (int64_t)0);
+  for (int i = 0; i < SETUP_IPT; ++i) {
+    const int w = i * SETUP_NT + threadIdx.x;  // consecutive lanes, consecutive sorted links
+    if (w < n_here) {
+      const int li = s_perm[w];
+      const int p = s_pth[li], k = s_kk[li];
+      const int32_t s0 = __ldg(seg_off + p), s1 = __ldg(seg_off + p + 1);
       LinkRec L = {};
       int nr = link_setup<MIXED, PX>(st, sp, sw, s0, s1 - s0, k, 0.5f * __ldg(width + p), join[p],
                                  cap[p], __ldg(miter + p), closed[p] != 0, q, tau, L);
@@ -1280,13 +1318,13 @@ __global__ void __launch_bounds__(SETUP_NT, 2) k_link_setup(
         L.meta = 0;
       }
       L.pad = 0;
-      recs[l] = L;
-      cnt[i] = nr;
-      pth[i] = p;
-      kk[i] = k;
-      local += nr;
+      recs[l_tile + li] = L;
+      s_cnt[li] = nr;
     }
   }
+  __syncthreads();
+  long long local = 0;
+  for (int i = 0; i < SETUP_IPT; ++i) local += s_cnt[threadIdx.x * SETUP_IPT + i];
   long long total;
   long long excl = block_excl_sum<SETUP_NT>(local, total, sm);
   if (threadIdx.x < 32) {
@@ -1296,17 +1334,18 @@ __global__ void __launch_bounds__(SETUP_NT, 2) k_link_setup(
   __syncthreads();
   long long off = s_prefix + excl;
   for (int i = 0; i < SETUP_IPT; ++i) {
-    int64_t l = tile * (SETUP_NT * SETUP_IPT) + (int64_t)threadIdx.x * SETUP_IPT + i;
+    const int li = threadIdx.x * SETUP_IPT + i;
+    const int64_t l = l_tile + li;
     if (l < n_link) {
       if (off > 0x7fffffffLL) ps_record_error(status, PS_ERR_CAPACITY);
       link_off[l] = (int32_t)off;
-      if (kk[i] == 0) path_off[pth[i]] = (int32_t)off;
-      off += cnt[i];
+      const int p = s_pth[li], kk = s_kk[li];
+      if (kk == 0) path_off[p] = (int32_t)off;
+      off += s_cnt[li];
       if (l == n_link - 1) {
         link_off[n_link] = (int32_t)off;
         // the end of the last path, when the range ends with that path's last link
-        const int p = pth[i];
-        if (kk[i] == 2 * (__ldg(seg_off + p + 1) - __ldg(seg_off + p))) path_off[p + 1] = (int32_t)off;
+        if (kk == 2 * (__ldg(seg_off + p + 1) - __ldg(seg_off + p))) path_off[p + 1] = (int32_t)off;
         *n_rib_out = off;
         if (off > capacity) ps_record_error(status, PS_ERR_CAPACITY);
       }
