@@ -60,7 +60,7 @@ int ps_ensure_raster(ps_context* ctx, int64_t n_tile, int64_t n_pair) {
 int ps_ensure_quad_hits(ps_context* ctx, int64_t n_rib) {
   if (n_rib <= ctx->quad_hits_cap) return PS_OK;
   int64_t cap = n_rib + n_rib / 8 + 1024;
-  int rc = grow((void**)&ctx->d_quad_hits, sizeof(uint32_t) * cap);
+  int rc = grow((void**)&ctx->d_quad_hits, 2 * sizeof(uint32_t) * cap);
   if (rc != PS_OK) return rc;
   ctx->quad_hits_cap = cap;
   return PS_OK;

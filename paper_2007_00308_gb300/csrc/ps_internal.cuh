@@ -89,7 +89,7 @@ struct ps_context {
   int32_t* d_tile_list;     // tiles with bin entries, then their count
   int64_t raster_tile_cap;
   uint32_t* d_bin;          // [pair_cap]
-  uint32_t* d_quad_hits;    // [quad_hits_cap] per-rib tile-hit masks of the binning passes
+  uint32_t* d_quad_hits;    // [2 quad_hits_cap] per-rib {hits, box} words of the binning passes
   int64_t quad_hits_cap;
   int64_t pair_cap;
   int64_t* d_scratch64;     // 16 int64 of per-call scalars

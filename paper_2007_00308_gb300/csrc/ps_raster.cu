@@ -152,10 +152,12 @@ __device__ __forceinline__ bool quad_meets_tile(const QuadFix& q, bool small, in
 // per lane, and flattens their (quad, candidate) pairs with a warp scan so that
 // each lane tests one pair at a time; lanes of the warp that hit the same tile
 // are grouped: one atomic per group.
-// Per-quad word from the count pass for the scatter pass: 0 = no tile; bit 31
-// with the tile index below it = the quad's bounding box lies in that one tile
-// (the scatter pass then skips the quad's ribs); HITS_RETEST = more than 31
-// candidate tiles (retested); otherwise the hit mask over the candidates.
+// Per-quad words from the count pass for the scatter pass, {hits, box}.  hits:
+// 0 = no tile; bit 31 with the tile index below it = the quad's bounding box
+// lies in that one tile; HITS_RETEST = more than 31 candidate tiles (the
+// scatter pass re-reads, snaps and re-tests the quad); otherwise the hit mask
+// over the candidates, with box = the first candidate tile's index | (columns
+// - 1) << 26, so that the scatter pass reads no ribs for the quad.
 constexpr uint32_t HITS_RETEST = 0xffffffffu;
 constexpr uint32_t HITS_DIRECT = 0x80000000u;
 constexpr int BIN_NT = 256;
@@ -163,6 +165,7 @@ constexpr int BIN_NT = 256;
 struct BinQuad {
   int x[4], y[4];
   int tx0, ty0, ntx, n;  // candidate tiles: ntx columns from (tx0, ty0), n in all
+  int tbase;             // index of tile (tx0, ty0)
   uint32_t mask;         // pass 1: hit mask from pass 0; pass 0: hits found
   int small;
 };
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
                                                 const int32_t* __restrict__ off,
                                                 int32_t* __restrict__ cursor,
                                                 uint32_t* __restrict__ bin, int64_t pair_cap,
-                                                uint32_t* __restrict__ hits, int32_t* status) {
+                                                uint2* __restrict__ hits, int32_t* status) {
   __shared__ BinQuad s_q[BIN_NT];
   __shared__ int s_pre[BIN_NT / 32][33];
   int64_t R = *n_rib;
@@ -187,13 +190,17 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
   for (int64_t base = (int64_t)blockIdx.x * BIN_NT; base < R; base += stride) {
     const int64_t r = base + threadIdx.x;
     const bool in = r >= 1 && r < R;
-    const uint32_t h = PASS == 1 && in ? __ldg(hits + r) : 0u;
+    const uint2 hb = PASS == 1 && in ? __ldg(hits + r) : make_uint2(0u, 0u);
+    const uint32_t h = hb.x;
     const bool direct1 = PASS == 1 && (h & HITS_DIRECT) && h != HITS_RETEST;
-    const bool act = PASS == 0 ? in && !(__ldg(tag + r) & PS_TAG_LINK_START) : h != 0u && !direct1;
+    const bool boxed1 = PASS == 1 && h != 0u && !direct1 && h != HITS_RETEST;
+    const bool act = PASS == 0 ? in && !(__ldg(tag + r) & PS_TAG_LINK_START) : h == HITS_RETEST;
     BinQuad& Q = wq[lane];
     int cnt = 0;
     Q.n = 0;
     Q.mask = 0;
+    Q.tbase = 0;
+    Q.ntx = 1;
     if (act) {
       QuadFix q;
       if (!snap_quad(__ldg(rib + r - 1), __ldg(rib + r), q)) {
@@ -214,6 +221,7 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
           }
           Q.tx0 = tx0;
           Q.ty0 = ty0;
+          Q.tbase = ty0 * tiles_x + tx0;
           Q.ntx = tx1 - tx0 + 1;
           Q.n = Q.ntx * (ty1 - ty0 + 1);
           Q.small = mxx - mnx < (1 << 14) && mxy - mny < (1 << 14);
@@ -225,6 +233,13 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
           }
         }
       }
+    }
+    if (boxed1) {  // hit mask and candidate box from the count pass
+      Q.mask = h;
+      Q.tbase = (int)(hb.y & 0x3ffffffu);
+      Q.ntx = (int)(hb.y >> 26) + 1;
+      Q.n = 31;  // any count from 2 to 31: the mask gives the candidates
+      cnt = __popc(h);
     }
     // a quad whose bounding box lies in one tile meets that tile: binned in one
     // direct round, outside the flattened (quad, candidate) loop
@@ -287,7 +302,7 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
           hit = B.n == 1 || quad_meets_tile<PASS == 0>(q, B.small != 0, tx, ty, W, H);
         }
         if (hit) {
-          t = (B.ty0 + i / B.ntx) * tiles_x + (B.tx0 + i % B.ntx);
+          t = B.tbase + (i / B.ntx) * tiles_x + i % B.ntx;
           if (PASS == 0 && i < 31) atomicOr(&wq[e].mask, 1u << i);
         }
       }
@@ -310,9 +325,10 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
     }
     __syncwarp();
     if (PASS == 0 && in)
-      hits[r] = !act ? 0u
-                : Q.n == 1 ? HITS_DIRECT | (uint32_t)tdir
-                : Q.n <= 31 ? Q.mask : HITS_RETEST;
+      hits[r] = make_uint2(!act ? 0u
+                           : Q.n == 1 ? HITS_DIRECT | (uint32_t)tdir
+                           : Q.n <= 31 ? Q.mask : HITS_RETEST,
+                           (uint32_t)Q.tbase | (uint32_t)(Q.ntx - 1) << 26);
     __syncwarp();
   }
 }
@@ -1559,7 +1575,7 @@ static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
   { ProfScope ps_(ctx, PK_BIN_COUNT, st);
   k_bin<0><<<grid_bin, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, tiles_x,
                                       ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor,
-                                      ctx->d_bin, ctx->pair_cap, ctx->d_quad_hits,
+                                      ctx->d_bin, ctx->pair_cap, reinterpret_cast<uint2*>(ctx->d_quad_hits),
                                       ctx->d_status); }
   { ProfScope ps_(ctx, PK_TILE_SCAN, st);
   const int ts_grid = (int)((n_tile + TS_TILE - 1) / TS_TILE);
@@ -1570,7 +1586,7 @@ static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
   { ProfScope ps_(ctx, PK_BIN_SCATTER, st);
   k_bin<1><<<grid_bin1, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, tiles_x,
                                       ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor,
-                                      ctx->d_bin, ctx->pair_cap, ctx->d_quad_hits,
+                                      ctx->d_bin, ctx->pair_cap, reinterpret_cast<uint2*>(ctx->d_quad_hits),
                                       ctx->d_status); }
   { ProfScope ps_(ctx, PK_COVERAGE, st);
 #define PS_COV_ARGS                                                                              \
