@@ -391,8 +391,9 @@ def alu_peak_tests(sm_mhz, ops):
 
 # DRAM traffic of one k_coverage launch per bin entry, from an ncu capture of
 # the first 1,000 paths of the workload (dram__bytes_read.sum + write.sum =
-# 124.4 MB over 8,351,880 bin entries); scaled to the launch by its bin entries.
-COVERAGE_TRAFFIC_PER_PAIR = (117.652480e6 + 6.708736e6) / 8351880
+# 124.2 MB over 8,351,878 bin entries, two pixel items per lane); scaled to the
+# launch by its bin entries.
+COVERAGE_TRAFFIC_PER_PAIR = (117.509376e6 + 6.654720e6) / 8351878
 
 
 AUTOTUNE = True
@@ -603,7 +604,8 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "variant": "batched+mixed: one CUDA graph per step, "
-                   "FP32 with compensated g(t) and FP64 islands" +
+                   "FP32 pipe with double-float angles, normals, t and vertices; FP64 only "
+                   "in the curvature discriminant and near-double-root islands" +
                    (", quads rasterized as polygons" if args.exact else "") +
                    (f", per-link step boosted to pixel scale (tolerance {args.pixel_tol:g} px)"
                     if args.pixel_tol > 0 else ""), "n_segments": segs,
