@@ -284,8 +284,8 @@ def run_reference(args, rank, world):
 # offset: 16R + 4 pairs + 4 tiles, split as count 16R, tile scan 4 tiles,
 # scatter 4 pairs.  The library's own workspace (per-link records, per-rib tags
 # and chords, the binning passes' per-rib hit words) is not the method's work:
-# it is listed per kernel as workspace_bytes (design figures; DRAM traffic
-# measured by ncu is in profiles/).
+# it is listed per kernel as workspace_bytes (design figures, not measured
+# traffic).
 def algorithmic(kernel, c):
     R, L, S, P, pairs, tiles = c["R"], c["L"], c["S"], c["P"], c["pairs"], c["tiles"]
     table = {
@@ -302,12 +302,13 @@ def algorithmic(kernel, c):
 
 def workspace_bytes(kernel, c):
     """Bytes of the library's own workspace a kernel writes and reads (design
-    figures): 240 B link records, 4 B tags and 4 B chords per rib, 4 B hit words
-    per rib between the binning passes, 4 B bin entries read by the scatter's
-    cursor pass."""
+    figures): 240 B link records, 4 B tags and 4 B chords per rib, and the two
+    4 B words per rib ({hits, box}) that the count pass leaves for the scatter
+    pass (which re-reads ribs only for quads with more than 31 candidate
+    tiles)."""
     R, L = c["R"], c["L"]
     return {"k_link_setup": 240 * L, "k_emit": 240 * L + 8 * R, "k_arclen_scan": 8 * R,
-            "k_bin_count": 8 * R, "k_bin_scatter": 16 * R + 8 * R}.get(kernel, 0)
+            "k_bin_count": 4 * R + 8 * R, "k_bin_scatter": 8 * R}.get(kernel, 0)
 
 
 STAGES = {
