@@ -14,6 +14,9 @@
  *   ps_rasterize_coverage   16-sample coverage of the stroked quads, binned into
  *                           16x16-pixel tiles (Sec. 4.1: quads drawn as two
  *                           triangles; Sec. 3.3.6: per-path union)
+ *   ps_rasterize_coverage_rows, ps_route_quads   the same on a window of rows,
+ *                           and the routing of quads to the owners of a canvas
+ *                           split by rows over several GPUs
  *
  * Conventions shared by every call
  *   - Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
@@ -341,6 +344,57 @@ int ps_rasterize_coverage_exact(ps_context* ctx, const float* d_rib, const uint3
                                 const int64_t* d_n_rib, int64_t capacity, int32_t n_path,
                                 int width, int height, int spp, uint16_t* d_canvas,
                                 uint64_t* d_covered, void* stream);
+
+/* Coverage of the pixel rows [row_begin, row_begin + height) of a picture
+ * (a window of a canvas split by tile rows over several GPUs; row_begin >= 0 a
+ * multiple of 16, the tile size).  Quads are snapped in picture coordinates
+ * (Sec. 4.1, as ps_rasterize_coverage) and moved to the window's origin after
+ * snapping, in 1/256-px integers, so every pixel of the window gets the same
+ * mask as in ps_rasterize_coverage of the whole picture; quads outside the
+ * window are clipped away.
+ *   d_canvas[y*width + x]   uint16 mask of picture pixel (x, row_begin + y),
+ *                           height x width (overwritten)
+ *   d_covered[p]            uint64 samples of path p inside the window
+ *                           (overwritten); summed over windows that partition
+ *                           the picture's rows they equal ps_rasterize_coverage's
+ * exact != 0 selects the crossing rule of ps_rasterize_coverage_exact.
+ * Returns PS_ERR_INVALID for a negative or unaligned row_begin; other arguments
+ * and errors as ps_rasterize_coverage. */
+int ps_rasterize_coverage_rows(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
+                               const int64_t* d_n_rib, int64_t capacity, int32_t n_path,
+                               int width, int row_begin, int height, int spp,
+                               uint16_t* d_canvas, uint64_t* d_covered, int exact, void* stream);
+
+/* Routes the quads of a rib stream to the owners of a canvas split by pixel
+ * rows (the raster half of splitting one batch over several GPUs; Sec. 4.4
+ * makes links independent, Sec. 3.3.6 makes coverage a per-path union, so the
+ * owner of a row must see every quad of every path that reaches it).
+ * Destination d owns rows [row_begin[d], row_begin[d+1]) of a width x height
+ * canvas; d_row_begin is a DEVICE int32 array of n_dest + 1 non-decreasing
+ * multiples of 16 (row_begin[0] = 0, row_begin[n_dest] = height; 1 <= n_dest
+ * <= 4096; an empty window receives nothing).  Quad (r-1, r) (tag r without
+ * PS_TAG_LINK_START) goes to every owner of a pixel row that its snapped
+ * bounding box reaches, in the same rows the binning would test it against.
+ * Output, grouped by destination (block d = quads [dest_off[d], dest_off[d+1])):
+ *   d_out_rib[2i], d_out_rib[2i+1]   float4 x 2: ribs r-1 and r of quad i
+ *                                     (2 * out_capacity float4 of room)
+ *   d_out_tag[2i], d_out_tag[2i+1]   tag r with PS_TAG_LINK_START set, tag r
+ *                                     (2 * out_capacity uint32 of room)
+ *   d_dest_count[d]                  int64 quads of destination d
+ *   d_dest_off[d]                    int64 exclusive prefix, n_dest + 1 entries
+ * so that a destination's block, and any concatenation of blocks from several
+ * ranks, is itself a rib stream whose quads are exactly the routed ones; it
+ * goes to ps_rasterize_coverage_rows with the destination's window.  Counts
+ * and offsets are written even when the quads do not fit: the device status
+ * then records PS_ERR_CAPACITY and only quads below out_capacity are written.
+ * With d_out_rib and d_out_tag NULL and out_capacity 0 the call only counts
+ * (d_dest_count, d_dest_off), so that the caller can size the output.
+ * Quads with a vertex beyond +-2^21 px record PS_ERR_RANGE and go nowhere. */
+int ps_route_quads(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
+                   const int64_t* d_n_rib, int64_t capacity, int32_t width, int32_t height,
+                   int32_t n_dest, const int32_t* d_row_begin, float* d_out_rib,
+                   uint32_t* d_out_tag, int64_t out_capacity, int64_t* d_dest_count,
+                   int64_t* d_dest_off, void* stream);
 
 /* ---- kernel timing (measurement hooks) ------------------------------------------
  * With profiling enabled the library records a CUDA event pair around each of its

@@ -27,7 +27,8 @@ EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_statu
            "ps_tessellate_backward", "ps_set_tuning", "ps_get_tuning", "ps_svg_arc_to_conics",
            "ps_uniform_tessellate", "ps_facet_stats", "ps_dash_capped",
            "ps_rasterize_coverage_exact", "ps_set_pixel_tolerance", "ps_get_pixel_tolerance",
-           "ps_check_wait_timeout", "ps_tessellate_links", "ps_add_s_carry"]
+           "ps_check_wait_timeout", "ps_tessellate_links", "ps_add_s_carry",
+           "ps_rasterize_coverage_rows", "ps_route_quads"]
 PS_PROF_SLOTS = 10
 PS_TUNE_EMIT_SLABS, PS_TUNE_SETUP_LINKS, PS_TUNE_BIN_BLOCKS = 0, 1, 2
 TUNE_CANDIDATES = {PS_TUNE_EMIT_SLABS: (4, 8, 16, 32), PS_TUNE_SETUP_LINKS: (1, 2, 4),
@@ -118,6 +119,9 @@ def lib():
                                           ctypes.c_float, ctypes.c_int, ctypes.c_uint32, I64, I64,
                                           ctypes.POINTER(_TessOut), P]
         L.ps_add_s_carry.argtypes = [P, P, P, P, I64, I32, ctypes.c_double, P, ctypes.c_int, P]
+        L.ps_rasterize_coverage_rows.argtypes = [P, P, P, P, I64, I32, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P]
+        L.ps_route_quads.argtypes = [P, P, P, P, I64, I32, I32, I32, P, P, P, I64, P, P, P]
         L.ps_tessellate_strokes_noalloc.argtypes = [ctypes.POINTER(_Segments),
                                                     ctypes.POINTER(_Paths), ctypes.c_float,
                                                     ctypes.c_int, ctypes.c_uint32,
@@ -424,6 +428,28 @@ def ps_rasterize_coverage(ctx: Context, rib, tag, n_rib, capacity, n_path, width
                                      int(n_path), int(width), int(height), int(spp), _ptr(canvas),
                                      _ptr(covered), _stream(stream))
     _check(rc, "ps_rasterize_coverage")
+
+
+def ps_rasterize_coverage_rows(ctx: Context, rib, tag, n_rib, capacity, n_path, width, row_begin,
+                               height, canvas, covered, spp=16, stream=None, exact=False):
+    """Coverage of picture rows [row_begin, row_begin + height) into ``canvas``
+    (height x width) and the per-path samples inside them into ``covered``."""
+    rc = lib().ps_rasterize_coverage_rows(ctx.handle, _ptr(rib), _ptr(tag), _ptr(n_rib),
+                                          int(capacity), int(n_path), int(width), int(row_begin),
+                                          int(height), int(spp), _ptr(canvas), _ptr(covered),
+                                          int(bool(exact)), _stream(stream))
+    _check(rc, "ps_rasterize_coverage_rows")
+
+
+def ps_route_quads(ctx: Context, rib, tag, n_rib, capacity, width, height, row_begin, out_rib,
+                   out_tag, out_capacity, dest_count, dest_off, stream=None):
+    """Group the quads of a rib stream by the owners of the canvas rows they reach
+    (``row_begin``: device int32 [n_dest + 1]); see the C header for the layout."""
+    rc = lib().ps_route_quads(ctx.handle, _ptr(rib), _ptr(tag), _ptr(n_rib), int(capacity),
+                              int(width), int(height), int(row_begin.numel() - 1), _ptr(row_begin),
+                              _ptr(out_rib), _ptr(out_tag), int(out_capacity), _ptr(dest_count),
+                              _ptr(dest_off), _stream(stream))
+    _check(rc, "ps_route_quads")
 
 
 def tessellate(ctx: Context, db: DeviceBatch, precision=PS_PREC_FP32, arclength=True,

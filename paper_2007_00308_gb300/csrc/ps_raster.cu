@@ -174,7 +174,7 @@ template <int PASS>
 __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
                                                 const uint32_t* __restrict__ tag,
                                                 const int64_t* __restrict__ n_rib, int64_t capacity,
-                                                int W, int H, int tiles_x,
+                                                int W, int H, int y0, int tiles_x,
                                                 int32_t* __restrict__ count,
                                                 const int32_t* __restrict__ off,
                                                 int32_t* __restrict__ cursor,
@@ -206,6 +206,8 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
       if (!snap_quad(__ldg(rib + r - 1), __ldg(rib + r), q)) {
         if (PASS == 0) ps_record_error(status, PS_ERR_RANGE);
       } else {
+        // relative to the window's first row (exact: snapped units)
+        for (int v = 0; v < 4; ++v) q.y[v] -= y0;
         int mnx = min(min(q.x[0], q.x[1]), min(q.x[2], q.x[3]));
         int mxx = max(max(q.x[0], q.x[1]), max(q.x[2], q.x[3]));
         int mny = min(min(q.y[0], q.y[1]), min(q.y[2], q.y[3]));
@@ -1200,7 +1202,7 @@ template <bool EXACT>
 __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
     const float4* __restrict__ rib, const uint32_t* __restrict__ tag,
     const int32_t* __restrict__ off, const uint32_t* __restrict__ bin, int64_t pair_cap, int W,
-    int H, int tiles_x, int n_tile, const int32_t* __restrict__ tile_list,
+    int H, int y0, int tiles_x, int n_tile, const int32_t* __restrict__ tile_list,
     uint16_t* __restrict__ canvas,
     unsigned long long* __restrict__ covered, int n_path, int32_t* counters, int32_t* status,
     unsigned long long* __restrict__ stats) {
@@ -1348,7 +1350,7 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
         unsigned long long packed = 0;
         if (valid && slot >= slot_lo && slot < slot_lo + SLOTS && slot < HKEYS) {
           EntrySetup& E = my[lane];
-          int tot = setup_edges<EXACT>(ra, rb, slot - slot_lo, ox, oy, tw, th, E);
+          int tot = setup_edges<EXACT>(ra, rb, slot - slot_lo, ox, oy + y0, tw, th, E);
           if (tot > 0) {
             st_rows += E.nrow;
             // pixel items per class in 21-bit fields (at most 32 x 256 each):
@@ -1525,14 +1527,20 @@ size_t coverage_smem_bytes() {
 
 }  // namespace
 
+// The canvas holds pixel rows [row0, row0 + height) of the picture (row0 a
+// multiple of the tile size); quads are snapped in picture coordinates and
+// moved to the window's origin after snapping, so every tile of the window is
+// covered exactly as in a canvas that starts at row 0.
 static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
                      const int64_t* d_n_rib, int64_t capacity, int32_t n_path, int width,
-                     int height, int spp, uint16_t* d_canvas, uint64_t* d_covered, void* stream,
-                     bool exact) {
+                     int row0, int height, int spp, uint16_t* d_canvas, uint64_t* d_covered,
+                     void* stream, bool exact) {
   if (!ctx || !d_rib || !d_tag || !d_n_rib || !d_canvas || !d_covered) return PS_ERR_INVALID;
   if (spp != 16 || width <= 0 || height <= 0 || capacity < 0 || n_path < 0) return PS_ERR_INVALID;
-  if ((int64_t)width * 256 >= COORD_LIMIT || (int64_t)height * 256 >= COORD_LIMIT)
+  if (row0 < 0 || row0 % TILE_PX != 0) return PS_ERR_INVALID;
+  if ((int64_t)width * 256 >= COORD_LIMIT || ((int64_t)row0 + height) * 256 >= COORD_LIMIT)
     return PS_ERR_INVALID;
+  const int y0 = row0 * 256;
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = stream;
   int tiles_x = (width + TILE_PX - 1) / TILE_PX, tiles_y = (height + TILE_PX - 1) / TILE_PX;
@@ -1573,7 +1581,7 @@ static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
                       : ps_persistent_grid(ctx, (const void*)k_bin<1>, BIN_NT, 0);
   const float4* rib = reinterpret_cast<const float4*>(d_rib);
   { ProfScope ps_(ctx, PK_BIN_COUNT, st);
-  k_bin<0><<<grid_bin, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, tiles_x,
+  k_bin<0><<<grid_bin, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, y0, tiles_x,
                                       ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor,
                                       ctx->d_bin, ctx->pair_cap, reinterpret_cast<uint2*>(ctx->d_quad_hits),
                                       ctx->d_status); }
@@ -1584,13 +1592,13 @@ static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
                                          ctx->d_tile_flag, ctx->d_tile_agg, ctx->d_tile_incl,
                                          ctx->d_status); }
   { ProfScope ps_(ctx, PK_BIN_SCATTER, st);
-  k_bin<1><<<grid_bin1, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, tiles_x,
+  k_bin<1><<<grid_bin1, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, y0, tiles_x,
                                       ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor,
                                       ctx->d_bin, ctx->pair_cap, reinterpret_cast<uint2*>(ctx->d_quad_hits),
                                       ctx->d_status); }
   { ProfScope ps_(ctx, PK_COVERAGE, st);
 #define PS_COV_ARGS                                                                              \
-  rib, d_tag, ctx->d_tile_off, ctx->d_bin, ctx->pair_cap, width, height, tiles_x, (int)n_tile,  \
+  rib, d_tag, ctx->d_tile_off, ctx->d_bin, ctx->pair_cap, width, height, y0, tiles_x, (int)n_tile, \
       ctx->d_tile_list, d_canvas, reinterpret_cast<unsigned long long*>(d_covered), n_path, ctx->d_counters,      \
       ctx->d_status, reinterpret_cast<unsigned long long*>(ctx->d_scratch64)
   if (exact) k_coverage<true><<<grid_cov, CV_NT, cov_smem, st>>>(PS_COV_ARGS);
@@ -1604,7 +1612,7 @@ extern "C" int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const 
                                      const int64_t* d_n_rib, int64_t capacity, int32_t n_path,
                                      int width, int height, int spp, uint16_t* d_canvas,
                                      uint64_t* d_covered, void* stream) {
-  return rasterize(ctx, d_rib, d_tag, d_n_rib, capacity, n_path, width, height, spp, d_canvas,
+  return rasterize(ctx, d_rib, d_tag, d_n_rib, capacity, n_path, width, 0, height, spp, d_canvas,
                    d_covered, stream, false);
 }
 
@@ -1613,8 +1621,167 @@ extern "C" int ps_rasterize_coverage_exact(ps_context* ctx, const float* d_rib,
                                            int64_t capacity, int32_t n_path, int width, int height,
                                            int spp, uint16_t* d_canvas, uint64_t* d_covered,
                                            void* stream) {
-  return rasterize(ctx, d_rib, d_tag, d_n_rib, capacity, n_path, width, height, spp, d_canvas,
+  return rasterize(ctx, d_rib, d_tag, d_n_rib, capacity, n_path, width, 0, height, spp, d_canvas,
                    d_covered, stream, true);
+}
+
+extern "C" int ps_rasterize_coverage_rows(ps_context* ctx, const float* d_rib,
+                                          const uint32_t* d_tag, const int64_t* d_n_rib,
+                                          int64_t capacity, int32_t n_path, int width,
+                                          int row_begin, int height, int spp,
+                                          uint16_t* d_canvas, uint64_t* d_covered, int exact,
+                                          void* stream) {
+  return rasterize(ctx, d_rib, d_tag, d_n_rib, capacity, n_path, width, row_begin, height, spp,
+                   d_canvas, d_covered, stream, exact != 0);
+}
+
+// ---------------------------------------------------------------------------
+// Routing quads to the ranks that own their pixel rows, for a raster split of
+// the canvas by tile rows over several GPUs: rank d owns rows [row_begin[d],
+// row_begin[d + 1]).  A quad goes to every owner of a pixel row its snapped
+// bounding box reaches (the rows the binning would test it against), as its
+// two ribs and tags; the receiving rank covers its rows from the quads of all
+// ranks, so each of its tiles sees every quad of every path that reaches it.
+namespace {
+
+constexpr int ROUTE_NT = 256;
+
+// the last d in [0, n_dest) with row_begin[d] <= py (0 when there is none)
+__device__ __forceinline__ int owner_of_row(const int32_t* __restrict__ row_begin, int n_dest,
+                                            int py) {
+  int lo = 0, hi = n_dest - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(row_begin + mid) <= py) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// pass 0 counts the quads of every destination; pass 1 writes them at the
+// destination's offset (count[] restarts from 0 between the passes).
+template <int PASS>
+__global__ void __launch_bounds__(ROUTE_NT) k_route(const float4* __restrict__ rib,
+                                                    const uint32_t* __restrict__ tag,
+                                                    const int64_t* __restrict__ n_rib,
+                                                    int64_t capacity, int W, int H, int n_dest,
+                                                    const int32_t* __restrict__ row_begin,
+                                                    unsigned long long* __restrict__ count,
+                                                    const long long* __restrict__ off,
+                                                    float4* __restrict__ out_rib,
+                                                    uint32_t* __restrict__ out_tag,
+                                                    int64_t out_cap, int32_t* status) {
+  int64_t R = *n_rib;
+  if (R > capacity) R = capacity;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * ROUTE_NT;
+  for (int64_t base = (int64_t)blockIdx.x * ROUTE_NT; base < R; base += stride) {
+    const int64_t r = base + threadIdx.x;
+    int q0 = 0, nq = 0;  // destinations q0 .. q0 + nq - 1
+    uint32_t tg = 0u;
+    float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
+    if (r >= 1 && r < R) {
+      tg = __ldg(tag + r);
+      if (!(tg & PS_TAG_LINK_START)) {
+        ra = __ldg(rib + r - 1);
+        rb = __ldg(rib + r);
+        QuadFix q;
+        if (!snap_quad(ra, rb, q)) {
+          if (PASS == 0) ps_record_error(status, PS_ERR_RANGE);
+        } else {
+          const int mnx = min(min(q.x[0], q.x[1]), min(q.x[2], q.x[3]));
+          const int mxx = max(max(q.x[0], q.x[1]), max(q.x[2], q.x[3]));
+          const int mny = min(min(q.y[0], q.y[1]), min(q.y[2], q.y[3]));
+          const int mxy = max(max(q.y[0], q.y[1]), max(q.y[2], q.y[3]));
+          int px0, px1, py0, py1;
+          pix_range(mnx, mxx, W, px0, px1);
+          pix_range(mny, mxy, H, py0, py1);
+          if (px0 <= px1 && py0 <= py1) {
+            q0 = owner_of_row(row_begin, n_dest, py0);
+            nq = owner_of_row(row_begin, n_dest, py1) - q0 + 1;
+          }
+        }
+      }
+    }
+    // round k takes every lane's k-th destination; lanes bound for one rank
+    // are grouped, one atomic per group
+    const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)max(nq, 0));
+    for (int k = 0; k < kmax; ++k) {
+      int d = k < nq ? q0 + k : -1;
+      if (d >= 0 && __ldg(row_begin + d) >= __ldg(row_begin + d + 1)) d = -1;  // empty window
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const int leader = __ffs(peers) - 1;
+      if (d >= 0) {
+        if (PASS == 0) {
+          if (lane == leader) atomicAdd(count + d, (unsigned long long)__popc(peers));
+        } else {
+          unsigned long long b = 0;
+          if (lane == leader) b = atomicAdd(count + d, (unsigned long long)__popc(peers));
+          b = __shfl_sync(peers, b, leader);
+          const long long pos = off[d] + (long long)b + __popc(peers & ((1u << lane) - 1u));
+          if (pos < out_cap && pos < off[d + 1]) {
+            out_rib[2 * pos] = ra;
+            out_rib[2 * pos + 1] = rb;
+            out_tag[2 * pos] = tg | PS_TAG_LINK_START;  // a pair starts a link: one quad
+            out_tag[2 * pos + 1] = tg;
+          } else {
+            ps_record_error(status, PS_ERR_CAPACITY);
+          }
+        }
+      }
+    }
+  }
+}
+
+// offsets of the destinations' blocks; the counts restart for pass 1 (kept
+// when the call only counts)
+__global__ void k_route_scan(unsigned long long* count, long long* off, int n_dest,
+                             int64_t out_cap, bool count_only, int32_t* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  long long acc = 0;
+  for (int d = 0; d < n_dest; ++d) {
+    off[d] = acc;
+    acc += (long long)count[d];
+    if (!count_only) count[d] = 0ull;
+  }
+  off[n_dest] = acc;
+  if (!count_only && acc > out_cap) ps_record_error(status, PS_ERR_CAPACITY);
+}
+
+}  // namespace
+
+extern "C" int ps_route_quads(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
+                              const int64_t* d_n_rib, int64_t capacity, int32_t width,
+                              int32_t height, int32_t n_dest, const int32_t* d_row_begin,
+                              float* d_out_rib, uint32_t* d_out_tag, int64_t out_capacity,
+                              int64_t* d_dest_count, int64_t* d_dest_off, void* stream) {
+  if (!ctx || !d_rib || !d_tag || !d_n_rib || !d_row_begin || !d_dest_count || !d_dest_off)
+    return PS_ERR_INVALID;
+  if (capacity < 0 || out_capacity < 0 || width <= 0 || height <= 0 || n_dest < 1 ||
+      n_dest > 4096)
+    return PS_ERR_INVALID;
+  const bool count_only = !d_out_rib && !d_out_tag && out_capacity == 0;
+  if (!count_only && (!d_out_rib || !d_out_tag)) return PS_ERR_INVALID;
+  if ((int64_t)width * 256 >= COORD_LIMIT || (int64_t)height * 256 >= COORD_LIMIT)
+    return PS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = stream;
+  int rc = ps_cuda_check(cudaMemsetAsync(d_dest_count, 0, sizeof(int64_t) * n_dest, st));
+  if (rc != PS_OK) return rc;
+  const float4* rib = reinterpret_cast<const float4*>(d_rib);
+  float4* orib = reinterpret_cast<float4*>(d_out_rib);
+  auto* cnt = reinterpret_cast<unsigned long long*>(d_dest_count);
+  auto* off = reinterpret_cast<long long*>(d_dest_off);
+  const int grid = ps_persistent_grid(ctx, (const void*)k_route<0>, ROUTE_NT, 0);
+  k_route<0><<<grid, ROUTE_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, n_dest,
+                                        d_row_begin, cnt, off, orib, d_out_tag, out_capacity,
+                                        ctx->d_status);
+  k_route_scan<<<1, 32, 0, st>>>(cnt, off, n_dest, out_capacity, count_only, ctx->d_status);
+  if (!count_only)
+    k_route<1><<<grid, ROUTE_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, n_dest,
+                                          d_row_begin, cnt, off, orib, d_out_tag, out_capacity,
+                                          ctx->d_status);
+  return ps_cuda_check(cudaGetLastError());
 }
 
 extern "C" int ps_raster_stats(ps_context* ctx, int64_t* h_counts, int n_counts) {

@@ -189,3 +189,92 @@ def exchange(n_rib: int, tail: float, group=None):
     dist.all_gather(out, mine, group=group)
     arr = torch.stack(out).cpu().numpy()
     return arr[:, 0].astype(np.int64), arr[:, 1]
+
+
+# ---------------------------------------------------------------------------
+# The raster half: the canvas is split by tile rows, rank d owning pixel rows
+# [bounds[d], bounds[d + 1]).  Each rank routes the quads of its links to the
+# owners of the rows they reach (``ps_route_quads``, on the device), one
+# all-to-all moves them, and each owner covers its rows from the quads of all
+# ranks (``ps_rasterize_coverage_rows``): every tile then sees every quad of
+# every path that reaches it, so its per-path unions (Sec. 3.3.6) are those of
+# one rank stroking the whole batch.  Per-path sample counts add up over the
+# windows (one all-reduce); the canvas is the windows stacked.
+
+TILE_PX = 16
+
+
+def raster_rows(height: int, G: int) -> np.ndarray:
+    """G + 1 pixel-row bounds splitting a canvas of ``height`` rows into G
+    windows of whole tile rows (int32; bounds[0] = 0, bounds[G] = height)."""
+    tiles_y = -(-int(height) // TILE_PX)
+    b = np.array([TILE_PX * ((r * tiles_y) // G) for r in range(G + 1)], np.int64)
+    b = np.minimum(b, int(height))
+    b[G] = int(height)
+    return b.astype(np.int32)
+
+
+def route(ps, ctx, rib, tag, n_rib, capacity, width, height, bounds, stream=None):
+    """Group this rank's quads by destination rank (``ps_route_quads``).
+    Returns (quad ribs float32 [Q, 8], quad tags int32 [Q, 2], counts int64 [G])
+    on the device, grouped by destination in rank order."""
+    import torch
+    dev = rib.device
+    G = len(bounds) - 1
+    rb = torch.as_tensor(np.asarray(bounds, np.int32), device=dev)
+    cnt = torch.zeros(G, dtype=torch.int64, device=dev)
+    off = torch.zeros(G + 1, dtype=torch.int64, device=dev)
+    # a quad reaches few windows: size the output from a counting call first
+    ps.ps_route_quads(ctx, rib, tag, n_rib, capacity, width, height, rb, None, None, 0, cnt, off,
+                      stream)
+    Q = int(off[G].item())  # synchronizes
+    out_rib = torch.empty((max(Q, 1), 8), dtype=torch.float32, device=dev)
+    out_tag = torch.empty((max(Q, 1), 2), dtype=torch.int32, device=dev)
+    ps.ps_route_quads(ctx, rib, tag, n_rib, capacity, width, height, rb, out_rib, out_tag, Q, cnt,
+                      off, stream)
+    return out_rib[:Q], out_tag[:Q], cnt
+
+
+def exchange_quads(out_rib, out_tag, counts, group=None):
+    """The all-to-all of routed quads: this rank's blocks (grouped by
+    destination, ``counts[d]`` quads for rank d) go to their ranks, and the
+    blocks addressed to this rank arrive in rank order.  Returns (ribs [2 n, 4],
+    tags [2 n], the dtypes of the inputs) for ``ps_rasterize_coverage_rows``:
+    the quads as a rib stream."""
+    import torch
+    import torch.distributed as dist
+    send = [int(c) for c in torch.as_tensor(counts).cpu().tolist()]
+    G = dist.get_world_size(group)
+    c_in = torch.tensor(send, dtype=torch.int64, device=out_rib.device)
+    c_out = torch.empty(G, dtype=torch.int64, device=out_rib.device)
+    dist.all_to_all_single(c_out, c_in, group=group)
+    recv = [int(c) for c in c_out.cpu().tolist()]
+    n = sum(recv)
+    r_rib = torch.empty((n, 8), dtype=out_rib.dtype, device=out_rib.device)
+    r_tag = torch.empty((n, 2), dtype=out_tag.dtype, device=out_tag.device)
+    dist.all_to_all_single(r_rib, out_rib.contiguous(), output_split_sizes=recv,
+                           input_split_sizes=send, group=group)
+    dist.all_to_all_single(r_tag, out_tag.contiguous(), output_split_sizes=recv,
+                           input_split_sizes=send, group=group)
+    return r_rib.reshape(2 * n, 4), r_tag.reshape(2 * n)
+
+
+def merge_covered(covered, group=None):
+    """Per-path sample counts of the whole canvas: the sum over the windows."""
+    import torch.distributed as dist
+    dist.all_reduce(covered, op=dist.ReduceOp.SUM, group=group)
+    return covered
+
+
+def gather_rows(canvas_rows, bounds, group=None):
+    """The whole canvas on every rank: the windows stacked in row order."""
+    import torch
+    import torch.distributed as dist
+    G = len(bounds) - 1
+    hmax = max(int(bounds[d + 1] - bounds[d]) for d in range(G))
+    W = canvas_rows.shape[1]
+    pad = torch.zeros((hmax, W), dtype=canvas_rows.dtype, device=canvas_rows.device)
+    pad[:canvas_rows.shape[0]] = canvas_rows
+    parts = [torch.empty_like(pad) for _ in range(G)]
+    dist.all_gather(parts, pad, group=group)
+    return torch.cat([parts[d][:int(bounds[d + 1] - bounds[d])] for d in range(G)])

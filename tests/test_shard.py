@@ -153,3 +153,108 @@ def test_estimates_balance_the_ranks():
     bounds = shard.split_links(est, 4)
     per_rank = [int(n[bounds[r]:bounds[r + 1]].sum()) for r in range(4)]
     assert max(per_rank) <= 1.2 * (sum(per_rank) / 4)
+
+
+# ---------------------------------------------------------------------------
+# The raster split by canvas rows, on the CPU: each gloo rank routes the quads
+# of its link range to the owners of the rows they reach (the routing rule of
+# ps_route_quads, restated here on the oracle's snapped coordinates), one
+# all-to-all moves them (shard.exchange_quads), each owner covers its rows with
+# the oracle's raster, and the per-path counts and the canvas rows are merged
+# (shard.merge_covered, shard.gather_rows).  The result must equal the oracle's
+# raster of the whole batch bit for bit.
+
+def _rows_reached(rib, W, H):
+    """Pixel rows [py0, py1] whose sample rows a quad's snapped bounding box
+    reaches (py0 > py1: none), for quads given as rib pairs [n, 8]."""
+    v = np.rint(np.asarray(rib, np.float64) * 256.0).astype(np.int64)
+    xs, ys = v[:, 0::2], v[:, 1::2]
+    mnx, mxx, mny, mxy = xs.min(1), xs.max(1), ys.min(1), ys.max(1)
+    px0 = np.maximum(-((248 - mnx) // 256), 0)
+    px1 = np.minimum((mxx - 8) // 256, W - 1)
+    py0 = np.maximum(-((248 - mny) // 256), 0)
+    py1 = np.minimum((mxy - 8) // 256, H - 1)
+    empty = (px0 > px1) | (py0 > py1)
+    return np.where(empty, 1, py0), np.where(empty, 0, py1)
+
+
+def host_route(rib, tag, W, H, bounds):
+    """Quads (r-1, r) of a rib stream grouped by destination: ([n, 8] ribs,
+    [n, 2] tags with the link-start bit on the first) and the counts."""
+    r = np.nonzero((tag[1:] & LINK_START) == 0)[0] + 1
+    q_rib = np.concatenate([rib[r - 1], rib[r]], axis=1)
+    q_tag = np.stack([tag[r] | LINK_START, tag[r]], axis=1).astype(np.int64)
+    py0, py1 = _rows_reached(q_rib, W, H)
+    G = len(bounds) - 1
+    out_r, out_t, cnt = [], [], []
+    for d in range(G):
+        a, b = int(bounds[d]), int(bounds[d + 1])
+        sel = (py0 <= py1) & (py0 < b) & (py1 >= a) & (b > a)
+        out_r.append(q_rib[sel])
+        out_t.append(q_tag[sel])
+        cnt.append(int(sel.sum()))
+    return np.concatenate(out_r), np.concatenate(out_t), np.array(cnt, np.int64)
+
+
+def oracle_rows(rib, tag, W, H, n_path, y0, h):
+    """The oracle's coverage of picture rows [y0, y0 + h): canvas rows and the
+    per-path samples inside them (each path rasterized alone: its union)."""
+    canvas = np.zeros((h, W), np.uint16)
+    cov = np.zeros(n_path, np.int64)
+    paths = tag[1::2] >> 2
+    for p in np.unique(paths):
+        sel = np.repeat(paths == p, 2)
+        c, _ = oracle.raster(rib[sel], tag[sel] & 3, W, H, 1)
+        rows = c[y0:y0 + h]
+        canvas |= rows
+        cov[p] = int(np.unpackbits(rows.view(np.uint8)).sum())
+    return canvas, cov
+
+
+def _raster_case():
+    return W.c2_batching(n_paths=40, seed=W.SEED_BASE + 2, canvas=512)
+
+
+def _raster_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    b = _raster_case()
+    Wd, Ht = b.canvas
+    o = oracle.tessellate(b)
+    lb = shard.split_links(shard.link_rib_estimates(b), world)
+    off = o["link_rib_off"]
+    a, e = int(off[lb[rank]]), int(off[lb[rank + 1]])
+    rb = shard.raster_rows(Ht, world)
+    q_rib, q_tag, cnt = host_route(o["rib"][a:e], o["tag"][a:e], Wd, Ht, rb)
+    r_rib, r_tag = shard.exchange_quads(torch.from_numpy(q_rib), torch.from_numpy(q_tag),
+                                        torch.from_numpy(cnt))
+    y0, h = int(rb[rank]), int(rb[rank + 1] - rb[rank])
+    rows, cov = oracle_rows(r_rib.numpy(), r_tag.numpy().astype(np.uint32), Wd, Ht, b.n_path, y0, h)
+    cov_t = shard.merge_covered(torch.from_numpy(cov))
+    canvas = shard.gather_rows(torch.from_numpy(rows.astype(np.int32)), rb)
+    q.put((rank, canvas.numpy().astype(np.uint16), cov_t.numpy(), int(cnt.sum())))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_split_the_raster_by_rows():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_raster_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    parts = [q.get(timeout=300) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    b = _raster_case()
+    o = oracle.tessellate(b)
+    canvas, cov = oracle.raster(o["rib"], o["tag"], b.canvas[0], b.canvas[1], b.n_path)
+    for rank, c, cv, n in sorted(parts, key=lambda x: x[0]):
+        assert n > 0
+        assert np.array_equal(c, canvas)       # every rank holds the whole canvas
+        assert np.array_equal(cv, cov.astype(np.int64))
