@@ -45,7 +45,7 @@ int ps_ensure_raster(ps_context* ctx, int64_t n_tile, int64_t n_pair) {
     int64_t cap = n_tile + 64;
     if ((rc = grow((void**)&ctx->d_tile_count, sizeof(int32_t) * (cap + 1))) != PS_OK) return rc;
     if ((rc = grow((void**)&ctx->d_tile_off, sizeof(int32_t) * (cap + 1))) != PS_OK) return rc;
-    if ((rc = grow((void**)&ctx->d_tile_cursor, sizeof(int32_t) * (cap + 1))) != PS_OK) return rc;
+    if ((rc = grow((void**)&ctx->d_tile_cursor, 2 * sizeof(int32_t) * (cap + 1))) != PS_OK) return rc;
     if ((rc = grow((void**)&ctx->d_tile_list, sizeof(int32_t) * (cap + 1))) != PS_OK) return rc;
     ctx->raster_tile_cap = cap;
   }

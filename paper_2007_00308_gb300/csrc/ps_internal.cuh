@@ -85,7 +85,7 @@ struct ps_context {
   // raster workspace
   int32_t* d_tile_count;    // [n_tile + 1]
   int32_t* d_tile_off;      // [n_tile + 1]
-  int32_t* d_tile_cursor;   // [n_tile]
+  int32_t* d_tile_cursor;   // [2 (n_tile + 1)]: scatter cursors from the front, then from the back
   int32_t* d_tile_list;     // tiles with bin entries, then their count
   int64_t raster_tile_cap;
   uint32_t* d_bin;          // [pair_cap]

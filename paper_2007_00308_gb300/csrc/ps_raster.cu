@@ -153,11 +153,16 @@ __device__ __forceinline__ bool quad_meets_tile(const QuadFix& q, bool small, in
 // each lane tests one pair at a time; lanes of the warp that hit the same tile
 // are grouped: one atomic per group.
 // Per-quad words from the count pass for the scatter pass, {hits, box}.  hits:
-// 0 = no tile; bit 31 with the tile index below it = the quad's bounding box
-// lies in that one tile; HITS_RETEST = more than 31 candidate tiles (the
-// scatter pass re-reads, snaps and re-tests the quad); otherwise the hit mask
-// over the candidates, with box = the first candidate tile's index | (columns
-// - 1) << 26, so that the scatter pass reads no ribs for the quad.
+// 0 = no tile; bit 31 with the tall flag in bit 30 and the tile index below it
+// = the quad's bounding box lies in that one tile; HITS_RETEST = more than 31
+// candidate tiles (the scatter pass re-reads, snaps and re-tests the quad);
+// otherwise the hit mask over the candidates, with box = the first candidate
+// tile's index | (columns - 1) << 26 | tall << 31, so that the scatter pass
+// reads no ribs for the quad.
+// The scatter pass fills each tile's entries from the front with quads that
+// span at most TALL_ROWS pixel rows and from the back with taller ones, so
+// that the coverage kernel's 32-entry batches hold entries of like heights
+// (a warp's row-span loop runs as long as its tallest entry).
 constexpr uint32_t HITS_RETEST = 0xffffffffu;
 constexpr uint32_t HITS_DIRECT = 0x80000000u;
 constexpr int BIN_NT = 256;
@@ -167,8 +172,11 @@ struct BinQuad {
   int tx0, ty0, ntx, n;  // candidate tiles: ntx columns from (tx0, ty0), n in all
   int tbase;             // index of tile (tx0, ty0)
   uint32_t mask;         // pass 1: hit mask from pass 0; pass 0: hits found
-  int small;
+  int small;             // bit 0: under 64 px (int32 tests); bit 1: tall (more
+                         // than TALL_ROWS pixel rows); one word, so that the
+                         // record stays 15 words (an odd stride: no bank conflicts)
 };
+constexpr int TALL_ROWS = 6;
 
 template <int PASS>
 __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
@@ -179,7 +187,9 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
                                                 const int32_t* __restrict__ off,
                                                 int32_t* __restrict__ cursor,
                                                 uint32_t* __restrict__ bin, int64_t pair_cap,
-                                                uint2* __restrict__ hits, int32_t* status) {
+                                                uint2* __restrict__ hits,
+                                                int32_t* __restrict__ back,  // tall fill, from the end
+                                                int32_t* status) {
   __shared__ BinQuad s_q[BIN_NT];
   __shared__ int s_pre[BIN_NT / 32][33];
   int64_t R = *n_rib;
@@ -201,6 +211,7 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
     Q.mask = 0;
     Q.tbase = 0;
     Q.ntx = 1;
+    Q.small = 0;
     if (act) {
       QuadFix q;
       if (!snap_quad(__ldg(rib + r - 1), __ldg(rib + r), q)) {
@@ -226,7 +237,8 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
           Q.tbase = ty0 * tiles_x + tx0;
           Q.ntx = tx1 - tx0 + 1;
           Q.n = Q.ntx * (ty1 - ty0 + 1);
-          Q.small = mxx - mnx < (1 << 14) && mxy - mny < (1 << 14);
+          Q.small = (mxx - mnx < (1 << 14) && mxy - mny < (1 << 14) ? 1 : 0) |
+                    (py1 - py0 + 1 > TALL_ROWS ? 2 : 0);
           if (PASS == 1) {
             Q.mask = h;
             cnt = Q.n <= 31 ? __popc(h) : Q.n;
@@ -239,30 +251,38 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
     if (boxed1) {  // hit mask and candidate box from the count pass
       Q.mask = h;
       Q.tbase = (int)(hb.y & 0x3ffffffu);
-      Q.ntx = (int)(hb.y >> 26) + 1;
+      Q.ntx = (int)((hb.y >> 26) & 31u) + 1;
+      Q.small = (int)(hb.y >> 31) << 1;
       Q.n = 31;  // any count from 2 to 31: the mask gives the candidates
       cnt = __popc(h);
     }
     // a quad whose bounding box lies in one tile meets that tile: binned in one
     // direct round, outside the flattened (quad, candidate) loop
     int tdir = Q.n == 1 ? Q.ty0 * tiles_x + Q.tx0 : -1;
-    if (direct1) tdir = (int)(h & ~HITS_DIRECT);
+    if (direct1) {
+      tdir = (int)(h & 0x3fffffffu);
+      Q.small = (int)((h >> 30) & 1u) << 1;
+    }
     {
       if (Q.n == 1) {
         cnt = 0;
         if (PASS == 0) Q.mask = 1u;
       }
-      const unsigned peers = __match_any_sync(0xffffffffu, tdir);
+      const int tall = Q.small >> 1;
+      // pass 1 groups by tile and height class (the two fill from either end)
+      const unsigned peers =
+          __match_any_sync(0xffffffffu, tdir >= 0 ? (PASS == 0 ? tdir : 2 * tdir + tall) : -1);
       const int leader = __ffs(peers) - 1;
       if (tdir >= 0) {
         if (PASS == 0) {
           if (lane == leader) atomicAdd(count + tdir, __popc(peers));
         } else {
           int basepos = 0;
-          if (lane == leader) basepos = atomicAdd(cursor + tdir, __popc(peers));
+          if (lane == leader) basepos = atomicAdd((tall ? back : cursor) + tdir, __popc(peers));
           basepos = __shfl_sync(peers, basepos, leader);
-          const int64_t at = (int64_t)off[tdir] + basepos + __popc(peers & ((1u << lane) - 1u));
-          if (at < pair_cap && at < off[tdir + 1]) bin[at] = (uint32_t)r;
+          const int rk = basepos + __popc(peers & ((1u << lane) - 1u));
+          const int64_t at = tall ? (int64_t)off[tdir + 1] - 1 - rk : (int64_t)off[tdir] + rk;
+          if (at < pair_cap && at >= off[tdir] && at < off[tdir + 1]) bin[at] = (uint32_t)r;
           else ps_record_error(status, PS_ERR_CAPACITY);
         }
       }
@@ -280,7 +300,7 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
     __syncwarp();
     for (int it0 = 0; it0 < total; it0 += 32) {
       const int it = it0 + lane;
-      int t = -1, e = 0, i = 0;
+      int t = -1, e = 0, i = 0, tl = 0;
       if (it < total) {
         int lo = 0;  // last quad whose prefix is <= it
 #pragma unroll
@@ -301,14 +321,15 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
             q.x[v] = B.x[v];
             q.y[v] = B.y[v];
           }
-          hit = B.n == 1 || quad_meets_tile<PASS == 0>(q, B.small != 0, tx, ty, W, H);
+          hit = B.n == 1 || quad_meets_tile<PASS == 0>(q, (B.small & 1) != 0, tx, ty, W, H);
         }
+        tl = B.small >> 1;
         if (hit) {
           t = B.tbase + (i / B.ntx) * tiles_x + i % B.ntx;
           if (PASS == 0 && i < 31) atomicOr(&wq[e].mask, 1u << i);
         }
       }
-      unsigned peers = __match_any_sync(0xffffffffu, t);
+      unsigned peers = __match_any_sync(0xffffffffu, t >= 0 ? (PASS == 0 ? t : 2 * t + tl) : -1);
       int leader = __ffs(peers) - 1;
       int cntg = __popc(peers);
       if (t >= 0) {
@@ -316,11 +337,12 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
           if (lane == leader) atomicAdd(count + t, cntg);
         } else {
           int basepos = 0;
-          if (lane == leader) basepos = atomicAdd(cursor + t, cntg);
+          if (lane == leader) basepos = atomicAdd((tl ? back : cursor) + t, cntg);
           basepos = __shfl_sync(peers, basepos, leader);
           int pos = basepos + __popc(peers & ((1u << lane) - 1u));
-          int64_t at = (int64_t)off[t] + pos;
-          if (at < pair_cap && at < off[t + 1]) bin[at] = (uint32_t)(base + wid * 32 + e);
+          int64_t at = tl ? (int64_t)off[t + 1] - 1 - pos : (int64_t)off[t] + pos;
+          if (at < pair_cap && at >= off[t] && at < off[t + 1])
+            bin[at] = (uint32_t)(base + wid * 32 + e);
           else ps_record_error(status, PS_ERR_CAPACITY);
         }
       }
@@ -328,14 +350,16 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
     __syncwarp();
     if (PASS == 0 && in)
       hits[r] = make_uint2(!act ? 0u
-                           : Q.n == 1 ? HITS_DIRECT | (uint32_t)tdir
+                           : Q.n == 1 ? HITS_DIRECT | (uint32_t)(Q.small >> 1) << 30 | (uint32_t)tdir
                            : Q.n <= 31 ? Q.mask : HITS_RETEST,
-                           (uint32_t)Q.tbase | (uint32_t)(Q.ntx - 1) << 26);
+                           (uint32_t)Q.tbase | (uint32_t)(Q.ntx - 1) << 26 |
+                               (uint32_t)(Q.small >> 1) << 31);
     __syncwarp();
   }
 }
 
-// Exclusive scan of tile counts, the cursors reset, and the list of tiles with
+// Exclusive scan of tile counts, the cursors reset (front cursors at
+// cursor[0 .. n_tile), back cursors at cursor[n_tile + 1 ..)), and the list of tiles with
 // entries in order: list[0 .. m) and m = list[n_tile].  CTA b takes tiles
 // [4096 b, 4096 (b+1)), 16 per thread; the sum and the count of non-empty tiles
 // are scanned together as one int64 (the count in bits 38 and up) with a
@@ -396,6 +420,7 @@ __global__ void __launch_bounds__(TS_NT) k_tile_scan(const int32_t* __restrict__
       if (sum > 0x7fffffffLL) ps_record_error(status, PS_ERR_CAPACITY);
       off[idx] = (int32_t)(sum > 0x7fffffffLL ? 0x7fffffff : sum);
       cursor[idx] = 0;
+      cursor[n_tile + 1 + idx] = 0;  // the tall entries' cursor (filled from the end)
       if (c[i] > 0) list[run >> TS_SHIFT] = (int32_t)idx;
       run += (long long)c[i] + ((long long)(c[i] > 0) << TS_SHIFT);
       if (idx == n_tile - 1) {
@@ -557,7 +582,7 @@ constexpr uint32_t EL_TRI1_NEG = 0xCu | 0xBu << 4 | 0x2u << 8;   // 0->3 3->2 2-
 // A (8 - x) + B (8 - y) is formed in int64 (|8 - x| < 2^16 + 4104, as the quad
 // meets the tile) and clamped into int32.  One code path serves all classes.
 __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax, int tw, int th,
-                                           EntrySetup& E) {
+                                           EntrySetup& E, int* __restrict__ sc) {
   const int X0 = q.x[0], Y0 = q.y[0], X1 = q.x[1], Y1 = q.y[1];  // N0 P0
   const int X2 = q.x[3], Y2 = q.y[3], X3 = q.x[2], Y3 = q.y[2];  // P1 N1
   auto cross = [](int ax, int ay, int bx, int by) {
@@ -601,16 +626,16 @@ __device__ __forceinline__ int setup_small(const QuadFix& q, int ymin, int ymax,
   float kq[6], ul[6], uh[6];
   float k0 = 0.f, u0 = 0.f, eps0 = 0.f;
   bool apos0 = false, anz0 = false;
-  // The polygon's vertices, parked in the entry's (not yet written) row
-  // prefixes so that each edge reads its end points by index instead of
-  // through chains of selects.
-  int* const vxs = reinterpret_cast<int*>(E.rowpre);      // 4 x, then 4 y (32 bytes)
-  reinterpret_cast<int4*>(E.rowpre)[0] = make_int4(X0, X1, X2, X3);
-  reinterpret_cast<int4*>(E.rowpre)[1] = make_int4(Y0, Y1, Y2, Y3);
+  // The polygon's vertices, parked in the lane's column of a warp scratch
+  // (sc: one int per lane per row, so that the lanes' accesses fall in
+  // distinct banks) so that each edge reads its end points by index instead
+  // of through chains of selects.
+  sc[0] = X0; sc[32] = X1; sc[64] = X2; sc[96] = X3;     // x of vertex v at sc[32 v],
+  sc[128] = Y0; sc[160] = Y1; sc[192] = Y2; sc[224] = Y3;  // y at sc[32 (4 + v)]
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     int ia = (el >> (4 * i)) & 3, ib = (el >> (4 * i + 2)) & 3;
-    int xa = vxs[ia], ya = vxs[4 + ia], xb = vxs[ib], yb = vxs[4 + ib];
+    int xa = sc[32 * ia], ya = sc[32 * (4 + ia)], xb = sc[32 * ib], yb = sc[32 * (4 + ib)];
     int A = ya - yb, B = xb - xa, S = abs(A) + abs(B);
     long long c64 = (long long)A * (8 - xa) + (long long)B * (8 - ya);
     int lim = 4080 * S + 1;
@@ -866,7 +891,8 @@ __device__ __forceinline__ uint32_t exact_mask_general(const EntrySetup& E, int 
 // returns the number of pixels in its spans (0: nothing to draw).
 template <bool EXACT>
 __device__ __forceinline__ int setup_edges(const float4 ra, const float4 rb, int slot, int ox,
-                                           int oy, int tw, int th, EntrySetup& E) {
+                                           int oy, int tw, int th, EntrySetup& E,
+                                           int* __restrict__ sc) {
   E.slot = (uint16_t)slot;
   E.valid = 0;
   E.row0 = 0;
@@ -883,7 +909,7 @@ __device__ __forceinline__ int setup_edges(const float4 ra, const float4 rb, int
     int mny = min(min(q.y[0], q.y[1]), min(q.y[2], q.y[3]));
     int mxy = max(max(q.y[0], q.y[1]), max(q.y[2], q.y[3]));
     if (mxx - mnx < (1 << 16) && mxy - mny < (1 << 16)) {
-      int tot = setup_small(q, mny, mxy, tw, th, E);
+      int tot = setup_small(q, mny, mxy, tw, th, E, sc);
       if (EXACT && tot > 0) store_exact(q, E);
       return tot;
     }
@@ -1219,7 +1245,8 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
   __shared__ uint32_t s_canvas[MASK_WORDS];
   __shared__ uint16_t s_rowmask[EXACT ? 17 * 17 : 1];
   // each lane's next bin entry (its two ribs and tag), copied in while the
-  // current batch's pixels are processed
+  // current batch's pixels are processed; between reading a batch's copies and
+  // issuing the next ones, a warp's 256 floats are its set-up scratch
   __shared__ __align__(16) float4 s_pre_rib[CV_WARPS][2][32];
   __shared__ uint32_t s_pre_tag[CV_WARPS][32];
 
@@ -1347,10 +1374,12 @@ __global__ void __launch_bounds__(CV_NT, 2) k_coverage(
           else if (slot >= HKEYS) ps_record_error(status, PS_ERR_TIMEOUT);
         }
         slot = __shfl_sync(0xffffffffu, slot, leader);
+        __syncwarp();  // the batch's copies are read: their buffer is the set-up's scratch
         unsigned long long packed = 0;
         if (valid && slot >= slot_lo && slot < slot_lo + SLOTS && slot < HKEYS) {
           EntrySetup& E = my[lane];
-          int tot = setup_edges<EXACT>(ra, rb, slot - slot_lo, ox, oy + y0, tw, th, E);
+          int tot = setup_edges<EXACT>(ra, rb, slot - slot_lo, ox, oy + y0, tw, th, E,
+                                        reinterpret_cast<int*>(&s_pre_rib[wid][0][0]) + lane);
           if (tot > 0) {
             st_rows += E.nrow;
             // pixel items per class in 21-bit fields (at most 32 x 256 each):
@@ -1583,7 +1612,7 @@ static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
   { ProfScope ps_(ctx, PK_BIN_COUNT, st);
   k_bin<0><<<grid_bin, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, y0, tiles_x,
                                       ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor,
-                                      ctx->d_bin, ctx->pair_cap, reinterpret_cast<uint2*>(ctx->d_quad_hits),
+                                      ctx->d_bin, ctx->pair_cap, reinterpret_cast<uint2*>(ctx->d_quad_hits), ctx->d_tile_cursor + n_tile + 1,
                                       ctx->d_status); }
   { ProfScope ps_(ctx, PK_TILE_SCAN, st);
   const int ts_grid = (int)((n_tile + TS_TILE - 1) / TS_TILE);
@@ -1594,7 +1623,7 @@ static int rasterize(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
   { ProfScope ps_(ctx, PK_BIN_SCATTER, st);
   k_bin<1><<<grid_bin1, BIN_NT, 0, st>>>(rib, d_tag, d_n_rib, capacity, width, height, y0, tiles_x,
                                       ctx->d_tile_count, ctx->d_tile_off, ctx->d_tile_cursor,
-                                      ctx->d_bin, ctx->pair_cap, reinterpret_cast<uint2*>(ctx->d_quad_hits),
+                                      ctx->d_bin, ctx->pair_cap, reinterpret_cast<uint2*>(ctx->d_quad_hits), ctx->d_tile_cursor + n_tile + 1,
                                       ctx->d_status); }
   { ProfScope ps_(ctx, PK_COVERAGE, st);
 #define PS_COV_ARGS                                                                              \
