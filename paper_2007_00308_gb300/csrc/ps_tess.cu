@@ -305,10 +305,12 @@ __device__ __noinline__ DF solve_t_quad_df(const Seg& g, DF sn, DF cs, DF pa, DF
 // double-float normal (sn, cs), and a second step where the first one's
 // quadratic term, c dt^2 / f', could exceed 1e-12.  A near double root (the
 // FP32 discriminant below 1e-3 of its scale), or a step that moved t by more
-// than 1e-4, takes the double-float quadratic solve instead.  Out of line: one
-// copy serves the emitter and the link set-up (emitter 1.98 -> 1.85 ms on c2,
-// link set-up +0.08 ms).
-__device__ __noinline__ DF solve_t_mx(const Seg& g, DF sn, DF cs, DF pa, DF pb) {
+// than 1e-4, takes the double-float quadratic solve instead.  The emitter calls
+// it out of line (solve_t_mx: one copy, fewer instruction-fetch stalls, 1.98 ->
+// 1.85 ms on c2); the link set-up, which needs it only for splits at pi, keeps
+// an inline copy (calling out of line there cost it 0.08 ms).
+template <int COPY>  // COPY only tells the two instances apart
+__device__ __forceinline__ DF solve_t_mx_impl(const Seg& g, DF sn, DF cs, DF pa, DF pb) {
   if (g.type == PS_LINE) return pa;
   float t0, a, b, c;
   const bool root = solve_t32<true>(g, sn.hi, cs.hi, pa.hi, pb.hi, t0, a, b, c);
@@ -334,6 +336,9 @@ __device__ __noinline__ DF solve_t_mx(const Seg& g, DF sn, DF cs, DF pa, DF pb) 
     }
   }
   return solve_t_quad_df(g, sn, cs, pa, pb);
+}
+__device__ __noinline__ DF solve_t_mx(const Seg& g, DF sn, DF cs, DF pa, DF pb) {
+  return solve_t_mx_impl<0>(g, sn, cs, pa, pb);
 }
 
 // ---------------------------------------------------------------------------
@@ -912,7 +917,7 @@ __device__ int seg_intervals_mx(const Seg& g, Step S, LinkRec& L) {
       const DF psi_s = df_add(Psi[k], half);
       DF sn, cs;
       sincos_ool(psi_s, sn, cs);
-      const DF ps_ = solve_t_mx(g, sn, cs, p[k], p[k + 1]);
+      const DF ps_ = solve_t_mx_impl<1>(g, sn, cs, p[k], p[k + 1]);
       const int Dh = steps_mx<PX>(df_abs(half), S, &g);
       const DF st = df_div_f(half, (float)Dh);
       if (M + 2 > 6) return -1;
