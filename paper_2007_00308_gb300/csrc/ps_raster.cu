@@ -321,7 +321,12 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
             q.x[v] = B.x[v];
             q.y[v] = B.y[v];
           }
-          hit = B.n == 1 || quad_meets_tile<PASS == 0>(q, (B.small & 1) != 0, tx, ty, W, H);
+          // a quad whose bounding box spans two tiles crosses their common
+          // edge, so it almost always meets both: it is entered in both
+          // untested (an entry without samples costs the coverage kernel only
+          // its set-up; measured: count pass -0.06 ms, coverage unchanged;
+          // boxes of up to four tiles cost coverage 0.26 ms)
+          hit = B.n <= 2 || quad_meets_tile<PASS == 0>(q, (B.small & 1) != 0, tx, ty, W, H);
         }
         tl = B.small >> 1;
         if (hit) {
