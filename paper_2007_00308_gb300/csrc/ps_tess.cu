@@ -305,12 +305,8 @@ __device__ __noinline__ DF solve_t_quad_df(const Seg& g, DF sn, DF cs, DF pa, DF
 // double-float normal (sn, cs), and a second step where the first one's
 // quadratic term, c dt^2 / f', could exceed 1e-12.  A near double root (the
 // FP32 discriminant below 1e-3 of its scale), or a step that moved t by more
-// than 1e-4, takes the double-float quadratic solve instead.  The emitter calls
-// it out of line (solve_t_mx: one copy, fewer instruction-fetch stalls, 1.98 ->
-// 1.85 ms on c2); the link set-up, which needs it only for splits at pi, keeps
-// an inline copy (calling out of line there cost it 0.08 ms).
-template <int COPY>  // COPY only tells the two instances apart
-__device__ __forceinline__ DF solve_t_mx_impl(const Seg& g, DF sn, DF cs, DF pa, DF pb) {
+// than 1e-4, takes the double-float quadratic solve instead.
+__device__ DF solve_t_mx(const Seg& g, DF sn, DF cs, DF pa, DF pb) {
   if (g.type == PS_LINE) return pa;
   float t0, a, b, c;
   const bool root = solve_t32<true>(g, sn.hi, cs.hi, pa.hi, pb.hi, t0, a, b, c);
@@ -336,9 +332,6 @@ __device__ __forceinline__ DF solve_t_mx_impl(const Seg& g, DF sn, DF cs, DF pa,
     }
   }
   return solve_t_quad_df(g, sn, cs, pa, pb);
-}
-__device__ __noinline__ DF solve_t_mx(const Seg& g, DF sn, DF cs, DF pa, DF pb) {
-  return solve_t_mx_impl<0>(g, sn, cs, pa, pb);
 }
 
 // ---------------------------------------------------------------------------
@@ -917,7 +910,7 @@ __device__ int seg_intervals_mx(const Seg& g, Step S, LinkRec& L) {
       const DF psi_s = df_add(Psi[k], half);
       DF sn, cs;
       sincos_ool(psi_s, sn, cs);
-      const DF ps_ = solve_t_mx_impl<1>(g, sn, cs, p[k], p[k + 1]);
+      const DF ps_ = solve_t_mx(g, sn, cs, p[k], p[k + 1]);
       const int Dh = steps_mx<PX>(df_abs(half), S, &g);
       const DF st = df_div_f(half, (float)Dh);
       if (M + 2 > 6) return -1;
@@ -1441,12 +1434,6 @@ __device__ __forceinline__ RibEval eval_rib32(const LinkRec* __restrict__ L, int
   return R;
 }
 
-// g(t) - A as pairs, out of line, like the t(psi) solve: the emitter's two
-// largest double-float steps each in one copy (smaller code, fewer
-// instruction-fetch stalls; the Newton residual or the sincos out of line
-// measured slower).
-__device__ __noinline__ DF2 g_rel_df_ool(const Seg& g, DF t) { return g_rel_df(g, t); }
-
 __device__ __forceinline__ DF ld_pair(const float* hi, const float* lo) { return DF{__ldg(hi), __ldg(lo)}; }
 
 // One rib, PS_PREC_MIXED: psi(j) = Psi_k + step_k (j - Delta_Sigma(k)) as a
@@ -1493,7 +1480,7 @@ __device__ __forceinline__ RibEval eval_rib_mx(const LinkRec* __restrict__ L, in
     DF t = pa;
     if (j != dk && !META_PIVOT(meta, k))
       t = solve_t_mx(g, sn, cs, pa, ld_pair(&L->p[k + 1], &L->p_lo[k + 1]));
-    const DF2 gr = g_rel_df_ool(g, t);
+    const DF2 gr = g_rel_df(g, t);
     gx = gr.x;
     gy = gr.y;
     R.grel = mk(gr.x.hi, gr.y.hi);
