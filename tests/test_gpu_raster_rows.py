@@ -144,3 +144,53 @@ def test_route_arguments_are_checked():
         with pytest.raises(ps.PolarStrokeError):
             ps.ps_rasterize_coverage_rows(ctx, out.rib, out.tag, out.n_rib, out.capacity, b.n_path,
                                           Wd, y0, 16, cw, cv)
+
+
+def test_route_edge_cases():
+    """An empty window receives nothing; a quad reaching every window goes to all
+    of them; quads outside the canvas go nowhere; the counting call and the
+    writing call agree."""
+    import torch
+    import paper_2007_00308_gb300 as ps
+    # one long vertical stroke through the whole canvas, one stroke outside it
+    b = W.single([W.LINE, W.LINE], [[[100, 5], [100, 5], [100, 250], [100, 250]],
+                                    [[100, 250], [100, 250], [400, 400], [400, 400]]],
+                 width=6, join=W.JOIN_BEVEL, cap=W.CAP_BUTT, dtheta_deg=2.0, canvas=(256, 256))
+    ctx = ps.Context()
+    db = ps.DeviceBatch(b)
+    out = ps.tessellate(ctx, db, ps.PS_PREC_MIXED, arclength=False)
+    Wd, Ht = b.canvas
+    bounds = np.array([0, 0, 64, 128, 128, Ht], np.int32)  # windows 0 and 3 are empty
+    qr, qt, cnt = shard.route(ps, ctx, out.rib, out.tag, out.n_rib, out.capacity, Wd, Ht, bounds)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    cnt = cnt.cpu().numpy()
+    assert cnt[0] == 0 and cnt[3] == 0
+    assert cnt[1] > 0 and cnt[2] > 0 and cnt[4] > 0
+    # every routed pair is one quad: link start on the first rib, not on the second
+    t = qt.cpu().numpy().view(np.uint32)
+    assert np.all(t[:, 0] & 1) and not np.any(t[:, 1] & 1)
+    # the windows give the whole canvas
+    canvas = torch.zeros((Ht, Wd), dtype=torch.int16, device="cuda")
+    cov = torch.zeros(b.n_path, dtype=torch.int64, device="cuda")
+    ps.ps_rasterize_coverage(ctx, out.rib, out.tag, out.n_rib, out.capacity, b.n_path, Wd, Ht,
+                             canvas, cov)
+    o = np.concatenate([[0], np.cumsum(cnt)])
+    got = torch.zeros_like(canvas)
+    total = torch.zeros_like(cov)
+    for d in range(len(bounds) - 1):
+        y0, h = int(bounds[d]), int(bounds[d + 1] - bounds[d])
+        if h == 0:
+            continue
+        n = int(cnt[d])
+        rib = qr[o[d]:o[d + 1]].reshape(2 * n, 4).contiguous()
+        tag = qt[o[d]:o[d + 1]].reshape(2 * n).contiguous()
+        n_rib = torch.tensor([2 * n], dtype=torch.int64, device="cuda")
+        cw = torch.zeros((h, Wd), dtype=torch.int16, device="cuda")
+        cv = torch.zeros_like(cov)
+        ps.ps_rasterize_coverage_rows(ctx, rib, tag, n_rib, 2 * n, b.n_path, Wd, y0, h, cw, cv)
+        got[y0:y0 + h] = cw
+        total += cv
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    assert torch.equal(got, canvas) and torch.equal(total, cov)
