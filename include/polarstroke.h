@@ -452,7 +452,7 @@ int ps_svg_arc_to_conics(float x0, float y0, float rx, float ry, float phi_deg, 
 /* Launch parameters of a context, for autotuning.  They change how work is
  * split over threads, never what is computed.
  *   PS_TUNE_EMIT_SLABS   ribs per warp task in the rib kernel, in slabs of 32:
- *                        4, 8, 16 (default) or 32
+ *                        4, 8, 16, 32 (default) or 64
  *   PS_TUNE_SETUP_LINKS  links per thread in the link-setup kernel: 1, 2
  *                        (default) or 4
  *   PS_TUNE_BIN_BLOCKS   CTAs per SM of the two binning passes: 0 (default: as

@@ -31,7 +31,7 @@ EXPORTS = ["ps_create", "ps_destroy", "ps_reserve", "ps_max_ribs", "ps_get_statu
            "ps_rasterize_coverage_rows", "ps_route_quads"]
 PS_PROF_SLOTS = 10
 PS_TUNE_EMIT_SLABS, PS_TUNE_SETUP_LINKS, PS_TUNE_BIN_BLOCKS = 0, 1, 2
-TUNE_CANDIDATES = {PS_TUNE_EMIT_SLABS: (4, 8, 16, 32), PS_TUNE_SETUP_LINKS: (1, 2, 4),
+TUNE_CANDIDATES = {PS_TUNE_EMIT_SLABS: (4, 8, 16, 32, 64), PS_TUNE_SETUP_LINKS: (1, 2, 4),
                    PS_TUNE_BIN_BLOCKS: (0, 2, 4, 8)}
 TUNE_NAMES = {PS_TUNE_EMIT_SLABS: "emit_slabs", PS_TUNE_SETUP_LINKS: "setup_links",
               PS_TUNE_BIN_BLOCKS: "bin_blocks"}

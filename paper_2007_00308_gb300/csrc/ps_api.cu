@@ -92,7 +92,7 @@ extern "C" int ps_create(ps_context** out) {
   }
   cudaMemset(ctx->d_status, 0, 64);
   cudaMemset(ctx->d_counters, 0, sizeof(int32_t) * 16);
-  ctx->tune[PS_TUNE_EMIT_SLABS] = 16;
+  ctx->tune[PS_TUNE_EMIT_SLABS] = 32;
   ctx->tune[PS_TUNE_SETUP_LINKS] = 2;
   ctx->tune[PS_TUNE_BIN_BLOCKS] = 0;
   ctx->pixel_tol = 0.f;
@@ -104,7 +104,8 @@ extern "C" int ps_set_tuning(ps_context* ctx, int key, int value) {
   if (!ctx) return PS_ERR_INVALID;
   switch (key) {
     case PS_TUNE_EMIT_SLABS:
-      if (value != 4 && value != 8 && value != 16 && value != 32) return PS_ERR_INVALID;
+      if (value != 4 && value != 8 && value != 16 && value != 32 && value != 64)
+        return PS_ERR_INVALID;
       break;
     case PS_TUNE_SETUP_LINKS:
       if (value != 1 && value != 2 && value != 4) return PS_ERR_INVALID;

@@ -1362,7 +1362,7 @@ __global__ void __launch_bounds__(SETUP_NT, 2) k_link_setup(
 // lane of the previous slab, or for the chunk's first rib a re-evaluation) are
 // written.  No block-wide synchronisation.
 constexpr int EMIT_NT = 256;
-constexpr int EMIT_K = 16;  // slabs of 32 ribs per chunk by default (tunable: 4, 8, 16, 32)
+constexpr int EMIT_K = 32;  // slabs of 32 ribs per chunk by default (tunable: 4, 8, 16, 32, 64)
 
 struct RibEval {
   float4 v;      // N.x N.y P.x P.y

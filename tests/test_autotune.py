@@ -14,7 +14,7 @@ class FakeCtx:
     """Stands in for ps.Context: the tunables only."""
 
     def __init__(self):
-        self.t = {ps.PS_TUNE_EMIT_SLABS: 16, ps.PS_TUNE_SETUP_LINKS: 2, ps.PS_TUNE_BIN_BLOCKS: 0}
+        self.t = {ps.PS_TUNE_EMIT_SLABS: 32, ps.PS_TUNE_SETUP_LINKS: 2, ps.PS_TUNE_BIN_BLOCKS: 0}
         self.reserved = []
 
     def set_tuning(self, k, v):
