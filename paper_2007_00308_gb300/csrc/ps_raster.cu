@@ -160,9 +160,10 @@ __device__ __forceinline__ bool quad_meets_tile(const QuadFix& q, bool small, in
 // tile's index | (columns - 1) << 26 | tall << 31, so that the scatter pass
 // reads no ribs for the quad.
 // The scatter pass fills each tile's entries from the front with quads that
-// span at most TALL_ROWS pixel rows and from the back with taller ones, so
-// that the coverage kernel's 32-entry batches hold entries of like heights
-// (a warp's row-span loop runs as long as its tallest entry).
+// span more than TALL_ROWS pixel rows and from the back with shorter ones, so
+// that the coverage kernel's 32-entry batches hold entries of like heights (a
+// warp's row-span loop runs as long as its tallest entry), and a tile's last
+// batches, where its warps wait on each other, are the cheap ones.
 constexpr uint32_t HITS_RETEST = 0xffffffffu;
 constexpr uint32_t HITS_DIRECT = 0x80000000u;
 constexpr int BIN_NT = 256;
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
                                                 int32_t* __restrict__ cursor,
                                                 uint32_t* __restrict__ bin, int64_t pair_cap,
                                                 uint2* __restrict__ hits,
-                                                int32_t* __restrict__ back,  // tall fill, from the end
+                                                int32_t* __restrict__ back,  // short fill, from the end
                                                 int32_t* status) {
   __shared__ BinQuad s_q[BIN_NT];
   __shared__ int s_pre[BIN_NT / 32][33];
@@ -278,10 +279,10 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
           if (lane == leader) atomicAdd(count + tdir, __popc(peers));
         } else {
           int basepos = 0;
-          if (lane == leader) basepos = atomicAdd((tall ? back : cursor) + tdir, __popc(peers));
+          if (lane == leader) basepos = atomicAdd((tall ? cursor : back) + tdir, __popc(peers));
           basepos = __shfl_sync(peers, basepos, leader);
           const int rk = basepos + __popc(peers & ((1u << lane) - 1u));
-          const int64_t at = tall ? (int64_t)off[tdir + 1] - 1 - rk : (int64_t)off[tdir] + rk;
+          const int64_t at = tall ? (int64_t)off[tdir] + rk : (int64_t)off[tdir + 1] - 1 - rk;
           if (at < pair_cap && at >= off[tdir] && at < off[tdir + 1]) bin[at] = (uint32_t)r;
           else ps_record_error(status, PS_ERR_CAPACITY);
         }
@@ -342,10 +343,10 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
           if (lane == leader) atomicAdd(count + t, cntg);
         } else {
           int basepos = 0;
-          if (lane == leader) basepos = atomicAdd((tl ? back : cursor) + t, cntg);
+          if (lane == leader) basepos = atomicAdd((tl ? cursor : back) + t, cntg);
           basepos = __shfl_sync(peers, basepos, leader);
           int pos = basepos + __popc(peers & ((1u << lane) - 1u));
-          int64_t at = tl ? (int64_t)off[t + 1] - 1 - pos : (int64_t)off[t] + pos;
+          int64_t at = tl ? (int64_t)off[t] + pos : (int64_t)off[t + 1] - 1 - pos;
           if (at < pair_cap && at >= off[t] && at < off[t + 1])
             bin[at] = (uint32_t)(base + wid * 32 + e);
           else ps_record_error(status, PS_ERR_CAPACITY);
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(TS_NT) k_tile_scan(const int32_t* __restrict__
       if (sum > 0x7fffffffLL) ps_record_error(status, PS_ERR_CAPACITY);
       off[idx] = (int32_t)(sum > 0x7fffffffLL ? 0x7fffffff : sum);
       cursor[idx] = 0;
-      cursor[n_tile + 1 + idx] = 0;  // the tall entries' cursor (filled from the end)
+      cursor[n_tile + 1 + idx] = 0;  // the short entries' cursor (filled from the end)
       if (c[i] > 0) list[run >> TS_SHIFT] = (int32_t)idx;
       run += (long long)c[i] + ((long long)(c[i] > 0) << TS_SHIFT);
       if (idx == n_tile - 1) {
