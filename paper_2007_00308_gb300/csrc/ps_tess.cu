@@ -1646,9 +1646,10 @@ __global__ void k_link_path(const int32_t* __restrict__ seg_off, int n_path, int
 
 // ---------------------------------------------------------------------------
 // K3: segmented inclusive scan of per-rib chords into cumulative arc length
-// (Eq. 18), restarting at every path's first rib: the standalone arc length of
-// a given rib stream (ps_arclength_scan) and the adjoint's suffix sums; the
-// tessellation itself computes s inside the emitter.
+// (Eq. 18), restarting at every path's first rib.  The tessellation runs it in
+// place on the chords the emitter wrote into s; it is also the standalone arc
+// length of a given rib stream (ps_arclength_scan) and the adjoint's suffix
+// sums.
 constexpr int SCAN_NT = 256;
 constexpr int SCAN_IPT = 16;
 constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
