@@ -1656,7 +1656,7 @@ constexpr int SCAN_TILE = SCAN_NT * SCAN_IPT;
 
 // Segmented (by path) inclusive scan of per-rib chords into s (Eq. 18), in
 // place allowed (chord_in == s_out).  Persistent CTAs claim tiles of 4,096 ribs
-// in order; thread k of a tile owns ribs 16k..16k+15 and, with VEC (all three
+// in order (by ticket); thread k of a tile owns ribs 16k..16k+15 and, with VEC (all three
 // arrays 16-byte aligned), moves them with 128-bit loads and stores.  Within a
 // tile sums are FP32 (relative error ~1e-6 of s); the carry between tiles,
 // which runs over a whole path, is a double-float pair from a warp-wide
@@ -1674,11 +1674,17 @@ __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
   int64_t R = *n_rib;
   if (R > capacity) R = capacity;
   const int64_t n_tiles = (R + SCAN_TILE - 1) / SCAN_TILE;
+  // tiles are claimed by ticket; a tile's successor ticket is claimed as soon as
+  // its look-back is done, so that the atomic's latency hides behind the
+  // tile's stores (claiming earlier would hold back tiles that later tiles'
+  // look-backs wait on)
+  __shared__ int64_t s_next;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&counters[1], 1);
+  __syncthreads();
   for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&counters[1], 1);
-    __syncthreads();
+    // every thread reads s_tile before the barriers below, and thread 0
+    // rewrites it only after them
     const int64_t tile = s_tile;
-    __syncthreads();
     if (tile >= n_tiles) return;
     const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_IPT;
     const bool full = base + SCAN_IPT <= R;
@@ -1750,6 +1756,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
       if (lane == 0) {
         s_carry[0] = carry.hi;
         s_carry[1] = carry.lo;
+        s_next = atomicAdd(&counters[1], 1);
       }
     }
     __syncthreads();
@@ -1787,6 +1794,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_arclen_scan(
       for (int i = 0; i < SCAN_IPT; ++i)
         if (base + i < R) s_out[base + i] = c[i];
     }
+    if (threadIdx.x == 0) s_tile = s_next;
     __syncthreads();
   }
 }
