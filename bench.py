@@ -392,9 +392,9 @@ def alu_peak_tests(sm_mhz, ops):
 
 # DRAM traffic of one k_coverage launch per bin entry, from an ncu capture of
 # the first 1,000 paths of the workload (dram__bytes_read.sum + write.sum =
-# 123.8 MB over 8,357,160 bin entries); scaled to the launch by its bin
+# 124.4 MB over 8,357,160 bin entries); scaled to the launch by its bin
 # entries.
-COVERAGE_TRAFFIC_PER_PAIR = (117.482240e6 + 6.290688e6) / 8357160
+COVERAGE_TRAFFIC_PER_PAIR = (117.854208e6 + 6.578688e6) / 8357160
 
 
 AUTOTUNE = True

@@ -1167,7 +1167,12 @@ __device__ __forceinline__ void row_span_fast(const EntrySetup& E, int ly, int t
   }
 }
 
-__device__ __forceinline__ uint32_t tri_or_quad_mask(const EntrySetup& E, int lx, int ly) {
+// The general form's mask (quads of 256 px or more: int64 or int32 edge
+// values, up to six edges), out of line: it is rare, and inlined into the item
+// loop it slowed the fast forms (12.25 ms against 12.02 out of line on the
+// bench workload; moving the general form's set-up out of line as well cost
+// more than it saved).
+__device__ __noinline__ uint32_t tri_or_quad_mask(const EntrySetup& E, int lx, int ly) {
   int cx = lx * 256, cy = ly * 256;
   bool big = (E.valid & 4) != 0;
   if (E.valid & 16) {  // int32 path
