@@ -257,12 +257,35 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
       Q.n = 31;  // any count from 2 to 31: the mask gives the candidates
       cnt = __popc(h);
     }
-    // a quad whose bounding box lies in one tile meets that tile: binned in one
-    // direct round, outside the flattened (quad, candidate) loop
+    // A quad whose bounding box lies in one tile meets that tile.  One whose box
+    // spans two tiles crosses their common edge, so it almost always meets both:
+    // it is entered in both untested (an entry without samples costs the
+    // coverage kernel only its set-up; measured: count pass -0.06 ms, coverage
+    // unchanged; boxes of up to four tiles cost coverage 0.26 ms).  Such
+    // quads, and in pass 1 every quad the count pass found in at most two tiles,
+    // are binned in up to two direct rounds, outside the flattened (quad,
+    // candidate) loop.
     int tdir = Q.n == 1 ? Q.ty0 * tiles_x + Q.tx0 : -1;
+    int tdir2 = -1;
+    if (PASS == 0 && Q.n == 2) {
+      tdir = Q.tbase;
+      tdir2 = Q.tbase + (Q.ntx == 2 ? 1 : tiles_x);
+      cnt = 0;
+      Q.mask = 3u;
+    }
     if (direct1) {
       tdir = (int)(h & 0x3fffffffu);
       Q.small = (int)((h >> 30) & 1u) << 1;
+    }
+    if (boxed1 && __popc(h) <= 2) {
+      const int i0 = __ffs(h) - 1;
+      tdir = Q.tbase + (i0 / Q.ntx) * tiles_x + i0 % Q.ntx;
+      const uint32_t h2 = h & (h - 1u);
+      if (h2) {
+        const int i1 = __ffs(h2) - 1;
+        tdir2 = Q.tbase + (i1 / Q.ntx) * tiles_x + i1 % Q.ntx;
+      }
+      cnt = 0;
     }
     {
       if (Q.n == 1) {
@@ -270,23 +293,27 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
         if (PASS == 0) Q.mask = 1u;
       }
       const int tall = Q.small >> 1;
-      // pass 1 groups by tile and height class (the two fill from either end)
-      const unsigned peers =
-          __match_any_sync(0xffffffffu, tdir >= 0 ? (PASS == 0 ? tdir : 2 * tdir + tall) : -1);
-      const int leader = __ffs(peers) - 1;
-      if (tdir >= 0) {
-        if (PASS == 0) {
-          if (lane == leader) atomicAdd(count + tdir, __popc(peers));
-        } else {
-          int basepos = 0;
-          if (lane == leader) basepos = atomicAdd((tall ? cursor : back) + tdir, __popc(peers));
-          basepos = __shfl_sync(peers, basepos, leader);
-          const int rk = basepos + __popc(peers & ((1u << lane) - 1u));
-          const int64_t at = tall ? (int64_t)off[tdir] + rk : (int64_t)off[tdir + 1] - 1 - rk;
-          if (at < pair_cap && at >= off[tdir] && at < off[tdir + 1]) bin[at] = (uint32_t)r;
-          else ps_record_error(status, PS_ERR_CAPACITY);
+      auto direct = [&](int td) {
+        // pass 1 groups by tile and height class (the two fill from either end)
+        const unsigned peers =
+            __match_any_sync(0xffffffffu, td >= 0 ? (PASS == 0 ? td : 2 * td + tall) : -1);
+        const int leader = __ffs(peers) - 1;
+        if (td >= 0) {
+          if (PASS == 0) {
+            if (lane == leader) atomicAdd(count + td, __popc(peers));
+          } else {
+            int basepos = 0;
+            if (lane == leader) basepos = atomicAdd((tall ? cursor : back) + td, __popc(peers));
+            basepos = __shfl_sync(peers, basepos, leader);
+            const int rk = basepos + __popc(peers & ((1u << lane) - 1u));
+            const int64_t at = tall ? (int64_t)off[td] + rk : (int64_t)off[td + 1] - 1 - rk;
+            if (at < pair_cap && at >= off[td] && at < off[td + 1]) bin[at] = (uint32_t)r;
+            else ps_record_error(status, PS_ERR_CAPACITY);
+          }
         }
-      }
+      };
+      direct(tdir);
+      if (__any_sync(0xffffffffu, tdir2 >= 0)) direct(tdir2);
     }
     // warp scan of the pair counts
     int x = cnt;
@@ -322,12 +349,9 @@ __global__ void __launch_bounds__(BIN_NT) k_bin(const float4* __restrict__ rib,
             q.x[v] = B.x[v];
             q.y[v] = B.y[v];
           }
-          // a quad whose bounding box spans two tiles crosses their common
-          // edge, so it almost always meets both: it is entered in both
-          // untested (an entry without samples costs the coverage kernel only
-          // its set-up; measured: count pass -0.06 ms, coverage unchanged;
-          // boxes of up to four tiles cost coverage 0.26 ms)
-          hit = B.n <= 2 || quad_meets_tile<PASS == 0>(q, (B.small & 1) != 0, tx, ty, W, H);
+          // (quads of one or two candidate tiles never get here: they are
+          // binned directly)
+          hit = quad_meets_tile<PASS == 0>(q, (B.small & 1) != 0, tx, ty, W, H);
         }
         tl = B.small >> 1;
         if (hit) {
