@@ -149,9 +149,10 @@ __device__ __forceinline__ bool quad_meets_tile(const QuadFix& q, bool small, in
 // candidate tiles (those of its pixel bounding box), the bit mask of the tiles
 // its triangles meet; pass 1: scatter rib ids into bins from those masks
 // (re-testing only quads with more candidates).  A warp takes 32 quads, one
-// per lane, and flattens their (quad, candidate) pairs with a warp scan so that
-// each lane tests one pair at a time; lanes of the warp that hit the same tile
-// are grouped: one atomic per group.
+// per lane.  Quads of one or two tiles are binned in direct rounds; the others'
+// (quad, candidate) pairs are flattened with a warp scan so that each lane
+// tests one pair at a time.  Lanes of the warp that hit the same tile are
+// grouped: one atomic per group.
 // Per-quad words from the count pass for the scatter pass, {hits, box}.  hits:
 // 0 = no tile; bit 31 with the tall flag in bit 30 and the tile index below it
 // = the quad's bounding box lies in that one tile; HITS_RETEST = more than 31
