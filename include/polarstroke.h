@@ -325,7 +325,10 @@ int ps_dash_capped(ps_context* ctx, const float* d_rib, const float* d_s, const 
  *                           quads; overwritten)
  * Quads with a vertex beyond +-2^21 px are skipped and record PS_ERR_RANGE.  A
  * 16x16-pixel tile met by more than 1024 distinct paths records
- * PS_ERR_CAPACITY (its coverage is then incomplete). */
+ * PS_ERR_CAPACITY (its coverage is then incomplete).  Returns PS_ERR_INVALID
+ * (before any launch) for a NULL pointer, spp != 16, a non-positive size, a
+ * width or height of 2^21 px or more, or more than 2^26 tiles (the binning
+ * words hold a tile index in 26 bits). */
 int ps_rasterize_coverage(ps_context* ctx, const float* d_rib, const uint32_t* d_tag,
                           const int64_t* d_n_rib, int64_t capacity, int32_t n_path,
                           int width, int height, int spp, uint16_t* d_canvas,

@@ -10,7 +10,9 @@ arithmetic, the GPU parity tests check the kernel itself).
   is at most the item index, as a plain binary search does.
 - Row spans: the union of the two edge groups' extents with saturating
   float-to-int conversions gives the same pixel range as clamping to +-1e9
-  first."""
+  first.
+- Binning words: the box word's fields and the direct rounds' tile indices name
+  the candidate tiles of the quad's box, up to the largest canvas accepted."""
 import math
 import random
 
@@ -134,3 +136,48 @@ def test_span_union_with_saturating_conversions():
         pb2 = min(tw - 1, _sat_int(hi2 / 256.0, False))
         new = (pa2, pb2 - pa2 + 1) if pb2 >= pa2 else (0, 0)
         assert new == ref, (L0, M0, L1, M1, two, tw)
+
+
+def test_bin_words_and_direct_rounds_give_the_candidate_tiles():
+    """The binning passes' per-quad words and direct rounds, restated: candidate i
+    of a box of ntx x nty tiles from (tx0, ty0) is tile (tx0 + i % ntx, ty0 + i //
+    ntx); the box word holds the first candidate's index in 26 bits, ntx - 1 in 5
+    and the tall flag in bit 31; a box of two tiles is binned directly in tbase and
+    tbase + 1 (two columns) or tbase + tiles_x (two rows); a hit mask of at most
+    two bits names the same tiles as the enumeration.  Checked against brute force
+    on random boxes up to the largest canvas the call accepts (2^26 tiles)."""
+    rng = random.Random(7)
+    for _ in range(20000):
+        tiles_x = rng.choice([1, 2, 3, 16, 128, 1 << 13])
+        tiles_y = max(1, min((1 << 26) // tiles_x, rng.choice([1, 2, 5, 128, 1 << 13])))
+        ntx = rng.randint(1, min(tiles_x, 31))
+        nty = rng.randint(1, min(tiles_y, 31 // ntx))
+        tx0 = rng.randrange(tiles_x - ntx + 1)
+        ty0 = rng.randrange(tiles_y - nty + 1)
+        n = ntx * nty
+        assert 1 <= n <= 31
+        cand = [(ty0 + dy) * tiles_x + tx0 + dx for dy in range(nty) for dx in range(ntx)]
+        tbase = ty0 * tiles_x + tx0
+        assert tbase < (1 << 26)
+        tall = rng.randrange(2)
+        box = tbase | (ntx - 1) << 26 | tall << 31
+        assert box < (1 << 32)
+        d_tbase, d_ntx, d_tall = box & 0x3ffffff, ((box >> 26) & 31) + 1, box >> 31
+        assert (d_tbase, d_ntx, d_tall) == (tbase, ntx, tall)
+        for i in range(n):
+            assert d_tbase + (i // d_ntx) * tiles_x + i % d_ntx == cand[i]
+        if n == 2:
+            assert [tbase, tbase + (1 if ntx == 2 else tiles_x)] == cand
+        # a mask of at most two hits: the set bits' tiles, lowest first
+        bits = sorted(rng.sample(range(n), rng.randint(1, min(2, n))))
+        h = sum(1 << b for b in bits)
+        i0 = (h & -h).bit_length() - 1
+        got = [d_tbase + (i0 // d_ntx) * tiles_x + i0 % d_ntx]
+        h2 = h & (h - 1)
+        if h2:
+            i1 = (h2 & -h2).bit_length() - 1
+            got.append(d_tbase + (i1 // d_ntx) * tiles_x + i1 % d_ntx)
+        assert got == [cand[b] for b in bits]
+        # the one-tile word: the tile index below the tall flag in bit 30
+        direct = 0x80000000 | tall << 30 | cand[0]
+        assert direct != 0xffffffff and (direct & 0x3fffffff) == cand[0]
